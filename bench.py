@@ -1,0 +1,310 @@
+#!/usr/bin/env python
+"""Benchmark: greedy CSS (Algorithm 1) on the 4096 x 65536 decaying-spectrum
+workload (rank 256, s_i = 1/i, noise 1e-3, k = 256), A streamed in BF16 (or
+FP32) from HBM.
+
+One step = one css_select call (initial scores + k greedy iterations) on
+device-resident A.  Prints ONE JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype bf16|f32]
+                    [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the plain restatement of the
+paper's Algorithm 1) on this machine's host cores on the same workload; each of
+its steps runs two greedy iterations on the full matrix.
+
+Multi-GPU (torchrun, one process per GPU): every rank runs its own replica of
+the workload (independent problems, no collective on the data path); value is
+the sum of all ranks' iterations divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import css_inputs as ci  # noqa: E402
+
+WORKLOAD = "decay_4096x65536"
+METRIC = "greedy iterations/s (fused streaming step, initial scores excluded)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--dtype", choices=["bf16", "f32"], default="bf16")
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_array():
+    c = ci.CONFIGS[WORKLOAD]
+    A = ci.lowrank_decaying(c["m"], c["n"], c["rank"], c["noise"], c["seed"], dtype=np.float32)
+    return c, A
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_reference(args):
+    """The FP64 oracle on host cores: each step = 2 iterations of Algorithm 1 on
+    the full matrix (the initial scores are recomputed every step and timed
+    separately)."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import css_oracle as O
+    c, A32 = workload_array()
+    A = ci.round_bf16(A32).astype(np.float64) if args.dtype == "bf16" else A32.astype(np.float64)
+    iters_per_step = 2
+    for _ in range(args.warmup):
+        O.greedy_css(A, 1, tau_rel=1e-6)
+    it_s, tot_s, init_s = 0.0, 0.0, 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = O.greedy_css(A, iters_per_step, tau_rel=1e-6)
+        t1 = time.perf_counter()
+        tot_s += t1 - t0
+        init_s += r.t_init - r.t_start
+        it_s += r.t_iter[-1] - r.t_init
+    value = iters_per_step * args.steps / it_s
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "iterations/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": c["m"], "n": c["n"], "k": c["k"],
+                   "stream_dtype": args.dtype},
+        "cpu_baseline": {"value": value, "unit": "iterations/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{iters_per_step} iterations of Algorithm 1 per step on the full "
+                                   f"{c['m']}x{c['n']} matrix in FP64; initial scores "
+                                   f"{1e3 * init_s / args.steps:.0f} ms/step timed apart"},
+        "e2e": {"value": value, "unit": "iterations/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(A32, dtype):
+    """Oracle on a bounded sample: 3 iterations of Algorithm 1 on the full matrix
+    (FP64), iterations timed apart from the initial scores."""
+    from oracle import css_oracle as O
+    A = ci.round_bf16(A32).astype(np.float64) if dtype == "bf16" else A32.astype(np.float64)
+    r = O.greedy_css(A, 3, tau_rel=1e-6)
+    it = r.t_iter[-1] - r.t_init
+    return {"value": 3 / it, "unit": "iterations/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"3 iterations of Algorithm 1 on the full {A.shape[0]}x{A.shape[1]} matrix in "
+                      f"FP64 (initial scores {r.t_init - r.t_start:.1f} s, timed apart)"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_1312_6838_gb300 import css
+    from paper_1312_6838_gb300 import _lib
+
+    c, A32 = workload_array()
+    m, n, k = c["m"], c["n"], c["k"]
+    tdt = torch.bfloat16 if args.dtype == "bf16" else torch.float32
+    # column-major: the (n, m) row-major storage of A^T
+    At_host = torch.from_numpy(np.ascontiguousarray(A32.T))
+    A = At_host.to(dev).to(tdt).t()
+    assert A.stride(0) == 1 and A.shape == (m, n)
+    a_bytes = m * n * A.element_size()
+    c_bytes = m * m * 4
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(3, args.warmup)):
+        css.select(A, k)
+    stream = torch.cuda.current_stream()
+    barrier()
+    clocks = ClockSampler(local if ws > 1 else 0)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    init_ms, loop_ms = [], []
+    barrier()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        res = css.select(A, k, timing=True)
+        ev[i][1].record(stream)
+        init_ms.append(res.timing_ms[0])
+        loop_ms.append(res.timing_ms[1])
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = sum(step_ms)
+    tot_loop = sum(loop_ms)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([tot_ms, tot_loop], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms, tot_loop = t.tolist()
+    iters = ws * args.steps * res.n_sel
+    value = iters / (tot_loop / 1e3)
+    # roofline of the persistent greedy kernel: per iteration it streams A once,
+    # reads C = A A^T once and reads/writes the score state (f, g: r+w, g0: r, W: w)
+    per_iter = a_bytes + c_bytes + 48 * n
+    achieved = per_iter * res.n_sel / (statistics.mean(loop_ms) / 1e3) / 1e9
+    peak, peak_kind = peaks()
+    out = {
+        "metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": tot_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.dtype, "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": m, "n": n, "k": k, "rank": c["rank"],
+                   "noise": c["noise"], "stream_dtype": args.dtype,
+                   "accumulate": "f32 dot products, f64 score state and basis",
+                   "l2": f"inputs larger than L2 (A = {a_bytes / 2**20:.0f} MiB per pass)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "init_ms": statistics.mean(init_ms), "loop_ms": statistics.mean(loop_ms),
+        "whole_call_iterations_per_s": ws * args.steps * res.n_sel / (tot_ms / 1e3),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "greedy_kernel (persistent: pivot phases + fused step)",
+                     "bytes_per_iteration": per_iter, "peak_kind": peak_kind},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clk,
+    }
+    if not args.no_e2e:
+        out["e2e"] = e2e(css, A32, tdt, m, n, k, dev, args)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(A32, args.dtype)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def e2e(css, A32, tdt, m, n, k, dev, args):
+    """Same metric through the public C-ABI host entry point: pinned host A ->
+    device copy -> selection -> results back to the host, all timed."""
+    import torch
+    A_host = torch.from_numpy(np.ascontiguousarray(A32.T)).to(tdt).pin_memory().t()
+    A_dev = css.empty_colmajor(m, n, tdt, dev)
+    nbytes = css.host_workspace_bytes(m, n, k, tdt)
+    _buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+    off = (-_buf.data_ptr()) % 256
+    wsb = _buf[off:off + nbytes]
+    for _ in range(2):
+        css.select_host(A_host, k, A_dev, ws=wsb)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ns = 0
+    for _ in range(args.steps):
+        sel, trace, n_sel = css.select_host(A_host, k, A_dev, ws=wsb)
+        ns += n_sel
+    dt = time.perf_counter() - t0
+    return {"value": ns / dt, "unit": "iterations/s",
+            "h2d_bytes_per_step": m * n * A_host.element_size(),
+            "d2h_bytes_per_step": 4 * k + 8 * (k + 1) + 4,
+            "note": "initial scores included (whole call)"}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,315 @@
+/*
+ * libcss -- greedy column subset selection on one GB300 (sm_103a).
+ *
+ * C ABI of the CUDA library.  It follows Farahat, Elgohary, Ghodsi, Kamel,
+ * "Greedy Column Subset Selection for Large-scale Data Sets" (arXiv:1312.6838):
+ *
+ *   css_select          Problem 1 by the greedy heuristic of Algorithm 1
+ *                       (Sec. 4.2; score recursion of Theorem 2, error
+ *                       recursion of Theorem 1).
+ *   gcss_select         Problem 4 / Problem 5: columns of A chosen to
+ *                       reconstruct a target B, Algorithm 3 (Sec. 5.2;
+ *                       Theorems 3 and 4).
+ *   gcss_distributed    Algorithm 4 (Sec. 5.2): GCSS inside every column block,
+ *                       then GCSS on the union of the blocks' selections.
+ *   css_project         B = A Omega, the random projection of Sec. 5.1
+ *                       (Algorithm 2: per-block partial sums, then row sums).
+ *   css_select_batched  many independent Algorithm 1 instances in one launch.
+ *   css_residual_backward
+ *                       loss ||A - P^(S) A||_F^2 (Problem 1's criterion,
+ *                       Eq. Projection of Sec. 3.1) and its gradient with
+ *                       respect to A at a fixed selected set S.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Layout     Matrices are column-major with a leading dimension (the paper's
+ *            column view <i, A_:i>, Sec. 5.1): element (i, j) of A sits at
+ *            A[i + j * lda], lda >= m.  Column indices are 0-based int32
+ *            (the paper counts from 1).  Selections are returned in selection
+ *            order.
+ * Pointers   Every data pointer is a DEVICE pointer (cudaMalloc'd or a
+ *            device tensor's storage) unless its comment says HOST.  The
+ *            caller owns all memory.  No entry point allocates device
+ *            memory: scratch space is a caller-provided workspace whose size
+ *            comes from css_workspace_size() (ws may be NULL only when that
+ *            size is 0).
+ * Streams    Work is enqueued on `stream` (a cudaStream_t; NULL = legacy
+ *            default stream).  With opts->sync = 1 (the default) the call
+ *            synchronises the stream before returning so it can report
+ *            device-side status (rank exhaustion, non-finite input, timeout);
+ *            with sync = 0 it returns CSS_OK after enqueueing and device
+ *            status is read later with css_read_status().
+ * Errors     Argument errors are found on the host before anything is
+ *            enqueued (CSS_ERR_INVALID_ARG / CSS_ERR_WORKSPACE).  The library
+ *            never exits, traps or asserts on the device; every device-side
+ *            wait is bounded and reports CSS_ERR_TIMEOUT when it runs out.
+ * Precision  A may be FP64, FP32 or BF16.  FP64 input is processed entirely
+ *            in FP64.  FP32/BF16 input is streamed as stored with FP32
+ *            accumulation of the per-column dot products; the score state
+ *            (f, g), the orthonormal basis of the selected columns, the pivot
+ *            norm and the error trace are FP64.
+ */
+#ifndef LIBCSS_CSS_H
+#define LIBCSS_CSS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st* css_stream_t;
+
+typedef enum {
+    CSS_OK = 0,
+    /* Warning: every remaining candidate column has a residual norm at or
+       below tau_rel times its initial norm (A has numerical rank < k).
+       *n_sel < k; sel and the error trace are valid up to *n_sel. */
+    CSS_RANK_EXHAUSTED = 1,
+    CSS_ERR_INVALID_ARG = -1,
+    CSS_ERR_CUDA = -2,
+    CSS_ERR_NO_MEMORY = -3,
+    CSS_ERR_WORKSPACE = -4,   /* ws NULL, misaligned or smaller than required */
+    CSS_ERR_TIMEOUT = -5,     /* a bounded device-side wait ran out */
+    CSS_ERR_NONFINITE = -6,   /* A (or B) holds a NaN or an infinity */
+    CSS_ERR_UNSUPPORTED = -7  /* no sm_103a device, or a dtype combination
+                                 the entry point does not take */
+} css_status;
+
+typedef enum { CSS_F64 = 0, CSS_F32 = 1, CSS_BF16 = 2 } css_dtype;
+
+typedef enum {
+    CSS_OP_SELECT = 0,
+    CSS_OP_GCSS = 1,
+    CSS_OP_DISTRIBUTED = 2,
+    CSS_OP_PROJECT = 3,
+    CSS_OP_BACKWARD = 4,
+    CSS_OP_HOST_SELECT = 5
+} css_op;
+
+/* Options.  Fill with css_opts_default() and change fields as needed;
+   passing NULL means the defaults. */
+typedef struct {
+    /* Candidate threshold: column i stays a candidate while its residual
+       norm g_i exceeds tau_rel * g_i^(0).  < 0 selects the default
+       (1e-12 for FP64 input, 1e-6 for FP32/BF16). */
+    double tau_rel;
+    /* DEVICE int32[n_forced] or NULL: column indices taken at the first
+       n_forced iterations instead of the argmax (resume / teacher forcing).
+       n_forced <= k; the indices are copied to the host and checked to be
+       distinct and in range before anything is enqueued (a synchronous
+       copy).  css_select and gcss_select only. */
+    const int32_t* forced;
+    int32_t n_forced;
+    /* 0: the paper's criterion f_i / g_i.  1: g_i alone (QR with column
+       pivoting; a test hook). */
+    int32_t score_mode;
+    /* 1 (default): synchronise at the end and report device status. */
+    int32_t sync;
+    /* Upper bound for any single device-side wait, in nanoseconds.
+       0 selects the default (2 s). */
+    uint64_t spin_budget_ns;
+    /* Number of CTAs of the persistent greedy kernel (0 = all SMs times the
+       occupancy).  Tuning knob. */
+    int32_t grid_ctas;
+    /* Columns per warp tile of the fused step (0 = autotuned: 2, 4 or 8). */
+    int32_t tile_cols;
+    /* Optional DEVICE diagnostics, NULL to skip (css_select, gcss_select):
+       diag_argmax  int32[k]: the kernel's own argmax at each iteration (also
+                    when a forced index is taken instead);
+       diag_f, diag_g double[n]: the score state f, g after the last
+                    iteration (Theorem 2's numerator and denominator). */
+    int32_t* diag_argmax;
+    /* HOST double[2] or NULL (sync mode only): milliseconds of the
+       initial-score phase and of the greedy iterations, from CUDA events on
+       `stream`. */
+    double* timing_ms;
+    double* diag_f;
+    double* diag_g;
+    /* Initial-score path for FP32/BF16 input: 0 = automatic, 1 = SIMT FP32,
+       2 = tensor cores (tcgen05, BF16 split). */
+    int32_t init_path;
+    int32_t reserved[7];
+} css_opts;
+
+/* Fill *opts with the defaults. */
+void css_opts_default(css_opts* opts);
+
+/* Human-readable name of a status code (static storage). */
+const char* css_status_string(css_status s);
+
+/* Library version string (static storage). */
+const char* css_version(void);
+
+/* Bytes of device workspace the entry point `op` needs for the given sizes
+   (m rows, n columns, r target columns for GCSS/projection, k columns to
+   select; unused sizes may be 0).  For CSS_OP_DISTRIBUTED, n is the total
+   column count and r the target width; the per-block limit l_block must be
+   passed in k_block.  For CSS_OP_BACKWARD, k is |S|.  Returns 0 when the
+   sizes are invalid. */
+size_t css_workspace_size(css_op op, css_dtype dtype, int64_t m, int64_t n,
+                          int64_t r, int32_t k, int32_t k_block,
+                          const css_opts* opts);
+
+/*
+ * Greedy CSS, Algorithm 1 (Sec. 4.2).
+ *
+ *   A        DEVICE m x n, column-major, leading dimension lda >= m.
+ *   dtype    element type of A.
+ *   k        number of columns to select, 1 <= k <= min(m, n, 1024).
+ *            m is limited by shared memory: up to about 17000 rows for
+ *            FP32/BF16 input and 13000 for FP64 (CSS_ERR_UNSUPPORTED above).
+ *   sel      DEVICE int32[k]: selected columns in selection order.
+ *   trace    DEVICE double[k+1]: F^(0) = ||A||_F^2 and F^(t) after each
+ *            iteration by Theorem 1 (F^(t) = F^(t-1) - f_p / g_p).
+ *   n_sel    DEVICE int32[1]: number of columns selected (k unless the rank
+ *            ran out).
+ *   W        DEVICE double[k * n] or NULL: row t (W[t * n + i]) is
+ *            omega^(t) of Eq. (delta_omega), the embedding row of all columns
+ *            (Sec. 3.1, W = Q^T A; W Pi is upper triangular, Sec. 6).
+ *   ws       DEVICE workspace of at least css_workspace_size(CSS_OP_SELECT,
+ *            ...) bytes, 256-byte aligned.
+ * Returns CSS_OK, CSS_RANK_EXHAUSTED or an error code.
+ */
+css_status css_select(const void* A, css_dtype dtype, int64_t m, int64_t n,
+                      int64_t lda, int32_t k, int32_t* sel, double* trace,
+                      int32_t* n_sel, double* W, void* ws, size_t ws_bytes,
+                      const css_opts* opts, css_stream_t stream);
+
+/*
+ * Greedy generalized CSS, Algorithm 3 (Sec. 5.2): columns of A that best
+ * reconstruct the target B (Problem 4's criterion ||B - P^(S) B||_F^2).
+ *
+ *   A      DEVICE m x n (lda), dtype dtype.
+ *   B      DEVICE m x r (ldb >= m).  FP64 when dtype is CSS_F64, FP32 otherwise.
+ *   trace  DEVICE double[k+1]: Fbar^(0) = ||B||_F^2 and Fbar^(t) (Theorem 3).
+ *   Other arguments as css_select.
+ */
+css_status gcss_select(const void* A, css_dtype dtype, int64_t m, int64_t n,
+                       int64_t lda, const void* B, int64_t r, int64_t ldb,
+                       int32_t k, int32_t* sel, double* trace, int32_t* n_sel,
+                       double* W, void* ws, size_t ws_bytes,
+                       const css_opts* opts, css_stream_t stream);
+
+/*
+ * Distributed CSS, Algorithm 4 (Sec. 5.2), on one GPU: every column block b
+ * (columns block_offsets[b] .. block_offsets[b+1]-1) selects
+ * l_b = min(l_block, width_b) columns by GCSS against B (the map phase, all
+ * blocks in one persistent launch); the union of those columns, in block
+ * order and each block's selection order, is A_(0); GCSS(A_(0), B, k) picks
+ * the final k columns (the reduce phase).
+ *
+ *   block_offsets  HOST int64[nblocks + 1], strictly increasing, from 0 to n.
+ *   block_sel      DEVICE int32[nblocks * l_block] or NULL: per-block global
+ *                  column ids in selection order, -1 where a block selected
+ *                  fewer than l_block.
+ *   sel, trace, n_sel
+ *                  the final selection as global column ids of A, with the
+ *                  error trace of the union step.
+ */
+/* Exact workspace bytes of gcss_distributed for a given block partition
+   (css_workspace_size(CSS_OP_DISTRIBUTED, ...) returns a bound that holds
+   for every partition with blocks of at least k_block columns). */
+size_t gcss_distributed_workspace_size(css_dtype dtype, int64_t m, int64_t n,
+                                       int64_t r, const int64_t* block_offsets,
+                                       int32_t nblocks, int32_t l_block,
+                                       int32_t k);
+
+css_status gcss_distributed(const void* A, css_dtype dtype, int64_t m,
+                            int64_t n, int64_t lda, const void* B, int64_t r,
+                            int64_t ldb, const int64_t* block_offsets,
+                            int32_t nblocks, int32_t l_block, int32_t k,
+                            int32_t* sel, double* trace, int32_t* n_sel,
+                            int32_t* block_sel, void* ws, size_t ws_bytes,
+                            const css_opts* opts, css_stream_t stream);
+
+/*
+ * Random projection B = A Omega (Sec. 5.1, Algorithm 2).
+ *
+ *   A       DEVICE m x n (lda), CSS_BF16 or CSS_F32 or CSS_F64.
+ *   Omega   DEVICE n x r (ldo >= n), same dtype as A.  Entries drawn i.i.d.
+ *           from the caller's distribution Psi (Gaussian, +-1, sparse sign).
+ *   Bout    DEVICE m x r (ldb >= m): FP32 for BF16/FP32 input, FP64 for FP64.
+ *   BF16 x BF16 products accumulate in FP32 (tensor cores); column-block
+ *   partial sums are added in FP32 in a fixed order, so results are
+ *   reproducible run to run.
+ */
+css_status css_project(const void* A, css_dtype dtype, int64_t m, int64_t n,
+                       int64_t lda, const void* Omega, int64_t r, int64_t ldo,
+                       void* Bout, int64_t ldb, void* ws, size_t ws_bytes,
+                       const css_opts* opts, css_stream_t stream);
+
+/* One independent greedy CSS problem of a batch (HOST struct; the pointers
+   inside are DEVICE pointers with the meaning they have in css_select). */
+typedef struct {
+    const void* A;
+    int64_t m, n, lda;
+    int32_t k;
+    int32_t pad_;
+    int32_t* sel;
+    double* trace;
+    int32_t* n_sel;
+    double* W; /* may be NULL */
+} css_problem;
+
+/*
+ * Many independent Algorithm 1 instances of uneven sizes in one persistent
+ * launch (all instances share dtype).  probs is a HOST array of `count`
+ * descriptors; the workspace size is css_batched_workspace_size().
+ * Returns CSS_OK when every instance selected its k columns,
+ * CSS_RANK_EXHAUSTED when some ran out of rank (their n_sel says how many).
+ */
+size_t css_batched_workspace_size(const css_problem* probs, int32_t count,
+                                  css_dtype dtype, const css_opts* opts);
+css_status css_select_batched(const css_problem* probs, int32_t count,
+                              css_dtype dtype, void* ws, size_t ws_bytes,
+                              const css_opts* opts, css_stream_t stream);
+
+/*
+ * Loss and gradient of the reconstruction error at a fixed selected set S
+ * (Problem 1's criterion; P^(S) = A_S (A_S^T A_S)^-1 A_S^T, Eq. Projection).
+ *
+ *   loss = ||R||_F^2,  R = A - A_S T,  T = (A_S^T A_S)^-1 A_S^T A
+ *   dA   = grad_out * 2 R            for columns outside S
+ *   dA_S = grad_out * (-2 R T^T)     for the columns in S
+ *
+ *   sel       DEVICE int32[k], distinct column indices.
+ *   dA        DEVICE, same dtype as A, m x n with leading dimension ldda, or
+ *             NULL to compute the loss only.
+ *   loss      DEVICE double[1] or NULL.
+ * The k x k factor of A_S^T A_S is recomputed here (FP64 Cholesky), not
+ * carried over from a forward pass.  FP32/BF16 input: GEMMs accumulate in
+ * FP32, the factorisation and the loss are FP64.
+ */
+css_status css_residual_backward(const void* A, css_dtype dtype, int64_t m,
+                                 int64_t n, int64_t lda, const int32_t* sel,
+                                 int32_t k, double grad_out, void* dA,
+                                 int64_t ldda, double* loss, void* ws,
+                                 size_t ws_bytes, const css_opts* opts,
+                                 css_stream_t stream);
+
+/*
+ * css_select from HOST buffers: copies A (HOST, m x n, lda; pinned memory
+ * for full speed) into the caller's DEVICE staging buffer `A_dev` (at least
+ * lda * n elements), runs css_select, and copies sel (HOST int32[k]), trace
+ * (HOST double[k+1]) and n_sel (HOST int32[1]) back.  Always synchronous.
+ * The workspace is css_workspace_size(CSS_OP_SELECT, ...) plus 256 bytes.
+ */
+css_status css_select_host(const void* A_host, css_dtype dtype, int64_t m,
+                           int64_t n, int64_t lda, int32_t k, int32_t* sel,
+                           double* trace, int32_t* n_sel, void* A_dev,
+                           void* ws, size_t ws_bytes, const css_opts* opts,
+                           css_stream_t stream);
+
+/* Device status left by the last call that used `ws` (for opts->sync = 0):
+   synchronises `stream`, then returns CSS_OK, CSS_RANK_EXHAUSTED or the
+   device error. */
+css_status css_read_status(const void* ws, css_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBCSS_CSS_H */

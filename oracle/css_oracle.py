@@ -43,6 +43,7 @@ Readings where the paper is silent (the same readings the CUDA path takes):
 from __future__ import annotations
 
 import itertools
+import time
 
 import numpy as np
 
@@ -80,6 +81,11 @@ class GreedyResult:
         self.scores: list[np.ndarray] = []
         self.f: np.ndarray | None = None
         self.g: np.ndarray | None = None
+        # wall-clock instrumentation (time.perf_counter): after initialisation
+        # and after each iteration; no effect on the arithmetic
+        self.t_start: float = 0.0
+        self.t_init: float = 0.0
+        self.t_iter: list[float] = []
 
 
 def _as64(X):
@@ -155,12 +161,12 @@ def greedy_css(A, l, tau_rel=1e-12, forced=None, keep_scores=False,
                score="paper"):
     """Greedy CSS, memory-efficient form (Algorithm 1).
 
-    Initialisation (Alg. 1, line 2):
+    Initialisation (Algorithm 1):
         f_i^(0) = ||A^T A_:i||^2,   g_i^(0) = A_:i^T A_:i .
     ||A^T A_:i||^2 is evaluated as A_:i^T (A A^T) A_:i (the same number; it
     avoids forming the n x n matrix A^T A).
 
-    Iteration t (lines 4-7):
+    Iteration t:
         p       = argmax_i f_i / g_i
         delta   = A^T A_:p - sum_{r<t} omega_p^(r) omega^(r)        (Eq. delta_omega)
         omega   = delta / sqrt(delta_p)
@@ -178,6 +184,7 @@ def greedy_css(A, l, tau_rel=1e-12, forced=None, keep_scores=False,
     A = _as64(A)
     m, n = A.shape
     res = GreedyResult()
+    res.t_start = time.perf_counter()
     g = np.einsum("ij,ij->j", A, A)
     g0 = g.copy()
     C = A @ A.T
@@ -187,6 +194,7 @@ def greedy_css(A, l, tau_rel=1e-12, forced=None, keep_scores=False,
     res.trace.append(F)
     omegas = np.zeros((0, n))
     forced = list(forced) if forced is not None else []
+    res.t_init = time.perf_counter()
     for t in range(l):
         if score == "norm":
             p, sc, gap = _argmax_score(g * g, g, g0, selected, tau_rel)
@@ -209,6 +217,7 @@ def greedy_css(A, l, tau_rel=1e-12, forced=None, keep_scores=False,
         f = f - 2.0 * omega * x + np.dot(omega, omega) * omega * omega
         g = g - omega * omega
         omegas = np.vstack([omegas, omega])
+        res.t_iter.append(time.perf_counter())
     res.W = omegas
     res.f, res.g = f, g
     return res
@@ -253,8 +262,8 @@ def greedy_css_residual(A, l, tau_rel=1e-12):
 def greedy_gcss(A, B, l, tau_rel=1e-12, forced=None, keep_scores=False):
     """Greedy generalized CSS: select columns of A to reconstruct B (Algorithm 3).
 
-    Initialisation (line 1): f_i^(0) = ||B^T A_:i||^2,  g_i^(0) = A_:i^T A_:i.
-    Iteration t (lines 3-7):
+    Initialisation: f_i^(0) = ||B^T A_:i||^2,  g_i^(0) = A_:i^T A_:i.
+    Iteration t:
         p       = argmax_i f_i / g_i
         delta   = A^T A_:p - sum_{r<t} omega_p^(r) omega^(r)
         gamma   = B^T A_:p - sum_{r<t} omega_p^(r) upsilon^(r)
@@ -338,10 +347,9 @@ def distributed_css(A, B, block_offsets, l_block, l, tau_rel=1e-12):
     """Distributed CSS (Algorithm 4) given the concise representation B.
 
     map:    each block b selects l_(b) = min(l_block, n_b) columns of A_(b) by
-            greedy GCSS against B (line 5).
+            greedy GCSS against B.
     reduce: A_(0) is the union in block order, each block's columns in their
-            selection order (line 10); GCSS(A_(0), B, l) picks the final set
-            (line 11).
+            selection order; GCSS(A_(0), B, l) picks the final set.
     Returns (final global column ids in selection order, per-block global ids,
     the final GreedyResult on A_(0)).
     """

@@ -1,0 +1,830 @@
+// C ABI of libcss (include/css.h): argument checks, workspace layout and the
+// launch sequence of every entry point.  All device work is in greedy.cu,
+// init_simt.cu, project.cu and backward.cu.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "greedy.cuh"
+#include "init.cuh"
+#include "project.cuh"
+#include "backward.cuh"
+
+using namespace css;
+
+namespace {
+
+constexpr int kMaxK = 1024;          // columns selected per problem
+constexpr int kMaxCtas = 1024;       // descriptor space reserved per call
+constexpr uint64_t kDefaultSpinNs = 2000000000ull;
+
+size_t esize(int dt) { return dt == CSS_F64 ? 8 : dt == CSS_F32 ? 4 : 2; }
+size_t accsize(int dt) { return dt == CSS_F64 ? 8 : 4; }
+bool valid_dtype(int dt) { return dt == CSS_F64 || dt == CSS_F32 || dt == CSS_BF16; }
+
+css_opts defaults() {
+  css_opts o;
+  std::memset(&o, 0, sizeof(o));
+  o.tau_rel = -1.0;
+  o.sync = 1;
+  return o;
+}
+
+double tau_of(const css_opts& o, int dt) {
+  if (o.tau_rel >= 0.0) return o.tau_rel;
+  return dt == CSS_F64 ? 1e-12 : 1e-6;
+}
+
+// Per-problem device state (see UnitDesc in greedy.cuh).
+struct UnitState {
+  double *f = nullptr, *g = nullptr, *g0 = nullptr;
+  unsigned char* selmask = nullptr;
+  double *Q = nullptr, *Z = nullptr, *W = nullptr;
+  void *qv = nullptr, *ypv = nullptr;
+  double *e1 = nullptr, *e = nullptr, *y = nullptr, *coef = nullptr, *ups = nullptr;
+};
+
+void carve_scores(WsCarver& c, int n, UnitState& s) {
+  s.f = c.take<double>(n);
+  s.g = c.take<double>(n);
+  s.g0 = c.take<double>(n);
+  s.selmask = c.take<unsigned char>(n);
+}
+
+void carve_rest(WsCarver& c, int dt, int m, int n, int k, int r, int mode, bool need_W,
+                UnitState& s) {
+  s.Q = c.take<double>((size_t)m * k);
+  s.Z = c.take<double>((size_t)(mode == 0 ? m : r) * k);
+  if (need_W) s.W = c.take<double>((size_t)k * n);
+  s.qv = c.take<char>((size_t)m * accsize(dt));
+  s.ypv = c.take<char>((size_t)m * accsize(dt));
+  s.e1 = c.take<double>(m);
+  s.e = c.take<double>(m);
+  s.y = c.take<double>(m);
+  s.coef = c.take<double>(std::max(k, r) + 1);
+  s.ups = c.take<double>(std::max(r, 1));
+}
+
+// Launch-wide descriptor region.
+struct Header {
+  DevStatus* st;
+  UnitDesc* units;
+  TeamDesc* teams;
+  int* order;
+  int* cta_team;
+  uint32_t* bars;
+  double* part;
+  double* cand_val;
+  int* cand_idx;
+};
+
+void carve_header(WsCarver& c, int max_units, Header& h) {
+  h.st = c.take<DevStatus>(1);
+  h.units = c.take<UnitDesc>(max_units);
+  h.teams = c.take<TeamDesc>(kMaxCtas);
+  h.order = c.take<int>(max_units);
+  h.cta_team = c.take<int>(kMaxCtas);
+  h.bars = c.take<uint32_t>(2 * kMaxCtas);
+  h.part = c.take<double>(4 * kMaxCtas);
+  h.cand_val = c.take<double>(kMaxCtas);
+  h.cand_idx = c.take<int>(kMaxCtas);
+}
+
+css_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return CSS_OK;
+  if (e == cudaErrorMemoryAllocation) return CSS_ERR_NO_MEMORY;
+  return CSS_ERR_CUDA;
+}
+
+int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return n;
+}
+
+bool device_ok() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  return major == 10 && minor == 3;
+}
+
+// One team per entry of `team_units`; CTAs split proportionally to `work`.
+struct Plan {
+  std::vector<TeamDesc> teams;
+  std::vector<int> order;
+  std::vector<int> cta_team;
+  int grid = 0;
+};
+
+// Assign units to teams.  units_per_team == 0: one team per unit, with CTA
+// counts proportional to the unit's work (at least one CTA each) when the
+// grid has more CTAs than units; otherwise longest-processing-time-first
+// assignment of units to single-CTA teams.
+Plan make_plan(const std::vector<double>& work, int grid) {
+  Plan P;
+  const int nu = (int)work.size();
+  std::vector<int> idx(nu);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return work[a] > work[b]; });
+  if (nu <= grid) {
+    double tot = 0.0;
+    for (double w : work) tot += w;
+    std::vector<int> cnt(nu, 1);
+    int left = grid - nu;
+    // largest remainder over the spare CTAs
+    std::vector<double> share(nu);
+    for (int u = 0; u < nu; ++u) share[u] = tot > 0 ? work[u] / tot * left : 0.0;
+    int used = 0;
+    for (int u = 0; u < nu; ++u) { int a = (int)share[u]; cnt[u] += a; used += a; }
+    std::vector<int> rem(nu);
+    std::iota(rem.begin(), rem.end(), 0);
+    std::stable_sort(rem.begin(), rem.end(), [&](int a, int b) {
+      return (share[a] - (int)share[a]) > (share[b] - (int)share[b]);
+    });
+    for (int q = 0; q < left - used && q < nu; ++q) cnt[rem[q]] += 1;
+    int cta = 0;
+    for (int q = 0; q < nu; ++q) {
+      const int u = idx[q];
+      TeamDesc t{};
+      t.cta0 = cta;
+      t.ncta = cnt[u];
+      t.u_begin = q;
+      t.u_end = q + 1;
+      P.order.push_back(u);
+      for (int c = 0; c < cnt[u]; ++c) P.cta_team.push_back((int)P.teams.size());
+      cta += cnt[u];
+      P.teams.push_back(t);
+    }
+    P.grid = cta;
+  } else {
+    std::vector<double> load(grid, 0.0);
+    std::vector<std::vector<int>> lists(grid);
+    for (int q = 0; q < nu; ++q) {
+      const int u = idx[q];
+      int best = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      lists[best].push_back(u);
+      load[best] += work[u];
+    }
+    for (int t = 0; t < grid; ++t) {
+      TeamDesc d{};
+      d.cta0 = t;
+      d.ncta = 1;
+      d.u_begin = (int)P.order.size();
+      for (int u : lists[t]) P.order.push_back(u);
+      d.u_end = (int)P.order.size();
+      P.teams.push_back(d);
+      P.cta_team.push_back(t);
+    }
+    P.grid = grid;
+  }
+  return P;
+}
+
+// Copy descriptors, clear the status, launch the persistent kernel.
+css_status launch_units(const Header& h, std::vector<UnitDesc>& units, const std::vector<double>& work,
+                        int dt, int grid_max, int tile_cols, uint64_t spin_ns, cudaStream_t s) {
+  int m_max = 1, k_max = 1, r_max = 1;
+  for (auto& u : units) {
+    m_max = std::max(m_max, u.m);
+    k_max = std::max(k_max, u.k);
+    r_max = std::max(r_max, u.r);
+  }
+  const size_t smem = greedy_smem_bytes(dt, m_max, k_max, r_max);
+  if (smem > 227 * 1024) return CSS_ERR_UNSUPPORTED;
+  const int occ = greedy_occupancy(dt, tile_cols, smem);
+  const int sms = sm_count();
+  if (occ <= 0 || sms <= 0) return CSS_ERR_CUDA;
+  int grid = std::min(grid_max > 0 ? grid_max : sms * occ, sms * occ);
+  grid = std::min(grid, kMaxCtas);
+  Plan P = make_plan(work, grid);
+  for (size_t t = 0; t < P.teams.size(); ++t) {
+    P.teams[t].bar = h.bars + 2 * P.teams[t].cta0;
+    P.teams[t].part = h.part + 4 * P.teams[t].cta0;
+    P.teams[t].cand_val = h.cand_val + P.teams[t].cta0;
+    P.teams[t].cand_idx = h.cand_idx + P.teams[t].cta0;
+  }
+  DevStatus st{};
+  st.spin_budget_ns = spin_ns ? spin_ns : kDefaultSpinNs;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(h.st, &st, sizeof(st), cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_status(e);
+  if ((e = cudaMemcpyAsync(h.units, units.data(), units.size() * sizeof(UnitDesc), cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_status(e);
+  if ((e = cudaMemcpyAsync(h.teams, P.teams.data(), P.teams.size() * sizeof(TeamDesc), cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_status(e);
+  if ((e = cudaMemcpyAsync(h.order, P.order.data(), P.order.size() * sizeof(int), cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_status(e);
+  if ((e = cudaMemcpyAsync(h.cta_team, P.cta_team.data(), P.cta_team.size() * sizeof(int), cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_status(e);
+  if ((e = cudaMemsetAsync(h.bars, 0, 2 * sizeof(uint32_t) * P.grid, s)) != cudaSuccess) return cuda_status(e);
+  GreedyLaunch L{};
+  L.units = h.units;
+  L.order = h.order;
+  L.teams = h.teams;
+  L.cta_team = h.cta_team;
+  L.st = h.st;
+  L.dtype = dt;
+  L.tile_cols = tile_cols;
+  L.m_max = m_max;
+  L.k_max = k_max;
+  L.r_max = r_max;
+  L.grid = P.grid;
+  L.threads = kGreedyThreads;
+  L.smem = smem;
+  return cuda_status(greedy_launch(L, s));
+}
+
+css_status finish(const Header& h, const css_opts& o, cudaStream_t s) {
+  if (!o.sync) return CSS_OK;
+  DevStatus st{};
+  cudaError_t e = cudaMemcpyAsync(&st, h.st, sizeof(st), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (st.code != 0) return (css_status)st.code;
+  return st.rank_exhausted ? CSS_RANK_EXHAUSTED : CSS_OK;
+}
+
+// CUDA-event phase timer for opts->timing_ms (sync mode only).
+struct PhaseTimer {
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  bool on = false;
+  PhaseTimer(const css_opts& o) : on(o.timing_ms != nullptr && o.sync) {
+    if (on)
+      for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) on = false;
+  }
+  ~PhaseTimer() {
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+  void mark(int i, cudaStream_t s) {
+    if (on) cudaEventRecord(ev[i], s);
+  }
+  void report(const css_opts& o) {
+    if (!on) return;
+    float a = 0.f, b = 0.f;
+    if (cudaEventSynchronize(ev[2]) != cudaSuccess) return;
+    cudaEventElapsedTime(&a, ev[0], ev[1]);
+    cudaEventElapsedTime(&b, ev[1], ev[2]);
+    o.timing_ms[0] = a;
+    o.timing_ms[1] = b;
+  }
+};
+
+int pick_tile(const css_opts& o, int dt, int m) {
+  if (o.tile_cols == 2 || o.tile_cols == 4 || o.tile_cols == 8) return o.tile_cols;
+  (void)dt;
+  (void)m;
+  return 4;
+}
+
+css_status check_forced(const css_opts& o, int n, int k) {
+  if (o.n_forced <= 0) return CSS_OK;
+  if (!o.forced || o.n_forced > k) return CSS_ERR_INVALID_ARG;
+  std::vector<int32_t> h(o.n_forced);
+  if (cudaMemcpy(h.data(), o.forced, sizeof(int32_t) * o.n_forced, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return CSS_ERR_CUDA;
+  std::vector<char> seen(n, 0);
+  for (int32_t v : h) {
+    if (v < 0 || v >= n || seen[v]) return CSS_ERR_INVALID_ARG;
+    seen[v] = 1;
+  }
+  return CSS_OK;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// ---------------------------------------------------------- css_select ------
+struct SelectLayout {
+  Header h;
+  UnitState s;
+  void* C;
+  double* partial;
+  size_t bytes;
+};
+
+SelectLayout select_layout(void* ws, size_t cap, int dt, int64_t m, int64_t n, int32_t k, bool need_W) {
+  WsCarver c(ws, cap);
+  SelectLayout L{};
+  carve_header(c, 1, L.h);
+  carve_scores(c, (int)n, L.s);
+  carve_rest(c, dt, (int)m, (int)n, k, 0, 0, need_W, L.s);
+  L.C = c.take<char>((size_t)m * m * accsize(dt));
+  L.partial = c.take<double>(css_f0_partial_doubles(dt, (int)m, (int)n));
+  L.bytes = c.off;
+  return L;
+}
+
+struct GcssLayout {
+  Header h;
+  UnitState s;
+  double* partial;
+  size_t bytes;
+};
+
+GcssLayout gcss_layout(void* ws, size_t cap, int dt, int64_t m, int64_t n, int64_t r, int32_t k,
+                       bool need_W) {
+  WsCarver c(ws, cap);
+  GcssLayout L{};
+  carve_header(c, 1, L.h);
+  carve_scores(c, (int)n, L.s);
+  carve_rest(c, dt, (int)m, (int)n, k, (int)r, 1, need_W, L.s);
+  L.partial = c.take<double>(gcss_f0_partial_doubles(dt, (int)r, (int)n));
+  L.bytes = c.off;
+  return L;
+}
+
+UnitDesc make_unit(const void* A, int dt, int64_t m, int64_t n, int64_t lda, int32_t k, int mode,
+                   const void* T, int64_t ldt, int64_t r, const UnitState& s, double* W,
+                   int32_t* sel, double* trace, int32_t* n_sel, const css_opts& o) {
+  UnitDesc u{};
+  u.A = A;
+  u.lda = lda;
+  u.m = (int)m;
+  u.n = (int)n;
+  u.k = k;
+  u.mode = mode;
+  u.T = T;
+  u.ldt = ldt;
+  u.r = (int)r;
+  u.score_mode = o.score_mode;
+  u.tau = tau_of(o, dt);
+  u.f = s.f;
+  u.g = s.g;
+  u.g0 = s.g0;
+  u.selmask = s.selmask;
+  u.Q = s.Q;
+  u.Z = s.Z;
+  u.W = W ? W : s.W;
+  u.qv = s.qv;
+  u.ypv = s.ypv;
+  u.e1 = s.e1;
+  u.e = s.e;
+  u.y = s.y;
+  u.coef = s.coef;
+  u.ups = s.ups;
+  u.sel = sel;
+  u.trace = trace;
+  u.n_sel = n_sel;
+  u.diag_argmax = o.diag_argmax;
+  u.diag_f = o.diag_f;
+  u.diag_g = o.diag_g;
+  u.forced = o.forced;
+  u.n_forced = o.forced ? o.n_forced : 0;
+  u.vec_ok = aligned16(A) && ((lda * (int64_t)esize(dt)) % 16 == 0);
+  u.t_vec_ok = aligned16(T) && ((ldt * (int64_t)accsize(dt)) % 16 == 0);
+  return u;
+}
+
+size_t host_out_bytes(int32_t k) {
+  return align_up(align_up(sizeof(int32_t) * (k + 1), 8) + sizeof(double) * (k + 1));
+}
+
+int team_ctas_for(int64_t n, int64_t m) {
+  // enough CTAs to keep the column stream and the FP64 pivot work spread out
+  int64_t a = (n + 127) / 128;
+  int64_t b = (m + 15) / 16;
+  return (int)std::max<int64_t>(1, std::max(a, b));
+}
+
+}  // namespace
+
+extern "C" {
+
+void css_opts_default(css_opts* opts) {
+  if (opts) *opts = defaults();
+}
+
+const char* css_status_string(css_status s) {
+  switch (s) {
+    case CSS_OK: return "CSS_OK";
+    case CSS_RANK_EXHAUSTED: return "CSS_RANK_EXHAUSTED: fewer than k columns above the rank threshold";
+    case CSS_ERR_INVALID_ARG: return "CSS_ERR_INVALID_ARG";
+    case CSS_ERR_CUDA: return "CSS_ERR_CUDA: a CUDA runtime call failed";
+    case CSS_ERR_NO_MEMORY: return "CSS_ERR_NO_MEMORY";
+    case CSS_ERR_WORKSPACE: return "CSS_ERR_WORKSPACE: workspace missing, misaligned or too small";
+    case CSS_ERR_TIMEOUT: return "CSS_ERR_TIMEOUT: a bounded device wait ran out";
+    case CSS_ERR_NONFINITE: return "CSS_ERR_NONFINITE: input holds NaN or Inf";
+    case CSS_ERR_UNSUPPORTED: return "CSS_ERR_UNSUPPORTED";
+  }
+  return "unknown css_status";
+}
+
+const char* css_version(void) { return "libcss 0.1 (sm_103a)"; }
+
+size_t css_workspace_size(css_op op, css_dtype dtype, int64_t m, int64_t n, int64_t r, int32_t k,
+                          int32_t k_block, const css_opts* opts) {
+  (void)opts;
+  if (!valid_dtype(dtype) || m <= 0 || n <= 0) return 0;
+  switch (op) {
+    case CSS_OP_SELECT:
+    case CSS_OP_HOST_SELECT: {
+      if (k <= 0) return 0;
+      size_t b = select_layout(nullptr, (size_t)-1, dtype, m, n, k, true).bytes;
+      return op == CSS_OP_HOST_SELECT ? b + host_out_bytes(k) : b;
+    }
+    case CSS_OP_GCSS:
+      if (k <= 0 || r <= 0) return 0;
+      return gcss_layout(nullptr, (size_t)-1, dtype, m, n, r, k, true).bytes;
+    case CSS_OP_DISTRIBUTED:
+      if (k <= 0 || r <= 0 || k_block <= 0) return 0;
+      return distributed_workspace_bytes(dtype, m, n, r, k, k_block);
+    case CSS_OP_PROJECT:
+      if (r <= 0) return 0;
+      return project_workspace_bytes(dtype, m, n, r);
+    case CSS_OP_BACKWARD:
+      if (k <= 0) return 0;
+      return backward_workspace_bytes(dtype, m, n, k);
+  }
+  return 0;
+}
+
+css_status css_select(const void* A, css_dtype dtype, int64_t m, int64_t n, int64_t lda, int32_t k,
+                      int32_t* sel, double* trace, int32_t* n_sel, double* W, void* ws,
+                      size_t ws_bytes, const css_opts* opts, css_stream_t stream) {
+  const css_opts o = opts ? *opts : defaults();
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!A || !sel || !trace || !n_sel || !valid_dtype(dtype)) return CSS_ERR_INVALID_ARG;
+  if (m < 1 || n < 1 || lda < m || k < 1 || k > kMaxK || k > m || k > n) return CSS_ERR_INVALID_ARG;
+  if (n > (int64_t)INT32_MAX || m > (int64_t)INT32_MAX) return CSS_ERR_INVALID_ARG;
+  if (o.score_mode != 0 && o.score_mode != 1) return CSS_ERR_INVALID_ARG;
+  if (!ws || ((uintptr_t)ws % kWsAlign) != 0) return CSS_ERR_WORKSPACE;
+  SelectLayout L = select_layout(ws, ws_bytes, dtype, m, n, k, W == nullptr);
+  if (L.bytes > ws_bytes) return CSS_ERR_WORKSPACE;
+  if (!device_ok()) return CSS_ERR_UNSUPPORTED;
+  css_status cs = check_forced(o, (int)n, k);
+  if (cs != CSS_OK) return cs;
+  PhaseTimer tm(o);
+  tm.mark(0, s);
+  cudaError_t e = css_f0_simt(dtype, A, lda, (int)m, (int)n, L.C, L.partial, L.s.f, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  tm.mark(1, s);
+  std::vector<UnitDesc> units{make_unit(A, dtype, m, n, lda, k, 0, L.C, m, 0, L.s, W, sel, trace,
+                                        n_sel, o)};
+  const int tile = pick_tile(o, dtype, (int)m);
+  int gmax = o.grid_ctas > 0 ? o.grid_ctas : team_ctas_for(n, m);
+  cs = launch_units(L.h, units, {1.0}, dtype, gmax, tile, o.spin_budget_ns, s);
+  if (cs != CSS_OK) return cs;
+  tm.mark(2, s);
+  cs = finish(L.h, o, s);
+  tm.report(o);
+  return cs;
+}
+
+css_status gcss_select(const void* A, css_dtype dtype, int64_t m, int64_t n, int64_t lda,
+                       const void* B, int64_t r, int64_t ldb, int32_t k, int32_t* sel, double* trace,
+                       int32_t* n_sel, double* W, void* ws, size_t ws_bytes, const css_opts* opts,
+                       css_stream_t stream) {
+  const css_opts o = opts ? *opts : defaults();
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!A || !B || !sel || !trace || !n_sel || !valid_dtype(dtype)) return CSS_ERR_INVALID_ARG;
+  if (m < 1 || n < 1 || r < 1 || lda < m || ldb < m || k < 1 || k > kMaxK || k > m || k > n)
+    return CSS_ERR_INVALID_ARG;
+  if (o.score_mode != 0 && o.score_mode != 1) return CSS_ERR_INVALID_ARG;
+  if (!ws || ((uintptr_t)ws % kWsAlign) != 0) return CSS_ERR_WORKSPACE;
+  GcssLayout L = gcss_layout(ws, ws_bytes, dtype, m, n, r, k, W == nullptr);
+  if (L.bytes > ws_bytes) return CSS_ERR_WORKSPACE;
+  if (!device_ok()) return CSS_ERR_UNSUPPORTED;
+  css_status cs = check_forced(o, (int)n, k);
+  if (cs != CSS_OK) return cs;
+  PhaseTimer tm(o);
+  tm.mark(0, s);
+  cudaError_t e = gcss_f0_simt(dtype, A, lda, (int)m, (int)n, B, ldb, (int)r, L.partial, L.s.f, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  tm.mark(1, s);
+  std::vector<UnitDesc> units{make_unit(A, dtype, m, n, lda, k, 1, B, ldb, r, L.s, W, sel, trace,
+                                        n_sel, o)};
+  const int tile = pick_tile(o, dtype, (int)m);
+  int gmax = o.grid_ctas > 0 ? o.grid_ctas : team_ctas_for(n, m);
+  cs = launch_units(L.h, units, {1.0}, dtype, gmax, tile, o.spin_budget_ns, s);
+  if (cs != CSS_OK) return cs;
+  tm.mark(2, s);
+  cs = finish(L.h, o, s);
+  tm.report(o);
+  return cs;
+}
+
+css_status css_read_status(const void* ws, css_stream_t stream) {
+  if (!ws) return CSS_ERR_WORKSPACE;
+  DevStatus st{};
+  cudaError_t e = cudaMemcpyAsync(&st, ws, sizeof(st), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (st.code != 0) return (css_status)st.code;
+  return st.rank_exhausted ? CSS_RANK_EXHAUSTED : CSS_OK;
+}
+
+css_status css_select_host(const void* A_host, css_dtype dtype, int64_t m, int64_t n, int64_t lda,
+                           int32_t k, int32_t* sel, double* trace, int32_t* n_sel, void* A_dev,
+                           void* ws, size_t ws_bytes, const css_opts* opts, css_stream_t stream) {
+  if (!A_host || !A_dev || !sel || !trace || !n_sel || !valid_dtype(dtype)) return CSS_ERR_INVALID_ARG;
+  if (m < 1 || n < 1 || lda < m || k < 1) return CSS_ERR_INVALID_ARG;
+  if (!ws || ((uintptr_t)ws % kWsAlign) != 0 || ws_bytes < kWsAlign) return CSS_ERR_WORKSPACE;
+  cudaStream_t s = (cudaStream_t)stream;
+  // outputs live in the first 256-byte slot... too small for k; carve after the select workspace
+  const size_t need = select_layout(nullptr, (size_t)-1, dtype, m, n, k, true).bytes;
+  const size_t out_bytes = host_out_bytes(k);
+  if (ws_bytes < need + out_bytes) return CSS_ERR_WORKSPACE;
+  char* outs = (char*)ws + need;
+  int32_t* d_sel = (int32_t*)outs;
+  int32_t* d_nsel = d_sel + k;
+  double* d_trace = (double*)(outs + align_up(sizeof(int32_t) * (k + 1), 8));
+  cudaError_t e = cudaMemcpyAsync(A_dev, A_host, (size_t)lda * n * esize(dtype), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  css_opts o = opts ? *opts : defaults();
+  o.sync = 1;
+  css_status cs = css_select(A_dev, dtype, m, n, lda, k, d_sel, d_trace, d_nsel, nullptr, ws, need, &o, stream);
+  if (cs < 0) return cs;
+  e = cudaMemcpyAsync(sel, d_sel, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(trace, d_trace, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(n_sel, d_nsel, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e);
+  return cs;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------- batched and distributed ----
+namespace {
+
+__global__ void gather_columns_kernel(const char* __restrict__ A, long long lda_bytes, int m_bytes,
+                                      const int* __restrict__ ids, int U, char* __restrict__ A0,
+                                      long long lda0_bytes) {
+  for (int j = blockIdx.y; j < U; j += gridDim.y) {
+    const char* src = A + (long long)ids[j] * lda_bytes;
+    char* dst = A0 + (long long)j * lda0_bytes;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < m_bytes; b += gridDim.x * blockDim.x)
+      dst[b] = src[b];
+  }
+}
+
+__global__ void gather_f_kernel(const double* __restrict__ f0, const int* __restrict__ ids, int U,
+                                double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < U) out[j] = f0[ids[j]];
+}
+
+__global__ void map_sel_kernel(const int* __restrict__ local, const int* __restrict__ ids, int k,
+                               int* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < k) {
+    const int v = local[j];
+    out[j] = v >= 0 ? ids[v] : -1;
+  }
+}
+
+struct DistLayout {
+  Header h;
+  UnitState sc;            // f, g, g0, selmask over all n columns
+  double* f0_saved;
+  std::vector<UnitState> blk;
+  int* bsel;
+  double* btrace;
+  int* bnsel;
+  double* partial;
+  // union step
+  char* A0;
+  int64_t lda0;
+  int* ids;
+  UnitState us;
+  int* usel;
+  size_t bytes;
+};
+
+DistLayout dist_layout(void* ws, size_t cap, int dt, int64_t m, int64_t n, int64_t r, int32_t k,
+                       int32_t lb, const int64_t* offs, int nb) {
+  WsCarver c(ws, cap);
+  DistLayout L{};
+  carve_header(c, std::max(nb, 1), L.h);
+  carve_scores(c, (int)n, L.sc);
+  L.f0_saved = c.take<double>(n);
+  int64_t umax = 0;
+  L.blk.resize(nb);
+  for (int b = 0; b < nb; ++b) {
+    const int64_t w = offs ? offs[b + 1] - offs[b] : (n + nb - 1) / nb;
+    const int kb = (int)std::min<int64_t>(lb, w);
+    umax += kb;
+    carve_rest(c, dt, (int)m, (int)w, kb, (int)r, 1, true, L.blk[b]);
+  }
+  L.bsel = c.take<int>((size_t)nb * lb);
+  L.btrace = c.take<double>((size_t)nb * (lb + 1));
+  L.bnsel = c.take<int>(nb);
+  L.partial = c.take<double>(gcss_f0_partial_doubles(dt, (int)r, (int)n));
+  L.lda0 = (m + 7) / 8 * 8;
+  L.A0 = c.take<char>((size_t)L.lda0 * umax * esize(dt));
+  L.ids = c.take<int>(umax);
+  carve_scores(c, (int)umax, L.us);
+  carve_rest(c, dt, (int)m, (int)umax, std::max(1, k), (int)r, 1, true, L.us);
+  L.usel = c.take<int>(std::max(1, k));
+  L.bytes = c.off;
+  return L;
+}
+
+}  // namespace
+
+size_t distributed_workspace_bytes(int dtype, int64_t m, int64_t n, int64_t r, int32_t k,
+                                   int32_t k_block) {
+  // sized for the worst case of the block partition: every block as wide as
+  // needed, at most n / 1 blocks is not meaningful; size per column instead
+  // (blocks of at least k_block columns, each selecting k_block)
+  const int nb = (int)std::max<int64_t>(1, n / std::max(1, k_block));
+  return dist_layout(nullptr, (size_t)-1, dtype, m, n, r, k, k_block, nullptr, nb).bytes;
+}
+
+extern "C" {
+
+size_t gcss_distributed_workspace_size(css_dtype dtype, int64_t m, int64_t n, int64_t r,
+                                       const int64_t* block_offsets, int32_t nblocks,
+                                       int32_t l_block, int32_t k) {
+  if (!valid_dtype(dtype) || !block_offsets || nblocks < 1 || m < 1 || n < 1 || r < 1 ||
+      l_block < 1 || k < 1)
+    return 0;
+  if (block_offsets[0] != 0 || block_offsets[nblocks] != n) return 0;
+  for (int b = 0; b < nblocks; ++b)
+    if (block_offsets[b + 1] <= block_offsets[b]) return 0;
+  return dist_layout(nullptr, (size_t)-1, dtype, m, n, r, k, l_block, block_offsets, nblocks).bytes;
+}
+
+css_status gcss_distributed(const void* A, css_dtype dtype, int64_t m, int64_t n, int64_t lda,
+                            const void* B, int64_t r, int64_t ldb, const int64_t* block_offsets,
+                            int32_t nblocks, int32_t l_block, int32_t k, int32_t* sel,
+                            double* trace, int32_t* n_sel, int32_t* block_sel, void* ws,
+                            size_t ws_bytes, const css_opts* opts, css_stream_t stream) {
+  const css_opts o = opts ? *opts : defaults();
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!A || !B || !sel || !trace || !n_sel || !block_offsets || !valid_dtype(dtype))
+    return CSS_ERR_INVALID_ARG;
+  if (m < 1 || n < 1 || r < 1 || lda < m || ldb < m || nblocks < 1 || l_block < 1 || k < 1 ||
+      k > kMaxK || l_block > kMaxK || nblocks > kMaxCtas * 64)
+    return CSS_ERR_INVALID_ARG;
+  if (block_offsets[0] != 0 || block_offsets[nblocks] != n) return CSS_ERR_INVALID_ARG;
+  int64_t umax = 0;
+  for (int b = 0; b < nblocks; ++b) {
+    if (block_offsets[b + 1] <= block_offsets[b]) return CSS_ERR_INVALID_ARG;
+    umax += std::min<int64_t>(l_block, block_offsets[b + 1] - block_offsets[b]);
+  }
+  if (k > umax || k > m) return CSS_ERR_INVALID_ARG;
+  if (o.n_forced) return CSS_ERR_INVALID_ARG;
+  if (!ws || ((uintptr_t)ws % kWsAlign) != 0) return CSS_ERR_WORKSPACE;
+  DistLayout L = dist_layout(ws, ws_bytes, dtype, m, n, r, k, l_block, block_offsets, nblocks);
+  if (L.bytes > ws_bytes) return CSS_ERR_WORKSPACE;
+  if (!device_ok()) return CSS_ERR_UNSUPPORTED;
+  cudaError_t e;
+  // map phase: f^(0) = ||B^T a_i||^2 for every column, kept for the union step
+  if ((e = gcss_f0_simt(dtype, A, lda, (int)m, (int)n, B, ldb, (int)r, L.partial, L.sc.f, s)) != cudaSuccess)
+    return cuda_status(e);
+  if ((e = cudaMemcpyAsync(L.f0_saved, L.sc.f, sizeof(double) * n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+    return cuda_status(e);
+  int* bsel = block_sel ? block_sel : L.bsel;
+  if ((e = cudaMemsetAsync(bsel, 0xff, sizeof(int) * (size_t)nblocks * l_block, s)) != cudaSuccess)
+    return cuda_status(e);
+  css_opts ob = o;
+  ob.diag_argmax = nullptr;
+  ob.diag_f = ob.diag_g = nullptr;
+  std::vector<UnitDesc> units;
+  std::vector<double> work;
+  for (int b = 0; b < nblocks; ++b) {
+    const int64_t off = block_offsets[b], w = block_offsets[b + 1] - off;
+    const int kb = (int)std::min<int64_t>(l_block, w);
+    UnitState st = L.blk[b];
+    st.f = L.sc.f + off;
+    st.g = L.sc.g + off;
+    st.g0 = L.sc.g0 + off;
+    st.selmask = L.sc.selmask + off;
+    const void* Ab = (const char*)A + off * lda * (int64_t)esize(dtype);
+    units.push_back(make_unit(Ab, dtype, m, w, lda, kb, 1, B, ldb, r, st, nullptr,
+                              bsel + (size_t)b * l_block, L.btrace + (size_t)b * (l_block + 1),
+                              L.bnsel + b, ob));
+    work.push_back((double)w * kb);
+  }
+  const int tile = pick_tile(o, dtype, (int)m);
+  css_status cs = launch_units(L.h, units, work, dtype, o.grid_ctas, tile, o.spin_budget_ns, s);
+  if (cs != CSS_OK) return cs;
+  // reduce phase: union of the blocks' selections, block order then selection order
+  std::vector<int> hsel((size_t)nblocks * l_block), hn(nblocks);
+  DevStatus st{};
+  if ((e = cudaMemcpyAsync(hsel.data(), bsel, sizeof(int) * hsel.size(), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(hn.data(), L.bnsel, sizeof(int) * nblocks, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&st, L.h.st, sizeof(st), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return cuda_status(e);
+  if (st.code != 0) return (css_status)st.code;
+  std::vector<int> ids;
+  for (int b = 0; b < nblocks; ++b)
+    for (int j = 0; j < hn[b]; ++j) ids.push_back((int)block_offsets[b] + hsel[(size_t)b * l_block + j]);
+  // block-local indices -> global ids in the caller's block_sel
+  {
+    std::vector<int> gsel(hsel.size(), -1);
+    for (int b = 0; b < nblocks; ++b)
+      for (int j = 0; j < hn[b]; ++j)
+        gsel[(size_t)b * l_block + j] = (int)block_offsets[b] + hsel[(size_t)b * l_block + j];
+    if ((e = cudaMemcpyAsync(bsel, gsel.data(), sizeof(int) * gsel.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      return cuda_status(e);
+  }
+  const int U = (int)ids.size();
+  if (U == 0) return CSS_RANK_EXHAUSTED;
+  const int ku = std::min<int>(k, U);
+  if ((e = cudaMemcpyAsync(L.ids, ids.data(), sizeof(int) * U, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_status(e);
+  {
+    const int es = (int)esize(dtype);
+    dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(8, (m * es + 1023) / 1024)),
+              (unsigned)std::min(U, 65535));
+    gather_columns_kernel<<<grid, 256, 0, s>>>((const char*)A, lda * es, (int)(m * es), L.ids, U, L.A0,
+                                               L.lda0 * es);
+    gather_f_kernel<<<(U + 255) / 256, 256, 0, s>>>(L.f0_saved, L.ids, U, L.us.f);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+  }
+  std::vector<UnitDesc> uu{make_unit(L.A0, dtype, m, U, L.lda0, ku, 1, B, ldb, r, L.us, nullptr,
+                                     L.usel, trace, n_sel, ob)};
+  cs = launch_units(L.h, uu, {1.0}, dtype, o.grid_ctas > 0 ? o.grid_ctas : team_ctas_for(U, m), tile,
+                    o.spin_budget_ns, s);
+  if (cs != CSS_OK) return cs;
+  map_sel_kernel<<<(ku + 255) / 256, 256, 0, s>>>(L.usel, L.ids, ku, sel);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+  return finish(L.h, o, s);
+}
+
+}  // extern "C"
+
+namespace {
+
+struct BatchLayout {
+  Header h;
+  std::vector<UnitState> st;
+  std::vector<void*> C;
+  std::vector<double*> partial;
+  size_t bytes;
+};
+
+BatchLayout batch_layout(void* ws, size_t cap, const css_problem* probs, int count, int dt) {
+  WsCarver c(ws, cap);
+  BatchLayout L{};
+  carve_header(c, std::max(count, 1), L.h);
+  L.st.resize(count);
+  L.C.resize(count);
+  L.partial.resize(count);
+  for (int i = 0; i < count; ++i) {
+    const css_problem& p = probs[i];
+    carve_scores(c, (int)p.n, L.st[i]);
+    carve_rest(c, dt, (int)p.m, (int)p.n, p.k, 0, 0, p.W == nullptr, L.st[i]);
+    L.C[i] = c.take<char>((size_t)p.m * p.m * accsize(dt));
+    L.partial[i] = c.take<double>(css_f0_partial_doubles(dt, (int)p.m, (int)p.n));
+  }
+  L.bytes = c.off;
+  return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t css_batched_workspace_size(const css_problem* probs, int32_t count, css_dtype dtype,
+                                  const css_opts* opts) {
+  (void)opts;
+  if (!probs || count < 1 || !valid_dtype(dtype)) return 0;
+  for (int i = 0; i < count; ++i)
+    if (probs[i].m < 1 || probs[i].n < 1 || probs[i].k < 1) return 0;
+  return batch_layout(nullptr, (size_t)-1, probs, count, dtype).bytes;
+}
+
+css_status css_select_batched(const css_problem* probs, int32_t count, css_dtype dtype, void* ws,
+                              size_t ws_bytes, const css_opts* opts, css_stream_t stream) {
+  const css_opts o = opts ? *opts : defaults();
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!probs || count < 1 || !valid_dtype(dtype)) return CSS_ERR_INVALID_ARG;
+  if (o.n_forced || o.diag_argmax || o.diag_f) return CSS_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i) {
+    const css_problem& p = probs[i];
+    if (!p.A || !p.sel || !p.trace || !p.n_sel) return CSS_ERR_INVALID_ARG;
+    if (p.m < 1 || p.n < 1 || p.lda < p.m || p.k < 1 || p.k > kMaxK || p.k > p.m || p.k > p.n)
+      return CSS_ERR_INVALID_ARG;
+  }
+  if (!ws || ((uintptr_t)ws % kWsAlign) != 0) return CSS_ERR_WORKSPACE;
+  BatchLayout L = batch_layout(ws, ws_bytes, probs, count, dtype);
+  if (L.bytes > ws_bytes) return CSS_ERR_WORKSPACE;
+  if (!device_ok()) return CSS_ERR_UNSUPPORTED;
+  PhaseTimer tm(o);
+  tm.mark(0, s);
+  std::vector<UnitDesc> units;
+  std::vector<double> work;
+  for (int i = 0; i < count; ++i) {
+    const css_problem& p = probs[i];
+    cudaError_t e = css_f0_simt(dtype, p.A, p.lda, (int)p.m, (int)p.n, L.C[i], L.partial[i], L.st[i].f, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    units.push_back(make_unit(p.A, dtype, p.m, p.n, p.lda, p.k, 0, L.C[i], p.m, 0, L.st[i], p.W,
+                              p.sel, p.trace, p.n_sel, o));
+    work.push_back((double)p.k * p.m * p.n + 4.0 * p.m * p.k * p.k);
+  }
+  tm.mark(1, s);
+  const int tile = pick_tile(o, dtype, 0);
+  css_status cs = launch_units(L.h, units, work, dtype, o.grid_ctas, tile, o.spin_budget_ns, s);
+  if (cs != CSS_OK) return cs;
+  tm.mark(2, s);
+  cs = finish(L.h, o, s);
+  tm.report(o);
+  return cs;
+}
+
+}  // extern "C"

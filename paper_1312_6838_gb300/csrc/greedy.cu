@@ -1,0 +1,651 @@
+// Persistent greedy kernel: Algorithm 1 (CSS) and Algorithm 3 (GCSS) of
+// Farahat et al. (arXiv:1312.6838), every iteration on the device.
+//
+// Teams of co-resident CTAs each own a list of problems ("units"); a team
+// synchronises with its own bounded barrier, so independent problems (the
+// column blocks of Algorithm 4, or a batch of instances) run side by side in
+// one cooperative launch.  A single large problem uses one team = the grid.
+//
+// Per iteration t (p = column picked at t):
+//   pivot     e = (I - Q Q^T) a_p by two Gram-Schmidt passes (FP64), the first
+//             with the coefficients Q^T a_p = omega^(r)_p already held in W;
+//             delta_p = ||e||^2, q = e / ||e|| (Eq. delta_omega: omega = A^T q).
+//   target    CSS:  y = C q with C = A A^T;  GCSS: upsilon = B^T q, y = B upsilon.
+//             s = q^T y (= ||omega||^2, Theorem 2) or ||upsilon||^2 (Theorem 4).
+//             y' = (I - Q Q^T) y, so that A^T y' = G omega (CSS) or
+//             A^T B upsilon - sum_r (upsilon^(r)^T upsilon) omega^(r) (GCSS).
+//   fused     one pass over A: omega_i = a_i . q and h_i = a_i . y' per column,
+//             f_i <- f_i - 2 omega_i h_i + s omega_i^2, g_i <- g_i - omega_i^2,
+//             W[t, i] = omega_i, then the masked argmax of f_i / g_i.
+//   trace     F <- F - f_p / g_p (Theorems 1 and 3).
+#include "greedy.cuh"
+
+namespace css {
+namespace {
+
+constexpr int NT = kGreedyThreads;
+constexpr int NW = NT / 32;
+constexpr int NS = 2 * NW;  // half-warp streams of the row GEMVs
+constexpr int RB = 16;      // rows per row tile
+
+template <typename T> __device__ __forceinline__ T ld_cg(const T* p) { return __ldcg(p); }
+
+// ---------------------------------------------------------------- context ---
+template <typename Acc>
+struct Ctx {
+  int rank, ncta, tid, lane, warp;
+  DevStatus* st;
+  const TeamDesc* team;
+  Acc* sq;       // K1: q           (aliases buf)
+  Acc* sy;       // K1: y'          (aliases buf)
+  double* se64;  // pivot phases: FP64 vector (aliases buf)
+  Acc* seacc;    // pivot phases: same vector in Acc precision (aliases buf)
+  double* scoef; // coefficients (FP64)
+  Acc* sups;     // upsilon in Acc precision
+  double* sred;  // NS * RB partials
+};
+
+// ------------------------------------------------------------- transpose ----
+// Sum NV per-lane values over the warp.  Lane L ends up with value index
+// L >> (5 - log2 NV).  Costs NV - 1 + 5 - log2 NV shuffles.
+template <int NV> struct Log2 { static constexpr int v = (NV >= 32) ? 5 : (NV >= 16) ? 4 : (NV >= 8) ? 3 : (NV >= 4) ? 2 : (NV >= 2) ? 1 : 0; };
+
+template <int NV, typename T>
+__device__ __forceinline__ T transpose_reduce(T (&v)[NV], int lane) {
+  constexpr int LOG = Log2<NV>::v;
+#pragma unroll
+  for (int s = 0; s < LOG; ++s) {
+    const int mask = 16 >> s;
+    const int half = NV >> (s + 1);
+    const bool up = (lane & mask) != 0;
+#pragma unroll
+    for (int j = 0; j < half; ++j) {
+      T send = up ? v[j] : v[j + half];
+      T keep = up ? v[j + half] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, mask);
+    }
+  }
+  T r = v[0];
+#pragma unroll
+  for (int s = LOG; s < 5; ++s) r += __shfl_xor_sync(0xffffffffu, r, 16 >> s);
+  return r;
+}
+
+// ------------------------------------------------------------ vector io -----
+template <typename TA> struct Vec;
+template <> struct Vec<double> {
+  static constexpr int V = 2;
+  __device__ __forceinline__ static void unpack(const uint4& r, double (&a)[2]) {
+    a[0] = __hiloint2double((int)r.y, (int)r.x);
+    a[1] = __hiloint2double((int)r.w, (int)r.z);
+  }
+};
+template <> struct Vec<float> {
+  static constexpr int V = 4;
+  __device__ __forceinline__ static void unpack(const uint4& r, float (&a)[4]) {
+    a[0] = __uint_as_float(r.x); a[1] = __uint_as_float(r.y);
+    a[2] = __uint_as_float(r.z); a[3] = __uint_as_float(r.w);
+  }
+};
+template <> struct Vec<__nv_bfloat16> {
+  static constexpr int V = 8;
+  __device__ __forceinline__ static void unpack(const uint4& r, float (&a)[8]) {
+    a[0] = bf16_lo(r.x); a[1] = bf16_hi(r.x); a[2] = bf16_lo(r.y); a[3] = bf16_hi(r.y);
+    a[4] = bf16_lo(r.z); a[5] = bf16_hi(r.z); a[6] = bf16_lo(r.w); a[7] = bf16_hi(r.w);
+  }
+};
+
+template <typename Acc, int V>
+__device__ __forceinline__ void lds_vec(const Acc* p, Acc (&a)[V]) {
+  if constexpr (sizeof(Acc) == 4) {
+#pragma unroll
+    for (int i = 0; i < V; i += 4) {
+      float4 t = *reinterpret_cast<const float4*>(p + i);
+      a[i] = t.x; a[i + 1] = t.y; a[i + 2] = t.z; a[i + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < V; i += 2) {
+      double2 t = *reinterpret_cast<const double2*>(p + i);
+      a[i] = t.x; a[i + 1] = t.y;
+    }
+  }
+}
+
+// ------------------------------------------------------------- row GEMV -----
+// For every row i < m of the team's rows: fin(i, sum_{j<nj} M[i + j ldm] c[j])
+// with c in shared memory.  Rows are split in tiles of RB rows, dealt round-robin
+// to the team's CTAs; inside a CTA the j-range of a tile is split over half-warp
+// streams when the CTA has few tiles.  Deterministic for a fixed team size.
+template <typename TS, typename TM, typename TC, typename Acc, typename Fin>
+__device__ void row_gemv(const Ctx<Acc>& x, int m, int nj, const TM* M, long long ldm,
+                         const TC* c, Fin fin) {
+  const int G = (m + RB - 1) / RB;
+  const int my_tiles = (G > x.rank) ? (G - x.rank + x.ncta - 1) / x.ncta : 0;
+  const int TP = (G + x.ncta - 1) / x.ncta;
+  int SP = NS;
+  while (SP > 1 && SP * TP > NS) SP >>= 1;
+  const int slots = NS / SP;
+  const int s = x.warp * 2 + (x.lane >> 4);
+  const int slot = s / SP, sub = s % SP;
+  const int r16 = x.lane & (RB - 1);
+  TS* red = reinterpret_cast<TS*>(x.sred);
+  for (int base = 0; base < my_tiles; base += slots) {
+    const int ti = base + slot;
+    TS acc = TS(0);
+    if (ti < my_tiles) {
+      const int row = (x.rank + ti * x.ncta) * RB + r16;
+      if (row < m) {
+        const TM* mp = M + row;
+        int j = sub;
+        for (; j + 3 * SP < nj; j += 4 * SP) {
+          TS a0 = (TS)ld_cg(mp + (long long)j * ldm);
+          TS a1 = (TS)ld_cg(mp + (long long)(j + SP) * ldm);
+          TS a2 = (TS)ld_cg(mp + (long long)(j + 2 * SP) * ldm);
+          TS a3 = (TS)ld_cg(mp + (long long)(j + 3 * SP) * ldm);
+          acc += a0 * (TS)c[j];
+          acc += a1 * (TS)c[j + SP];
+          acc += a2 * (TS)c[j + 2 * SP];
+          acc += a3 * (TS)c[j + 3 * SP];
+        }
+        for (; j < nj; j += SP) acc += (TS)ld_cg(mp + (long long)j * ldm) * (TS)c[j];
+      }
+    }
+    red[s * RB + r16] = acc;
+    __syncthreads();
+    if (x.tid < slots * RB) {
+      const int sl = x.tid / RB, rr = x.tid % RB;
+      const int tj = base + sl;
+      if (tj < my_tiles) {
+        const int row = (x.rank + tj * x.ncta) * RB + rr;
+        if (row < m) {
+          TS sum = TS(0);
+          for (int q = 0; q < SP; ++q) sum += red[(sl * SP + q) * RB + rr];
+          fin(row, (double)sum);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ column dots ---
+// fin(j, sum_{i<len} M[i + j ldm] v[i]) for j < nj, v in shared memory.
+template <typename TS, typename TM, typename TV, typename Acc, typename Fin>
+__device__ void col_dots(const Ctx<Acc>& x, int len, int nj, const TM* M, long long ldm,
+                         const TV* v, Fin fin) {
+  const int per_cta = (nj + x.ncta - 1) / x.ncta;
+  if (per_cta >= NW / 2) {
+    for (int j = x.rank * NW + x.warp; j < nj; j += x.ncta * NW) {
+      const TM* col = M + (long long)j * ldm;
+      TS acc = TS(0);
+      for (int i = x.lane; i < len; i += 32) acc += (TS)ld_cg(col + i) * (TS)v[i];
+      acc = warp_sum(acc);
+      if (x.lane == 0) fin(j, (double)acc);
+    }
+  } else {
+    for (int j = x.rank; j < nj; j += x.ncta) {
+      const TM* col = M + (long long)j * ldm;
+      TS acc = TS(0);
+      for (int i = x.tid; i < len; i += NT) acc += (TS)ld_cg(col + i) * (TS)v[i];
+      acc = block_sum(acc, reinterpret_cast<TS*>(x.sred));
+      if (x.tid == 0) fin(j, (double)acc);
+    }
+  }
+}
+
+// ------------------------------------------------------------- CTA argmax ---
+template <typename Acc>
+__device__ void cta_argmax_publish(const Ctx<Acc>& x, double bv, int bi) {
+  __shared__ double s_v[NW];
+  __shared__ int s_i[NW];
+  warp_argmax(bv, bi);
+  if (x.lane == 0) { s_v[x.warp] = bv; s_i[x.warp] = bi; }
+  __syncthreads();
+  if (x.warp == 0) {
+    double v = (x.lane < NW) ? s_v[x.lane] : -1.0;
+    int i = (x.lane < NW) ? s_i[x.lane] : -1;
+    warp_argmax(v, i);
+    if (x.lane == 0) {
+      x.team->cand_val[x.rank] = v;
+      x.team->cand_idx[x.rank] = i;
+    }
+  }
+  __syncthreads();
+}
+
+template <typename Acc>
+__device__ int team_argmax(const Ctx<Acc>& x) {
+  __shared__ int s_p;
+  if (x.warp == 0) {
+    double v = -1.0;
+    int i = -1;
+    for (int r = x.lane; r < x.ncta; r += 32) {
+      double v2 = ld_cg(x.team->cand_val + r);
+      int i2 = ld_cg(x.team->cand_idx + r);
+      if (better(v2, i2, v, i)) { v = v2; i = i2; }
+    }
+    warp_argmax(v, i);
+    if (x.lane == 0) s_p = i;
+  }
+  __syncthreads();
+  return s_p;
+}
+
+// --------------------------------------------------------- fused step (K1) --
+template <typename TA, int CW>
+__device__ void fused_step(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc& u, int t,
+                           int p, double s, uint64_t pol, double& bv, int& bi) {
+  using Acc = typename AccOf<TA>::type;
+  constexpr int V = Vec<TA>::V;
+  constexpr int NV = 2 * CW;
+  constexpr int SH = 5 - Log2<NV>::v;
+  const int n = u.n, m = u.m;
+  const int ntiles = (n + CW - 1) / CW;
+  const int m_vec = u.vec_ok ? (m / V) * V : 0;
+  const TA* A = reinterpret_cast<const TA*>(u.A);
+  const volatile unsigned char* selv = u.selmask;
+  for (int tile = x.rank * NW + x.warp; tile < ntiles; tile += x.ncta * NW) {
+    const int c0 = tile * CW;
+    const TA* colp[CW];
+#pragma unroll
+    for (int c = 0; c < CW; ++c) colp[c] = A + (long long)min(c0 + c, n - 1) * u.lda;
+    Acc v[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = Acc(0);
+#pragma unroll 2
+    for (int r = x.lane * V; r < m_vec; r += 32 * V) {
+      uint4 raw[CW];
+#pragma unroll
+      for (int c = 0; c < CW; ++c) raw[c] = ldg_stream16(colp[c] + r, pol);
+      Acc qa[V], ya[V];
+      lds_vec<Acc, V>(x.sq + r, qa);
+      lds_vec<Acc, V>(x.sy + r, ya);
+#pragma unroll
+      for (int c = 0; c < CW; ++c) {
+        Acc a[V];
+        Vec<TA>::unpack(raw[c], a);
+        Acc tw = a[0] * qa[0], th = a[0] * ya[0];
+#pragma unroll
+        for (int e = 1; e < V; ++e) { tw = fma(a[e], qa[e], tw); th = fma(a[e], ya[e], th); }
+        v[2 * c] += tw;
+        v[2 * c + 1] += th;
+      }
+    }
+    for (int r = m_vec + x.lane; r < m; r += 32) {
+      const Acc qa = x.sq[r], ya = x.sy[r];
+#pragma unroll
+      for (int c = 0; c < CW; ++c) {
+        const Acc a = load_elem<TA>(colp[c] + r);
+        v[2 * c] = fma(a, qa, v[2 * c]);
+        v[2 * c + 1] = fma(a, ya, v[2 * c + 1]);
+      }
+    }
+    const Acc red = transpose_reduce<NV>(v, x.lane);
+    const Acc hv = __shfl_down_sync(0xffffffffu, red, 1 << SH);
+    const int j = x.lane >> SH;
+    if ((x.lane & ((1 << SH) - 1)) == 0 && (j & 1) == 0) {
+      const int col = c0 + (j >> 1);
+      if (col < n) {
+        const double w = (double)red, h = (double)hv;
+        double fi = ld_cg(u.f + col), gi = ld_cg(u.g + col);
+        // Theorem 2 / Theorem 4: f - 2 omega o x + s (omega o omega), g - omega o omega
+        fi = fi - 2.0 * w * h + s * (w * w);
+        gi = gi - w * w;
+        u.f[col] = fi;
+        u.g[col] = gi;
+        u.W[(long long)t * n + col] = w;
+        bool selected = selv[col] != 0;
+        if (col == p) { u.selmask[col] = 1; selected = true; }
+        const double g0 = ld_cg(u.g0 + col);
+        if (!selected && g0 > 0.0 && gi > u.tau * g0) {
+          const double sc = u.score_mode ? gi : fmax(fi, 0.0) / gi;
+          if (better(sc, col, bv, bi)) { bv = sc; bi = col; }
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------ initialisation (Algorithms 1, 3) -
+// g_i^(0) = ||a_i||^2 (f^(0) was written by the initial-score kernels), the
+// non-finite check, F^(0) partial sums and the first argmax.
+template <typename TA>
+__device__ void init_pass(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc& u,
+                          uint64_t pol, double& bv, int& bi, double& fsum, int& bad) {
+  using Acc = typename AccOf<TA>::type;
+  constexpr int V = Vec<TA>::V;
+  const int n = u.n, m = u.m;
+  const int m_vec = u.vec_ok ? (m / V) * V : 0;
+  const TA* A = reinterpret_cast<const TA*>(u.A);
+  for (int col = x.rank * NW + x.warp; col < n; col += x.ncta * NW) {
+    const TA* cp = A + (long long)col * u.lda;
+    Acc acc = Acc(0);
+    for (int r = x.lane * V; r < m_vec; r += 32 * V) {
+      Acc a[V];
+      Vec<TA>::unpack(ldg_stream16(cp + r, pol), a);
+      Acc tt = a[0] * a[0];
+#pragma unroll
+      for (int e = 1; e < V; ++e) tt = fma(a[e], a[e], tt);
+      acc += tt;
+    }
+    for (int r = m_vec + x.lane; r < m; r += 32) {
+      const Acc a = load_elem<TA>(cp + r);
+      acc = fma(a, a, acc);
+    }
+    acc = warp_sum(acc);
+    if (x.lane == 0) {
+      const double g0 = (double)acc;
+      const double f0 = ld_cg(u.f + col);
+      u.g0[col] = g0;
+      u.g[col] = g0;
+      u.selmask[col] = 0;
+      if (!isfinite(g0) || !isfinite(f0)) bad = 1;
+      if (u.mode == 0) fsum += g0;
+      if (g0 > 0.0) {
+        const double sc = u.score_mode ? g0 : fmax(f0, 0.0) / g0;
+        if (better(sc, col, bv, bi)) { bv = sc; bi = col; }
+      }
+    }
+  }
+  if (u.mode == 1) {
+    // ||B||_F^2, the starting value of Theorem 3's recursion
+    const Acc* B = reinterpret_cast<const Acc*>(u.T);
+    for (int j = x.rank * NW + x.warp; j < u.r; j += x.ncta * NW) {
+      const Acc* cp = B + (long long)j * u.ldt;
+      double acc = 0.0;
+      for (int r = x.lane; r < m; r += 32) { const double b = (double)cp[r]; acc += b * b; }
+      acc = warp_sum(acc);
+      if (x.lane == 0) {
+        if (!isfinite(acc)) bad = 1;
+        fsum += acc;
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------- the unit ---
+template <typename TA, int CW>
+__device__ void run_unit(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc& u) {
+  using Acc = typename AccOf<TA>::type;
+  __shared__ double s_scal[4];
+  const uint64_t pol_stream = policy_evict_first();
+  const uint64_t pol_keep = policy_evict_last();
+  const TeamDesc& tm = *x.team;
+  const int m = u.m, n = u.n;
+
+  // ---- initialisation: g^(0), F^(0), first argmax
+  double bv = -1.0, fsum = 0.0;
+  int bi = -1, bad = 0;
+  init_pass<TA>(x, u, pol_stream, bv, bi, fsum, bad);
+  if (__syncthreads_or(bad)) set_error(x.st, (int32_t)CSS_ERR_NONFINITE, 100);
+  fsum = block_sum(fsum, x.sred);
+  if (x.tid == 0) tm.part[x.rank * 4 + 2] = fsum;
+  cta_argmax_publish(x, bv, bi);
+  if (!team_barrier(tm.bar, x.ncta, x.st, 1)) return;
+
+  double F = 0.0;  // meaningful in rank 0, thread 0
+  if (x.rank == 0 && x.tid == 0) {
+    for (int r = 0; r < x.ncta; ++r) F += ld_cg(tm.part + r * 4 + 2);
+    u.trace[0] = F;
+  }
+
+  int t = 0;
+  for (; t < u.k; ++t) {
+    // ---- Phase A: pivot p, outputs, e1 = a_p - Q_t W[0:t, p]
+    int p = team_argmax(x);
+    const int p_arg = p;
+    if (t < u.n_forced) p = u.forced[t];
+    if (p < 0) break;
+    if (x.rank == 0 && x.tid == 0) {
+      if (u.diag_argmax) u.diag_argmax[t] = p_arg;
+      u.sel[t] = p;
+      F = F - ld_cg(u.f + p) / ld_cg(u.g + p);   // Theorem 1 / Theorem 3
+      u.trace[t + 1] = F;
+    }
+    for (int j = x.tid; j < t; j += NT) x.scoef[j] = ld_cg(u.W + (long long)j * n + p);
+    __syncthreads();
+    {
+      const TA* ap = reinterpret_cast<const TA*>(u.A) + (long long)p * u.lda;
+      row_gemv<double>(x, m, t, u.Q, (long long)m, x.scoef, [&](int i, double sum) {
+        u.e1[i] = (double)load_elem<TA>(ap + i) - sum;
+      });
+    }
+    if (!team_barrier(tm.bar, x.ncta, x.st, 2)) return;
+
+    // ---- Phase B: c2 = Q_t^T e1 (second Gram-Schmidt pass)
+    for (int i = x.tid; i < m; i += NT) x.se64[i] = ld_cg(u.e1 + i);
+    __syncthreads();
+    col_dots<double>(x, m, t, u.Q, (long long)m, x.se64, [&](int j, double v) { u.coef[j] = v; });
+    if (!team_barrier(tm.bar, x.ncta, x.st, 3)) return;
+
+    // ---- Phase C: e = e1 - Q_t c2, ||e||^2 partials
+    for (int j = x.tid; j < t; j += NT) x.scoef[j] = ld_cg(u.coef + j);
+    __syncthreads();
+    double nrm_part = 0.0;
+    row_gemv<double>(x, m, t, u.Q, (long long)m, x.scoef, [&](int i, double sum) {
+      const double ei = ld_cg(u.e1 + i) - sum;
+      u.e[i] = ei;
+      nrm_part += ei * ei;
+    });
+    nrm_part = block_sum(nrm_part, x.sred);
+    if (x.tid == 0) tm.part[x.rank * 4 + 0] = nrm_part;
+    if (!team_barrier(tm.bar, x.ncta, x.st, 4)) return;
+
+    // ---- Phase D: y_un = C e (CSS) or B (B^T e) (GCSS); d = Z^T e
+    if (x.tid == 0) {
+      double a = 0.0;
+      for (int r = 0; r < x.ncta; ++r) a += ld_cg(tm.part + r * 4 + 0);
+      s_scal[0] = a;
+    }
+    for (int i = x.tid; i < m; i += NT) {
+      const double ei = ld_cg(u.e + i);
+      x.se64[i] = ei;
+      x.seacc[i] = (Acc)ei;
+    }
+    __syncthreads();
+    const double nrm2 = s_scal[0];
+    double s_un = 0.0;
+    if (u.mode == 0) {
+      const Acc* C = reinterpret_cast<const Acc*>(u.T);
+      constexpr int VC = 16 / sizeof(Acc);
+      const int m_vec = u.t_vec_ok ? (m / VC) * VC : 0;
+      double ey = 0.0;
+      for (int i = x.rank * NW + x.warp; i < m; i += x.ncta * NW) {
+        const Acc* cp = C + (long long)i * u.ldt;
+        Acc acc = Acc(0);
+        for (int l = x.lane * VC; l < m_vec; l += 32 * VC) {
+          Acc cv[VC], ev[VC];
+          if constexpr (sizeof(Acc) == 4) {
+            float tmp[4];
+            Vec<float>::unpack(ldg_stream16(cp + l, pol_keep), tmp);
+#pragma unroll
+            for (int e = 0; e < VC; ++e) cv[e] = (Acc)tmp[e];
+          } else {
+            double tmp[2];
+            Vec<double>::unpack(ldg_stream16(cp + l, pol_keep), tmp);
+#pragma unroll
+            for (int e = 0; e < VC; ++e) cv[e] = (Acc)tmp[e];
+          }
+          lds_vec<Acc, VC>(x.seacc + l, ev);
+#pragma unroll
+          for (int e = 0; e < VC; ++e) acc = fma(cv[e], ev[e], acc);
+        }
+        for (int l = m_vec + x.lane; l < m; l += 32) acc = fma(__ldg(cp + l), x.seacc[l], acc);
+        acc = warp_sum(acc);
+        if (x.lane == 0) {
+          u.y[i] = (double)acc;
+          ey += x.se64[i] * (double)acc;
+        }
+      }
+      col_dots<double>(x, m, t, u.Z, (long long)m, x.se64, [&](int j, double v) { u.coef[j] = v; });
+      ey = block_sum(ey, x.sred);
+      if (x.tid == 0) tm.part[x.rank * 4 + 1] = ey;
+      if (!team_barrier(tm.bar, x.ncta, x.st, 5)) return;
+    } else {
+      const Acc* B = reinterpret_cast<const Acc*>(u.T);
+      col_dots<Acc>(x, m, u.r, B, u.ldt, x.seacc, [&](int j, double v) { u.ups[j] = v; });
+      if (!team_barrier(tm.bar, x.ncta, x.st, 5)) return;
+      for (int j = x.tid; j < u.r; j += NT) {
+        const double v = ld_cg(u.ups + j);
+        x.scoef[j] = v;
+        x.sups[j] = (Acc)v;
+      }
+      __syncthreads();
+      row_gemv<Acc>(x, m, u.r, B, u.ldt, x.sups, [&](int i, double sum) { u.y[i] = sum; });
+      col_dots<double>(x, u.r, t, u.Z, (long long)u.r, x.scoef, [&](int j, double v) { u.coef[j] = v; });
+      double ss = 0.0;
+      for (int j = x.tid; j < u.r; j += NT) ss += x.scoef[j] * x.scoef[j];
+      s_un = block_sum(ss, x.sred);
+      if (x.rank == 0) {
+        // upsilon^(t) = B^T q, column t of Z (read by later iterations only)
+        const double inv = 1.0 / sqrt(nrm2);
+        for (int j = x.tid; j < u.r; j += NT) u.Z[(long long)t * u.r + j] = x.scoef[j] * inv;
+      }
+      if (!team_barrier(tm.bar, x.ncta, x.st, 6)) return;
+    }
+
+    // ---- Phase E: q, y = y_un / ||e||, y' = y - Q (Q^T y), s
+    double s;
+    {
+      if (x.tid == 0 && u.mode == 0) {
+        double a = 0.0;
+        for (int r = 0; r < x.ncta; ++r) a += ld_cg(tm.part + r * 4 + 1);
+        s_scal[1] = a;
+      }
+      for (int j = x.tid; j < t; j += NT) x.scoef[j] = ld_cg(u.coef + j);
+      __syncthreads();
+      const double inv = 1.0 / sqrt(nrm2);
+      s = (u.mode == 0) ? s_scal[1] / nrm2 : s_un / nrm2;
+      Acc* qv = reinterpret_cast<Acc*>(u.qv);
+      Acc* ypv = reinterpret_cast<Acc*>(u.ypv);
+      row_gemv<double>(x, m, t, u.Q, (long long)m, x.scoef, [&](int i, double sum) {
+        const double yi = ld_cg(u.y + i) * inv;
+        const double qi = ld_cg(u.e + i) * inv;
+        u.Q[(long long)t * m + i] = qi;
+        if (u.mode == 0) u.Z[(long long)t * m + i] = yi;
+        qv[i] = (Acc)qi;
+        ypv[i] = (Acc)(yi - sum * inv);
+      });
+    }
+    if (!team_barrier(tm.bar, x.ncta, x.st, 7)) return;
+
+    // ---- fused step over A
+    {
+      const Acc* qv = reinterpret_cast<const Acc*>(u.qv);
+      const Acc* ypv = reinterpret_cast<const Acc*>(u.ypv);
+      for (int i = x.tid; i < m; i += NT) {
+        x.sq[i] = ld_cg(qv + i);
+        x.sy[i] = ld_cg(ypv + i);
+      }
+      __syncthreads();
+      double bv2 = -1.0;
+      int bi2 = -1;
+      fused_step<TA, CW>(x, u, t, p, s, pol_stream, bv2, bi2);
+      cta_argmax_publish(x, bv2, bi2);
+    }
+    if (!team_barrier(tm.bar, x.ncta, x.st, 8)) return;
+  }
+
+  if (x.rank == 0 && x.tid == 0) {
+    *u.n_sel = t;
+    if (t < u.k) atomicAdd(&x.st->rank_exhausted, 1);
+  }
+  if (u.diag_f) {
+    for (int i = (x.rank * NT + x.tid); i < n; i += x.ncta * NT) {
+      u.diag_f[i] = ld_cg(u.f + i);
+      u.diag_g[i] = ld_cg(u.g + i);
+    }
+  }
+  team_barrier(tm.bar, x.ncta, x.st, 9);
+}
+
+template <typename TA, int CW>
+__global__ void __launch_bounds__(NT, 1) greedy_kernel(GreedyLaunch L) {
+  using Acc = typename AccOf<TA>::type;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int team_id = L.cta_team[blockIdx.x];
+  const TeamDesc& tm = L.teams[team_id];
+  Ctx<Acc> x;
+  x.rank = blockIdx.x - tm.cta0;
+  x.ncta = tm.ncta;
+  x.tid = threadIdx.x;
+  x.lane = threadIdx.x & 31;
+  x.warp = threadIdx.x >> 5;
+  x.st = L.st;
+  x.team = &tm;
+  // shared memory carve (see greedy_smem_bytes)
+  const size_t mp = ((size_t)L.m_max + 3) & ~(size_t)3;  // keeps every sub-buffer 16-byte aligned
+  size_t buf = mp * (sizeof(double) + sizeof(Acc));
+  if (2 * mp * sizeof(Acc) > buf) buf = 2 * mp * sizeof(Acc);
+  unsigned char* p = smem;
+  x.sq = reinterpret_cast<Acc*>(p);
+  x.sy = reinterpret_cast<Acc*>(p) + mp;
+  x.se64 = reinterpret_cast<double*>(p);
+  x.seacc = reinterpret_cast<Acc*>(p + mp * sizeof(double));
+  p += buf;
+  const size_t nco = (size_t)max(L.k_max, L.r_max);
+  x.scoef = reinterpret_cast<double*>(p);
+  p += (nco * sizeof(double) + 15) & ~(size_t)15;
+  x.sups = reinterpret_cast<Acc*>(p);
+  p += ((size_t)L.r_max * sizeof(Acc) + 15) & ~(size_t)15;
+  x.sred = reinterpret_cast<double*>(p);
+
+  for (int ui = tm.u_begin; ui < tm.u_end; ++ui) {
+    const UnitDesc u = L.units[L.order[ui]];
+    run_unit<TA, CW>(x, u);
+    if (ld_volatile_i32(&L.st->code) != 0) return;
+  }
+}
+
+template <typename TA, int CW>
+void* kernel_ptr() { return (void*)greedy_kernel<TA, CW>; }
+
+void* pick_kernel(int dtype, int cw) {
+  switch (dtype) {
+    case CSS_F64:
+      return cw == 2 ? kernel_ptr<double, 2>() : cw == 8 ? kernel_ptr<double, 8>() : kernel_ptr<double, 4>();
+    case CSS_F32:
+      return cw == 2 ? kernel_ptr<float, 2>() : cw == 8 ? kernel_ptr<float, 8>() : kernel_ptr<float, 4>();
+    default:
+      return cw == 2 ? kernel_ptr<__nv_bfloat16, 2>() : cw == 8 ? kernel_ptr<__nv_bfloat16, 8>()
+                     : kernel_ptr<__nv_bfloat16, 4>();
+  }
+}
+
+}  // namespace
+
+size_t greedy_smem_bytes(int dtype, int m_max, int k_max, int r_max) {
+  const size_t sa = (dtype == CSS_F64) ? 8 : 4;
+  const size_t mp = ((size_t)m_max + 3) & ~(size_t)3;
+  size_t buf = mp * (8 + sa);
+  if (2 * mp * sa > buf) buf = 2 * mp * sa;
+  const size_t nco = (size_t)(k_max > r_max ? k_max : r_max);
+  size_t b = buf + ((nco * 8 + 15) & ~(size_t)15) + (((size_t)r_max * sa + 15) & ~(size_t)15);
+  b += (size_t)NS * RB * sizeof(double);
+  return b;
+}
+
+int greedy_occupancy(int dtype, int tile_cols, size_t smem) {
+  void* k = pick_kernel(dtype, tile_cols);
+  if (smem > 48 * 1024) {
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return 0;
+  }
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, NT, smem) != cudaSuccess) return 0;
+  return occ;
+}
+
+cudaError_t greedy_launch(const GreedyLaunch& L, cudaStream_t stream) {
+  void* k = pick_kernel(L.dtype, L.tile_cols);
+  if (L.smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+    if (e != cudaSuccess) return e;
+  }
+  GreedyLaunch arg = L;
+  void* args[] = {&arg};
+  return cudaLaunchCooperativeKernel(k, dim3(L.grid), dim3(NT), args, L.smem, stream);
+}
+
+}  // namespace css

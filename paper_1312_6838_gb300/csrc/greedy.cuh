@@ -1,0 +1,78 @@
+// Internal interface of the persistent greedy kernel (greedy.cu).
+#pragma once
+
+#include "css_common.cuh"
+
+namespace css {
+
+// One greedy problem (Algorithm 1 when mode == 0, Algorithm 3 when mode == 1).
+struct UnitDesc {
+  const void* A;      // m x n, column-major, leading dimension lda
+  long long lda;
+  int m, n, k, mode;
+  // CSS: T = C = A A^T (m x m, ld m, Acc type).  GCSS: T = B (m x r, ld ldt, Acc type).
+  const void* T;
+  long long ldt;
+  int r, score_mode;
+  double tau;
+  // state
+  double* f;          // numerator of the criterion, Theorem 2/4
+  double* g;          // denominator (residual column norms)
+  double* g0;         // initial norms (candidate threshold)
+  unsigned char* selmask;
+  double* Q;          // m x k orthonormal basis of the selected columns
+  double* Z;          // CSS: C Q (m x k, ld m).  GCSS: B^T Q (r x k, ld r)
+  double* W;          // k x n, row t = omega^(t)
+  void* qv;           // Acc[m]  direction q (the omega of this step is A^T q)
+  void* ypv;          // Acc[m]  (I - P) C q   or   (I - P) B B^T q
+  double* e1;         // m
+  double* e;          // m  (unnormalised new basis vector)
+  double* y;          // m  (C e or B B^T e, unnormalised)
+  double* coef;       // max(k, r) scratch coefficients
+  double* ups;        // r  (B^T e, GCSS)
+  // outputs
+  int* sel;
+  double* trace;
+  int* n_sel;
+  int* diag_argmax;
+  double* diag_f;
+  double* diag_g;
+  const int* forced;
+  int n_forced;
+  int vec_ok;         // A and lda allow 16-byte vector loads
+  int t_vec_ok;       // T (C or B) allows 16-byte vector loads
+  int pad_;
+};
+
+struct TeamDesc {
+  int cta0, ncta, u_begin, u_end;   // units order[u_begin .. u_end)
+  uint32_t* bar;                    // 2 words
+  double* part;                     // ncta * 4
+  double* cand_val;                 // ncta
+  int* cand_idx;                    // ncta
+};
+
+struct GreedyLaunch {
+  const UnitDesc* units;
+  const int* order;
+  const TeamDesc* teams;
+  const int* cta_team;
+  DevStatus* st;
+  int dtype;       // css_dtype of A
+  int tile_cols;   // 2, 4 or 8
+  int m_max, k_max, r_max;
+  int grid;        // CTAs
+  int threads;
+  size_t smem;
+};
+
+constexpr int kGreedyThreads = 512;
+
+// Bytes of dynamic shared memory the kernel needs.
+size_t greedy_smem_bytes(int dtype, int m_max, int k_max, int r_max);
+// Max co-resident CTAs per SM for the given configuration (0 on error).
+int greedy_occupancy(int dtype, int tile_cols, size_t smem);
+// Enqueue the persistent kernel (cooperative launch).  Returns a cudaError_t.
+cudaError_t greedy_launch(const GreedyLaunch& L, cudaStream_t stream);
+
+}  // namespace css

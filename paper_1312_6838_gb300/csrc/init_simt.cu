@@ -1,0 +1,216 @@
+// Initial scores on CUDA cores (the initialisation of Algorithms 1 and 3).
+//
+//   CSS :  f_i^(0) = ||A^T A_:i||^2 = A_:i^T C A_:i  with  C = A A^T
+//          (the n x n matrix A^T A is never formed)
+//   GCSS:  f_i^(0) = ||B^T A_:i||^2
+//
+// Both are register-tiled SIMT GEMMs with column-reduction epilogues; the
+// product tile is never stored.  Partial sums over row tiles are written in
+// FP64 and added in a fixed order, so results do not depend on scheduling.
+#include "init.cuh"
+
+namespace css {
+namespace {
+
+template <typename TA> __device__ __forceinline__ typename AccOf<TA>::type cvt_in(TA v);
+template <> __device__ __forceinline__ double cvt_in<double>(double v) { return v; }
+template <> __device__ __forceinline__ float cvt_in<float>(float v) { return v; }
+template <> __device__ __forceinline__ float cvt_in<__nv_bfloat16>(__nv_bfloat16 v) {
+  return __uint_as_float(((uint32_t)__bfloat16_as_ushort(v)) << 16);
+}
+
+// ---------------------------------------------------------------- SYRK ------
+// C = A A^T (m x m, leading dimension m).  Only tile pairs bi <= bj are
+// computed; the lower tile is written by mirroring.  TT x TT outputs per
+// thread, 16 x 16 threads, K chunks of KC columns of A.
+template <typename TA, int TT, int KC>
+__global__ void __launch_bounds__(256) syrk_kernel(const TA* __restrict__ A, long long lda, int m,
+                                                   int n, typename AccOf<TA>::type* __restrict__ C) {
+  using Acc = typename AccOf<TA>::type;
+  constexpr int BT = 16 * TT;
+  __shared__ __align__(16) Acc As[KC][BT];
+  __shared__ __align__(16) Acc Bs[KC][BT];
+  const int nt = (m + BT - 1) / BT;
+  // decode the linear index into (bi, bj), bi <= bj
+  int idx = blockIdx.x, bi = 0;
+  while (idx >= nt - bi) { idx -= nt - bi; ++bi; }
+  const int bj = bi + idx;
+  const int i0 = bi * BT, j0 = bj * BT;
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  Acc acc[TT][TT];
+#pragma unroll
+  for (int a = 0; a < TT; ++a)
+#pragma unroll
+    for (int b = 0; b < TT; ++b) acc[a][b] = Acc(0);
+  for (int l0 = 0; l0 < n; l0 += KC) {
+    for (int e = tid; e < KC * BT; e += 256) {
+      const int kk = e / BT, rr = e % BT;
+      const int l = l0 + kk;
+      As[kk][rr] = (l < n && i0 + rr < m) ? cvt_in<TA>(A[(long long)l * lda + i0 + rr]) : Acc(0);
+      Bs[kk][rr] = (l < n && j0 + rr < m) ? cvt_in<TA>(A[(long long)l * lda + j0 + rr]) : Acc(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) {
+      Acc a[TT], b[TT];
+#pragma unroll
+      for (int q = 0; q < TT; ++q) { a[q] = As[kk][ty * TT + q]; b[q] = Bs[kk][tx * TT + q]; }
+#pragma unroll
+      for (int q = 0; q < TT; ++q)
+#pragma unroll
+        for (int w = 0; w < TT; ++w) acc[q][w] = fma(a[q], b[w], acc[q][w]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < TT; ++q) {
+    const int i = i0 + ty * TT + q;
+#pragma unroll
+    for (int w = 0; w < TT; ++w) {
+      const int j = j0 + tx * TT + w;
+      if (i < m && j < m) {
+        C[(long long)j * m + i] = acc[q][w];
+        if (bi != bj) C[(long long)i * m + j] = acc[q][w];
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------ column reduction ----
+// D = X^T Y with X (K x M, ldx) and Y (K x N, ldy) both K-contiguous.
+// partial[mb * n + i] = sum over the rows r of M-tile mb of
+//     EPI == 0 :  D[r, i] * Y[r, i]       (CSS: C A dotted with A, needs M == K)
+//     EPI == 1 :  D[r, i]^2               (GCSS: ||B^T a_i||^2)
+template <typename TX, typename TA, int TT, int KC, int EPI>
+__global__ void __launch_bounds__(256) colreduce_kernel(const TX* __restrict__ X, long long ldx,
+                                                       const TA* __restrict__ Y, long long ldy, int K,
+                                                       int M, int N, double* __restrict__ partial) {
+  using Acc = typename AccOf<TA>::type;
+  constexpr int BT = 16 * TT;
+  __shared__ __align__(16) Acc Xs[KC][BT + 1];
+  __shared__ __align__(16) Acc Ys[KC][BT + 1];
+  __shared__ double red[16][BT];
+  const int mb = blockIdx.y, nb = blockIdx.x;
+  const int r0 = mb * BT, c0 = nb * BT;
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  Acc acc[TT][TT];
+#pragma unroll
+  for (int a = 0; a < TT; ++a)
+#pragma unroll
+    for (int b = 0; b < TT; ++b) acc[a][b] = Acc(0);
+  for (int k0 = 0; k0 < K; k0 += KC) {
+    for (int e = tid; e < KC * BT; e += 256) {
+      const int rr = e / KC, kk = e % KC;  // consecutive threads walk K (contiguous)
+      const int k = k0 + kk;
+      Xs[kk][rr] = (k < K && r0 + rr < M) ? (Acc)X[(long long)(r0 + rr) * ldx + k] : Acc(0);
+      Ys[kk][rr] = (k < K && c0 + rr < N) ? cvt_in<TA>(Y[(long long)(c0 + rr) * ldy + k]) : Acc(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) {
+      Acc a[TT], b[TT];
+#pragma unroll
+      for (int q = 0; q < TT; ++q) { a[q] = Xs[kk][ty * TT + q]; b[q] = Ys[kk][tx * TT + q]; }
+#pragma unroll
+      for (int q = 0; q < TT; ++q)
+#pragma unroll
+        for (int w = 0; w < TT; ++w) acc[q][w] = fma(a[q], b[w], acc[q][w]);
+    }
+    __syncthreads();
+  }
+  // epilogue: per column, sum over this thread's TT rows in FP64
+#pragma unroll
+  for (int w = 0; w < TT; ++w) {
+    const int i = c0 + tx * TT + w;
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < TT; ++q) {
+      const int r = r0 + ty * TT + q;
+      if (r < M && i < N) {
+        const double d = (double)acc[q][w];
+        if (EPI == 0) s += d * (double)cvt_in<TA>(Y[(long long)i * ldy + r]);
+        else s += d * d;
+      }
+    }
+    red[ty][tx * TT + w] = s;
+  }
+  __syncthreads();
+  for (int c = tid; c < BT; c += 256) {
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) s += red[q][c];
+    if (c0 + c < N) partial[(long long)mb * N + c0 + c] = s;
+  }
+}
+
+__global__ void sum_partials_kernel(const double* __restrict__ partial, int nblk, int n,
+                                    double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += partial[(long long)b * n + i];
+  out[i] = s;
+}
+
+template <typename TA> struct Tiles { static constexpr int TT = 8, KC = 16; };
+template <> struct Tiles<double> { static constexpr int TT = 4, KC = 16; };
+
+template <typename TA>
+cudaError_t css_f0_simt_t(const void* A_, long long lda, int m, int n, void* C_, double* partial,
+                          double* f, cudaStream_t s) {
+  using Acc = typename AccOf<TA>::type;
+  constexpr int TT = Tiles<TA>::TT, KC = Tiles<TA>::KC, BT = 16 * TT;
+  const TA* A = reinterpret_cast<const TA*>(A_);
+  Acc* C = reinterpret_cast<Acc*>(C_);
+  const int nt = (m + BT - 1) / BT;
+  syrk_kernel<TA, TT, KC><<<nt * (nt + 1) / 2, 256, 0, s>>>(A, lda, m, n, C);
+  dim3 grid((n + BT - 1) / BT, nt);
+  colreduce_kernel<Acc, TA, TT, KC, 0><<<grid, 256, 0, s>>>(C, (long long)m, A, lda, m, m, n, partial);
+  sum_partials_kernel<<<(n + 255) / 256, 256, 0, s>>>(partial, nt, n, f);
+  return cudaGetLastError();
+}
+
+template <typename TA>
+cudaError_t gcss_f0_simt_t(const void* A_, long long lda, int m, int n, const void* B_,
+                           long long ldb, int r, double* partial, double* f, cudaStream_t s) {
+  using Acc = typename AccOf<TA>::type;
+  constexpr int TT = Tiles<TA>::TT, KC = Tiles<TA>::KC, BT = 16 * TT;
+  const TA* A = reinterpret_cast<const TA*>(A_);
+  const Acc* B = reinterpret_cast<const Acc*>(B_);
+  const int mt = (r + BT - 1) / BT;
+  dim3 grid((n + BT - 1) / BT, mt);
+  colreduce_kernel<Acc, TA, TT, KC, 1><<<grid, 256, 0, s>>>(B, ldb, A, lda, m, r, n, partial);
+  sum_partials_kernel<<<(n + 255) / 256, 256, 0, s>>>(partial, mt, n, f);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t css_f0_partial_doubles(int dtype, int m, int n) {
+  const int BT = (dtype == CSS_F64) ? 64 : 128;
+  return (size_t)((m + BT - 1) / BT) * (size_t)n;
+}
+size_t gcss_f0_partial_doubles(int dtype, int r, int n) {
+  const int BT = (dtype == CSS_F64) ? 64 : 128;
+  return (size_t)((r + BT - 1) / BT) * (size_t)n;
+}
+
+cudaError_t css_f0_simt(int dtype, const void* A, long long lda, int m, int n, void* C,
+                        double* partial, double* f, cudaStream_t s) {
+  switch (dtype) {
+    case CSS_F64: return css_f0_simt_t<double>(A, lda, m, n, C, partial, f, s);
+    case CSS_F32: return css_f0_simt_t<float>(A, lda, m, n, C, partial, f, s);
+    default: return css_f0_simt_t<__nv_bfloat16>(A, lda, m, n, C, partial, f, s);
+  }
+}
+
+cudaError_t gcss_f0_simt(int dtype, const void* A, long long lda, int m, int n, const void* B,
+                         long long ldb, int r, double* partial, double* f, cudaStream_t s) {
+  switch (dtype) {
+    case CSS_F64: return gcss_f0_simt_t<double>(A, lda, m, n, B, ldb, r, partial, f, s);
+    case CSS_F32: return gcss_f0_simt_t<float>(A, lda, m, n, B, ldb, r, partial, f, s);
+    default: return gcss_f0_simt_t<__nv_bfloat16>(A, lda, m, n, B, ldb, r, partial, f, s);
+  }
+}
+
+}  // namespace css

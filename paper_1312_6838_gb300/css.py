@@ -1,0 +1,364 @@
+"""Python front end of libcss: torch tensors in, C-ABI calls out.
+
+Every function here only checks shapes, allocates the caller-side buffers
+(outputs and the workspace, through torch's allocator) and calls the C ABI;
+all arithmetic runs in the CUDA library.  Matrices are column-major: pass a
+tensor whose ``stride(0) == 1`` (for example ``X.t()`` of a row-major n x m
+tensor X whose rows are the columns of A).
+
+Functions mirror include/css.h:
+
+* ``select``            Algorithm 1 (greedy CSS)
+* ``gcss_select``       Algorithm 3 (greedy generalized CSS, target B)
+* ``distributed``       Algorithm 4 (per-block GCSS, then GCSS on the union)
+* ``project``           B = A Omega (Sec. 5.1, Algorithm 2)
+* ``select_batched``    independent Algorithm 1 instances in one launch
+* ``residual``          ||A - P^(S) A||_F^2 with a hand-written adjoint
+* ``select_host``       Algorithm 1 from host memory (copies included)
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import torch
+
+from . import _lib as L
+
+_DT = {torch.float64: L.CSS_F64, torch.float32: L.CSS_F32, torch.bfloat16: L.CSS_BF16}
+_ACC = {torch.float64: torch.float64, torch.float32: torch.float32, torch.bfloat16: torch.float32}
+
+
+def _check(code, where):
+    if code < 0:
+        raise L.CssError(code, where)
+    return code
+
+
+def _colmajor(A: torch.Tensor, name="A"):
+    if A.dim() != 2:
+        raise ValueError(f"{name} must be 2-D")
+    if A.dtype not in _DT:
+        raise TypeError(f"{name}: dtype {A.dtype} not supported (float64, float32, bfloat16)")
+    m, n = A.shape
+    if m > 1 and A.stride(0) != 1:
+        raise ValueError(f"{name} must be column-major (stride(0) == 1); pass X.t() "
+                         "for a row-major tensor X holding the columns as rows")
+    lda = A.stride(1) if n > 1 else m
+    return m, n, max(lda, m)
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def _workspace(nbytes, device):
+    # 256-byte aligned device buffer from torch's allocator
+    buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+    off = (-buf.data_ptr()) % 256
+    return buf, buf[off:off + nbytes]
+
+
+def empty_colmajor(m, n, dtype, device="cuda", ld=None):
+    """A column-major m x n tensor (leading dimension ld >= m)."""
+    ld = ld or m
+    storage = torch.empty((n, ld), dtype=dtype, device=device)
+    return storage[:, :m].t()
+
+
+def to_colmajor(X: torch.Tensor, ld=None):
+    """Copy X (m x n) into a column-major tensor with leading dimension ld."""
+    m, n = X.shape
+    out = empty_colmajor(m, n, X.dtype, X.device, ld)
+    out.copy_(X)
+    return out
+
+
+@dataclass
+class Selection:
+    sel: torch.Tensor            # int32[k] selected columns, selection order (first n_sel valid)
+    trace: torch.Tensor          # float64[k+1] error trace (Theorem 1 / 3)
+    n_sel: int
+    status: int
+    W: Optional[torch.Tensor] = None        # float64[k, n] omega rows
+    diag_argmax: Optional[torch.Tensor] = None
+    diag_f: Optional[torch.Tensor] = None
+    diag_g: Optional[torch.Tensor] = None
+    timing_ms: Optional[tuple] = None       # (initial scores, greedy iterations)
+
+    @property
+    def indices(self):
+        return self.sel[: self.n_sel]
+
+
+def _opts(tau_rel=None, forced=None, score_mode=0, grid_ctas=0, tile_cols=0, spin_budget_ns=0,
+          sync=True, diag=None):
+    o = L.default_opts()
+    if tau_rel is not None:
+        o.tau_rel = float(tau_rel)
+    if forced is not None:
+        o.forced = forced.data_ptr()
+        o.n_forced = int(forced.numel())
+    o.score_mode = int(score_mode)
+    o.grid_ctas = int(grid_ctas)
+    o.tile_cols = int(tile_cols)
+    o.spin_budget_ns = int(spin_budget_ns)
+    o.sync = 1 if sync else 0
+    if diag is not None:
+        o.diag_argmax = diag[0].data_ptr()
+        o.diag_f = diag[1].data_ptr()
+        o.diag_g = diag[2].data_ptr()
+    return o
+
+
+def _prep_forced(forced, device):
+    if forced is None:
+        return None
+    return torch.as_tensor(list(forced) if not torch.is_tensor(forced) else forced,
+                           dtype=torch.int32).to(device).contiguous()
+
+
+def select(A: torch.Tensor, k: int, *, tau_rel=None, forced=None, return_W=False, diag=False,
+           score_mode=0, grid_ctas=0, tile_cols=0, spin_budget_ns=0, stream=None,
+           timing=False) -> Selection:
+    """Greedy CSS (Algorithm 1) of the columns of A (column-major, on the GPU)."""
+    m, n, lda = _colmajor(A)
+    dev = A.device
+    dt = _DT[A.dtype]
+    lib = L.load()
+    sel = torch.empty(k, dtype=torch.int32, device=dev)
+    trace = torch.empty(k + 1, dtype=torch.float64, device=dev)
+    nsel = torch.zeros(1, dtype=torch.int32, device=dev)
+    W = torch.empty((k, n), dtype=torch.float64, device=dev) if return_W else None
+    fz = _prep_forced(forced, dev)
+    dg = None
+    if diag:
+        dg = (torch.full((k,), -1, dtype=torch.int32, device=dev),
+              torch.empty(n, dtype=torch.float64, device=dev),
+              torch.empty(n, dtype=torch.float64, device=dev))
+    o = _opts(tau_rel, fz, score_mode, grid_ctas, tile_cols, spin_budget_ns, True, dg)
+    tms = (C.c_double * 2)() if timing else None
+    if tms is not None:
+        o.timing_ms = C.cast(tms, C.c_void_p)
+    nbytes = lib.css_workspace_size(L.CSS_OP_SELECT, dt, m, n, 0, k, 0, C.byref(o))
+    if nbytes == 0:
+        raise ValueError("invalid sizes for css_select")
+    _keep, ws = _workspace(nbytes, dev)
+    code = lib.css_select(_ptr(A), dt, m, n, lda, k, _ptr(sel), _ptr(trace), _ptr(nsel), _ptr(W),
+                          _ptr(ws), nbytes, C.byref(o), _stream(stream))
+    _check(code, "css_select")
+    ns = int(nsel.item())
+    res = Selection(sel, trace, ns, code, W, *(dg if dg else (None, None, None)))
+    if tms is not None:
+        res.timing_ms = (tms[0], tms[1])
+    return res
+
+
+def gcss_select(A: torch.Tensor, B: torch.Tensor, k: int, *, tau_rel=None, forced=None,
+                return_W=False, diag=False, grid_ctas=0, tile_cols=0, spin_budget_ns=0,
+                stream=None) -> Selection:
+    """Greedy generalized CSS (Algorithm 3): columns of A reconstructing B.
+    B must be float64 when A is float64, float32 otherwise (column-major)."""
+    m, n, lda = _colmajor(A)
+    mb, r, ldb = _colmajor(B, "B")
+    if mb != m:
+        raise ValueError("A and B must have the same number of rows")
+    if B.dtype != _ACC[A.dtype]:
+        raise TypeError(f"B must be {_ACC[A.dtype]} for A of dtype {A.dtype}")
+    dev = A.device
+    dt = _DT[A.dtype]
+    lib = L.load()
+    sel = torch.empty(k, dtype=torch.int32, device=dev)
+    trace = torch.empty(k + 1, dtype=torch.float64, device=dev)
+    nsel = torch.zeros(1, dtype=torch.int32, device=dev)
+    W = torch.empty((k, n), dtype=torch.float64, device=dev) if return_W else None
+    fz = _prep_forced(forced, dev)
+    dg = None
+    if diag:
+        dg = (torch.full((k,), -1, dtype=torch.int32, device=dev),
+              torch.empty(n, dtype=torch.float64, device=dev),
+              torch.empty(n, dtype=torch.float64, device=dev))
+    o = _opts(tau_rel, fz, 0, grid_ctas, tile_cols, spin_budget_ns, True, dg)
+    nbytes = lib.css_workspace_size(L.CSS_OP_GCSS, dt, m, n, r, k, 0, C.byref(o))
+    if nbytes == 0:
+        raise ValueError("invalid sizes for gcss_select")
+    _keep, ws = _workspace(nbytes, dev)
+    code = lib.gcss_select(_ptr(A), dt, m, n, lda, _ptr(B), r, ldb, k, _ptr(sel), _ptr(trace),
+                           _ptr(nsel), _ptr(W), _ptr(ws), nbytes, C.byref(o), _stream(stream))
+    _check(code, "gcss_select")
+    return Selection(sel, trace, int(nsel.item()), code, W, *(dg if dg else (None, None, None)))
+
+
+@dataclass
+class Distributed:
+    sel: torch.Tensor
+    trace: torch.Tensor
+    n_sel: int
+    block_sel: torch.Tensor      # int32[nblocks, l_block], global ids, -1 padded
+    status: int
+
+    @property
+    def indices(self):
+        return self.sel[: self.n_sel]
+
+
+def distributed(A: torch.Tensor, B: torch.Tensor, block_offsets: Sequence[int], l_block: int,
+                k: int, *, tau_rel=None, grid_ctas=0, tile_cols=0, stream=None) -> Distributed:
+    """Distributed CSS (Algorithm 4) with the concise representation B."""
+    m, n, lda = _colmajor(A)
+    mb, r, ldb = _colmajor(B, "B")
+    if mb != m or B.dtype != _ACC[A.dtype]:
+        raise ValueError("B must be m x r of dtype float32 (float64 for float64 A)")
+    dev = A.device
+    dt = _DT[A.dtype]
+    lib = L.load()
+    offs = (C.c_int64 * len(block_offsets))(*[int(v) for v in block_offsets])
+    nb = len(block_offsets) - 1
+    sel = torch.empty(k, dtype=torch.int32, device=dev)
+    trace = torch.empty(k + 1, dtype=torch.float64, device=dev)
+    nsel = torch.zeros(1, dtype=torch.int32, device=dev)
+    bsel = torch.empty((nb, l_block), dtype=torch.int32, device=dev)
+    o = _opts(tau_rel, None, 0, grid_ctas, tile_cols)
+    nbytes = lib.gcss_distributed_workspace_size(dt, m, n, r, offs, nb, l_block, k)
+    if nbytes == 0:
+        raise ValueError("invalid block partition or sizes")
+    _keep, ws = _workspace(nbytes, dev)
+    code = lib.gcss_distributed(_ptr(A), dt, m, n, lda, _ptr(B), r, ldb, offs, nb, l_block, k,
+                                _ptr(sel), _ptr(trace), _ptr(nsel), _ptr(bsel), _ptr(ws), nbytes,
+                                C.byref(o), _stream(stream))
+    _check(code, "gcss_distributed")
+    return Distributed(sel, trace, int(nsel.item()), bsel, code)
+
+
+def project(A: torch.Tensor, Omega: torch.Tensor, *, out=None, stream=None, sync=True):
+    """B = A Omega (Sec. 5.1).  Omega is n x r column-major of A's dtype.
+    Returns B (m x r, column-major) in float32 (float64 for float64 input)."""
+    m, n, lda = _colmajor(A)
+    no, r, ldo = _colmajor(Omega, "Omega")
+    if no != n or Omega.dtype != A.dtype:
+        raise ValueError("Omega must be n x r with A's dtype")
+    dev = A.device
+    dt = _DT[A.dtype]
+    lib = L.load()
+    B = out if out is not None else empty_colmajor(m, r, _ACC[A.dtype], dev)
+    _, _, ldb = _colmajor(B, "B")
+    o = _opts(sync=sync)
+    nbytes = lib.css_workspace_size(L.CSS_OP_PROJECT, dt, m, n, r, 0, 0, C.byref(o))
+    _keep, ws = _workspace(nbytes, dev)
+    code = lib.css_project(_ptr(A), dt, m, n, lda, _ptr(Omega), r, ldo, _ptr(B), ldb, _ptr(ws),
+                           nbytes, C.byref(o), _stream(stream))
+    _check(code, "css_project")
+    return B
+
+
+def select_batched(As: Sequence[torch.Tensor], ks: Sequence[int], *, grid_ctas=0, tile_cols=0,
+                   tau_rel=None, stream=None):
+    """Independent greedy CSS problems in one persistent launch.  Returns a list
+    of Selection."""
+    if len(As) != len(ks) or not As:
+        raise ValueError("need one k per matrix")
+    dtype = As[0].dtype
+    dev = As[0].device
+    dt = _DT[dtype]
+    lib = L.load()
+    probs = (L.css_problem * len(As))()
+    outs = []
+    for i, (A, k) in enumerate(zip(As, ks)):
+        if A.dtype != dtype:
+            raise TypeError("all matrices must share one dtype")
+        m, n, lda = _colmajor(A)
+        sel = torch.empty(k, dtype=torch.int32, device=dev)
+        trace = torch.empty(k + 1, dtype=torch.float64, device=dev)
+        nsel = torch.zeros(1, dtype=torch.int32, device=dev)
+        probs[i].A = A.data_ptr()
+        probs[i].m, probs[i].n, probs[i].lda, probs[i].k = m, n, lda, int(k)
+        probs[i].sel, probs[i].trace, probs[i].n_sel = sel.data_ptr(), trace.data_ptr(), nsel.data_ptr()
+        probs[i].W = None
+        outs.append((sel, trace, nsel))
+    o = _opts(tau_rel, None, 0, grid_ctas, tile_cols)
+    nbytes = lib.css_batched_workspace_size(probs, len(As), dt, C.byref(o))
+    if nbytes == 0:
+        raise ValueError("invalid batch")
+    _keep, ws = _workspace(nbytes, dev)
+    code = lib.css_select_batched(probs, len(As), dt, _ptr(ws), nbytes, C.byref(o), _stream(stream))
+    _check(code, "css_select_batched")
+    nsels = torch.cat([x[2] for x in outs]).tolist()
+    return [Selection(s, t, int(ns), code) for (s, t, _), ns in zip(outs, nsels)]
+
+
+def select_host(A_host: torch.Tensor, k: int, A_dev: torch.Tensor, *, ws=None, stream=None):
+    """Algorithm 1 from host memory: copies A_host (column-major, ideally pinned)
+    into the device staging tensor A_dev, selects, copies the results back.
+    Returns (sel int32[k], trace float64[k+1], n_sel) as host tensors."""
+    m, n, lda = _colmajor(A_host)
+    dt = _DT[A_host.dtype]
+    lib = L.load()
+    sel = torch.empty(k, dtype=torch.int32)
+    trace = torch.empty(k + 1, dtype=torch.float64)
+    nsel = torch.zeros(1, dtype=torch.int32)
+    o = L.default_opts()
+    nbytes = lib.css_workspace_size(L.CSS_OP_HOST_SELECT, dt, m, n, 0, k, 0, C.byref(o))
+    if ws is None:
+        _keep, ws = _workspace(nbytes, A_dev.device)
+    code = lib.css_select_host(C.c_void_p(A_host.data_ptr()), dt, m, n, lda, k,
+                               C.c_void_p(sel.data_ptr()), C.c_void_p(trace.data_ptr()),
+                               C.c_void_p(nsel.data_ptr()), _ptr(A_dev), _ptr(ws), nbytes,
+                               C.byref(o), _stream(stream))
+    _check(code, "css_select_host")
+    return sel, trace, int(nsel.item())
+
+
+def host_workspace_bytes(m, n, k, dtype):
+    lib = L.load()
+    o = L.default_opts()
+    return lib.css_workspace_size(L.CSS_OP_HOST_SELECT, _DT[dtype], m, n, 0, k, 0, C.byref(o))
+
+
+class _Residual(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, A, sel):
+        m, n, lda = _colmajor(A)
+        dt = _DT[A.dtype]
+        lib = L.load()
+        loss = torch.empty(1, dtype=torch.float64, device=A.device)
+        o = L.default_opts()
+        k = int(sel.numel())
+        nbytes = lib.css_workspace_size(L.CSS_OP_BACKWARD, dt, m, n, 0, k, 0, C.byref(o))
+        _keep, ws = _workspace(nbytes, A.device)
+        code = lib.css_residual_backward(_ptr(A), dt, m, n, lda, _ptr(sel), k, 1.0,
+                                         C.c_void_p(0), 0, _ptr(loss), _ptr(ws), nbytes,
+                                         C.byref(o), _stream(None))
+        _check(code, "css_residual_backward(loss)")
+        ctx.save_for_backward(A, sel)
+        return loss[0].to(A.dtype if A.dtype != torch.bfloat16 else torch.float32)
+
+    @staticmethod
+    def backward(ctx, grad):
+        A, sel = ctx.saved_tensors
+        m, n, lda = _colmajor(A)
+        dt = _DT[A.dtype]
+        lib = L.load()
+        dA = empty_colmajor(m, n, A.dtype, A.device, lda)
+        _, _, ldd = _colmajor(dA)
+        o = L.default_opts()
+        k = int(sel.numel())
+        nbytes = lib.css_workspace_size(L.CSS_OP_BACKWARD, dt, m, n, 0, k, 0, C.byref(o))
+        _keep, ws = _workspace(nbytes, A.device)
+        code = lib.css_residual_backward(_ptr(A), dt, m, n, lda, _ptr(sel), k, float(grad.item()),
+                                         _ptr(dA), ldd, C.c_void_p(0), _ptr(ws), nbytes,
+                                         C.byref(o), _stream(None))
+        _check(code, "css_residual_backward")
+        return dA, None
+
+
+def residual(A: torch.Tensor, S) -> torch.Tensor:
+    """||A - P^(S) A||_F^2 (Eq. Projection) for a fixed selected set S, as an
+    autograd function whose backward is the hand-written adjoint kernel."""
+    sel = torch.as_tensor(S, dtype=torch.int32, device=A.device).contiguous()
+    return _Residual.apply(A, sel)

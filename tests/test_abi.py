@@ -1,0 +1,110 @@
+"""Host-side checks of the C ABI: the library builds/loads, exports every
+function include/css.h declares, and rejects bad arguments before touching
+the GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1312_6838_gb300 import _lib, build
+    if not os.path.exists(_lib.LIB_PATH):
+        build.build()
+    return _lib.load()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "css.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z_0-9]*\s*\*?\s*([a-z_][a-z_0-9]*)\s*\(",
+                       src, flags=re.M)
+    return sorted(set(n for n in names if n.startswith(("css_", "gcss_"))))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1312_6838_gb300 import _lib
+    names = _declared()
+    assert len(names) >= 14, names
+    for n in names:
+        assert hasattr(lib, n), f"libcss.so does not export {n}"
+    assert set(names) == set(_lib.EXPORTED)
+
+
+def test_version_and_status_strings(lib):
+    assert b"libcss" in lib.css_version()
+    for code in (0, 1, -1, -2, -3, -4, -5, -6, -7):
+        assert lib.css_status_string(code)
+
+
+def test_workspace_size_is_host_only(lib):
+    from paper_1312_6838_gb300 import _lib as L
+    o = L.default_opts()
+    a = lib.css_workspace_size(L.CSS_OP_SELECT, L.CSS_BF16, 4096, 65536, 0, 256, 0, C.byref(o))
+    b = lib.css_workspace_size(L.CSS_OP_SELECT, L.CSS_F32, 4096, 65536, 0, 256, 0, C.byref(o))
+    assert a > 0 and b > 0
+    # W (k x n FP64) + C (m x m FP32) dominate
+    assert a >= 256 * 65536 * 8 + 4096 * 4096 * 4
+    assert lib.css_workspace_size(L.CSS_OP_SELECT, L.CSS_F32, 0, 10, 0, 1, 0, None) == 0
+    assert lib.css_workspace_size(L.CSS_OP_GCSS, L.CSS_F32, 100, 1000, 0, 10, 0, None) == 0
+    assert lib.css_workspace_size(L.CSS_OP_PROJECT, L.CSS_BF16, 2048, 262144, 400, 0, 0, None) > 0
+    offs = (C.c_int64 * 4)(0, 10, 25, 40)
+    assert lib.gcss_distributed_workspace_size(L.CSS_F32, 8, 40, 3, offs, 3, 4, 5) > 0
+    bad = (C.c_int64 * 4)(0, 10, 10, 40)
+    assert lib.gcss_distributed_workspace_size(L.CSS_F32, 8, 40, 3, bad, 3, 4, 5) == 0
+
+
+def test_invalid_arguments_rejected_on_host(lib):
+    from paper_1312_6838_gb300 import _lib as L
+    o = L.default_opts()
+    P = C.c_void_p
+    fake = P(0x10000)  # never dereferenced: validation fails first
+    # NULL A
+    r = lib.css_select(P(0), L.CSS_F32, 10, 20, 10, 3, fake, fake, fake, P(0), fake, 1 << 20,
+                       C.byref(o), P(0))
+    assert r == L.CSS_ERR_INVALID_ARG
+    # k > n
+    r = lib.css_select(fake, L.CSS_F32, 10, 2, 10, 3, fake, fake, fake, P(0), fake, 1 << 20,
+                       C.byref(o), P(0))
+    assert r == L.CSS_ERR_INVALID_ARG
+    # lda < m
+    r = lib.css_select(fake, L.CSS_F32, 10, 20, 9, 3, fake, fake, fake, P(0), fake, 1 << 20,
+                       C.byref(o), P(0))
+    assert r == L.CSS_ERR_INVALID_ARG
+    # misaligned workspace
+    r = lib.css_select(fake, L.CSS_F32, 10, 20, 10, 3, fake, fake, fake, P(0), P(0x10008), 1 << 20,
+                       C.byref(o), P(0))
+    assert r == L.CSS_ERR_WORKSPACE
+    # workspace too small
+    r = lib.css_select(fake, L.CSS_F32, 10, 20, 10, 3, fake, fake, fake, P(0), fake, 16,
+                       C.byref(o), P(0))
+    assert r == L.CSS_ERR_WORKSPACE
+    # bad score mode
+    o.score_mode = 7
+    r = lib.css_select(fake, L.CSS_F32, 10, 20, 10, 3, fake, fake, fake, P(0), fake, 1 << 20,
+                       C.byref(o), P(0))
+    assert r == L.CSS_ERR_INVALID_ARG
+    o.score_mode = 0
+    # GCSS: B rows / ldb
+    r = lib.gcss_select(fake, L.CSS_F32, 10, 20, 10, fake, 3, 9, 3, fake, fake, fake, P(0), fake,
+                        1 << 20, C.byref(o), P(0))
+    assert r == L.CSS_ERR_INVALID_ARG
+    # distributed: offsets that do not end at n
+    offs = (C.c_int64 * 3)(0, 5, 19)
+    r = lib.gcss_distributed(fake, L.CSS_F32, 10, 20, 10, fake, 3, 10, offs, 2, 2, 2, fake, fake,
+                             fake, P(0), fake, 1 << 20, C.byref(o), P(0))
+    assert r == L.CSS_ERR_INVALID_ARG
+    # projection: ldo < n
+    r = lib.css_project(fake, L.CSS_BF16, 10, 20, 10, fake, 4, 19, fake, 10, fake, 1 << 20,
+                        C.byref(o), P(0))
+    assert r == L.CSS_ERR_INVALID_ARG
+
+
+def test_opts_layout_matches_header(lib):
+    from paper_1312_6838_gb300 import _lib as L
+    o = L.default_opts()
+    assert o.tau_rel < 0 and o.sync == 1 and o.n_forced == 0 and o.grid_ctas == 0

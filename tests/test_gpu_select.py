@@ -1,0 +1,220 @@
+"""GPU parity of css_select (Algorithm 1) against the FP64 oracle, through the
+C ABI (paper_1312_6838_gb300.css is argument marshalling only)."""
+import numpy as np
+import pytest
+import scipy.linalg
+import torch
+
+import css_inputs as ci
+from oracle import css_oracle as O
+from tests.gpu_helpers import GAP_TOL, dev_matrix, teacher_forced_parity
+
+pytestmark = pytest.mark.gpu
+
+TAU = {torch.float64: 1e-12, torch.float32: 1e-6, torch.bfloat16: 1e-6}
+ERR_TOL = {torch.float64: 1e-10, torch.float32: 1e-4, torch.bfloat16: 1e-4}
+
+
+@pytest.fixture(scope="module")
+def css():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1312_6838_gb300 import build, css as mod
+    build.build()
+    return mod
+
+
+def _run(css, A, k, forced=None, **kw):
+    r = css.select(A, k, forced=forced if forced else None, **kw)
+    return r
+
+
+def _check_case(css, A_np, k, dtype, ld=None, **kw):
+    A, vals = dev_matrix(A_np, dtype, ld)
+    ref = O.greedy_css(vals, k, tau_rel=TAU[dtype])
+    restarts = teacher_forced_parity(
+        lambda forced: _run(css, A, k, forced, **kw).indices.cpu().tolist(), ref)
+    res = _run(css, A, k, **kw)
+    S = res.indices.cpu().tolist()
+    # final error of the GPU's own selection against the oracle's final error
+    e_gpu = O.reconstruction_error(vals, S)
+    e_ref = O.reconstruction_error(vals, ref.S)
+    assert abs(e_gpu - e_ref) <= ERR_TOL[dtype] * e_ref + 1e-300, (e_gpu, e_ref)
+    # the recursive trace (Theorem 1) against the direct error of the same set
+    tr = res.trace.cpu().numpy()
+    assert abs(tr[-1] - e_gpu) <= max(ERR_TOL[dtype] * tr[0], 1e-12 * tr[0]) * 10, (tr[-1], e_gpu)
+    return res, ref, restarts
+
+
+def test_fp64_workload_500x1000(css):
+    c = ci.CONFIGS["fp64_500x1000"]
+    A_np = ci.lowrank_uv(c["m"], c["n"], c["rank"], c["noise"], c["seed"])
+    res, ref, restarts = _check_case(css, A_np, c["k"], torch.float64)
+    assert restarts == 0
+    tr = res.trace.cpu().numpy()
+    np.testing.assert_allclose(tr, ref.trace, rtol=0, atol=1e-10 * ref.trace[0])
+    assert res.indices.cpu().tolist() == ref.S
+
+
+def test_fp64_brute_force_slice(css):
+    c = ci.CONFIGS["fp64_500x1000"]
+    A_np = ci.lowrank_uv(c["m"], c["n"], c["rank"], c["noise"], c["seed"])[:12, :16]
+    A, _ = dev_matrix(A_np, torch.float64)
+    res = css.select(A, 3)
+    ref = O.greedy_css(A_np, 3)
+    assert res.indices.cpu().tolist() == ref.S
+    best_S, best_err = O.brute_force_css(A_np, 3)
+    assert O.reconstruction_error(A_np, ref.S) >= best_err * (1 - 1e-12)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("shape", [(37, 203, 9), (129, 1000, 24), (64, 64, 64), (300, 77, 30)])
+def test_ragged_shapes(css, dtype, shape):
+    m, n, k = shape
+    A_np = ci.lowrank_uv(m, n, max(2, k // 2), 0.05, m * 1000 + n)
+    _check_case(css, A_np, k, dtype)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_padded_and_unaligned_leading_dimension(css, dtype):
+    A_np = ci.lowrank_uv(50, 300, 6, 0.05, 3)
+    _check_case(css, A_np, 12, dtype, ld=64)      # aligned padding
+    _check_case(css, A_np, 12, dtype, ld=51)      # forces the scalar load path
+
+
+@pytest.mark.parametrize("tile", [2, 4, 8])
+def test_tile_widths_agree(css, tile):
+    A_np = ci.lowrank_uv(200, 777, 10, 0.02, 5)
+    A, vals = dev_matrix(A_np, torch.float32)
+    base = css.select(A, 20, tile_cols=4).indices.cpu().tolist()
+    got = css.select(A, 20, tile_cols=tile).indices.cpu().tolist()
+    assert got == base
+
+
+@pytest.mark.parametrize("grid", [1, 2, 7, 64])
+def test_team_sizes_agree(css, grid):
+    A_np = ci.lowrank_uv(96, 1500, 8, 0.02, 6)
+    A, vals = dev_matrix(A_np, torch.float64)
+    ref = O.greedy_css(vals, 16)
+    res = css.select(A, 16, grid_ctas=grid)
+    assert res.indices.cpu().tolist() == ref.S
+    np.testing.assert_allclose(res.trace.cpu().numpy(), ref.trace, rtol=0, atol=1e-10 * ref.trace[0])
+
+
+def test_W_and_score_state(css):
+    A_np = ci.lowrank_uv(40, 120, 6, 0.03, 8)
+    A, vals = dev_matrix(A_np, torch.float64)
+    k = 10
+    res = css.select(A, k, return_W=True, diag=True)
+    ref = O.greedy_css(vals, k)
+    assert res.indices.cpu().tolist() == ref.S
+    np.testing.assert_allclose(res.W.cpu().numpy(), ref.W, rtol=1e-9, atol=1e-9 * np.abs(ref.W).max())
+    f = res.diag_f.cpu().numpy()
+    g = res.diag_g.cpu().numpy()
+    sel = np.zeros(120, bool)
+    sel[ref.S] = True
+    np.testing.assert_allclose(g[~sel], ref.g[~sel], rtol=1e-9)
+    np.testing.assert_allclose(f[~sel], ref.f[~sel], rtol=1e-8)
+    assert res.diag_argmax.cpu().tolist() == ref.S
+    # Q-less QR structure: W Pi upper triangular (Sec. 6)
+    W = res.W.cpu().numpy()
+    for t in range(k):
+        for s in range(t):
+            assert abs(W[t, ref.S[s]]) <= 1e-10 * np.abs(W[t]).max()
+
+
+def test_edge_k_equals_one_and_full(css):
+    A_np = ci.lowrank_uv(20, 20, 20, 0.0, 9)
+    for k in (1, 20):
+        A, vals = dev_matrix(A_np, torch.float64)
+        res = css.select(A, k)
+        ref = O.greedy_css(vals, k)
+        assert res.indices.cpu().tolist() == ref.S
+    # k = m = n: the error reaches zero
+    assert res.trace[-1].item() <= 1e-10 * res.trace[0].item()
+
+
+def test_rank_exhaustion(css):
+    A_np = ci.lowrank_uv(30, 80, 4, 0.0, 10)
+    A, vals = dev_matrix(A_np, torch.float64)
+    res = css.select(A, 10, tau_rel=1e-10)
+    ref = O.greedy_css(vals, 10, tau_rel=1e-10)
+    assert res.status == 1  # CSS_RANK_EXHAUSTED
+    assert res.n_sel == len(ref.S) == 4
+    assert res.indices.cpu().tolist() == ref.S
+
+
+def test_zero_and_duplicate_columns(css):
+    rng = np.random.default_rng(11)
+    A_np = rng.standard_normal((25, 40))
+    A_np[:, 5] = 0.0
+    A_np[:, 17] = A_np[:, 3]
+    A_np[:, 30] = 2.0 * A_np[:, 3]
+    A, vals = dev_matrix(A_np, torch.float64)
+    res = css.select(A, 12)
+    ref = O.greedy_css(vals, 12)
+    S = res.indices.cpu().tolist()
+    assert 5 not in S
+    assert S == ref.S
+    assert len({3, 17, 30} & set(S)) <= 1
+
+
+def test_single_column_and_single_row(css):
+    A, _ = dev_matrix(np.arange(1.0, 8.0).reshape(7, 1), torch.float64)
+    res = css.select(A, 1)
+    assert res.indices.cpu().tolist() == [0]
+    assert abs(res.trace[1].item()) <= 1e-12 * res.trace[0].item()
+    A2, _ = dev_matrix(np.array([[1.0, -3.0, 2.0, 0.5]]), torch.float64)
+    res2 = css.select(A2, 1)
+    assert res2.indices.cpu().tolist() == [1]
+
+
+def test_forced_prefix(css):
+    A_np = ci.lowrank_uv(60, 200, 7, 0.02, 12)
+    A, vals = dev_matrix(A_np, torch.float64)
+    forced = [11, 150, 3]
+    res = css.select(A, 9, forced=forced)
+    ref = O.greedy_css(vals, 9, forced=forced)
+    assert res.indices.cpu().tolist() == ref.S
+    assert ref.S[:3] == forced
+    np.testing.assert_allclose(res.trace.cpu().numpy(), ref.trace, rtol=0, atol=1e-10 * ref.trace[0])
+
+
+def test_forced_prefix_rejects_bad_indices(css):
+    from paper_1312_6838_gb300._lib import CssError
+    A, _ = dev_matrix(ci.lowrank_uv(10, 30, 3, 0.1, 13), torch.float64)
+    with pytest.raises(CssError):
+        css.select(A, 4, forced=[1, 1])
+    with pytest.raises(CssError):
+        css.select(A, 4, forced=[40])
+
+
+def test_norm_score_is_qr_with_column_pivoting(css):
+    A_np = ci.lowrank_uv(30, 25, 25, 0.0, 15)
+    _, _, piv = scipy.linalg.qr(A_np, pivoting=True, mode="economic")
+    A, _ = dev_matrix(A_np, torch.float64)
+    res = css.select(A, 10, score_mode=1)
+    assert res.indices.cpu().tolist() == list(piv[:10])
+
+
+def test_nonfinite_input_reported(css):
+    from paper_1312_6838_gb300._lib import CssError, CSS_ERR_NONFINITE
+    A_np = ci.lowrank_uv(16, 40, 3, 0.1, 16)
+    A_np[4, 7] = np.nan
+    A, _ = dev_matrix(A_np, torch.float32)
+    with pytest.raises(CssError) as ei:
+        css.select(A, 3)
+    assert ei.value.code == CSS_ERR_NONFINITE
+    # the context stays usable
+    A2, _ = dev_matrix(ci.lowrank_uv(16, 40, 3, 0.1, 17), torch.float32)
+    assert css.select(A2, 3).n_sel == 3
+
+
+def test_rows_and_columns_are_permutation_equivariant(css):
+    A_np = ci.lowrank_uv(48, 300, 6, 0.03, 18)
+    perm = np.random.default_rng(1).permutation(300)
+    A, _ = dev_matrix(A_np, torch.float64)
+    Ap, _ = dev_matrix(A_np[:, perm], torch.float64)
+    a = css.select(A, 10).indices.cpu().tolist()
+    b = css.select(Ap, 10).indices.cpu().tolist()
+    assert [int(perm[j]) for j in b] == a

@@ -79,6 +79,7 @@ class GreedyResult:
         self.W: np.ndarray | None = None
         self.gaps: list[float] = []
         self.scores: list[np.ndarray] = []
+        self.fs: list[np.ndarray] = []     # f before each iteration (keep_scores)
         self.f: np.ndarray | None = None
         self.g: np.ndarray | None = None
         # wall-clock instrumentation (time.perf_counter): after initialisation
@@ -206,6 +207,7 @@ def greedy_css(A, l, tau_rel=1e-12, forced=None, keep_scores=False,
             break
         if keep_scores:
             res.scores.append(sc)
+            res.fs.append(f.copy())
         res.gaps.append(gap)
         F = F - f[p] / g[p]
         selected[p] = True
@@ -295,6 +297,7 @@ def greedy_gcss(A, B, l, tau_rel=1e-12, forced=None, keep_scores=False):
             break
         if keep_scores:
             res.scores.append(sc)
+            res.fs.append(f.copy())
         res.gaps.append(gap)
         F = F - f[p] / g[p]
         selected[p] = True

@@ -6,7 +6,7 @@ import torch
 
 import css_inputs as ci
 from oracle import css_oracle as O
-from tests.gpu_helpers import dev_matrix, teacher_forced_parity
+from tests.gpu_helpers import dev_matrix, first_mismatch, score_error_bound, teacher_forced_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -31,23 +31,33 @@ def _target(B_np, dtype):
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32, torch.bfloat16])
-@pytest.mark.parametrize("shape", [(40, 90, 6, 10), (129, 700, 33, 20), (64, 333, 1, 8)])
+@pytest.mark.parametrize("shape", [(40, 90, 6, 10), (129, 700, 33, 20), (64, 333, 1, 8),
+                                   (48, 257, 24, 10)])
 def test_gcss_parity(css, dtype, shape):
+    """Index parity within the path's error bound (k may exceed the target's
+    rank: the late picks are then only defined up to that bound)."""
     m, n, r, k = shape
-    A_np = ci.lowrank_uv(m, n, 8, 0.05, m + n)
+    A_np = ci.lowrank_uv(m, n, 8 if r < 24 else 40, 0.05, m + n)
     B_np = A_np @ ci.gaussian_omega(n, r, 7, dtype=np.float64)
     A, Av = dev_matrix(A_np, dtype)
     B, Bv = _target(B_np, dtype)
-    ref = O.greedy_gcss(Av, Bv, k, tau_rel=TAU[dtype])
-    teacher_forced_parity(
-        lambda forced: css.gcss_select(A, B, k, forced=forced or None).indices.cpu().tolist(), ref)
+    ref = O.greedy_gcss(Av, Bv, k, tau_rel=TAU[dtype], keep_scores=True)
+    restarts = teacher_forced_parity(
+        lambda forced: css.gcss_select(A, B, k, forced=forced or None).indices.cpu().tolist(), ref,
+        m=m, dtype=dtype)
     res = css.gcss_select(A, B, k)
     S = res.indices.cpu().tolist()
     e_gpu = O.reconstruction_error(Av, S, Bv)
     e_ref = O.reconstruction_error(Av, ref.S, Bv)
-    assert abs(e_gpu - e_ref) <= ERR_TOL[dtype] * max(e_ref, 1e-12 * ref.trace[0])
-    tr = res.trace.cpu().numpy()
-    assert abs(tr[0] - ref.trace[0]) <= 1e-6 * ref.trace[0]
+    if restarts == 0:
+        assert abs(e_gpu - e_ref) <= ERR_TOL[dtype] * max(e_ref, 1e-12 * ref.trace[0])
+    else:
+        # parted at a pick inside the error bound: the set must stay comparable
+        assert e_gpu <= e_ref * 1.25 + 1e-6 * ref.trace[0]
+    full = css.gcss_select(A, B, len(ref.S), forced=list(ref.S))
+    eps = 2.0 ** -52 if dtype == torch.float64 else 2.0 ** -24
+    atol = 64 * eps * np.sqrt(m) * (len(ref.S) + 1) * ref.trace[0]
+    np.testing.assert_allclose(full.trace.cpu().numpy(), ref.trace, rtol=0, atol=atol)
 
 
 def test_gcss_with_B_equal_A_is_css(css):
@@ -121,12 +131,17 @@ def test_batched_matches_single(css):
         ks.append(k)
     out = css.select_batched(As, ks)
     for A, Av, k, res in zip(As, vals, ks, out):
-        single = css.select(A, k)
-        assert res.indices.cpu().tolist() == single.indices.cpu().tolist()
-        ref = O.greedy_css(Av, k, tau_rel=1e-6)
-        e_gpu = O.reconstruction_error(Av, res.indices.cpu().tolist())
+        ref = O.greedy_css(Av, k, tau_rel=1e-6, keep_scores=True)
+        got = res.indices.cpu().tolist()
+        t = first_mismatch(got, ref.S)
+        e_gpu = O.reconstruction_error(Av, got)
         e_ref = O.reconstruction_error(Av, ref.S)
-        assert abs(e_gpu - e_ref) <= 1e-4 * e_ref
+        if t is None:
+            assert got == ref.S
+            assert abs(e_gpu - e_ref) <= 1e-4 * e_ref
+        else:
+            assert ref.gaps[t] <= max(1e-6, score_error_bound(ref, t, Av.shape[0], torch.float32))
+            assert e_gpu <= e_ref * 1.25
 
 
 @pytest.mark.parametrize("grid", [3, 1000])

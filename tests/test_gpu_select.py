@@ -31,18 +31,28 @@ def _run(css, A, k, forced=None, **kw):
 
 def _check_case(css, A_np, k, dtype, ld=None, **kw):
     A, vals = dev_matrix(A_np, dtype, ld)
-    ref = O.greedy_css(vals, k, tau_rel=TAU[dtype])
+    ref = O.greedy_css(vals, k, tau_rel=TAU[dtype], keep_scores=True)
     restarts = teacher_forced_parity(
-        lambda forced: _run(css, A, k, forced, **kw).indices.cpu().tolist(), ref)
+        lambda forced: _run(css, A, k, forced, **kw).indices.cpu().tolist(), ref,
+        m=vals.shape[0], dtype=dtype)
     res = _run(css, A, k, **kw)
     S = res.indices.cpu().tolist()
-    # final error of the GPU's own selection against the oracle's final error
+    # final error of the GPU's own selection against the oracle's final error;
+    # when the selections legitimately part (restarts > 0) the device's set
+    # must still be as good to 1 percent
     e_gpu = O.reconstruction_error(vals, S)
     e_ref = O.reconstruction_error(vals, ref.S)
-    assert abs(e_gpu - e_ref) <= ERR_TOL[dtype] * e_ref + 1e-300, (e_gpu, e_ref)
-    # the recursive trace (Theorem 1) against the direct error of the same set
-    tr = res.trace.cpu().numpy()
-    assert abs(tr[-1] - e_gpu) <= max(ERR_TOL[dtype] * tr[0], 1e-12 * tr[0]) * 10, (tr[-1], e_gpu)
+    if restarts == 0:
+        assert abs(e_gpu - e_ref) <= ERR_TOL[dtype] * e_ref + 1e-300, (e_gpu, e_ref)
+    else:
+        assert e_gpu <= e_ref * 1.01, (e_gpu, e_ref)
+    # Theorem 1's recursive trace on the oracle's own path (teacher-forced)
+    # against the oracle's trace: absolute error of the device recursion
+    full = _run(css, A, len(ref.S), list(ref.S), **kw)
+    tr = full.trace.cpu().numpy()
+    eps = 2.0 ** -52 if dtype == torch.float64 else 2.0 ** -24
+    atol = 64 * eps * np.sqrt(vals.shape[0]) * (len(ref.S) + 1) * ref.trace[0]
+    np.testing.assert_allclose(tr, ref.trace, rtol=0, atol=atol)
     return res, ref, restarts
 
 
@@ -70,14 +80,35 @@ def test_fp64_brute_force_slice(css):
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32, torch.bfloat16])
 @pytest.mark.parametrize("shape", [(37, 203, 9), (129, 1000, 24), (64, 64, 64), (300, 77, 30)])
 def test_ragged_shapes(css, dtype, shape):
+    """Ragged sizes.  The signal rank is 2k, so every pick is made while the
+    scores are far above the FP32 accumulation floor."""
     m, n, k = shape
-    A_np = ci.lowrank_uv(m, n, max(2, k // 2), 0.05, m * 1000 + n)
+    A_np = ci.lowrank_uv(m, n, min(2 * k, m, n), 0.05, m * 1000 + n)
     _check_case(css, A_np, k, dtype)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32, torch.bfloat16])
+def test_beyond_numerical_rank(css, dtype):
+    """k larger than the signal rank: the late scores are differences of O(f0)
+    quantities, so the mixed path's picks are only defined up to its error
+    bound (FP64 resolves them).  Index parity within the bound, the trace on
+    the oracle's path, and the error of the mixed path's own set within 25%
+    of the oracle's (it picks among noise-level candidates)."""
+    A_np = ci.lowrank_uv(60, 400, 5, 0.05, 77)
+    A, vals = dev_matrix(A_np, dtype)
+    k = 14
+    ref = O.greedy_css(vals, k, tau_rel=TAU[dtype], keep_scores=True)
+    teacher_forced_parity(lambda forced: _run(css, A, k, forced).indices.cpu().tolist(), ref,
+                          m=60, dtype=dtype)
+    S = _run(css, A, k).indices.cpu().tolist()
+    e_gpu = O.reconstruction_error(vals, S)
+    e_ref = O.reconstruction_error(vals, ref.S)
+    assert e_gpu <= e_ref * (1.0 + 1e-9 if dtype == torch.float64 else 1.25)
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
 def test_padded_and_unaligned_leading_dimension(css, dtype):
-    A_np = ci.lowrank_uv(50, 300, 6, 0.05, 3)
+    A_np = ci.lowrank_uv(50, 300, 24, 0.05, 3)
     _check_case(css, A_np, 12, dtype, ld=64)      # aligned padding
     _check_case(css, A_np, 12, dtype, ld=51)      # forces the scalar load path
 
@@ -113,8 +144,11 @@ def test_W_and_score_state(css):
     g = res.diag_g.cpu().numpy()
     sel = np.zeros(120, bool)
     sel[ref.S] = True
-    np.testing.assert_allclose(g[~sel], ref.g[~sel], rtol=1e-9)
-    np.testing.assert_allclose(f[~sel], ref.f[~sel], rtol=1e-8)
+    # f and g are differences of O(f0) and O(g0) terms: compare on that scale
+    f0 = np.einsum("ij,ij->j", vals, (vals @ vals.T) @ vals)
+    g0 = np.sum(vals * vals, axis=0)
+    np.testing.assert_allclose(g[~sel], ref.g[~sel], rtol=0, atol=1e-13 * g0.max())
+    np.testing.assert_allclose(f[~sel], ref.f[~sel], rtol=0, atol=1e-13 * f0.max())
     assert res.diag_argmax.cpu().tolist() == ref.S
     # Q-less QR structure: W Pi upper triangular (Sec. 6)
     W = res.W.cpu().numpy()
@@ -138,10 +172,15 @@ def test_rank_exhaustion(css):
     A_np = ci.lowrank_uv(30, 80, 4, 0.0, 10)
     A, vals = dev_matrix(A_np, torch.float64)
     res = css.select(A, 10, tau_rel=1e-10)
-    ref = O.greedy_css(vals, 10, tau_rel=1e-10)
+    ref = O.greedy_css(vals, 10, tau_rel=1e-10, keep_scores=True)
     assert res.status == 1  # CSS_RANK_EXHAUSTED
     assert res.n_sel == len(ref.S) == 4
-    assert res.indices.cpu().tolist() == ref.S
+    # the last pick is an exact tie (the residual has rank one), so any column
+    # is correct there; the prefix before it is unique
+    teacher_forced_parity(
+        lambda forced: css.select(A, 10, tau_rel=1e-10, forced=forced or None).indices.cpu().tolist(),
+        ref, m=30, dtype=torch.float64)
+    assert O.reconstruction_error(vals, res.indices.cpu().tolist()) <= 1e-12 * ref.trace[0]
 
 
 def test_zero_and_duplicate_columns(css):
@@ -164,9 +203,11 @@ def test_single_column_and_single_row(css):
     res = css.select(A, 1)
     assert res.indices.cpu().tolist() == [0]
     assert abs(res.trace[1].item()) <= 1e-12 * res.trace[0].item()
+    # one row: every column scores the same (sum of squares of the row), so
+    # the tie goes to the lowest index
     A2, _ = dev_matrix(np.array([[1.0, -3.0, 2.0, 0.5]]), torch.float64)
     res2 = css.select(A2, 1)
-    assert res2.indices.cpu().tolist() == [1]
+    assert res2.indices.cpu().tolist() == O.greedy_css(np.array([[1.0, -3.0, 2.0, 0.5]]), 1).S == [0]
 
 
 def test_forced_prefix(css):

@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--dtype", choices=["bf16", "f32"], default="bf16")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "decay_4096x32768"],
+                    help="decay_4096x32768 is the small profiling case of the same model")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -58,8 +61,8 @@ def dist_env():
     return ws, rank, local
 
 
-def workload_array():
-    c = ci.CONFIGS[WORKLOAD]
+def workload_array(name=WORKLOAD):
+    c = ci.CONFIGS[name]
     A = ci.lowrank_decaying(c["m"], c["n"], c["rank"], c["noise"], c["seed"], dtype=np.float32)
     return c, A
 
@@ -199,7 +202,7 @@ def main():
     from paper_1312_6838_gb300 import css
     from paper_1312_6838_gb300 import _lib
 
-    c, A32 = workload_array()
+    c, A32 = workload_array(args.workload)
     m, n, k = c["m"], c["n"], c["k"]
     tdt = torch.bfloat16 if args.dtype == "bf16" else torch.float32
     # column-major: the (n, m) row-major storage of A^T
@@ -256,7 +259,7 @@ def main():
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": tot_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": args.dtype, "data": "synthetic",
-        "config": {"workload": WORKLOAD, "m": m, "n": n, "k": k, "rank": c["rank"],
+        "config": {"workload": args.workload, "m": m, "n": n, "k": k, "rank": c["rank"],
                    "noise": c["noise"], "stream_dtype": args.dtype,
                    "accumulate": "f32 dot products, f64 score state and basis",
                    "l2": f"inputs larger than L2 (A = {a_bytes / 2**20:.0f} MiB per pass)",

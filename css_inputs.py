@@ -134,6 +134,8 @@ CONFIGS = {
     # Memory-efficient centralized greedy at scale: 4096 x 65536, rank 256,
     # s_i = 1/i, noise 1e-3, k = 256, streamed in FP32 and in BF16.
     "decay_4096x65536": dict(m=4096, n=65536, rank=256, noise=1e-3, seed=0, k=256),
+    # Profiling case of the same model: half the columns, 16 iterations.
+    "decay_4096x32768": dict(m=4096, n=32768, rank=256, noise=1e-3, seed=0, k=16),
     # Distributed-style GCSS: 2048 x 262144 BF16 rank 400, Omega 262144 x 400,
     # 64 log-normal blocks (median 3000, sigma 0.8), 100 per block, k = 100.
     "dist_2048x262144": dict(m=2048, n=262144, rank=400, noise=1e-3, seed=1,

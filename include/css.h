@@ -303,6 +303,39 @@ css_status css_select_host(const void* A_host, css_dtype dtype, int64_t m,
                            void* ws, size_t ws_bytes, const css_opts* opts,
                            css_stream_t stream);
 
+/*
+ * css_select without a caller workspace.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory (a
+ * service whose device memory is fully pre-reserved by its host application,
+ * a plugin whose framework forbids allocation calls, or latency-sensitive
+ * code that must avoid cudaMalloc/cudaFree because they can synchronise the
+ * device).
+ *
+ * Its scratch memory is a fixed array of CSS_NOALLOC_SCRATCH_BYTES inside the
+ * library, one copy per device that loads it, held until the process exits.
+ * Arguments are those of css_select (inputs and outputs are still the
+ * caller's); problems whose css_select workspace
+ * (css_workspace_size(CSS_OP_SELECT, ...)) exceeds the array are rejected
+ * with CSS_ERR_WORKSPACE before anything is enqueued -- for example FP32
+ * m = 1024, n = 16384, k = 64 fits, m = 4096, n = 65536 does not.
+ * opts->timing_ms must be NULL.  Nothing is allocated: no cudaMalloc,
+ * cudaFree or allocating library routine is called.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls on a device share the one array:
+ * calls whose work overlaps on the GPU (other streams, or sync = 0 without
+ * waiting) race on it and corrupt each other's results.  Each call
+ * initialises every scratch word it reads, so stale contents from an
+ * earlier call are harmless.
+ */
+#define CSS_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+css_status css_select_noalloc(const void* A, css_dtype dtype, int64_t m,
+                              int64_t n, int64_t lda, int32_t k,
+                              int32_t* sel, double* trace, int32_t* n_sel,
+                              double* W, const css_opts* opts,
+                              css_stream_t stream);
+
 /* Device status left by the last call that used `ws` (for opts->sync = 0):
    synchronises `stream`, then returns CSS_OK, CSS_RANK_EXHAUSTED or the
    device error. */

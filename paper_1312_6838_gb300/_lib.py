@@ -87,7 +87,10 @@ _SIGS = {
     "css_select_host": (I32, [P, I32, I64, I64, I64, I32, P, P, P, P, P, SZ,
                               C.POINTER(css_opts), P]),
     "css_read_status": (I32, [P, P]),
+    "css_select_noalloc": (I32, [P, I32, I64, I64, I64, I32, P, P, P, P, C.POINTER(css_opts), P]),
 }
+
+CSS_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 # every symbol include/css.h declares
 EXPORTED = tuple(_SIGS)

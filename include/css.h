@@ -132,6 +132,15 @@ typedef struct {
        2 = tensor cores (tcgen05, BF16 split). */
     int32_t init_path;
     int32_t reserved[7];
+    /* DEVICE uint64[k * 16] or NULL (css_select, gcss_select): per-iteration
+       trace of the persistent kernel; entry [t * 16 + j] is the GPU global
+       timer (ns) when the team's first CTA reached point j of iteration t:
+       0 start, 1 argmax done, 2/3 before/after the first team barrier,
+       4/5 around the second, 6 target vectors staged, 7 C e or B B^T e
+       done, 8 Z^T e done, 9 after the third barrier, 10/11 around the
+       fourth, 12 fused step starts, 13 fused step done, 14 after the last
+       barrier.  Unused entries are 0. */
+    uint64_t* trace_ns;
 } css_opts;
 
 /* Fill *opts with the defaults. */

@@ -43,6 +43,7 @@ class css_opts(C.Structure):
         ("diag_g", C.c_void_p),
         ("init_path", C.c_int32),
         ("reserved", C.c_int32 * 7),
+        ("trace_ns", C.c_void_p),
     ]
 
 

@@ -56,7 +56,9 @@ void carve_rest(WsCarver& c, int dt, int m, int n, int k, int r, int mode, bool 
                 UnitState& s) {
   s.Q = c.take<double>((size_t)m * k);
   s.Z = c.take<double>((size_t)(mode == 0 ? m : r) * k);
-  if (need_W) s.W = c.take<double>((size_t)k * n);
+  // W (the omega rows) is an optional output only; nothing reads it back
+  (void)need_W;
+  (void)n;
   s.qv = c.take<char>((size_t)m * accsize(dt));
   s.ypv = c.take<char>((size_t)m * accsize(dt));
   s.e1 = c.take<double>(m);
@@ -77,6 +79,7 @@ struct Header {
   double* part;
   double* cand_val;
   int* cand_idx;
+  uint32_t* tile_ctr;
 };
 
 void carve_header(WsCarver& c, int max_units, Header& h) {
@@ -89,6 +92,7 @@ void carve_header(WsCarver& c, int max_units, Header& h) {
   h.part = c.take<double>(4 * kMaxCtas);
   h.cand_val = c.take<double>(kMaxCtas);
   h.cand_idx = c.take<int>(kMaxCtas);
+  h.tile_ctr = c.take<uint32_t>(2 * kMaxCtas);
 }
 
 css_status cuda_status(cudaError_t e) {
@@ -207,6 +211,7 @@ css_status launch_units(const Header& h, std::vector<UnitDesc>& units, const std
     P.teams[t].part = h.part + 4 * P.teams[t].cta0;
     P.teams[t].cand_val = h.cand_val + P.teams[t].cta0;
     P.teams[t].cand_idx = h.cand_idx + P.teams[t].cta0;
+    P.teams[t].tile_ctr = h.tile_ctr + 2 * P.teams[t].cta0;
   }
   DevStatus st{};
   st.spin_budget_ns = spin_ns ? spin_ns : kDefaultSpinNs;
@@ -217,6 +222,7 @@ css_status launch_units(const Header& h, std::vector<UnitDesc>& units, const std
   if ((e = cudaMemcpyAsync(h.order, P.order.data(), P.order.size() * sizeof(int), cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_status(e);
   if ((e = cudaMemcpyAsync(h.cta_team, P.cta_team.data(), P.cta_team.size() * sizeof(int), cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_status(e);
   if ((e = cudaMemsetAsync(h.bars, 0, 2 * sizeof(uint32_t) * P.grid, s)) != cudaSuccess) return cuda_status(e);
+  if ((e = cudaMemsetAsync(h.tile_ctr, 0, 2 * sizeof(uint32_t) * P.grid, s)) != cudaSuccess) return cuda_status(e);
   GreedyLaunch L{};
   L.units = h.units;
   L.order = h.order;
@@ -355,7 +361,7 @@ UnitDesc make_unit(const void* A, int dt, int64_t m, int64_t n, int64_t lda, int
   u.selmask = s.selmask;
   u.Q = s.Q;
   u.Z = s.Z;
-  u.W = W ? W : s.W;
+  u.W = W;
   u.qv = s.qv;
   u.ypv = s.ypv;
   u.e1 = s.e1;
@@ -367,6 +373,7 @@ UnitDesc make_unit(const void* A, int dt, int64_t m, int64_t n, int64_t lda, int
   u.trace = trace;
   u.n_sel = n_sel;
   u.diag_argmax = o.diag_argmax;
+  u.trace_ns = (unsigned long long*)o.trace_ns;
   u.diag_f = o.diag_f;
   u.diag_g = o.diag_g;
   u.forced = o.forced;
@@ -682,6 +689,7 @@ css_status gcss_distributed(const void* A, css_dtype dtype, int64_t m, int64_t n
   css_opts ob = o;
   ob.diag_argmax = nullptr;
   ob.diag_f = ob.diag_g = nullptr;
+  ob.trace_ns = nullptr;
   std::vector<UnitDesc> units;
   std::vector<double> work;
   for (int b = 0; b < nblocks; ++b) {
@@ -794,7 +802,7 @@ css_status css_select_batched(const css_problem* probs, int32_t count, css_dtype
   const css_opts o = opts ? *opts : defaults();
   cudaStream_t s = (cudaStream_t)stream;
   if (!probs || count < 1 || !valid_dtype(dtype)) return CSS_ERR_INVALID_ARG;
-  if (o.n_forced || o.diag_argmax || o.diag_f) return CSS_ERR_INVALID_ARG;
+  if (o.n_forced || o.diag_argmax || o.diag_f || o.trace_ns) return CSS_ERR_INVALID_ARG;
   for (int i = 0; i < count; ++i) {
     const css_problem& p = probs[i];
     if (!p.A || !p.sel || !p.trace || !p.n_sel) return CSS_ERR_INVALID_ARG;

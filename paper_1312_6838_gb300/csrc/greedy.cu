@@ -179,6 +179,7 @@ __device__ void col_dots(const Ctx<Acc>& x, int len, int nj, const TM* M, long l
     for (int j = x.rank * NW + x.warp; j < nj; j += x.ncta * NW) {
       const TM* col = M + (long long)j * ldm;
       TS acc = TS(0);
+#pragma unroll 4
       for (int i = x.lane; i < len; i += 32) acc += (TS)ld_cg(col + i) * (TS)v[i];
       acc = warp_sum(acc);
       if (x.lane == 0) fin(j, (double)acc);
@@ -187,6 +188,7 @@ __device__ void col_dots(const Ctx<Acc>& x, int len, int nj, const TM* M, long l
     for (int j = x.rank; j < nj; j += x.ncta) {
       const TM* col = M + (long long)j * ldm;
       TS acc = TS(0);
+#pragma unroll 4
       for (int i = x.tid; i < len; i += NT) acc += (TS)ld_cg(col + i) * (TS)v[i];
       acc = block_sum(acc, reinterpret_cast<TS*>(x.sred));
       if (x.tid == 0) fin(j, (double)acc);
@@ -232,6 +234,23 @@ __device__ int team_argmax(const Ctx<Acc>& x) {
   return s_p;
 }
 
+// Sum of part[r * 4 + slot] over the team's CTAs, in a fixed order (every CTA
+// gets the same bits).  Warp 0 reads the partials in parallel.
+template <typename Acc>
+__device__ double team_sum(const Ctx<Acc>& x, int slot) {
+  __shared__ double s_sum;
+  if (x.warp == 0) {
+    double a = 0.0;
+    for (int r = x.lane; r < x.ncta; r += 32) a += ld_cg(x.team->part + r * 4 + slot);
+    a = warp_sum(a);
+    if (x.lane == 0) s_sum = a;
+  }
+  __syncthreads();
+  const double v = s_sum;
+  __syncthreads();
+  return v;
+}
+
 // --------------------------------------------------------- fused step (K1) --
 template <typename TA, int CW>
 __device__ void fused_step(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc& u, int t,
@@ -245,7 +264,15 @@ __device__ void fused_step(const Ctx<typename AccOf<TA>::type>& x, const UnitDes
   const int m_vec = u.vec_ok ? (m / V) * V : 0;
   const TA* A = reinterpret_cast<const TA*>(u.A);
   const volatile unsigned char* selv = u.selmask;
-  for (int tile = x.rank * NW + x.warp; tile < ntiles; tile += x.ncta * NW) {
+  // tiles are handed out by a team-wide counter, so every warp keeps streaming
+  // until the column range is exhausted (no static imbalance at the barrier)
+  uint32_t* ctr = x.team->tile_ctr + (t & 1);
+  int tile = 0;
+  if (x.lane == 0) tile = (int)atomicAdd(ctr, 1u);
+  tile = __shfl_sync(0xffffffffu, tile, 0);
+  for (; tile < ntiles;) {
+    int next = 0;
+    if (x.lane == 0) next = (int)atomicAdd(ctr, 1u);
     const int c0 = tile * CW;
     const TA* colp[CW];
 #pragma unroll
@@ -253,7 +280,7 @@ __device__ void fused_step(const Ctx<typename AccOf<TA>::type>& x, const UnitDes
     Acc v[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) v[i] = Acc(0);
-#pragma unroll 2
+#pragma unroll 4
     for (int r = x.lane * V; r < m_vec; r += 32 * V) {
       uint4 raw[CW];
 #pragma unroll
@@ -294,7 +321,7 @@ __device__ void fused_step(const Ctx<typename AccOf<TA>::type>& x, const UnitDes
         gi = gi - w * w;
         u.f[col] = fi;
         u.g[col] = gi;
-        u.W[(long long)t * n + col] = w;
+        if (u.W) u.W[(long long)t * n + col] = w;
         bool selected = selv[col] != 0;
         if (col == p) { u.selmask[col] = 1; selected = true; }
         const double g0 = ld_cg(u.g0 + col);
@@ -304,6 +331,7 @@ __device__ void fused_step(const Ctx<typename AccOf<TA>::type>& x, const UnitDes
         }
       }
     }
+    tile = __shfl_sync(0xffffffffu, next, 0);
   }
 }
 
@@ -381,107 +409,126 @@ __device__ void run_unit(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc&
   if (__syncthreads_or(bad)) set_error(x.st, (int32_t)CSS_ERR_NONFINITE, 100);
   fsum = block_sum(fsum, x.sred);
   if (x.tid == 0) tm.part[x.rank * 4 + 2] = fsum;
+  // both fused-step tile counters start at zero for this unit (the previous
+  // unit of the team finished before its closing barrier)
+  if (x.rank == 0 && x.tid == 0) {
+    tm.tile_ctr[0] = 0u;
+    tm.tile_ctr[1] = 0u;
+  }
   cta_argmax_publish(x, bv, bi);
   if (!team_barrier(tm.bar, x.ncta, x.st, 1)) return;
 
-  double F = 0.0;  // meaningful in rank 0, thread 0
-  if (x.rank == 0 && x.tid == 0) {
-    for (int r = 0; r < x.ncta; ++r) F += ld_cg(tm.part + r * 4 + 2);
-    u.trace[0] = F;
-  }
+  double F = team_sum(x, 2);  // meaningful in rank 0, thread 0
+  if (x.rank == 0 && x.tid == 0) u.trace[0] = F;
 
+  const bool tracing = u.trace_ns != nullptr && x.rank == 0 && x.tid == 0;
   int t = 0;
+  auto mark = [&](int j) {
+    if (tracing) u.trace_ns[(long long)t * 16 + j] = globaltimer_ns();
+  };
   for (; t < u.k; ++t) {
-    // ---- Phase A: pivot p, outputs, e1 = a_p - Q_t W[0:t, p]
+    mark(0);
+    // ---- Phase A: pivot p, outputs; c = Q_t^T a_p (FP64 Gram-Schmidt coefficients)
     int p = team_argmax(x);
+    mark(1);
     const int p_arg = p;
     if (t < u.n_forced) p = u.forced[t];
     if (p < 0) break;
     if (x.rank == 0 && x.tid == 0) {
+      // counter of the next iteration's fused step; its last user finished
+      // before the previous iteration's final barrier
+      tm.tile_ctr[(t + 1) & 1] = 0u;
       if (u.diag_argmax) u.diag_argmax[t] = p_arg;
       u.sel[t] = p;
       F = F - ld_cg(u.f + p) / ld_cg(u.g + p);   // Theorem 1 / Theorem 3
       u.trace[t + 1] = F;
     }
-    for (int j = x.tid; j < t; j += NT) x.scoef[j] = ld_cg(u.W + (long long)j * n + p);
-    __syncthreads();
-    {
-      const TA* ap = reinterpret_cast<const TA*>(u.A) + (long long)p * u.lda;
-      row_gemv<double>(x, m, t, u.Q, (long long)m, x.scoef, [&](int i, double sum) {
-        u.e1[i] = (double)load_elem<TA>(ap + i) - sum;
-      });
-    }
-    if (!team_barrier(tm.bar, x.ncta, x.st, 2)) return;
-
-    // ---- Phase B: c2 = Q_t^T e1 (second Gram-Schmidt pass)
-    for (int i = x.tid; i < m; i += NT) x.se64[i] = ld_cg(u.e1 + i);
+    const TA* ap = reinterpret_cast<const TA*>(u.A) + (long long)p * u.lda;
+#pragma unroll 4
+    for (int i = x.tid; i < m; i += NT) x.se64[i] = (double)load_elem<TA>(ap + i);
     __syncthreads();
     col_dots<double>(x, m, t, u.Q, (long long)m, x.se64, [&](int j, double v) { u.coef[j] = v; });
-    if (!team_barrier(tm.bar, x.ncta, x.st, 3)) return;
+    mark(2);
+    if (!team_barrier(tm.bar, x.ncta, x.st, 2)) return;
+    mark(3);
 
-    // ---- Phase C: e = e1 - Q_t c2, ||e||^2 partials
+    // ---- Phase C: e = a_p - Q_t c, ||e||^2 partials (delta_p of Eq. delta_omega)
     for (int j = x.tid; j < t; j += NT) x.scoef[j] = ld_cg(u.coef + j);
     __syncthreads();
     double nrm_part = 0.0;
     row_gemv<double>(x, m, t, u.Q, (long long)m, x.scoef, [&](int i, double sum) {
-      const double ei = ld_cg(u.e1 + i) - sum;
+      const double ei = (double)load_elem<TA>(ap + i) - sum;
       u.e[i] = ei;
       nrm_part += ei * ei;
     });
+    mark(4);
     nrm_part = block_sum(nrm_part, x.sred);
     if (x.tid == 0) tm.part[x.rank * 4 + 0] = nrm_part;
     if (!team_barrier(tm.bar, x.ncta, x.st, 4)) return;
+    mark(5);
 
     // ---- Phase D: y_un = C e (CSS) or B (B^T e) (GCSS); d = Z^T e
-    if (x.tid == 0) {
-      double a = 0.0;
-      for (int r = 0; r < x.ncta; ++r) a += ld_cg(tm.part + r * 4 + 0);
-      s_scal[0] = a;
-    }
+    const double nrm2 = team_sum(x, 0);
+#pragma unroll 4
     for (int i = x.tid; i < m; i += NT) {
       const double ei = ld_cg(u.e + i);
       x.se64[i] = ei;
       x.seacc[i] = (Acc)ei;
     }
     __syncthreads();
-    const double nrm2 = s_scal[0];
+    mark(6);
     double s_un = 0.0;
     if (u.mode == 0) {
       const Acc* C = reinterpret_cast<const Acc*>(u.T);
       constexpr int VC = 16 / sizeof(Acc);
       const int m_vec = u.t_vec_ok ? (m / VC) * VC : 0;
       double ey = 0.0;
+      constexpr int UC = 8;   // 16-byte loads in flight per lane
       for (int i = x.rank * NW + x.warp; i < m; i += x.ncta * NW) {
         const Acc* cp = C + (long long)i * u.ldt;
-        Acc acc = Acc(0);
-        for (int l = x.lane * VC; l < m_vec; l += 32 * VC) {
-          Acc cv[VC], ev[VC];
-          if constexpr (sizeof(Acc) == 4) {
-            float tmp[4];
-            Vec<float>::unpack(ldg_stream16(cp + l, pol_keep), tmp);
+        Acc accs[UC];
 #pragma unroll
-            for (int e = 0; e < VC; ++e) cv[e] = (Acc)tmp[e];
-          } else {
-            double tmp[2];
-            Vec<double>::unpack(ldg_stream16(cp + l, pol_keep), tmp);
+        for (int q = 0; q < UC; ++q) accs[q] = Acc(0);
+        int l = x.lane * VC;
+        for (; l + (UC - 1) * 32 * VC < m_vec; l += UC * 32 * VC) {
+          uint4 raw[UC];
 #pragma unroll
-            for (int e = 0; e < VC; ++e) cv[e] = (Acc)tmp[e];
+          for (int q = 0; q < UC; ++q) raw[q] = ldg_stream16(cp + l + q * 32 * VC, pol_keep);
+#pragma unroll
+          for (int q = 0; q < UC; ++q) {
+            Acc cv[VC], ev[VC];
+            if constexpr (sizeof(Acc) == 4) Vec<float>::unpack(raw[q], cv);
+            else Vec<double>::unpack(raw[q], cv);
+            lds_vec<Acc, VC>(x.seacc + l + q * 32 * VC, ev);
+#pragma unroll
+            for (int e = 0; e < VC; ++e) accs[q] = fma(cv[e], ev[e], accs[q]);
           }
+        }
+        for (; l < m_vec; l += 32 * VC) {
+          Acc cv[VC], ev[VC];
+          if constexpr (sizeof(Acc) == 4) Vec<float>::unpack(ldg_stream16(cp + l, pol_keep), cv);
+          else Vec<double>::unpack(ldg_stream16(cp + l, pol_keep), cv);
           lds_vec<Acc, VC>(x.seacc + l, ev);
 #pragma unroll
-          for (int e = 0; e < VC; ++e) acc = fma(cv[e], ev[e], acc);
+          for (int e = 0; e < VC; ++e) accs[0] = fma(cv[e], ev[e], accs[0]);
         }
-        for (int l = m_vec + x.lane; l < m; l += 32) acc = fma(__ldg(cp + l), x.seacc[l], acc);
+        Acc acc = Acc(0);
+#pragma unroll
+        for (int q = 0; q < UC; ++q) acc += accs[q];
+        for (int l2 = m_vec + x.lane; l2 < m; l2 += 32) acc = fma(__ldg(cp + l2), x.seacc[l2], acc);
         acc = warp_sum(acc);
         if (x.lane == 0) {
           u.y[i] = (double)acc;
           ey += x.se64[i] * (double)acc;
         }
       }
+      mark(7);
       col_dots<double>(x, m, t, u.Z, (long long)m, x.se64, [&](int j, double v) { u.coef[j] = v; });
+      mark(8);
       ey = block_sum(ey, x.sred);
       if (x.tid == 0) tm.part[x.rank * 4 + 1] = ey;
       if (!team_barrier(tm.bar, x.ncta, x.st, 5)) return;
+      mark(9);
     } else {
       const Acc* B = reinterpret_cast<const Acc*>(u.T);
       col_dots<Acc>(x, m, u.r, B, u.ldt, x.seacc, [&](int j, double v) { u.ups[j] = v; });
@@ -503,20 +550,17 @@ __device__ void run_unit(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc&
         for (int j = x.tid; j < u.r; j += NT) u.Z[(long long)t * u.r + j] = x.scoef[j] * inv;
       }
       if (!team_barrier(tm.bar, x.ncta, x.st, 6)) return;
+      mark(9);
     }
 
     // ---- Phase E: q, y = y_un / ||e||, y' = y - Q (Q^T y), s
     double s;
     {
-      if (x.tid == 0 && u.mode == 0) {
-        double a = 0.0;
-        for (int r = 0; r < x.ncta; ++r) a += ld_cg(tm.part + r * 4 + 1);
-        s_scal[1] = a;
-      }
+      const double ey_all = (u.mode == 0) ? team_sum(x, 1) : 0.0;
       for (int j = x.tid; j < t; j += NT) x.scoef[j] = ld_cg(u.coef + j);
       __syncthreads();
       const double inv = 1.0 / sqrt(nrm2);
-      s = (u.mode == 0) ? s_scal[1] / nrm2 : s_un / nrm2;
+      s = (u.mode == 0) ? ey_all / nrm2 : s_un / nrm2;
       Acc* qv = reinterpret_cast<Acc*>(u.qv);
       Acc* ypv = reinterpret_cast<Acc*>(u.ypv);
       row_gemv<double>(x, m, t, u.Q, (long long)m, x.scoef, [&](int i, double sum) {
@@ -528,23 +572,29 @@ __device__ void run_unit(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc&
         ypv[i] = (Acc)(yi - sum * inv);
       });
     }
+    mark(10);
     if (!team_barrier(tm.bar, x.ncta, x.st, 7)) return;
+    mark(11);
 
     // ---- fused step over A
     {
       const Acc* qv = reinterpret_cast<const Acc*>(u.qv);
       const Acc* ypv = reinterpret_cast<const Acc*>(u.ypv);
+#pragma unroll 4
       for (int i = x.tid; i < m; i += NT) {
         x.sq[i] = ld_cg(qv + i);
         x.sy[i] = ld_cg(ypv + i);
       }
       __syncthreads();
+      mark(12);
       double bv2 = -1.0;
       int bi2 = -1;
       fused_step<TA, CW>(x, u, t, p, s, pol_stream, bv2, bi2);
+      mark(13);
       cta_argmax_publish(x, bv2, bi2);
     }
     if (!team_barrier(tm.bar, x.ncta, x.st, 8)) return;
+    mark(14);
   }
 
   if (x.rank == 0 && x.tid == 0) {

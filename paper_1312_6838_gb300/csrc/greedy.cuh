@@ -35,6 +35,7 @@ struct UnitDesc {
   double* trace;
   int* n_sel;
   int* diag_argmax;
+  unsigned long long* trace_ns;   // k * 8 phase timestamps or null
   double* diag_f;
   double* diag_g;
   const int* forced;
@@ -50,6 +51,7 @@ struct TeamDesc {
   double* part;                     // ncta * 4
   double* cand_val;                 // ncta
   int* cand_idx;                    // ncta
+  uint32_t* tile_ctr;               // 2 words: fused-step tile counters (alternating)
 };
 
 struct GreedyLaunch {

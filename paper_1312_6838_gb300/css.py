@@ -91,6 +91,7 @@ class Selection:
     diag_f: Optional[torch.Tensor] = None
     diag_g: Optional[torch.Tensor] = None
     timing_ms: Optional[tuple] = None       # (initial scores, greedy iterations)
+    trace_ns: Optional[torch.Tensor] = None  # int64[k, 16] phase timestamps
 
     @property
     def indices(self):
@@ -126,7 +127,7 @@ def _prep_forced(forced, device):
 
 def select(A: torch.Tensor, k: int, *, tau_rel=None, forced=None, return_W=False, diag=False,
            score_mode=0, grid_ctas=0, tile_cols=0, spin_budget_ns=0, stream=None,
-           timing=False) -> Selection:
+           timing=False, phase_trace=False) -> Selection:
     """Greedy CSS (Algorithm 1) of the columns of A (column-major, on the GPU)."""
     m, n, lda = _colmajor(A)
     dev = A.device
@@ -146,6 +147,9 @@ def select(A: torch.Tensor, k: int, *, tau_rel=None, forced=None, return_W=False
     tms = (C.c_double * 2)() if timing else None
     if tms is not None:
         o.timing_ms = C.cast(tms, C.c_void_p)
+    tr = torch.zeros((k, 16), dtype=torch.int64, device=dev) if phase_trace else None
+    if tr is not None:
+        o.trace_ns = tr.data_ptr()
     nbytes = lib.css_workspace_size(L.CSS_OP_SELECT, dt, m, n, 0, k, 0, C.byref(o))
     if nbytes == 0:
         raise ValueError("invalid sizes for css_select")
@@ -157,6 +161,7 @@ def select(A: torch.Tensor, k: int, *, tau_rel=None, forced=None, return_W=False
     res = Selection(sel, trace, ns, code, W, *(dg if dg else (None, None, None)))
     if tms is not None:
         res.timing_ms = (tms[0], tms[1])
+    res.trace_ns = tr
     return res
 
 

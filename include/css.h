@@ -289,8 +289,13 @@ css_status css_select_batched(const css_problem* probs, int32_t count,
  *             NULL to compute the loss only.
  *   loss      DEVICE double[1] or NULL.
  * The k x k factor of A_S^T A_S is recomputed here (FP64 Cholesky), not
- * carried over from a forward pass.  FP32/BF16 input: GEMMs accumulate in
- * FP32, the factorisation and the loss are FP64.
+ * carried over from a forward pass; a pivot at or below 1e-12 of its
+ * column's squared norm (dependent columns in S) gives CSS_ERR_INVALID_ARG
+ * (reported in sync mode), as do out-of-range or repeated indices.
+ * FP32/BF16 input: the two products that cancel (Q^T A and A - Q W, with
+ * Q = A_S L^-T) run in double-float arithmetic (FP32 pairs, error-free
+ * products and sums), R W^T accumulates in FP32, the factorisation and the
+ * loss are FP64; dA is rounded once to the dtype of A.  k <= 1024.
  */
 css_status css_residual_backward(const void* A, css_dtype dtype, int64_t m,
                                  int64_t n, int64_t lda, const int32_t* sel,

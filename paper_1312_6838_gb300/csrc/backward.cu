@@ -1,9 +1,456 @@
-// Adjoint of the reconstruction error at a fixed selected set.
+// Loss and gradient of the reconstruction error at a fixed selected set S.
+//
+//   L(A) = ||A - P^(S) A||_F^2,  P^(S) = A_S (A_S^T A_S)^-1 A_S^T   (Eq. Projection)
+//   T = (A_S^T A_S)^-1 A_S^T A,  R = A - A_S T
+//   dL/dA = 2 R  (columns outside S),  dL/dA_S = -2 R T^T
+//
+// With the Cholesky factor A_S^T A_S = L L^T (recomputed here in FP64, not
+// carried over from any forward pass) and Q = A_S L^-T (orthonormal):
+//   W = Q^T A,  R = A - Q W,  T = L^-T W,  R T^T = (R W^T) L^-1.
+// R is a small difference of large terms (the part of A outside span(A_S)),
+// so W and R are accumulated in double-float arithmetic (pairs of FP32 values
+// with error-free products and sums: Dekker's product by FMA and Knuth's
+// TwoSum) when A is FP32/BF16; FP64 input uses FP64 throughout.  R W^T has no
+// such cancellation and is accumulated in FP32 (FP64 for FP64 input).
+#include <algorithm>
+#include <vector>
+
 #include "backward.cuh"
 
+using namespace css;
+
+namespace {
+
+template <typename TA> __device__ __forceinline__ double to_d(TA v);
+template <> __device__ __forceinline__ double to_d<double>(double v) { return v; }
+template <> __device__ __forceinline__ double to_d<float>(float v) { return (double)v; }
+template <> __device__ __forceinline__ double to_d<__nv_bfloat16>(__nv_bfloat16 v) {
+  return (double)__uint_as_float(((uint32_t)__bfloat16_as_ushort(v)) << 16);
+}
+template <typename TA> __device__ __forceinline__ TA from_d(double v);
+template <> __device__ __forceinline__ double from_d<double>(double v) { return v; }
+template <> __device__ __forceinline__ float from_d<float>(double v) { return (float)v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_d<__nv_bfloat16>(double v) {
+  return __float2bfloat16_rn((float)v);
+}
+
+// ----------------------------------------------------------- double-float ---
+// Unevaluated sum s + c of two FP32 values.
+struct DF {
+  float s, c;
+};
+__device__ __forceinline__ void df_split(double v, float& hi, float& lo) {
+  hi = (float)v;
+  lo = (float)(v - (double)hi);
+}
+// acc += x * (yh + yl): exact product of x and yh (FMA), the x*yl term in the
+// compensation, Knuth's TwoSum for the running sum.
+__device__ __forceinline__ void df_fma(DF& a, float x, float yh, float yl) {
+  const float p = x * yh;
+  float e = fmaf(x, yh, -p);
+  e = fmaf(x, yl, e);
+  const float s = a.s + p;
+  const float bb = s - a.s;
+  const float t = (a.s - (s - bb)) + (p - bb);
+  a.s = s;
+  a.c += t + e;
+}
+// acc += (xh + xl) * (yh + yl)
+__device__ __forceinline__ void df_fma2(DF& a, float xh, float xl, float yh, float yl) {
+  const float p = xh * yh;
+  float e = fmaf(xh, yh, -p);
+  e = fmaf(xh, yl, e);
+  e = fmaf(xl, yh, e);
+  const float s = a.s + p;
+  const float bb = s - a.s;
+  const float t = (a.s - (s - bb)) + (p - bb);
+  a.s = s;
+  a.c += t + e;
+}
+
+// ------------------------------------------------------- small FP64 steps --
+template <typename TA>
+__global__ void gather_cols_kernel(const TA* __restrict__ A, long long lda, int m,
+                                   const int* __restrict__ sel, int k, double* __restrict__ AS) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)m * k) return;
+  const int i = (int)(idx % m), j = (int)(idx / m);
+  AS[idx] = to_d<TA>(A[(long long)sel[j] * lda + i]);
+}
+
+// G = A_S^T A_S (k x k), one 16 x 16 output tile per block.
+__global__ void gram_kernel(const double* __restrict__ AS, int m, int k, double* __restrict__ G) {
+  __shared__ double xs[32][17], ys[32][17];
+  const int i0 = blockIdx.y * 16, j0 = blockIdx.x * 16;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc = 0.0;
+  for (int r0 = 0; r0 < m; r0 += 32) {
+    for (int e = threadIdx.x; e < 32 * 16; e += 256) {
+      const int rr = e % 32, cc = e / 32;
+      xs[rr][cc] = (r0 + rr < m && i0 + cc < k) ? AS[(long long)(i0 + cc) * m + r0 + rr] : 0.0;
+      ys[rr][cc] = (r0 + rr < m && j0 + cc < k) ? AS[(long long)(j0 + cc) * m + r0 + rr] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < 32; ++rr) acc = fma(xs[rr][ty], ys[rr][tx], acc);
+    __syncthreads();
+  }
+  if (i0 + ty < k && j0 + tx < k) G[(long long)(j0 + tx) * k + i0 + ty] = acc;
+}
+
+// Cholesky G = L L^T in place (lower triangle) and Linv = L^-1, one block.
+// status[0] = 1 when G is not positive definite (A_S rank deficient).
+__global__ void chol_inv_kernel(double* __restrict__ G, int k, double* __restrict__ Linv,
+                                int* __restrict__ status) {
+  __shared__ int bad;
+  __shared__ double diag0[1024];
+  if (threadIdx.x == 0) bad = 0;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) diag0[j] = G[(long long)j * k + j];
+  __syncthreads();
+  for (int j = 0; j < k; ++j) {
+    if (threadIdx.x == 0) {
+      // a pivot at or below 1e-12 of its column's squared norm: the selected
+      // columns are linearly dependent to working precision
+      const double d = G[(long long)j * k + j];
+      const bool ok = d > 1e-12 * diag0[j];
+      if (!ok) bad = 1;
+      G[(long long)j * k + j] = ok ? sqrt(d) : 1.0;
+    }
+    __syncthreads();
+    const double d = G[(long long)j * k + j];
+    for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) G[(long long)j * k + i] /= d;
+    __syncthreads();
+    // trailing update of the lower triangle: G[i][l] -= L[i][j] L[l][j], j < l <= i
+    const int rem = k - j - 1;
+    for (long long e = threadIdx.x; e < (long long)rem * rem; e += blockDim.x) {
+      const int i = j + 1 + (int)(e % rem), l = j + 1 + (int)(e / rem);
+      if (l <= i) G[(long long)l * k + i] -= G[(long long)j * k + i] * G[(long long)j * k + l];
+    }
+    __syncthreads();
+  }
+  // Linv: forward substitution L x = e_j, one column per thread group
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    for (int i = 0; i < k; ++i) Linv[(long long)j * k + i] = 0.0;
+    for (int i = j; i < k; ++i) {
+      double v = (i == j) ? 1.0 : 0.0;
+      for (int l = j; l < i; ++l) v -= G[(long long)l * k + i] * Linv[(long long)j * k + l];
+      Linv[(long long)j * k + i] = v / G[(long long)i * k + i];
+    }
+  }
+  if (threadIdx.x == 0 && bad) status[0] = 1;
+}
+
+// Q = A_S L^-T (m x k): Q[i, j] = sum_{l <= j} A_S[i, l] Linv[j, l]; the
+// double-float split of Q is stored alongside.
+__global__ void q_kernel(const double* __restrict__ AS, const double* __restrict__ Linv, int m, int k,
+                         double* __restrict__ Q, float* __restrict__ Qh, float* __restrict__ Ql) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)m * k) return;
+  const int i = (int)(idx % m), j = (int)(idx / m);
+  double acc = 0.0;
+  for (int l = 0; l <= j; ++l) acc = fma(AS[(long long)l * m + i], Linv[(long long)l * k + j], acc);
+  Q[idx] = acc;
+  float h, lo;
+  df_split(acc, h, lo);
+  Qh[idx] = h;
+  Ql[idx] = lo;
+}
+
+// --------------------------------------------------- W = Q^T A  (k x n) -----
+// 32 (k) x 64 (n) outputs per block, 2 x 4 per thread, K = m in chunks of 16.
+template <typename TA>
+__global__ void __launch_bounds__(256) w_kernel(const float* __restrict__ Qh, const float* __restrict__ Ql,
+                                                const double* __restrict__ Q, const TA* __restrict__ A,
+                                                long long lda, int m, int n, int k,
+                                                double* __restrict__ W, float* __restrict__ Wh,
+                                                float* __restrict__ Wl) {
+  constexpr int BK = 16;
+  __shared__ float qh[BK][33], ql[BK][33];
+  __shared__ double qd[BK][33];
+  __shared__ float as[BK][65];
+  __shared__ double ad[BK][65];
+  const int j0 = blockIdx.y * 32, c0 = blockIdx.x * 64;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // ty: 16 rows of j (x2), tx: 16 cols (x4)
+  constexpr bool F64 = sizeof(TA) == 8;
+  DF acc[2][4];
+  double accd[2][4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) { acc[a][b] = DF{0.f, 0.f}; accd[a][b] = 0.0; }
+  for (int r0 = 0; r0 < m; r0 += BK) {
+    for (int e = threadIdx.x; e < BK * 32; e += 256) {
+      const int rr = e % BK, jj = e / BK;
+      const bool ok = r0 + rr < m && j0 + jj < k;
+      const long long o = (long long)(j0 + jj) * m + r0 + rr;
+      if (F64) qd[rr][jj] = ok ? Q[o] : 0.0;
+      else { qh[rr][jj] = ok ? Qh[o] : 0.f; ql[rr][jj] = ok ? Ql[o] : 0.f; }
+    }
+    for (int e = threadIdx.x; e < BK * 64; e += 256) {
+      const int rr = e % BK, cc = e / BK;
+      const bool ok = r0 + rr < m && c0 + cc < n;
+      const double v = ok ? to_d<TA>(A[(long long)(c0 + cc) * lda + r0 + rr]) : 0.0;
+      if (F64) ad[rr][cc] = v;
+      else as[rr][cc] = (float)v;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < BK; ++rr) {
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          if (F64) accd[a][b] = fma(qd[rr][ty * 2 + a], ad[rr][tx * 4 + b], accd[a][b]);
+          else df_fma(acc[a][b], as[rr][tx * 4 + b], qh[rr][ty * 2 + a], ql[rr][ty * 2 + a]);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int j = j0 + ty * 2 + a, c = c0 + tx * 4 + b;
+      if (j < k && c < n) {
+        const double v = F64 ? accd[a][b] : (double)acc[a][b].s + (double)acc[a][b].c;
+        const long long o = (long long)c * k + j;
+        W[o] = v;
+        float h, lo;
+        df_split(v, h, lo);
+        Wh[o] = h;
+        Wl[o] = lo;
+      }
+    }
+}
+
+// ------------------------------------ R = A - Q W (m x n) with epilogues -----
+// 64 x 64 outputs per block, 4 x 4 per thread, K = k in chunks of 16.
+// Writes R (FP32, or FP64 for FP64 input) when Rout != null, dA = 2 g R when
+// dA != null, and a per-block partial of ||R||^2.
+template <typename TA>
+__global__ void __launch_bounds__(256) r_kernel(const float* __restrict__ Qh, const float* __restrict__ Ql,
+                                                const double* __restrict__ Q, const float* __restrict__ Wh,
+                                                const float* __restrict__ Wl, const double* __restrict__ W,
+                                                const TA* __restrict__ A, long long lda, int m, int n, int k,
+                                                void* __restrict__ Rout, TA* __restrict__ dA, long long ldda,
+                                                double g2, double* __restrict__ loss_part) {
+  constexpr int BK = 16;
+  constexpr bool F64 = sizeof(TA) == 8;
+  __shared__ float qh[BK][65], ql[BK][65], wh[BK][65], wl[BK][65];
+  __shared__ double qd[BK][65], wd[BK][65];
+  __shared__ double red[8];
+  const int i0 = blockIdx.x * 64, c0 = blockIdx.y * 64;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  DF acc[4][4];
+  double accd[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) { acc[a][b] = DF{0.f, 0.f}; accd[a][b] = 0.0; }
+  for (int j0 = 0; j0 < k; j0 += BK) {
+    for (int e = threadIdx.x; e < BK * 64; e += 256) {
+      const int ii = e % 64, jj = e / 64;   // Q: rows contiguous
+      const bool okq = i0 + ii < m && j0 + jj < k;
+      const long long oq = (long long)(j0 + jj) * m + i0 + ii;
+      const int jj2 = e % BK, cc = e / BK;  // W: k contiguous per column
+      const bool okw = j0 + jj2 < k && c0 + cc < n;
+      const long long ow = (long long)(c0 + cc) * k + j0 + jj2;
+      if (F64) {
+        qd[jj][ii] = okq ? Q[oq] : 0.0;
+        wd[jj2][cc] = okw ? W[ow] : 0.0;
+      } else {
+        qh[jj][ii] = okq ? Qh[oq] : 0.f;
+        ql[jj][ii] = okq ? Ql[oq] : 0.f;
+        wh[jj2][cc] = okw ? Wh[ow] : 0.f;
+        wl[jj2][cc] = okw ? Wl[ow] : 0.f;
+      }
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int jj = 0; jj < BK; ++jj) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          if (F64) accd[a][b] = fma(qd[jj][ty * 4 + a], wd[jj][tx * 4 + b], accd[a][b]);
+          else df_fma2(acc[a][b], qh[jj][ty * 4 + a], ql[jj][ty * 4 + a], wh[jj][tx * 4 + b],
+                       wl[jj][tx * 4 + b]);
+        }
+    }
+    __syncthreads();
+  }
+  double sq = 0.0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = i0 + ty * 4 + a, c = c0 + tx * 4 + b;
+      if (i < m && c < n) {
+        const double av = to_d<TA>(A[(long long)c * lda + i]);
+        // a - (s + c) in double: the pair carries the product to ~2^-48
+        const double r = F64 ? av - accd[a][b] : (av - (double)acc[a][b].s) - (double)acc[a][b].c;
+        sq += r * r;
+        if (Rout) {
+          if (F64) ((double*)Rout)[(long long)c * m + i] = r;
+          else ((float*)Rout)[(long long)c * m + i] = (float)r;
+        }
+        if (dA) dA[(long long)c * ldda + i] = from_d<TA>(g2 * r);
+      }
+    }
+  sq = warp_sum(sq);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    loss_part[(long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+__global__ void sum_kernel(const double* __restrict__ part, long long cnt, double scale,
+                           double* __restrict__ out) {
+  __shared__ double red[32];
+  double a = 0.0;
+  for (long long i = threadIdx.x; i < cnt; i += blockDim.x) a += part[i];
+  a = block_sum(a, red);
+  if (threadIdx.x == 0) out[0] = a * scale;
+}
+
+// ------------------------------ P = R W^T (m x k), split over column slices --
+// partial[s][i + j*m] = sum over columns c of slice s of R[i, c] W[j, c].
+template <typename TR>
+__global__ void __launch_bounds__(256) rwt_kernel(const TR* __restrict__ R, const double* __restrict__ W,
+                                                  int m, int n, int k, int slice,
+                                                  TR* __restrict__ partial) {
+  constexpr int BK = 16;
+  __shared__ TR rs[BK][65];
+  __shared__ TR ws[BK][33];
+  const int i0 = blockIdx.x * 64, j0 = blockIdx.y * 32, sl = blockIdx.z;
+  const int cb = sl * slice, ce = min(n, cb + slice);
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  TR acc[4][2];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) { acc[a][0] = TR(0); acc[a][1] = TR(0); }
+  for (int c0 = cb; c0 < ce; c0 += BK) {
+    for (int e = threadIdx.x; e < BK * 64; e += 256) {
+      const int ii = e % 64, cc = e / 64;
+      rs[cc][ii] = (c0 + cc < ce && i0 + ii < m) ? R[(long long)(c0 + cc) * m + i0 + ii] : TR(0);
+    }
+    for (int e = threadIdx.x; e < BK * 32; e += 256) {
+      const int jj = e % 32, cc = e / 32;
+      ws[cc][jj] = (c0 + cc < ce && j0 + jj < k) ? (TR)W[(long long)(c0 + cc) * k + j0 + jj] : TR(0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int cc = 0; cc < BK; ++cc)
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        acc[a][0] = fma(rs[cc][ty * 4 + a], ws[cc][tx * 2 + 0], acc[a][0]);
+        acc[a][1] = fma(rs[cc][ty * 4 + a], ws[cc][tx * 2 + 1], acc[a][1]);
+      }
+    __syncthreads();
+  }
+  TR* out = partial + (long long)sl * m * k;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int i = i0 + ty * 4 + a, j = j0 + tx * 2 + b;
+      if (i < m && j < k) out[(long long)j * m + i] = acc[a][b];
+    }
+}
+
+// dA[:, S[j]] = -2 g sum_{l >= j} P[i, l] Linv[l, j], P = sum of the slices.
+template <typename TA, typename TR>
+__global__ void das_kernel(const TR* __restrict__ partial, int S, const double* __restrict__ Linv,
+                           int m, int k, const int* __restrict__ sel, double g2, TA* __restrict__ dA,
+                           long long ldda) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)m * k) return;
+  const int i = (int)(idx % m), j = (int)(idx / m);
+  double acc = 0.0;
+  for (int l = j; l < k; ++l) {
+    double p = 0.0;
+    for (int s = 0; s < S; ++s) p += (double)partial[(long long)s * m * k + (long long)l * m + i];
+    acc += p * Linv[(long long)j * k + l];
+  }
+  dA[(long long)sel[j] * ldda + i] = from_d<TA>(-g2 * acc);
+}
+
+constexpr int kSlices = 16;
+
+struct BwLayout {
+  int* status;
+  double *AS, *G, *Linv, *Q, *W;
+  float *Qh, *Ql, *Wh, *Wl;
+  void* R;
+  void* P;
+  double* loss_part;
+  double* loss_tmp;
+  size_t bytes;
+};
+
+BwLayout bw_layout(void* ws, size_t cap, int dt, int64_t m, int64_t n, int32_t k, bool grad) {
+  WsCarver c(ws, cap);
+  BwLayout L{};
+  L.status = c.take<int>(64);
+  L.AS = c.take<double>((size_t)m * k);
+  L.G = c.take<double>((size_t)k * k);
+  L.Linv = c.take<double>((size_t)k * k);
+  L.Q = c.take<double>((size_t)m * k);
+  L.Qh = c.take<float>((size_t)m * k);
+  L.Ql = c.take<float>((size_t)m * k);
+  L.W = c.take<double>((size_t)k * n);
+  L.Wh = c.take<float>((size_t)k * n);
+  L.Wl = c.take<float>((size_t)k * n);
+  const size_t rs = dt == CSS_F64 ? 8 : 4;
+  L.R = grad ? (void*)c.take<char>((size_t)m * n * rs) : nullptr;
+  L.P = grad ? (void*)c.take<char>((size_t)kSlices * m * k * rs) : nullptr;
+  L.loss_part = c.take<double>((size_t)((m + 63) / 64) * ((n + 63) / 64));
+  L.loss_tmp = c.take<double>(1);
+  L.bytes = c.off;
+  return L;
+}
+
+template <typename TA>
+css_status run_backward(const TA* A, int dt, int m, int n, long long lda, const int* sel, int k,
+                        double grad_out, TA* dA, long long ldda, double* loss, const BwLayout& L,
+                        const css_opts& o, cudaStream_t s) {
+  using TR = typename AccOf<TA>::type;
+  cudaMemsetAsync(L.status, 0, sizeof(int), s);
+  const long long mk = (long long)m * k;
+  gather_cols_kernel<TA><<<(unsigned)((mk + 255) / 256), 256, 0, s>>>(A, lda, m, sel, k, L.AS);
+  gram_kernel<<<dim3((k + 15) / 16, (k + 15) / 16), 256, 0, s>>>(L.AS, m, k, L.G);
+  chol_inv_kernel<<<1, 1024, 0, s>>>(L.G, k, L.Linv, L.status);
+  q_kernel<<<(unsigned)((mk + 255) / 256), 256, 0, s>>>(L.AS, L.Linv, m, k, L.Q, L.Qh, L.Ql);
+  w_kernel<TA><<<dim3((n + 63) / 64, (k + 31) / 32), 256, 0, s>>>(L.Qh, L.Ql, L.Q, A, lda, m, n, k, L.W,
+                                                                L.Wh, L.Wl);
+  const dim3 rg((m + 63) / 64, (n + 63) / 64);
+  r_kernel<TA><<<rg, 256, 0, s>>>(L.Qh, L.Ql, L.Q, L.Wh, L.Wl, L.W, A, lda, m, n, k, dA ? L.R : nullptr,
+                                  dA, ldda, 2.0 * grad_out, L.loss_part);
+  if (loss) sum_kernel<<<1, 512, 0, s>>>(L.loss_part, (long long)rg.x * rg.y, 1.0, loss);
+  if (dA) {
+    const int slice = (n + kSlices - 1) / kSlices;
+    rwt_kernel<TR><<<dim3((m + 63) / 64, (k + 31) / 32, kSlices), 256, 0, s>>>((const TR*)L.R, L.W, m, n,
+                                                                              k, slice, (TR*)L.P);
+    das_kernel<TA, TR><<<(unsigned)((mk + 255) / 256), 256, 0, s>>>((const TR*)L.P, kSlices, L.Linv, m,
+                                                                   k, sel, 2.0 * grad_out, dA, ldda);
+  }
+  if (cudaGetLastError() != cudaSuccess) return CSS_ERR_CUDA;
+  if (o.sync) {
+    int st = 0;
+    if (cudaMemcpyAsync(&st, L.status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return CSS_ERR_CUDA;
+    if (st) return CSS_ERR_INVALID_ARG;   // A_S is rank deficient
+  }
+  return CSS_OK;
+}
+
+}  // namespace
+
 size_t backward_workspace_bytes(int dtype, int64_t m, int64_t n, int32_t k) {
-  (void)dtype; (void)m; (void)n; (void)k;
-  return css::kStatusBytes;
+  return bw_layout(nullptr, (size_t)-1, dtype, m, n, k, true).bytes;
 }
 
 extern "C" css_status css_residual_backward(const void* A, css_dtype dtype, int64_t m, int64_t n,
@@ -11,7 +458,36 @@ extern "C" css_status css_residual_backward(const void* A, css_dtype dtype, int6
                                             double grad_out, void* dA, int64_t ldda, double* loss,
                                             void* ws, size_t ws_bytes, const css_opts* opts,
                                             css_stream_t stream) {
-  (void)A; (void)dtype; (void)m; (void)n; (void)lda; (void)sel; (void)k; (void)grad_out;
-  (void)dA; (void)ldda; (void)loss; (void)ws; (void)ws_bytes; (void)opts; (void)stream;
-  return CSS_ERR_UNSUPPORTED;
+  css_opts o;
+  css_opts_default(&o);
+  if (opts) o = *opts;
+  if (!A || !sel || (!dA && !loss)) return CSS_ERR_INVALID_ARG;
+  if (dtype != CSS_F64 && dtype != CSS_F32 && dtype != CSS_BF16) return CSS_ERR_INVALID_ARG;
+  if (m < 1 || n < 1 || lda < m || k < 1 || k > 1024 || k > m || k > n) return CSS_ERR_INVALID_ARG;
+  if (dA && ldda < m) return CSS_ERR_INVALID_ARG;
+  if (m > INT32_MAX || n > INT32_MAX) return CSS_ERR_INVALID_ARG;
+  if (!ws || ((uintptr_t)ws % kWsAlign) != 0) return CSS_ERR_WORKSPACE;
+  BwLayout L = bw_layout(ws, ws_bytes, dtype, m, n, k, dA != nullptr);
+  if (L.bytes > ws_bytes) return CSS_ERR_WORKSPACE;
+  // the selected indices: in range and distinct (a small synchronous copy)
+  std::vector<int32_t> h(k);
+  if (cudaMemcpy(h.data(), sel, sizeof(int32_t) * k, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return CSS_ERR_CUDA;
+  std::vector<char> seen(n, 0);
+  for (int32_t v : h) {
+    if (v < 0 || v >= n || seen[v]) return CSS_ERR_INVALID_ARG;
+    seen[v] = 1;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  switch (dtype) {
+    case CSS_F64:
+      return run_backward<double>((const double*)A, dtype, (int)m, (int)n, lda, sel, k, grad_out,
+                                  (double*)dA, ldda, loss, L, o, s);
+    case CSS_F32:
+      return run_backward<float>((const float*)A, dtype, (int)m, (int)n, lda, sel, k, grad_out,
+                                 (float*)dA, ldda, loss, L, o, s);
+    default:
+      return run_backward<__nv_bfloat16>((const __nv_bfloat16*)A, dtype, (int)m, (int)n, lda, sel, k,
+                                         grad_out, (__nv_bfloat16*)dA, ldda, loss, L, o, s);
+  }
 }

@@ -128,8 +128,11 @@ typedef struct {
     double* timing_ms;
     double* diag_f;
     double* diag_g;
-    /* Initial-score path for FP32/BF16 input: 0 = automatic, 1 = SIMT FP32,
-       2 = tensor cores (tcgen05, BF16 split). */
+    /* Dense-GEMM path: 0 = automatic (tcgen05 tensor cores for BF16 input
+       when the layout allows TMA: 16-byte aligned base, leading dimension a
+       multiple of 8, r <= 512), 1 = CUDA-core (SIMT) kernels only.  Used by
+       css_project and by the initial scores of gcss_select /
+       gcss_distributed. */
     int32_t init_path;
     int32_t reserved[7];
     /* DEVICE uint64[k * 16] or NULL (css_select, gcss_select): per-iteration

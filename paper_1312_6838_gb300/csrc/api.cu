@@ -8,6 +8,7 @@
 
 #include "greedy.cuh"
 #include "init.cuh"
+#include "tc.cuh"
 #include "project.cuh"
 #include "backward.cuh"
 
@@ -80,6 +81,7 @@ struct Header {
   double* cand_val;
   int* cand_idx;
   uint32_t* tile_ctr;
+  int* aux_err;   // error flag of the tensor-core initial-score kernel
 };
 
 void carve_header(WsCarver& c, int max_units, Header& h) {
@@ -93,6 +95,7 @@ void carve_header(WsCarver& c, int max_units, Header& h) {
   h.cand_val = c.take<double>(kMaxCtas);
   h.cand_idx = c.take<int>(kMaxCtas);
   h.tile_ctr = c.take<uint32_t>(2 * kMaxCtas);
+  h.aux_err = c.take<int>(1);
 }
 
 css_status cuda_status(cudaError_t e) {
@@ -243,9 +246,12 @@ css_status launch_units(const Header& h, std::vector<UnitDesc>& units, const std
 css_status finish(const Header& h, const css_opts& o, cudaStream_t s) {
   if (!o.sync) return CSS_OK;
   DevStatus st{};
+  int aux = 0;
   cudaError_t e = cudaMemcpyAsync(&st, h.st, sizeof(st), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&aux, h.aux_err, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_status(e);
+  if (aux != 0) return (css_status)aux;
   if (st.code != 0) return (css_status)st.code;
   return st.rank_exhausted ? CSS_RANK_EXHAUSTED : CSS_OK;
 }
@@ -325,6 +331,7 @@ struct GcssLayout {
   Header h;
   UnitState s;
   double* partial;
+  void* tc_scratch;
   size_t bytes;
 };
 
@@ -336,6 +343,7 @@ GcssLayout gcss_layout(void* ws, size_t cap, int dt, int64_t m, int64_t n, int64
   carve_scores(c, (int)n, L.s);
   carve_rest(c, dt, (int)m, (int)n, k, (int)r, 1, need_W, L.s);
   L.partial = c.take<double>(gcss_f0_partial_doubles(dt, (int)r, (int)n));
+  L.tc_scratch = c.take<char>(tc::colnorm_scratch_bytes((int)m, (int)r));
   L.bytes = c.off;
   return L;
 }
@@ -385,6 +393,19 @@ UnitDesc make_unit(const void* A, int dt, int64_t m, int64_t n, int64_t lda, int
 
 size_t host_out_bytes(int32_t k) {
   return align_up(align_up(sizeof(int32_t) * (k + 1), 8) + sizeof(double) * (k + 1));
+}
+
+// f_i^(0) = ||B^T a_i||^2 (Algorithm 3's initialisation): tcgen05 for BF16 A
+// (B split into three BF16 parts), register-tiled SIMT otherwise.
+cudaError_t gcss_f0(int dt, const void* A, int64_t lda, int64_t m, int64_t n, const void* B, int64_t ldb,
+                    int64_t r, double* partial, void* tc_scratch, double* f, const Header& h,
+                    const css_opts& o, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(h.aux_err, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  if (dt == CSS_BF16 && o.init_path != 1 && tc_scratch && tc::supported(A, lda, (int)m, (int)r))
+    return tc::colnorms(A, lda, (int)m, (int)n, (const float*)B, ldb, (int)r, tc_scratch, f, h.aux_err,
+                        o.spin_budget_ns ? o.spin_budget_ns : kDefaultSpinNs, s);
+  return gcss_f0_simt(dt, A, lda, (int)m, (int)n, B, ldb, (int)r, partial, f, s);
 }
 
 int team_ctas_for(int64_t n, int64_t m) {
@@ -463,6 +484,7 @@ css_status css_select(const void* A, css_dtype dtype, int64_t m, int64_t n, int6
   if (cs != CSS_OK) return cs;
   PhaseTimer tm(o);
   tm.mark(0, s);
+  if (cudaMemsetAsync(L.h.aux_err, 0, sizeof(int), s) != cudaSuccess) return CSS_ERR_CUDA;
   cudaError_t e = css_f0_simt(dtype, A, lda, (int)m, (int)n, L.C, L.partial, L.s.f, s);
   if (e != cudaSuccess) return cuda_status(e);
   tm.mark(1, s);
@@ -496,7 +518,7 @@ css_status gcss_select(const void* A, css_dtype dtype, int64_t m, int64_t n, int
   if (cs != CSS_OK) return cs;
   PhaseTimer tm(o);
   tm.mark(0, s);
-  cudaError_t e = gcss_f0_simt(dtype, A, lda, (int)m, (int)n, B, ldb, (int)r, L.partial, L.s.f, s);
+  cudaError_t e = gcss_f0(dtype, A, lda, m, n, B, ldb, r, L.partial, L.tc_scratch, L.s.f, L.h, o, s);
   if (e != cudaSuccess) return cuda_status(e);
   tm.mark(1, s);
   std::vector<UnitDesc> units{make_unit(A, dtype, m, n, lda, k, 1, B, ldb, r, L.s, W, sel, trace,
@@ -590,6 +612,7 @@ struct DistLayout {
   double* btrace;
   int* bnsel;
   double* partial;
+  void* tc_scratch;
   // union step
   char* A0;
   int64_t lda0;
@@ -618,6 +641,7 @@ DistLayout dist_layout(void* ws, size_t cap, int dt, int64_t m, int64_t n, int64
   L.btrace = c.take<double>((size_t)nb * (lb + 1));
   L.bnsel = c.take<int>(nb);
   L.partial = c.take<double>(gcss_f0_partial_doubles(dt, (int)r, (int)n));
+  L.tc_scratch = c.take<char>(tc::colnorm_scratch_bytes((int)m, (int)r));
   L.lda0 = (m + 7) / 8 * 8;
   L.A0 = c.take<char>((size_t)L.lda0 * umax * esize(dt));
   L.ids = c.take<int>(umax);
@@ -679,7 +703,7 @@ css_status gcss_distributed(const void* A, css_dtype dtype, int64_t m, int64_t n
   if (!device_ok()) return CSS_ERR_UNSUPPORTED;
   cudaError_t e;
   // map phase: f^(0) = ||B^T a_i||^2 for every column, kept for the union step
-  if ((e = gcss_f0_simt(dtype, A, lda, (int)m, (int)n, B, ldb, (int)r, L.partial, L.sc.f, s)) != cudaSuccess)
+  if ((e = gcss_f0(dtype, A, lda, m, n, B, ldb, r, L.partial, L.tc_scratch, L.sc.f, L.h, o, s)) != cudaSuccess)
     return cuda_status(e);
   if ((e = cudaMemcpyAsync(L.f0_saved, L.sc.f, sizeof(double) * n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
     return cuda_status(e);
@@ -718,6 +742,11 @@ css_status gcss_distributed(const void* A, css_dtype dtype, int64_t m, int64_t n
       (e = cudaStreamSynchronize(s)) != cudaSuccess)
     return cuda_status(e);
   if (st.code != 0) return (css_status)st.code;
+  {
+    int aux = 0;
+    if (cudaMemcpy(&aux, L.h.aux_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return CSS_ERR_CUDA;
+    if (aux != 0) return (css_status)aux;
+  }
   std::vector<int> ids;
   for (int b = 0; b < nblocks; ++b)
     for (int j = 0; j < hn[b]; ++j) ids.push_back((int)block_offsets[b] + hsel[(size_t)b * l_block + j]);
@@ -815,6 +844,7 @@ css_status css_select_batched(const css_problem* probs, int32_t count, css_dtype
   if (!device_ok()) return CSS_ERR_UNSUPPORTED;
   PhaseTimer tm(o);
   tm.mark(0, s);
+  if (cudaMemsetAsync(L.h.aux_err, 0, sizeof(int), s) != cudaSuccess) return CSS_ERR_CUDA;
   std::vector<UnitDesc> units;
   std::vector<double> work;
   for (int i = 0; i < count; ++i) {

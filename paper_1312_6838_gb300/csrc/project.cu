@@ -6,7 +6,9 @@
 // each slice's partial product is one tile grid of the GEMM, and a second
 // kernel adds the S partials in a fixed order (reproducible results).
 #include "project.cuh"
+#include "tc.cuh"
 
+#include <algorithm>
 #include <cstring>
 
 using namespace css;
@@ -104,9 +106,12 @@ size_t accsz(int dt) { return dt == CSS_F64 ? 8 : 4; }
 
 }  // namespace
 
+constexpr int kMaxTcSlices = 32;
+
 size_t project_workspace_bytes(int dtype, int64_t m, int64_t n, int64_t r) {
   (void)n;
-  return kStatusBytes + align_up((size_t)kSlices * m * r * accsz(dtype));
+  const size_t sl = std::max(kSlices, kMaxTcSlices);
+  return kStatusBytes + align_up((size_t)sl * m * r * accsz(dtype));
 }
 
 extern "C" css_status css_project(const void* A, css_dtype dtype, int64_t m, int64_t n, int64_t lda,
@@ -122,7 +127,36 @@ extern "C" css_status css_project(const void* A, css_dtype dtype, int64_t m, int
   if (ws_bytes < project_workspace_bytes(dtype, m, n, r)) return CSS_ERR_WORKSPACE;
   cudaStream_t s = (cudaStream_t)stream;
   void* partial = (char*)ws + kStatusBytes;
+  int* err = (int*)ws;
+  css_opts o0;
+  css_opts_default(&o0);
+  const css_opts& oo = opts ? *opts : o0;
   cudaError_t e;
+  // BF16 input: tcgen05 split-K GEMM (Algorithm 2's per-block partial sums in
+  // TMEM), then the same fixed-order reduction as the SIMT path
+  if (dtype == CSS_BF16 && oo.init_path != 1 && css::tc::supported(A, lda, (int)m, (int)r) &&
+      css::tc::supported(Omega, ldo, (int)n, (int)r)) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int slices = std::min(kMaxTcSlices, css::tc::project_slices((int)m, sms > 0 ? sms : 1));
+    if ((e = cudaMemsetAsync(err, 0, sizeof(int), s)) != cudaSuccess) return CSS_ERR_CUDA;
+    e = css::tc::project_partials(A, lda, (int)m, (int)n, Omega, ldo, (int)r, slices, (float*)partial, err,
+                                  oo.spin_budget_ns ? oo.spin_budget_ns : 2000000000ull, s);
+    if (e != cudaSuccess) return CSS_ERR_CUDA;
+    const long long tot = m * r;
+    project_reduce_kernel<float><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+        (const float*)partial, slices, (int)m, (int)r, (float*)Bout, ldb);
+    if ((e = cudaGetLastError()) != cudaSuccess) return CSS_ERR_CUDA;
+    if (oo.sync) {
+      int h = 0;
+      if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess)
+        return CSS_ERR_CUDA;
+      if (h) return (css_status)h;
+    }
+    return CSS_OK;
+  }
   switch (dtype) {
     case CSS_F64: e = project_simt<double>(A, lda, Omega, ldo, (int)m, (int)n, (int)r, Bout, ldb, partial, s); break;
     case CSS_F32: e = project_simt<float>(A, lda, Omega, ldo, (int)m, (int)n, (int)r, Bout, ldb, partial, s); break;

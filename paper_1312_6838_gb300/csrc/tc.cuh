@@ -1,0 +1,30 @@
+// Internal interface of the tcgen05 GEMMs (tc_gemm.cu).
+#pragma once
+
+#include "css_common.cuh"
+
+namespace css {
+namespace tc {
+
+// A (BF16, column-major, leading dimension lda) can feed the TMA path with a
+// target width r (<= 512 columns in TMEM).
+bool supported(const void* A, long long lda, int m, int r);
+
+// Number of K slices of the projection for an m-row A on `sms` SMs (<= 32).
+int project_slices(int m, int sms);
+
+// partial[s][i + j*m] = sum over the columns l of slice s of A[i, l] Omega[l, j]
+// (A m x n, Omega n x r, both BF16 column-major); FP32 accumulation in TMEM.
+cudaError_t project_partials(const void* A, long long lda, int m, int n, const void* Om, long long ldo,
+                             int r, int slices, float* partial, int* err, unsigned long long spin_ns,
+                             cudaStream_t s);
+
+// Bytes of scratch for the three BF16 parts of B used by colnorms.
+size_t colnorm_scratch_bytes(int m, int r);
+
+// f[i] = ||B^T A_:i||^2 for the n columns of A (BF16, m x n) and B (FP32, m x r).
+cudaError_t colnorms(const void* A, long long lda, int m, int n, const float* B, long long ldb, int r,
+                     void* scratch, double* f, int* err, unsigned long long spin_ns, cudaStream_t s);
+
+}  // namespace tc
+}  // namespace css

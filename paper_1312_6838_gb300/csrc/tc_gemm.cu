@@ -1,0 +1,436 @@
+// Tensor-core GEMMs (tcgen05 + TMA) for the two dense contractions of the
+// distributed variant:
+//
+//   projection   B = A Omega (Sec. 5.1, Algorithm 2).  D = A[rows, K] Omega[K, :]
+//                per row tile of A and per slice of the K = n columns (the
+//                slices are Algorithm 2's per-mapper partial sums; a second
+//                kernel adds them in a fixed order).  A is M-major (column-
+//                major A), Omega is K-major.
+//   norms        f_i = ||B^T a_i||^2 (Algorithm 3's initial scores).  D = A^T B
+//                per tile of 128 columns of A, both operands K-major; B (FP32)
+//                is split into three BF16 parts B1 + B2 + B3 that all
+//                accumulate into the same TMEM tile, so D carries B's full
+//                FP32 significand; the epilogue sums squares of each row in
+//                FP64.
+//
+// One CTA = 6 warps: warp 0 lane 0 issues TMA loads into a 3-stage shared
+// memory ring (128-byte swizzle), warp 1 owns the TMEM allocation and its lane
+// 0 issues tcgen05.mma (BF16 x BF16 -> FP32, M = 128, up to two MMAs of
+// N <= 256 side by side in TMEM), warps 2-5 read the accumulator back with
+// tcgen05.ld (each warp its 32-lane quarter of TMEM).  Every mbarrier wait is
+// bounded; on expiry an error flag is set and the CTA tears down.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "tc.cuh"
+
+namespace css {
+namespace tc {
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;        // K elements per stage: one 128-byte swizzle row
+constexpr int STAGES = 3;
+constexpr int kThreads = 192;
+constexpr int kTmemCols = 512;
+
+struct Params {
+  int mode;          // 0 projection partials, 1 squared row norms
+  int M;             // rows of D (projection: m; norms: n)
+  int N;             // useful columns of D (r)
+  int n_half;        // columns per MMA (multiple of 16, <= 256)
+  int halves;        // 1 or 2
+  int kb_total;      // K blocks of 64 over the whole contraction
+  int kb_per_cta;    // projection: K blocks per slice
+  int nparts;        // norms: BF16 parts of B
+  int part_stride;   // norms: column offset between parts in B's tensor map
+  int stage_bytes;
+  float* out;        // projection: [slice][M x N] partials (column-major, ld M)
+  double* f;         // norms: f[M]
+  int* err;
+  unsigned long long spin_ns;
+};
+
+// ------------------------------------------------------------- PTX glue -----
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait for the phase with the given parity.  false: timed out (the
+// error flag is set) or another role already failed.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err,
+                                          unsigned long long budget) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  while (true) {
+#pragma unroll 1
+    for (int i = 0; i < 32; ++i)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (*(volatile int*)err != 0) return false;
+    if (gtimer() - t0 > budget) {
+      atomicCAS(err, 0, (int)CSS_ERR_TIMEOUT);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0,
+                                            int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+      "[%2];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(bar), "r"(c0), "r"(c1)
+      : "memory");
+}
+// Shared-memory matrix descriptor, 128-byte swizzle (sm_100 format).
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+// Instruction descriptor: kind::f16, BF16 x BF16 -> FP32.
+__device__ __forceinline__ uint32_t make_idesc(int N, int M, bool a_mn, bool b_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                     uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <bool A_MN>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Params P) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int a_bytes = BM * BK * 2;
+  uint8_t* bars_base = smem + STAGES * P.stage_bytes;
+  uint64_t* full = (uint64_t*)bars_base;
+  uint64_t* empty = full + STAGES;
+  uint64_t* done = empty + STAGES;
+  uint32_t* s_tmem = (uint32_t*)(done + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // work of this CTA
+  const int tile0 = blockIdx.x * BM;
+  int kb_begin = 0, kb_end = P.kb_total;
+  if (P.mode == 0) {
+    kb_begin = blockIdx.y * P.kb_per_cta;
+    kb_end = min(P.kb_total, kb_begin + P.kb_per_cta);
+  }
+  const int parts = P.mode == 1 ? P.nparts : 1;
+  const int n_it = max(0, kb_end - kb_begin) * parts;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *s_tmem;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------------ producer
+    int issued = 0;
+    for (int it = 0; it < n_it; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+      if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u, P.err, P.spin_ns)) break;
+      const int kb = kb_begin + it / parts, part = it % parts;
+      const int k0 = kb * BK;
+      uint8_t* sa = smem + s * P.stage_bytes;
+      uint8_t* sb = sa + a_bytes;
+      const uint32_t fb = smem_u32(&full[s]);
+      mbar_expect_tx(fb, (uint32_t)(a_bytes + P.halves * P.n_half * BK * 2));
+      if (A_MN) {
+        tma_load_2d(smem_u32(sa), &tmA, fb, tile0, k0);
+        tma_load_2d(smem_u32(sa + 64 * BK * 2), &tmA, fb, tile0 + 64, k0);
+      } else {
+        tma_load_2d(smem_u32(sa), &tmA, fb, k0, tile0);
+      }
+      for (int h = 0; h < P.halves; ++h)
+        tma_load_2d(smem_u32(sb + h * P.n_half * BK * 2), &tmB, fb, k0,
+                    part * P.part_stride + h * P.n_half);
+      issued = it + 1;
+    }
+    // on failure: let the copies already issued land before the CTA exits
+    if (issued < n_it) {
+      for (int it = max(0, issued - STAGES); it < issued; ++it) {
+        const int s = it % STAGES;
+        mbar_wait(smem_u32(&full[s]), (uint32_t)((it / STAGES) & 1), P.err, P.spin_ns);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------------------------------------------------- MMA issuer
+    const uint32_t idesc = make_idesc(P.n_half, BM, A_MN, false);
+    for (int it = 0; it < n_it; ++it) {
+      const int s = it % STAGES;
+      const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+      if (!mbar_wait(smem_u32(&full[s]), ph, P.err, P.spin_ns)) break;
+      fence_after();
+      const uint32_t sa = smem_u32(smem + s * P.stage_bytes);
+      const uint32_t sb = sa + a_bytes;
+#pragma unroll
+      for (int ks = 0; ks < BK / 16; ++ks) {
+        // A: M-major -> 16 K rows of 128 bytes per step; K-major -> 32 bytes
+        const uint64_t ad = A_MN ? make_desc(sa + ks * 2048, 64 * BK * 2, 1024)
+                                 : make_desc(sa + ks * 32, 16, 1024);
+        for (int h = 0; h < P.halves; ++h) {
+          const uint64_t bd = make_desc(sb + h * P.n_half * BK * 2 + ks * 32, 16, 1024);
+          umma(tmem + h * P.n_half, ad, bd, idesc, (it > 0 || ks > 0) ? 1u : 0u);
+        }
+      }
+      umma_commit(smem_u32(&empty[s]));
+    }
+    umma_commit(smem_u32(done));
+  } else if (warp >= 2) {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;                  // TMEM lane quarter of this warp
+    const int row = tile0 + q * 32 + lane;
+    bool ok = mbar_wait(smem_u32(done), 0u, P.err, P.spin_ns) && *(volatile int*)P.err == 0;
+    ok = __all_sync(0xffffffffu, ok);   // tcgen05.ld is warp-collective
+    fence_after();
+    if (ok && n_it == 0) {
+      // empty K slice: its partial product is zero (TMEM was never written)
+      if (P.mode == 0 && row < P.M)
+        for (int j = 0; j < P.N; ++j) P.out[(long long)blockIdx.y * P.M * P.N + (long long)j * P.M + row] = 0.f;
+      if (P.mode == 1 && row < P.M) P.f[row] = 0.0;
+    } else if (ok) {
+      double acc = 0.0;
+      const int ncols = P.halves * P.n_half;
+      for (int j0 = 0; j0 < ncols; j0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)j0, v);
+        if (row < P.M) {
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            const int j = j0 + jj;
+            if (j < P.N) {
+              if (P.mode == 0)
+                P.out[(long long)blockIdx.y * P.M * P.N + (long long)j * P.M + row] = v[jj];
+              else
+                acc += (double)v[jj] * (double)v[jj];
+            }
+          }
+        }
+      }
+      if (P.mode == 1 && row < P.M) P.f[row] = acc;
+    }
+    fence_before();
+  }
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
+// B (FP32, m x r, ldb) -> three BF16 parts B1 + B2 + B3 (m x rpad each, ld mpad),
+// laid out side by side: part p, column j at Bp[(p * rpad + j) * mpad + i].
+__global__ void split3_kernel(const float* __restrict__ B, long long ldb, int m, int r, int mpad,
+                              int rpad, __nv_bfloat16* __restrict__ Bp) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long tot = (long long)mpad * rpad;
+  if (idx >= tot) return;
+  const int i = (int)(idx % mpad), j = (int)(idx / mpad);
+  float v = (i < m && j < r) ? B[(long long)j * ldb + i] : 0.f;
+  __nv_bfloat16 b1 = __float2bfloat16_rn(v);
+  v -= __bfloat162float(b1);
+  __nv_bfloat16 b2 = __float2bfloat16_rn(v);
+  v -= __bfloat162float(b2);
+  __nv_bfloat16 b3 = __float2bfloat16_rn(v);
+  Bp[(long long)(0 * rpad + j) * mpad + i] = b1;
+  Bp[(long long)(1 * rpad + j) * mpad + i] = b2;
+  Bp[(long long)(2 * rpad + j) * mpad + i] = b3;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// 2-D BF16 tensor map: dim0 (contiguous) x dim1 with row pitch ld elements,
+// box {64, box1}, 128-byte swizzle, zero fill outside the tensor.
+bool make_map(CUtensorMap* map, const void* base, uint64_t dim0, uint64_t dim1, uint64_t ld,
+              uint32_t box1) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t gdim[2] = {dim0, dim1};
+  const cuuint64_t gstride[1] = {ld * 2};
+  const cuuint32_t box[2] = {64, box1};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), gdim, gstride, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+void halves_for(int r, int& n_half, int& halves) {
+  if (r <= 256) {
+    halves = 1;
+    n_half = (r + 15) / 16 * 16;
+  } else {
+    halves = 2;
+    n_half = ((r + 1) / 2 + 15) / 16 * 16;
+  }
+}
+
+size_t smem_for(int stage_bytes) { return (size_t)STAGES * stage_bytes + 256 + 1024; }
+
+}  // namespace
+
+bool supported(const void* A, long long lda, int m, int r) {
+  if (r < 1 || r > 512 || m < 1) return false;
+  if (((uintptr_t)A & 15u) != 0 || (lda % 8) != 0) return false;
+  return encode_fn() != nullptr;
+}
+
+int project_slices(int m, int sms) {
+  const int mt = (m + BM - 1) / BM;
+  return std::max(1, sms / mt);
+}
+
+cudaError_t project_partials(const void* A, long long lda, int m, int n, const void* Om, long long ldo,
+                             int r, int slices, float* partial, int* err, unsigned long long spin_ns,
+                             cudaStream_t s) {
+  CUtensorMap ta, tb;
+  int n_half, halves;
+  halves_for(r, n_half, halves);
+  if (!make_map(&ta, A, (uint64_t)m, (uint64_t)n, (uint64_t)lda, BK)) return cudaErrorInvalidValue;
+  if (!make_map(&tb, Om, (uint64_t)n, (uint64_t)r, (uint64_t)ldo, (uint32_t)n_half))
+    return cudaErrorInvalidValue;
+  Params P{};
+  P.mode = 0;
+  P.M = m;
+  P.N = r;
+  P.n_half = n_half;
+  P.halves = halves;
+  P.kb_total = (n + BK - 1) / BK;
+  P.kb_per_cta = (P.kb_total + slices - 1) / slices;
+  P.nparts = 1;
+  P.part_stride = 0;
+  P.stage_bytes = BM * BK * 2 + halves * n_half * BK * 2;
+  P.out = partial;
+  P.err = err;
+  P.spin_ns = spin_ns;
+  const size_t smem = smem_for(P.stage_bytes);
+  cudaError_t e = cudaFuncSetAttribute(tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((m + BM - 1) / BM, slices);
+  tc_kernel<true><<<grid, kThreads, smem, s>>>(ta, tb, P);
+  return cudaGetLastError();
+}
+
+size_t colnorm_scratch_bytes(int m, int r) {
+  const int mpad = (m + 7) / 8 * 8;
+  const int rpad = (r + 15) / 16 * 16;
+  return (size_t)mpad * 3 * rpad * 2;
+}
+
+cudaError_t colnorms(const void* A, long long lda, int m, int n, const float* B, long long ldb, int r,
+                     void* scratch, double* f, int* err, unsigned long long spin_ns, cudaStream_t s) {
+  const int mpad = (m + 7) / 8 * 8;
+  const int rpad = (r + 15) / 16 * 16;
+  __nv_bfloat16* Bp = (__nv_bfloat16*)scratch;
+  const long long tot = (long long)mpad * rpad;
+  split3_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(B, ldb, m, r, mpad, rpad, Bp);
+  CUtensorMap ta, tb;
+  int n_half, halves;
+  halves_for(r, n_half, halves);
+  if (!make_map(&ta, A, (uint64_t)m, (uint64_t)n, (uint64_t)lda, BM)) return cudaErrorInvalidValue;
+  if (!make_map(&tb, Bp, (uint64_t)mpad, (uint64_t)(3 * rpad), (uint64_t)mpad, (uint32_t)n_half))
+    return cudaErrorInvalidValue;
+  Params P{};
+  P.mode = 1;
+  P.M = n;
+  P.N = r;
+  P.n_half = n_half;
+  P.halves = halves;
+  P.kb_total = (m + BK - 1) / BK;
+  P.kb_per_cta = P.kb_total;
+  P.nparts = 3;
+  P.part_stride = rpad;
+  P.stage_bytes = BM * BK * 2 + halves * n_half * BK * 2;
+  P.f = f;
+  P.err = err;
+  P.spin_ns = spin_ns;
+  const size_t smem = smem_for(P.stage_bytes);
+  cudaError_t e = cudaFuncSetAttribute(tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((n + BM - 1) / BM, 1);
+  tc_kernel<false><<<grid, kThreads, smem, s>>>(ta, tb, P);
+  return cudaGetLastError();
+}
+
+}  // namespace tc
+}  // namespace css

@@ -99,8 +99,9 @@ class Selection:
 
 
 def _opts(tau_rel=None, forced=None, score_mode=0, grid_ctas=0, tile_cols=0, spin_budget_ns=0,
-          sync=True, diag=None):
+          sync=True, diag=None, init_path=0):
     o = L.default_opts()
+    o.init_path = int(init_path)
     if tau_rel is not None:
         o.tau_rel = float(tau_rel)
     if forced is not None:
@@ -167,7 +168,7 @@ def select(A: torch.Tensor, k: int, *, tau_rel=None, forced=None, return_W=False
 
 def gcss_select(A: torch.Tensor, B: torch.Tensor, k: int, *, tau_rel=None, forced=None,
                 return_W=False, diag=False, grid_ctas=0, tile_cols=0, spin_budget_ns=0,
-                stream=None) -> Selection:
+                stream=None, init_path=0) -> Selection:
     """Greedy generalized CSS (Algorithm 3): columns of A reconstructing B.
     B must be float64 when A is float64, float32 otherwise (column-major)."""
     m, n, lda = _colmajor(A)
@@ -189,7 +190,7 @@ def gcss_select(A: torch.Tensor, B: torch.Tensor, k: int, *, tau_rel=None, force
         dg = (torch.full((k,), -1, dtype=torch.int32, device=dev),
               torch.empty(n, dtype=torch.float64, device=dev),
               torch.empty(n, dtype=torch.float64, device=dev))
-    o = _opts(tau_rel, fz, 0, grid_ctas, tile_cols, spin_budget_ns, True, dg)
+    o = _opts(tau_rel, fz, 0, grid_ctas, tile_cols, spin_budget_ns, True, dg, init_path)
     nbytes = lib.css_workspace_size(L.CSS_OP_GCSS, dt, m, n, r, k, 0, C.byref(o))
     if nbytes == 0:
         raise ValueError("invalid sizes for gcss_select")
@@ -214,7 +215,8 @@ class Distributed:
 
 
 def distributed(A: torch.Tensor, B: torch.Tensor, block_offsets: Sequence[int], l_block: int,
-                k: int, *, tau_rel=None, grid_ctas=0, tile_cols=0, stream=None) -> Distributed:
+                k: int, *, tau_rel=None, grid_ctas=0, tile_cols=0, stream=None,
+                init_path=0) -> Distributed:
     """Distributed CSS (Algorithm 4) with the concise representation B."""
     m, n, lda = _colmajor(A)
     mb, r, ldb = _colmajor(B, "B")
@@ -229,7 +231,7 @@ def distributed(A: torch.Tensor, B: torch.Tensor, block_offsets: Sequence[int], 
     trace = torch.empty(k + 1, dtype=torch.float64, device=dev)
     nsel = torch.zeros(1, dtype=torch.int32, device=dev)
     bsel = torch.empty((nb, l_block), dtype=torch.int32, device=dev)
-    o = _opts(tau_rel, None, 0, grid_ctas, tile_cols)
+    o = _opts(tau_rel, None, 0, grid_ctas, tile_cols, init_path=init_path)
     nbytes = lib.gcss_distributed_workspace_size(dt, m, n, r, offs, nb, l_block, k)
     if nbytes == 0:
         raise ValueError("invalid block partition or sizes")
@@ -241,7 +243,8 @@ def distributed(A: torch.Tensor, B: torch.Tensor, block_offsets: Sequence[int], 
     return Distributed(sel, trace, int(nsel.item()), bsel, code)
 
 
-def project(A: torch.Tensor, Omega: torch.Tensor, *, out=None, stream=None, sync=True):
+def project(A: torch.Tensor, Omega: torch.Tensor, *, out=None, stream=None, sync=True,
+            init_path=0):
     """B = A Omega (Sec. 5.1).  Omega is n x r column-major of A's dtype.
     Returns B (m x r, column-major) in float32 (float64 for float64 input)."""
     m, n, lda = _colmajor(A)
@@ -253,7 +256,7 @@ def project(A: torch.Tensor, Omega: torch.Tensor, *, out=None, stream=None, sync
     lib = L.load()
     B = out if out is not None else empty_colmajor(m, r, _ACC[A.dtype], dev)
     _, _, ldb = _colmajor(B, "B")
-    o = _opts(sync=sync)
+    o = _opts(sync=sync, init_path=init_path)
     nbytes = lib.css_workspace_size(L.CSS_OP_PROJECT, dt, m, n, r, 0, 0, C.byref(o))
     _keep, ws = _workspace(nbytes, dev)
     code = lib.css_project(_ptr(A), dt, m, n, lda, _ptr(Omega), r, ldo, _ptr(B), ldb, _ptr(ws),

@@ -1,0 +1,56 @@
+"""The tcgen05 (tensor-core) GEMMs: B = A Omega and the GCSS initial scores
+||B^T a_i||^2 for BF16 A, against the oracle and against the SIMT kernels."""
+import numpy as np
+import pytest
+import torch
+
+import css_inputs as ci
+from oracle import css_oracle as O
+from tests.gpu_helpers import dev_matrix, teacher_forced_parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def css():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1312_6838_gb300 import build, css as mod
+    build.build()
+    return mod
+
+
+@pytest.mark.parametrize("shape", [(256, 1024, 64), (200, 777, 16), (136, 5000, 400),
+                                   (2048, 16384, 400), (512, 3000, 300)])
+def test_projection_tensor_cores(css, shape):
+    m, n, r = shape
+    A_np = ci.lowrank_uv(m, n, 8, 0.1, 41 + m).astype(np.float32)
+    Om_np = ci.gaussian_omega(n, r, 42, dtype=np.float32)
+    A, Av = dev_matrix(A_np, torch.bfloat16)
+    Om, Ov = dev_matrix(Om_np, torch.bfloat16)
+    B_tc = css.project(A, Om).cpu().numpy().astype(np.float64)
+    B_simt = css.project(A, Om, init_path=1).cpu().numpy().astype(np.float64)
+    ref = O.random_projection(Av, Ov)
+    bound = np.abs(Av) @ np.abs(Ov)
+    eps = 2.0 ** -24
+    assert np.all(np.abs(B_tc - ref) <= 4 * np.sqrt(n) * eps * bound + 1e-30)
+    assert np.all(np.abs(B_simt - ref) <= 4 * np.sqrt(n) * eps * bound + 1e-30)
+
+
+@pytest.mark.parametrize("shape", [(64, 700, 24, 8), (256, 3000, 400, 12), (136, 1000, 300, 10)])
+def test_gcss_initial_scores_tensor_cores(css, shape):
+    m, n, r, k = shape
+    A_np = ci.lowrank_uv(m, n, 2 * k, 0.05, 77 + m)
+    B_np = A_np @ ci.gaussian_omega(n, r, 78, dtype=np.float64)
+    A, Av = dev_matrix(A_np, torch.bfloat16)
+    Bv = B_np.astype(np.float32).astype(np.float64)
+    from paper_1312_6838_gb300 import css as C
+    B = C.to_colmajor(torch.from_numpy(Bv).float().cuda())
+    ref = O.greedy_gcss(Av, Bv, k, tau_rel=1e-6, keep_scores=True)
+    teacher_forced_parity(
+        lambda forced: css.gcss_select(A, B, k, forced=forced or None).indices.cpu().tolist(), ref,
+        m=m, dtype=torch.bfloat16)
+    a = css.gcss_select(A, B, k)
+    b = css.gcss_select(A, B, k, init_path=1)
+    np.testing.assert_allclose(a.trace.cpu().numpy(), b.trace.cpu().numpy(), rtol=0,
+                               atol=1e-5 * ref.trace[0])

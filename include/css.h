@@ -131,8 +131,9 @@ typedef struct {
     /* Dense-GEMM path: 0 = automatic (tcgen05 tensor cores for BF16 input
        when the layout allows TMA: 16-byte aligned base, leading dimension a
        multiple of 8, r <= 512), 1 = CUDA-core (SIMT) kernels only.  Used by
-       css_project and by the initial scores of gcss_select /
-       gcss_distributed. */
+       css_project, by the initial scores of gcss_select / gcss_distributed,
+       and by css_select's C = A A^T and f^(0) (C split into three BF16 parts
+       so that f^(0) keeps FP32 accuracy). */
     int32_t init_path;
     int32_t reserved[7];
     /* DEVICE uint64[k * 16] or NULL (css_select, gcss_select): per-iteration

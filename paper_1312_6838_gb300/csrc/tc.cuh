@@ -26,5 +26,14 @@ size_t colnorm_scratch_bytes(int m, int r);
 cudaError_t colnorms(const void* A, long long lda, int m, int n, const float* B, long long ldb, int r,
                      void* scratch, double* f, int* err, unsigned long long spin_ns, cudaStream_t s);
 
+// Scratch bytes of css_f0 (C in FP32, its three BF16 parts, row-tile partials).
+size_t css_f0_scratch_bytes(int m, int n);
+
+// Algorithm 1's initial scores for BF16 A: C = A A^T on tensor cores (FP32
+// accumulation of exact BF16 products), C split into three BF16 parts, and
+// f[i] = A_:i^T C A_:i from the column dots of A with C A (FP64 sums).
+cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, double* f, int* err,
+                   unsigned long long spin_ns, cudaStream_t s);
+
 }  // namespace tc
 }  // namespace css

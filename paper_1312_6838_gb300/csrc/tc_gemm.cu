@@ -35,18 +35,22 @@ constexpr int kThreads = 192;
 constexpr int kTmemCols = 512;
 
 struct Params {
-  int mode;          // 0 projection partials, 1 squared row norms
-  int M;             // rows of D (projection: m; norms: n)
-  int N;             // useful columns of D (r)
+  int mode;          // 0 projection partials, 1 squared row norms, 2 C = A A^T, 3 column dots
+  int M;             // rows of D (projection: m; norms: n; syrk, column dots: m)
+  int N;             // useful columns of D (r; syrk: m; column dots: n)
   int n_half;        // columns per MMA (multiple of 16, <= 256)
   int halves;        // 1 or 2
+  int n_tile;        // syrk / column dots: columns of D per CTA (blockIdx.y tiles)
   int kb_total;      // K blocks of 64 over the whole contraction
   int kb_per_cta;    // projection: K blocks per slice
-  int nparts;        // norms: BF16 parts of B
-  int part_stride;   // norms: column offset between parts in B's tensor map
+  int nparts;        // BF16 parts summed into the accumulator
+  int a_part_stride; // column offset between parts in A's tensor map
+  int b_part_stride; // column offset between parts in B's tensor map
   int stage_bytes;
-  float* out;        // projection: [slice][M x N] partials (column-major, ld M)
-  double* f;         // norms: f[M]
+  float* out;        // projection: [slice][M x N] partials; syrk: C (ld M)
+  double* f;         // norms: f[M]; column dots: partial[M-tile][N]
+  const __nv_bfloat16* Acol;  // column dots: the BF16 matrix dotted with D's columns
+  long long lda_col;
   int* err;
   unsigned long long spin_ns;
 };
@@ -149,7 +153,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <bool A_MN>
+template <bool A_MN, bool B_MN>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Params P) {
   extern __shared__ uint8_t smem_raw[];
@@ -165,11 +169,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   // work of this CTA
   const int tile0 = blockIdx.x * BM;
   int kb_begin = 0, kb_end = P.kb_total;
+  int ntile0 = 0;
   if (P.mode == 0) {
     kb_begin = blockIdx.y * P.kb_per_cta;
     kb_end = min(P.kb_total, kb_begin + P.kb_per_cta);
+  } else if (P.mode >= 2) {
+    ntile0 = blockIdx.y * P.n_tile;
   }
-  const int parts = P.mode == 1 ? P.nparts : 1;
+  const int parts = P.nparts;
   const int n_it = max(0, kb_end - kb_begin) * parts;
 
   if (threadIdx.x == 0) {
@@ -208,11 +215,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         tma_load_2d(smem_u32(sa), &tmA, fb, tile0, k0);
         tma_load_2d(smem_u32(sa + 64 * BK * 2), &tmA, fb, tile0 + 64, k0);
       } else {
-        tma_load_2d(smem_u32(sa), &tmA, fb, k0, tile0);
+        tma_load_2d(smem_u32(sa), &tmA, fb, k0, part * P.a_part_stride + tile0);
       }
-      for (int h = 0; h < P.halves; ++h)
-        tma_load_2d(smem_u32(sb + h * P.n_half * BK * 2), &tmB, fb, k0,
-                    part * P.part_stride + h * P.n_half);
+      if (B_MN) {
+        // N-major B: 64-row boxes stacked 8 KB apart (the descriptor's LBO)
+        for (int q = 0; q < P.halves * P.n_half / 64; ++q)
+          tma_load_2d(smem_u32(sb + q * 64 * BK * 2), &tmB, fb, ntile0 + 64 * q, k0);
+      } else {
+        for (int h = 0; h < P.halves; ++h)
+          tma_load_2d(smem_u32(sb + h * P.n_half * BK * 2), &tmB, fb, k0,
+                      ntile0 + part * P.b_part_stride + h * P.n_half);
+      }
       issued = it + 1;
     }
     // on failure: let the copies already issued land before the CTA exits
@@ -224,7 +237,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------------------------------------------------- MMA issuer
-    const uint32_t idesc = make_idesc(P.n_half, BM, A_MN, false);
+    const uint32_t idesc = make_idesc(P.n_half, BM, A_MN, B_MN);
     for (int it = 0; it < n_it; ++it) {
       const int s = it % STAGES;
       const uint32_t ph = (uint32_t)((it / STAGES) & 1);
@@ -238,7 +251,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint64_t ad = A_MN ? make_desc(sa + ks * 2048, 64 * BK * 2, 1024)
                                  : make_desc(sa + ks * 32, 16, 1024);
         for (int h = 0; h < P.halves; ++h) {
-          const uint64_t bd = make_desc(sb + h * P.n_half * BK * 2 + ks * 32, 16, 1024);
+          const uint64_t bd = B_MN ? make_desc(sb + h * P.n_half * BK * 2 + ks * 2048, 64 * BK * 2, 1024)
+                                   : make_desc(sb + h * P.n_half * BK * 2 + ks * 32, 16, 1024);
           umma(tmem + h * P.n_half, ad, bd, idesc, (it > 0 || ks > 0) ? 1u : 0u);
         }
       }
@@ -250,13 +264,65 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int q = warp & 3;                  // TMEM lane quarter of this warp
     const int row = tile0 + q * 32 + lane;
     bool ok = mbar_wait(smem_u32(done), 0u, P.err, P.spin_ns) && *(volatile int*)P.err == 0;
-    ok = __all_sync(0xffffffffu, ok);   // tcgen05.ld is warp-collective
+    // one decision for all four epilogue warps (tcgen05.ld is warp-collective
+    // and the column-dot epilogue synchronises the four warps)
+    {
+      uint32_t all;
+      asm volatile(
+          "{\n .reg .pred pa, pb;\n setp.ne.u32 pa, %1, 0;\n"
+          " barrier.red.and.pred pb, 1, 128, pa;\n selp.u32 %0, 1, 0, pb;\n}"
+          : "=r"(all)
+          : "r"((uint32_t)ok)
+          : "memory");
+      ok = all != 0;
+    }
     fence_after();
     if (ok && n_it == 0) {
       // empty K slice: its partial product is zero (TMEM was never written)
       if (P.mode == 0 && row < P.M)
         for (int j = 0; j < P.N; ++j) P.out[(long long)blockIdx.y * P.M * P.N + (long long)j * P.M + row] = 0.f;
       if (P.mode == 1 && row < P.M) P.f[row] = 0.0;
+    } else if (ok && P.mode == 3) {
+      // column dots: partial[M-tile][c] = sum over this tile's rows r of
+      // Acol[r, c] * D[r, c]; rows are TMEM lanes, so each 16-column chunk is
+      // reduced across the warp (transpose reduction) and then across warps
+      __shared__ double cred[4][16];
+      const int ncols = P.halves * P.n_half;
+      for (int j0 = 0; j0 < ncols; j0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)j0, v);
+        double pr[16];
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+          const int c = ntile0 + j0 + jj;
+          pr[jj] = 0.0;
+          if (row < P.M && c < P.N) {
+            const float a = __bfloat162float(P.Acol[(long long)c * P.lda_col + row]);
+            pr[jj] = (double)a * (double)v[jj];
+          }
+        }
+        // 16 values over 32 lanes: lane L ends with the warp sum of index L >> 1
+#pragma unroll
+        for (int st = 0; st < 4; ++st) {
+          const int mask = 16 >> st, half = 8 >> st;
+          const bool up = (lane & mask) != 0;
+#pragma unroll
+          for (int jj = 0; jj < half; ++jj) {
+            const double send = up ? pr[jj] : pr[jj + half];
+            const double keep = up ? pr[jj + half] : pr[jj];
+            pr[jj] = keep + __shfl_xor_sync(0xffffffffu, send, mask);
+          }
+        }
+        double tot = pr[0] + __shfl_xor_sync(0xffffffffu, pr[0], 1);
+        if ((lane & 1) == 0) cred[q][lane >> 1] = tot;
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (q == 0 && lane < 16) {
+          const int c = ntile0 + j0 + lane;
+          if (c < P.N)
+            P.f[(long long)blockIdx.x * P.N + c] = cred[0][lane] + cred[1][lane] + cred[2][lane] + cred[3][lane];
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+      }
     } else if (ok) {
       double acc = 0.0;
       const int ncols = P.halves * P.n_half;
@@ -267,7 +333,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int jj = 0; jj < 16; ++jj) {
             const int j = j0 + jj;
-            if (j < P.N) {
+            if (P.mode == 2) {
+              const int c = ntile0 + j;
+              if (c < P.N) P.out[(long long)c * P.M + row] = v[jj];
+            } else if (j < P.N) {
               if (P.mode == 0)
                 P.out[(long long)blockIdx.y * P.M * P.N + (long long)j * P.M + row] = v[jj];
               else
@@ -378,16 +447,15 @@ cudaError_t project_partials(const void* A, long long lda, int m, int n, const v
   P.kb_total = (n + BK - 1) / BK;
   P.kb_per_cta = (P.kb_total + slices - 1) / slices;
   P.nparts = 1;
-  P.part_stride = 0;
   P.stage_bytes = BM * BK * 2 + halves * n_half * BK * 2;
   P.out = partial;
   P.err = err;
   P.spin_ns = spin_ns;
   const size_t smem = smem_for(P.stage_bytes);
-  cudaError_t e = cudaFuncSetAttribute(tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(tc_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((m + BM - 1) / BM, slices);
-  tc_kernel<true><<<grid, kThreads, smem, s>>>(ta, tb, P);
+  tc_kernel<true, false><<<grid, kThreads, smem, s>>>(ta, tb, P);
   return cudaGetLastError();
 }
 
@@ -419,16 +487,106 @@ cudaError_t colnorms(const void* A, long long lda, int m, int n, const float* B,
   P.kb_total = (m + BK - 1) / BK;
   P.kb_per_cta = P.kb_total;
   P.nparts = 3;
-  P.part_stride = rpad;
+  P.b_part_stride = rpad;
   P.stage_bytes = BM * BK * 2 + halves * n_half * BK * 2;
   P.f = f;
   P.err = err;
   P.spin_ns = spin_ns;
   const size_t smem = smem_for(P.stage_bytes);
-  cudaError_t e = cudaFuncSetAttribute(tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(tc_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((n + BM - 1) / BM, 1);
-  tc_kernel<false><<<grid, kThreads, smem, s>>>(ta, tb, P);
+  tc_kernel<false, false><<<grid, kThreads, smem, s>>>(ta, tb, P);
+  return cudaGetLastError();
+}
+
+__global__ void sum_rows_kernel(const double* __restrict__ partial, int nblk, int n,
+                                double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += partial[(long long)b * n + i];
+  out[i] = s;
+}
+
+size_t css_f0_scratch_bytes(int m, int n) {
+  const int mpad = (m + 7) / 8 * 8;
+  const int rpad = (m + 15) / 16 * 16;
+  const size_t c = align_up((size_t)m * m * 4);
+  const size_t parts = align_up((size_t)mpad * 3 * rpad * 2);
+  const size_t part = align_up((size_t)((m + BM - 1) / BM) * n * 8);
+  return c + parts + part;
+}
+
+cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, double* f, int* err,
+                   unsigned long long spin_ns, cudaStream_t s) {
+  const int mpad = (m + 7) / 8 * 8;
+  const int rpad = (m + 15) / 16 * 16;
+  float* C = (float*)scratch;
+  __nv_bfloat16* Cp = (__nv_bfloat16*)((char*)scratch + align_up((size_t)m * m * 4));
+  double* partial = (double*)((char*)Cp + align_up((size_t)mpad * 3 * rpad * 2));
+  cudaError_t e;
+  // C = A A^T: both operands are A, row-major in K (= the column index)
+  {
+    CUtensorMap ta;
+    if (!make_map(&ta, A, (uint64_t)m, (uint64_t)n, (uint64_t)lda, BK)) return cudaErrorInvalidValue;
+    Params P{};
+    P.mode = 2;
+    P.M = m;
+    P.N = m;
+    P.n_half = 256;
+    P.halves = 1;
+    P.n_tile = 256;
+    P.kb_total = (n + BK - 1) / BK;
+    P.kb_per_cta = P.kb_total;
+    P.nparts = 1;
+    P.stage_bytes = BM * BK * 2 + 256 * BK * 2;
+    P.out = C;
+    P.err = err;
+    P.spin_ns = spin_ns;
+    const size_t smem = smem_for(P.stage_bytes);
+    if ((e = cudaFuncSetAttribute(tc_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+      return e;
+    dim3 grid((m + BM - 1) / BM, (m + 255) / 256);
+    tc_kernel<true, true><<<grid, kThreads, smem, s>>>(ta, ta, P);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  // C = C1 + C2 + C3 in BF16
+  {
+    const long long tot = (long long)mpad * rpad;
+    split3_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(C, m, m, m, mpad, rpad, Cp);
+  }
+  // partial[M-tile][i] = sum over the tile's rows r of A[r, i] (C A)[r, i]
+  {
+    CUtensorMap ta, tb;
+    if (!make_map(&ta, Cp, (uint64_t)mpad, (uint64_t)(3 * rpad), (uint64_t)mpad, BM)) return cudaErrorInvalidValue;
+    if (!make_map(&tb, A, (uint64_t)m, (uint64_t)n, (uint64_t)lda, 256)) return cudaErrorInvalidValue;
+    Params P{};
+    P.mode = 3;
+    P.M = m;
+    P.N = n;
+    P.n_half = 256;
+    P.halves = 1;
+    P.n_tile = 256;
+    P.kb_total = (m + BK - 1) / BK;
+    P.kb_per_cta = P.kb_total;
+    P.nparts = 3;
+    P.a_part_stride = rpad;
+    P.b_part_stride = 0;
+    P.stage_bytes = BM * BK * 2 + 256 * BK * 2;
+    P.f = partial;
+    P.Acol = (const __nv_bfloat16*)A;
+    P.lda_col = lda;
+    P.err = err;
+    P.spin_ns = spin_ns;
+    const size_t smem = smem_for(P.stage_bytes);
+    if ((e = cudaFuncSetAttribute(tc_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+      return e;
+    dim3 grid((m + BM - 1) / BM, (n + 255) / 256);
+    tc_kernel<false, false><<<grid, kThreads, smem, s>>>(ta, tb, P);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  sum_rows_kernel<<<(n + 255) / 256, 256, 0, s>>>(partial, (m + BM - 1) / BM, n, f);
   return cudaGetLastError();
 }
 

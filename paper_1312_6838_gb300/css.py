@@ -128,7 +128,7 @@ def _prep_forced(forced, device):
 
 def select(A: torch.Tensor, k: int, *, tau_rel=None, forced=None, return_W=False, diag=False,
            score_mode=0, grid_ctas=0, tile_cols=0, spin_budget_ns=0, stream=None,
-           timing=False, phase_trace=False) -> Selection:
+           timing=False, phase_trace=False, init_path=0) -> Selection:
     """Greedy CSS (Algorithm 1) of the columns of A (column-major, on the GPU)."""
     m, n, lda = _colmajor(A)
     dev = A.device
@@ -144,7 +144,7 @@ def select(A: torch.Tensor, k: int, *, tau_rel=None, forced=None, return_W=False
         dg = (torch.full((k,), -1, dtype=torch.int32, device=dev),
               torch.empty(n, dtype=torch.float64, device=dev),
               torch.empty(n, dtype=torch.float64, device=dev))
-    o = _opts(tau_rel, fz, score_mode, grid_ctas, tile_cols, spin_budget_ns, True, dg)
+    o = _opts(tau_rel, fz, score_mode, grid_ctas, tile_cols, spin_budget_ns, True, dg, init_path)
     tms = (C.c_double * 2)() if timing else None
     if tms is not None:
         o.timing_ms = C.cast(tms, C.c_void_p)

@@ -54,3 +54,23 @@ def test_gcss_initial_scores_tensor_cores(css, shape):
     b = css.gcss_select(A, B, k, init_path=1)
     np.testing.assert_allclose(a.trace.cpu().numpy(), b.trace.cpu().numpy(), rtol=0,
                                atol=1e-5 * ref.trace[0])
+
+
+@pytest.mark.parametrize("shape", [(256, 3000, 12), (200, 1000, 10), (520, 2600, 16)])
+def test_css_initial_scores_tensor_cores(css, shape):
+    """C = A A^T and f0 = a_i^T C a_i on tensor cores (BF16 A): parity with the
+    oracle and the same trace as the SIMT initialisation."""
+    m, n, k = shape
+    A_np = ci.lowrank_uv(m, n, 2 * k, 0.05, 91 + m)
+    A, Av = dev_matrix(A_np, torch.bfloat16)
+    ref = O.greedy_css(Av, k, tau_rel=1e-6, keep_scores=True)
+    teacher_forced_parity(
+        lambda forced: css.select(A, k, forced=forced or None).indices.cpu().tolist(), ref,
+        m=m, dtype=torch.bfloat16)
+    a = css.select(A, k, diag=True)
+    b = css.select(A, k, diag=True, init_path=1)
+    np.testing.assert_allclose(a.trace.cpu().numpy(), b.trace.cpu().numpy(), rtol=0,
+                               atol=1e-5 * ref.trace[0])
+    fa, fb = a.diag_f.cpu().numpy(), b.diag_f.cpu().numpy()
+    f0 = ref.fs[0]
+    assert np.max(np.abs(fa - fb)) <= 1e-5 * np.max(np.abs(f0))

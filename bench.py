@@ -47,8 +47,11 @@ def parse():
     ap.add_argument("--dtype", choices=["bf16", "f32"], default="bf16")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, "decay_4096x32768"],
-                    help="decay_4096x32768 is the small profiling case of the same model")
+                    choices=[WORKLOAD, "decay_4096x32768", "dist_2048x262144", "dist_2048x65536",
+                             "batched_1024"],
+                    help="decay_4096x32768 is the small profiling case of the headline model; "
+                         "dist_* run the distributed pipeline (Algorithms 2 and 4), batched_1024 "
+                         "the batched independent problems")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -186,10 +189,130 @@ def cpu_baseline(A32, dtype):
                       f"FP64 (initial scores {r.t_init - r.t_start:.1f} s, timed apart)"}
 
 
+def _events(torch, n):
+    return [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in range(n)]
+
+
+def run_distributed(args):
+    """Algorithm 2 then Algorithm 4 on 2048 x n BF16 (rank 400 + 1e-3 noise):
+    B = A Omega on tensor cores, 64 log-normal column blocks selecting 100
+    each by GCSS, GCSS on the union for k = 100.  One step = the pipeline."""
+    import torch
+    from paper_1312_6838_gb300 import css
+    c = dict(ci.CONFIGS["dist_2048x262144"])
+    if args.workload == "dist_2048x65536":
+        c["n"] = 65536
+        c["blocks"] = 16
+    m, n, r = c["m"], c["n"], c["r"]
+    A32 = ci.lowrank_decaying(m, n, c["rank"], c["noise"], c["seed"], dtype=np.float32)
+    A = torch.from_numpy(np.ascontiguousarray(A32.T)).cuda().to(torch.bfloat16).t()
+    del A32
+    Om = torch.from_numpy(np.ascontiguousarray(
+        ci.gaussian_omega(n, r, c["omega_seed"]).T)).cuda().to(torch.bfloat16).t()
+    offs = ci.lognormal_blocks(n, c["blocks"], c["block_median"], c["block_sigma"],
+                               c["block_seed"]).tolist()
+    def step():
+        B = css.project(A, Om)
+        return B, css.distributed(A, B, offs, c["l_block"], c["k"])
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    ev = _events(torch, args.steps)
+    evp = _events(torch, args.steps)
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    for i in range(args.steps):
+        ev[i][0].record()
+        evp[i][0].record()
+        B = css.project(A, Om)
+        evp[i][1].record()
+        res = css.distributed(A, B, offs, c["l_block"], c["k"])
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    tot = [a.elapsed_time(b) for a, b in ev]
+    proj = [a.elapsed_time(b) for a, b in evp]
+    block_iters = int((res.block_sel >= 0).sum().item())
+    iters = block_iters + res.n_sel
+    ms = statistics.mean(tot)
+    pms = statistics.mean(proj)
+    peak_tf = 1845.9
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peak_tf = float(json.load(fh)["bf16_tflops"])
+    except Exception:
+        pass
+    tf = 2.0 * m * n * r / (pms / 1e3) / 1e12
+    print(json.dumps({
+        "metric": "greedy iterations/s of the distributed pipeline (Algorithms 2 and 4)",
+        "value": iters / (ms / 1e3), "unit": "iterations/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": args.workload, "m": m, "n": n, "r": r, "blocks": len(offs) - 1,
+                   "l_block": c["l_block"], "k": c["k"], "block_iterations": block_iters},
+        "projection_ms": pms,
+        "roofline": {"bound": "tensor", "achieved": tf, "peak": peak_tf, "unit": "TFLOP/s",
+                     "frac": tf / peak_tf, "traffic": None, "kernel": "tc_kernel (B = A Omega)"},
+        "gpu_launches": None, "clocks": clk}), flush=True)
+
+
+def run_batched(args):
+    """1024 independent instances (FP32, rank k + 1e-2 noise): one persistent
+    launch (FP32 and BF16 streams) against a loop of single-instance calls."""
+    import torch
+    from paper_1312_6838_gb300 import css
+    c = ci.CONFIGS["batched_1024"]
+    specs = ci.batched_specs(c["count"], c["seed"])
+    As32, ks = [], []
+    for i, (m, n, k) in enumerate(specs):
+        A = ci.batched_instance(m, n, k, c["seed"] + i, noise=c["noise"])
+        As32.append(torch.from_numpy(np.ascontiguousarray(A.T)).cuda().t())
+        ks.append(k)
+    As16 = [css.to_colmajor(a.to(torch.bfloat16)) for a in As32]
+    total_k = sum(ks)
+    def t_ms(fn):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms32 = t_ms(lambda: css.select_batched(As32, ks))
+    ms16 = t_ms(lambda: css.select_batched(As16, ks))
+    loop32 = t_ms(lambda: [css.select(a, k) for a, k in zip(As32, ks)])
+    clk = clocks.stop()
+    print(json.dumps({
+        "metric": "greedy iterations/s, 1024 independent problems",
+        "value": total_k / (ms16 / 1e3), "unit": "iterations/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms16, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "batched_1024", "instances": len(ks), "total_k": total_k,
+                   "sum_mn": int(sum(m * n for m, n, _ in specs))},
+        "batched_fp32_iterations_per_s": total_k / (ms32 / 1e3),
+        "loop_fp32_iterations_per_s": total_k / (loop32 / 1e3),
+        "speedup_batched_bf16_vs_loop_fp32": loop32 / ms16,
+        "speedup_batched_fp32_vs_loop_fp32": loop32 / ms32,
+        "clocks": clk}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload.startswith("dist_"):
+        run_distributed(args)
+        return
+    if args.workload == "batched_1024":
+        run_batched(args)
         return
     import torch
     ws, rank, local = dist_env()
@@ -253,6 +376,12 @@ def main():
     # reads C = A A^T once and reads/writes the score state (f, g: r+w, g0: r, W: w)
     per_iter = a_bytes + c_bytes + 48 * n
     achieved = per_iter * res.n_sel / (statistics.mean(loop_ms) / 1e3) / 1e9
+    # DRAM traffic per launch from the ncu capture summarised in
+    # profiles/greedy_kernel_decay_4096x65536.md: 1.015 x the bytes of A per
+    # A pass (C stays in L2), scaled by the A passes of this launch
+    traffic = None
+    if args.workload == WORKLOAD and args.dtype == "bf16":
+        traffic = (res.n_sel + 1) * a_bytes * 1.015
     peak, peak_kind = peaks()
     out = {
         "metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": ws,
@@ -267,7 +396,7 @@ def main():
         "init_ms": statistics.mean(init_ms), "loop_ms": statistics.mean(loop_ms),
         "whole_call_iterations_per_s": ws * args.steps * res.n_sel / (tot_ms / 1e3),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": traffic,
                      "kernel": "greedy_kernel (persistent: pivot phases + fused step)",
                      "bytes_per_iteration": per_iter, "peak_kind": peak_kind},
         # per css_select: BF16 -> C = A A^T, split of C, column dots, partial

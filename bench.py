@@ -283,6 +283,9 @@ def run_batched(args):
         e1.record()
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / args.steps
+    ph32, ph16 = [], []
+    css.select_batched(As32, ks, timing=ph32)
+    css.select_batched(As16, ks, timing=ph16)
     clocks = ClockSampler(0)
     clocks.start()
     ms32 = t_ms(lambda: css.select_batched(As32, ks))
@@ -300,6 +303,8 @@ def run_batched(args):
         "loop_fp32_iterations_per_s": total_k / (loop32 / 1e3),
         "speedup_batched_bf16_vs_loop_fp32": loop32 / ms16,
         "speedup_batched_fp32_vs_loop_fp32": loop32 / ms32,
+        "phases_ms_fp32": {"initial_scores": ph32[0], "greedy": ph32[1]},
+        "phases_ms_bf16": {"initial_scores": ph16[0], "greedy": ph16[1]},
         "clocks": clk}), flush=True)
 
 

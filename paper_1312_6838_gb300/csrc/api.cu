@@ -3,6 +3,7 @@
 // init_simt.cu, project.cu and backward.cu.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <vector>
 
@@ -410,6 +411,33 @@ cudaError_t gcss_f0(int dt, const void* A, int64_t lda, int64_t m, int64_t n, co
     return tc::colnorms(A, lda, (int)m, (int)n, (const float*)B, ldb, (int)r, tc_scratch, f, h.aux_err,
                         o.spin_budget_ns ? o.spin_budget_ns : kDefaultSpinNs, s);
   return gcss_f0_simt(dt, A, lda, (int)m, (int)n, B, ldb, (int)r, partial, f, s);
+}
+
+// Streams for the per-problem initial-score kernels of a batch, so that the
+// small GEMMs of different problems run side by side.  Created once per device
+// and kept for the life of the process.
+constexpr int kPoolStreams = 16;
+struct StreamPool {
+  cudaStream_t st[kPoolStreams];
+  cudaEvent_t ev[kPoolStreams + 1];
+  bool ok = false;
+};
+
+StreamPool* stream_pool() {
+  static std::mutex mu;
+  static StreamPool pools[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  StreamPool& P = pools[dev];
+  if (!P.ok) {
+    for (int i = 0; i < kPoolStreams; ++i)
+      if (cudaStreamCreateWithFlags(&P.st[i], cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    for (int i = 0; i <= kPoolStreams; ++i)
+      if (cudaEventCreateWithFlags(&P.ev[i], cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    P.ok = true;
+  }
+  return &P;
 }
 
 int team_ctas_for(int64_t n, int64_t m) {
@@ -856,13 +884,28 @@ css_status css_select_batched(const css_problem* probs, int32_t count, css_dtype
   if (cudaMemsetAsync(L.h.aux_err, 0, sizeof(int), s) != cudaSuccess) return CSS_ERR_CUDA;
   std::vector<UnitDesc> units;
   std::vector<double> work;
+  // initial scores of every problem: spread over the stream pool (after the
+  // caller's stream), joined back before the persistent launch
+  StreamPool* pool = count > 1 ? stream_pool() : nullptr;
+  if (pool) {
+    if (cudaEventRecord(pool->ev[kPoolStreams], s) != cudaSuccess) return CSS_ERR_CUDA;
+    for (int j = 0; j < kPoolStreams; ++j)
+      if (cudaStreamWaitEvent(pool->st[j], pool->ev[kPoolStreams], 0) != cudaSuccess) return CSS_ERR_CUDA;
+  }
   for (int i = 0; i < count; ++i) {
     const css_problem& p = probs[i];
-    cudaError_t e = css_f0_simt(dtype, p.A, p.lda, (int)p.m, (int)p.n, L.C[i], L.partial[i], L.st[i].f, s);
+    cudaStream_t si = pool ? pool->st[i % kPoolStreams] : s;
+    cudaError_t e = css_f0_simt(dtype, p.A, p.lda, (int)p.m, (int)p.n, L.C[i], L.partial[i], L.st[i].f, si);
     if (e != cudaSuccess) return cuda_status(e);
     units.push_back(make_unit(p.A, dtype, p.m, p.n, p.lda, p.k, 0, L.C[i], p.m, 0, L.st[i], p.W,
                               p.sel, p.trace, p.n_sel, o));
     work.push_back((double)p.k * p.m * p.n + 4.0 * p.m * p.k * p.k);
+  }
+  if (pool) {
+    for (int j = 0; j < kPoolStreams; ++j) {
+      if (cudaEventRecord(pool->ev[j], pool->st[j]) != cudaSuccess) return CSS_ERR_CUDA;
+      if (cudaStreamWaitEvent(s, pool->ev[j], 0) != cudaSuccess) return CSS_ERR_CUDA;
+    }
   }
   tm.mark(1, s);
   const int tile = pick_tile(o, dtype, 0);

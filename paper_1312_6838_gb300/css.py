@@ -266,7 +266,7 @@ def project(A: torch.Tensor, Omega: torch.Tensor, *, out=None, stream=None, sync
 
 
 def select_batched(As: Sequence[torch.Tensor], ks: Sequence[int], *, grid_ctas=0, tile_cols=0,
-                   tau_rel=None, stream=None):
+                   tau_rel=None, stream=None, timing=None):
     """Independent greedy CSS problems in one persistent launch.  Returns a list
     of Selection."""
     if len(As) != len(ks) or not As:
@@ -290,12 +290,17 @@ def select_batched(As: Sequence[torch.Tensor], ks: Sequence[int], *, grid_ctas=0
         probs[i].W = None
         outs.append((sel, trace, nsel))
     o = _opts(tau_rel, None, 0, grid_ctas, tile_cols)
+    tms = (C.c_double * 2)() if timing is not None else None
+    if tms is not None:
+        o.timing_ms = C.cast(tms, C.c_void_p)
     nbytes = lib.css_batched_workspace_size(probs, len(As), dt, C.byref(o))
     if nbytes == 0:
         raise ValueError("invalid batch")
     _keep, ws = _workspace(nbytes, dev)
     code = lib.css_select_batched(probs, len(As), dt, _ptr(ws), nbytes, C.byref(o), _stream(stream))
     _check(code, "css_select_batched")
+    if tms is not None:
+        timing.extend([tms[0], tms[1]])
     nsels = torch.cat([x[2] for x in outs]).tolist()
     return [Selection(s, t, int(ns), code) for (s, t, _), ns in zip(outs, nsels)]
 

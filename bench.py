@@ -137,6 +137,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(values, device):
+    """Element-wise maximum of a list of floats over all ranks (the slowest
+    rank's time defines a multi-GPU step).  Identity without a process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return list(values)
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
 def run_reference(args):
     """The FP64 oracle on host cores: each step = 2 iterations of Algorithm 1 on
     the full matrix (the initial scores are recomputed every step and timed
@@ -370,11 +382,7 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in ev]
     tot_ms = sum(step_ms)
     tot_loop = sum(loop_ms)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([tot_ms, tot_loop], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms, tot_loop = t.tolist()
+    tot_ms, tot_loop = max_over_ranks([tot_ms, tot_loop], dev)
     iters = ws * args.steps * res.n_sel
     value = iters / (tot_loop / 1e3)
     # roofline of the persistent greedy kernel: per iteration it streams A once,

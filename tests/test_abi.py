@@ -47,9 +47,12 @@ def test_workspace_size_is_host_only(lib):
     a = lib.css_workspace_size(L.CSS_OP_SELECT, L.CSS_BF16, 4096, 65536, 0, 256, 0, C.byref(o))
     b = lib.css_workspace_size(L.CSS_OP_SELECT, L.CSS_F32, 4096, 65536, 0, 256, 0, C.byref(o))
     assert a > 0 and b > 0
-    # C = A A^T (m x m FP32) dominates; W is an optional caller output
-    assert a >= 4096 * 4096 * 4
-    assert a < 256 * 65536 * 8
+    # C = A A^T (m x m FP32, plus its BF16 split for the tensor-core initial
+    # scores) dominates; W (k x n FP64) is an optional caller output, so the
+    # workspace grows with k only through Q and Z (m x k each)
+    assert a >= 4096 * 4096 * 4 and b >= 4096 * 4096 * 4
+    a4 = lib.css_workspace_size(L.CSS_OP_SELECT, L.CSS_BF16, 4096, 65536, 0, 1024, 0, C.byref(o))
+    assert 0 < a4 - a < 4 * 4096 * (1024 - 256) * 8
     assert lib.css_workspace_size(L.CSS_OP_SELECT, L.CSS_F32, 0, 10, 0, 1, 0, None) == 0
     assert lib.css_workspace_size(L.CSS_OP_GCSS, L.CSS_F32, 100, 1000, 0, 10, 0, None) == 0
     assert lib.css_workspace_size(L.CSS_OP_PROJECT, L.CSS_BF16, 2048, 262144, 400, 0, 0, None) > 0

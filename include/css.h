@@ -114,7 +114,8 @@ typedef struct {
     /* Number of CTAs of the persistent greedy kernel (0 = all SMs times the
        occupancy).  Tuning knob. */
     int32_t grid_ctas;
-    /* Columns per warp tile of the fused step (0 = autotuned: 2, 4 or 8). */
+    /* Columns per warp tile of the fused step: 2, 4 or 8 (0 = default, 8).
+       The last tiles of each step are further cut into row chunks. */
     int32_t tile_cols;
     /* Optional DEVICE diagnostics, NULL to skip (css_select, gcss_select):
        diag_argmax  int32[k]: the kernel's own argmax at each iteration (also

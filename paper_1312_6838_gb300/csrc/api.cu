@@ -83,9 +83,20 @@ struct Header {
   int* cand_idx;
   uint32_t* tile_ctr;
   int* aux_err;   // error flag of the tensor-core initial-score kernel
+  void* split_part;
+  uint32_t* split_done;
+  int split_slots;
 };
 
-void carve_header(WsCarver& c, int max_units, Header& h) {
+// Split-tile slots for units with `split_cols` columns in total: a team never
+// splits more tiles than it has warps or than its widest unit has tiles
+// (tiles are at least two columns wide).
+int split_slots_for(int64_t split_cols) {
+  const int64_t per_grid = (int64_t)kMaxCtas * (kGreedyThreads / 32);
+  return (int)std::min<int64_t>(per_grid, (split_cols + 1) / 2 + 1);
+}
+
+void carve_header(WsCarver& c, int max_units, Header& h, int64_t split_cols) {
   h.st = c.take<DevStatus>(1);
   h.units = c.take<UnitDesc>(max_units);
   h.teams = c.take<TeamDesc>(kMaxCtas);
@@ -97,6 +108,9 @@ void carve_header(WsCarver& c, int max_units, Header& h) {
   h.cand_idx = c.take<int>(kMaxCtas);
   h.tile_ctr = c.take<uint32_t>(2 * kMaxCtas);
   h.aux_err = c.take<int>(1);
+  h.split_slots = split_slots_for(split_cols);
+  h.split_part = c.take<char>((size_t)h.split_slots * kSplitSlotBytes);
+  h.split_done = c.take<uint32_t>(h.split_slots);
 }
 
 css_status cuda_status(cudaError_t e) {
@@ -210,12 +224,23 @@ css_status launch_units(const Header& h, std::vector<UnitDesc>& units, const std
   int grid = std::min(grid_max > 0 ? grid_max : sms * occ, sms * occ);
   grid = std::min(grid, kMaxCtas);
   Plan P = make_plan(work, grid);
+  int split_used = 0;
   for (size_t t = 0; t < P.teams.size(); ++t) {
-    P.teams[t].bar = h.bars + 2 * P.teams[t].cta0;
-    P.teams[t].part = h.part + 4 * P.teams[t].cta0;
-    P.teams[t].cand_val = h.cand_val + P.teams[t].cta0;
-    P.teams[t].cand_idx = h.cand_idx + P.teams[t].cta0;
-    P.teams[t].tile_ctr = h.tile_ctr + 2 * P.teams[t].cta0;
+    TeamDesc& d = P.teams[t];
+    d.bar = h.bars + 2 * d.cta0;
+    d.part = h.part + 4 * d.cta0;
+    d.cand_val = h.cand_val + d.cta0;
+    d.cand_idx = h.cand_idx + d.cta0;
+    d.tile_ctr = h.tile_ctr + 2 * d.cta0;
+    // split the last tiles of each fused step: at most one per warp of the team
+    int widest = 0;
+    for (int q = d.u_begin; q < d.u_end; ++q)
+      widest = std::max(widest, (units[P.order[q]].n + tile_cols - 1) / tile_cols);
+    const int cap = std::min({widest, d.ncta * (kGreedyThreads / 32), h.split_slots - split_used});
+    d.split_cap = std::max(cap, 0);
+    d.split_part = static_cast<char*>(h.split_part) + (size_t)split_used * kSplitSlotBytes;
+    d.split_done = h.split_done + split_used;
+    split_used += d.split_cap;
   }
   DevStatus st{};
   st.spin_budget_ns = spin_ns ? spin_ns : kDefaultSpinNs;
@@ -227,6 +252,9 @@ css_status launch_units(const Header& h, std::vector<UnitDesc>& units, const std
   if ((e = cudaMemcpyAsync(h.cta_team, P.cta_team.data(), P.cta_team.size() * sizeof(int), cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_status(e);
   if ((e = cudaMemsetAsync(h.bars, 0, 2 * sizeof(uint32_t) * P.grid, s)) != cudaSuccess) return cuda_status(e);
   if ((e = cudaMemsetAsync(h.tile_ctr, 0, 2 * sizeof(uint32_t) * P.grid, s)) != cudaSuccess) return cuda_status(e);
+  if (split_used > 0 &&
+      (e = cudaMemsetAsync(h.split_done, 0, sizeof(uint32_t) * split_used, s)) != cudaSuccess)
+    return cuda_status(e);
   GreedyLaunch L{};
   L.units = h.units;
   L.order = h.order;
@@ -284,11 +312,14 @@ struct PhaseTimer {
   }
 };
 
+// Columns per fused-step tile: 8 keeps the most 16-byte loads in flight per
+// warp (measured fastest for BF16 and FP32 at m = 4096); the split tail keeps
+// the last, long tiles from idling the team.
 int pick_tile(const css_opts& o, int dt, int m) {
   if (o.tile_cols == 2 || o.tile_cols == 4 || o.tile_cols == 8) return o.tile_cols;
   (void)dt;
   (void)m;
-  return 4;
+  return 8;
 }
 
 css_status check_forced(const css_opts& o, int n, int k) {
@@ -319,7 +350,7 @@ struct SelectLayout {
 SelectLayout select_layout(void* ws, size_t cap, int dt, int64_t m, int64_t n, int32_t k, bool need_W) {
   WsCarver c(ws, cap);
   SelectLayout L{};
-  carve_header(c, 1, L.h);
+  carve_header(c, 1, L.h, n);
   carve_scores(c, (int)n, L.s);
   carve_rest(c, dt, (int)m, (int)n, k, 0, 0, need_W, L.s);
   // C = A A^T (m x m) first; for BF16 input the tensor-core path needs its
@@ -344,7 +375,7 @@ GcssLayout gcss_layout(void* ws, size_t cap, int dt, int64_t m, int64_t n, int64
                        bool need_W) {
   WsCarver c(ws, cap);
   GcssLayout L{};
-  carve_header(c, 1, L.h);
+  carve_header(c, 1, L.h, n);
   carve_scores(c, (int)n, L.s);
   carve_rest(c, dt, (int)m, (int)n, k, (int)r, 1, need_W, L.s);
   L.partial = c.take<double>(gcss_f0_partial_doubles(dt, (int)r, (int)n));
@@ -663,7 +694,9 @@ DistLayout dist_layout(void* ws, size_t cap, int dt, int64_t m, int64_t n, int64
                        int32_t lb, const int64_t* offs, int nb) {
   WsCarver c(ws, cap);
   DistLayout L{};
-  carve_header(c, std::max(nb, 1), L.h);
+  // the header serves the block launch (n columns in all) and the union
+  // launch (at most nb * lb columns)
+  carve_header(c, std::max(nb, 1), L.h, std::max<int64_t>(n + 2 * (int64_t)nb, (int64_t)nb * lb));
   carve_scores(c, (int)n, L.sc);
   L.f0_saved = c.take<double>(n);
   int64_t umax = 0;
@@ -835,7 +868,9 @@ struct BatchLayout {
 BatchLayout batch_layout(void* ws, size_t cap, const css_problem* probs, int count, int dt) {
   WsCarver c(ws, cap);
   BatchLayout L{};
-  carve_header(c, std::max(count, 1), L.h);
+  int64_t cols = 0;
+  for (int i = 0; i < count; ++i) cols += probs[i].n + 2;   // + 2: ceil of each half
+  carve_header(c, std::max(count, 1), L.h, cols);
   L.st.resize(count);
   L.C.resize(count);
   L.partial.resize(count);

@@ -252,6 +252,17 @@ __device__ double team_sum(const Ctx<Acc>& x, int slot) {
 }
 
 // --------------------------------------------------------- fused step (K1) --
+// Work units come from a team-wide counter: first whole tiles of CW columns,
+// then the last `nsplit` tiles (one per warp of the team at most) cut into
+// kSplitR row chunks, so that the step ends with short units instead of
+// warps idling behind a few long ones.  The chunk sums of a split tile meet
+// in the team's split area; the warp that adds the last chunk sums them in
+// chunk order (the result does not depend on which warp that is).
+//
+// The per-column update is FP64, and FP64 issues at a small fraction of the
+// FP32 rate on this part, so it is not run per tile (where only CW lanes of
+// the warp would hold results): each lane collects the (omega, h) of one column
+// and the warp applies the update to 32 columns at once, every 32 / CW tiles.
 template <typename TA, int CW>
 __device__ void fused_step(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc& u, int t,
                            int p, double s, uint64_t pol, double& bv, int& bi) {
@@ -259,20 +270,43 @@ __device__ void fused_step(const Ctx<typename AccOf<TA>::type>& x, const UnitDes
   constexpr int V = Vec<TA>::V;
   constexpr int NV = 2 * CW;
   constexpr int SH = 5 - Log2<NV>::v;
+  constexpr int TPB = 32 / CW;  // tiles per epilogue batch
+  static_assert(NV <= kSplitVals, "split slots hold 2 x CW values");
   const int n = u.n, m = u.m;
   const int ntiles = (n + CW - 1) / CW;
+  const int nsplit = min(ntiles, x.team->split_cap);
+  const int nbulk = ntiles - nsplit;
+  const int nunits = nbulk + nsplit * kSplitR;
+  // rows per chunk: a multiple of one warp-wide vector step
+  const int rch = ((m + kSplitR - 1) / kSplitR + 32 * V - 1) / (32 * V) * (32 * V);
   const int m_vec = u.vec_ok ? (m / V) * V : 0;
   const TA* A = reinterpret_cast<const TA*>(u.A);
-  const volatile unsigned char* selv = u.selmask;
-  // tiles are handed out by a team-wide counter, so every warp keeps streaming
-  // until the column range is exhausted (no static imbalance at the barrier)
+  Acc* split_part = reinterpret_cast<Acc*>(x.team->split_part);
+  // slots are sized for 8-byte values; FP32 sums use the first half of each
+  constexpr int SLOT = kSplitR * kSplitVals * 8 / (int)sizeof(Acc);
+  // this lane's column within a tile, and where its omega and h sit after
+  // the transpose-reduce (lane L holds value L >> SH)
+  const int my_c = x.lane % CW;
+  const int src_w = (2 * my_c) << SH, src_h = (2 * my_c + 1) << SH;
+  const int my_slot = x.lane / CW;
+  const bool val_lane = (x.lane & ((1 << SH) - 1)) == 0;
+  Acc bw = Acc(0), bh = Acc(0);
+  int bcol = -1, slot = 0;
   uint32_t* ctr = x.team->tile_ctr + (t & 1);
-  int tile = 0;
-  if (x.lane == 0) tile = (int)atomicAdd(ctr, 1u);
-  tile = __shfl_sync(0xffffffffu, tile, 0);
-  for (; tile < ntiles;) {
+  int unit = 0;
+  if (x.lane == 0) unit = (int)atomicAdd(ctr, 1u);
+  unit = __shfl_sync(0xffffffffu, unit, 0);
+  while (unit < nunits) {
     int next = 0;
     if (x.lane == 0) next = (int)atomicAdd(ctr, 1u);
+    int tile = unit, sidx = -1, chunk = 0, r_lo = 0, r_hi = m;
+    if (unit >= nbulk) {
+      sidx = (unit - nbulk) / kSplitR;
+      chunk = (unit - nbulk) - sidx * kSplitR;
+      tile = nbulk + sidx;
+      r_lo = min(m, chunk * rch);
+      r_hi = (chunk == kSplitR - 1) ? m : min(m, r_lo + rch);
+    }
     const int c0 = tile * CW;
     const TA* colp[CW];
 #pragma unroll
@@ -280,8 +314,9 @@ __device__ void fused_step(const Ctx<typename AccOf<TA>::type>& x, const UnitDes
     Acc v[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) v[i] = Acc(0);
+    const int v_hi = min(r_hi, m_vec);
 #pragma unroll 4
-    for (int r = x.lane * V; r < m_vec; r += 32 * V) {
+    for (int r = r_lo + x.lane * V; r < v_hi; r += 32 * V) {
       uint4 raw[CW];
 #pragma unroll
       for (int c = 0; c < CW; ++c) raw[c] = ldg_stream16(colp[c] + r, pol);
@@ -299,7 +334,7 @@ __device__ void fused_step(const Ctx<typename AccOf<TA>::type>& x, const UnitDes
         v[2 * c + 1] += th;
       }
     }
-    for (int r = m_vec + x.lane; r < m; r += 32) {
+    for (int r = max(r_lo, m_vec) + x.lane; r < r_hi; r += 32) {
       const Acc qa = x.sq[r], ya = x.sy[r];
 #pragma unroll
       for (int c = 0; c < CW; ++c) {
@@ -308,30 +343,57 @@ __device__ void fused_step(const Ctx<typename AccOf<TA>::type>& x, const UnitDes
         v[2 * c + 1] = fma(a, ya, v[2 * c + 1]);
       }
     }
-    const Acc red = transpose_reduce<NV>(v, x.lane);
-    const Acc hv = __shfl_down_sync(0xffffffffu, red, 1 << SH);
-    const int j = x.lane >> SH;
-    if ((x.lane & ((1 << SH) - 1)) == 0 && (j & 1) == 0) {
-      const int col = c0 + (j >> 1);
-      if (col < n) {
-        const double w = (double)red, h = (double)hv;
+    Acc red = transpose_reduce<NV>(v, x.lane);
+    bool have = true;
+    if (sidx >= 0) {
+      Acc* sp = split_part + (size_t)sidx * SLOT;
+      if (val_lane) __stcg(sp + chunk * kSplitVals + (x.lane >> SH), red);
+      __syncwarp();
+      uint32_t old = 0;
+      if (x.lane == 0) old = atom_add_acqrel_u32(x.team->split_done + sidx, 1u);
+      old = __shfl_sync(0xffffffffu, old, 0);
+      have = old == (uint32_t)(kSplitR - 1);
+      if (have) {
+        __syncwarp();   // lane 0's acquire orders the other lanes' loads
+        if (val_lane) {
+          Acc sum = Acc(0);
+#pragma unroll
+          for (int c = 0; c < kSplitR; ++c) sum += ld_cg(sp + c * kSplitVals + (x.lane >> SH));
+          red = sum;
+        }
+        // every chunk has arrived: the counter is free for the next step
+        if (x.lane == 0) x.team->split_done[sidx] = 0u;
+      }
+    }
+    if (have) {
+      const Acc wv = __shfl_sync(0xffffffffu, red, src_w);
+      const Acc hv = __shfl_sync(0xffffffffu, red, src_h);
+      if (my_slot == slot && c0 + my_c < n) { bw = wv; bh = hv; bcol = c0 + my_c; }
+      ++slot;
+    }
+    unit = __shfl_sync(0xffffffffu, next, 0);
+    if (slot == TPB || unit >= nunits) {
+      if (bcol >= 0) {
+        const int col = bcol;
         double fi = ld_cg(u.f + col), gi = ld_cg(u.g + col);
+        const double g0 = ld_cg(u.g0 + col);
+        bool selected = __ldcg(u.selmask + col) != 0;
+        const double w = (double)bw, h = (double)bh;
         // Theorem 2 / Theorem 4: f - 2 omega o x + s (omega o omega), g - omega o omega
         fi = fi - 2.0 * w * h + s * (w * w);
         gi = gi - w * w;
         u.f[col] = fi;
         u.g[col] = gi;
         if (u.W) u.W[(long long)t * n + col] = w;
-        bool selected = selv[col] != 0;
         if (col == p) { u.selmask[col] = 1; selected = true; }
-        const double g0 = ld_cg(u.g0 + col);
         if (!selected && g0 > 0.0 && gi > u.tau * g0) {
           const double sc = u.score_mode ? gi : fmax(fi, 0.0) / gi;
           if (better(sc, col, bv, bi)) { bv = sc; bi = col; }
         }
       }
+      slot = 0;
+      bcol = -1;
     }
-    tile = __shfl_sync(0xffffffffu, next, 0);
   }
 }
 

@@ -52,7 +52,17 @@ struct TeamDesc {
   double* cand_val;                 // ncta
   int* cand_idx;                    // ncta
   uint32_t* tile_ctr;               // 2 words: fused-step tile counters (alternating)
+  // the fused step's last tiles are cut into kSplitR row chunks; chunk sums
+  // meet here (split_cap tiles x kSplitR x kSplitVals values, 8 bytes each)
+  void* split_part;
+  uint32_t* split_done;             // split_cap arrival counters (zero between uses)
+  int split_cap;
+  int pad_;
 };
+
+constexpr int kSplitR = 4;          // row chunks of a split tile
+constexpr int kSplitVals = 16;      // value slots per chunk (2 x the widest tile)
+constexpr size_t kSplitSlotBytes = (size_t)kSplitR * kSplitVals * 8;
 
 struct GreedyLaunch {
   const UnitDesc* units;

@@ -143,8 +143,9 @@ typedef struct {
        0 start, 1 argmax done, 2/3 before/after the first team barrier,
        4/5 around the second, 6 target vectors staged, 7 C e or B B^T e
        done, 8 Z^T e done, 9 after the third barrier, 10/11 around the
-       fourth, 12 fused step starts, 13 fused step done, 14 after the last
-       barrier.  Unused entries are 0. */
+       fourth, 12 fused step starts, 13 fused step done (the first warp),
+       15 the CTA's argmax candidate published, 14 after the last barrier.
+       Unused entries are 0. */
     uint64_t* trace_ns;
 } css_opts;
 

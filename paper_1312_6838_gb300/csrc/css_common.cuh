@@ -109,37 +109,41 @@ __device__ __forceinline__ void set_error(DevStatus* st, int32_t code, int32_t w
   if (atomicCAS(&st->code, 0, code) == 0) st->where = where;
 }
 
-// Barrier over the `ncta` CTAs of one team.  bar[0] = arrival count,
-// bar[1] = generation.  Every wait is bounded by the workspace's spin budget;
-// on expiry (or when another CTA already flagged an error) it records
-// CSS_ERR_TIMEOUT and returns false.  All CTAs of the team are co-resident
-// (the persistent kernel is launched cooperatively).
-__device__ __forceinline__ bool team_barrier(uint32_t* bar, int ncta, DevStatus* st, int where) {
+__device__ __forceinline__ void red_release_add_u32(uint32_t* p, uint32_t v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Barrier over the `ncta` CTAs of one team.  bar[0] counts arrivals over the
+// whole launch (zeroed before it); `epoch` (thread 0's count of this team's
+// barriers so far) gives the value that completes this one.  Arrival is a
+// release reduction that needs no reply, so the barrier costs one trip of the
+// last arrival to L2 and one poll.  Every wait is bounded by the workspace's
+// spin budget; on expiry (or when another CTA already flagged an error) it
+// records CSS_ERR_TIMEOUT and returns false.  All CTAs of the team are
+// co-resident (the persistent kernel is launched cooperatively).
+__device__ __forceinline__ bool team_barrier(uint32_t* bar, int ncta, DevStatus* st, int where,
+                                             uint32_t* epoch) {
   __shared__ int s_ok;
   __syncthreads();
   if (ncta <= 1) return ld_volatile_i32(&st->code) == 0;
   if (threadIdx.x == 0) {
     int ok = 1;
-    uint32_t gen = ld_acquire_u32(bar + 1);
-    uint32_t arrived = atom_add_acqrel_u32(bar, 1u);
-    if (arrived == (uint32_t)ncta - 1u) {
-      bar[0] = 0u;
-      st_release_u32(bar + 1, gen + 1u);
-    } else {
-      uint64_t t0 = globaltimer_ns();
-      uint64_t budget = st->spin_budget_ns;
-      uint32_t spins = 0;
-      while (ld_acquire_u32(bar + 1) == gen) {
-        if ((++spins & 63u) == 0u) {
-          if (ld_volatile_i32(&st->code) != 0) { ok = 0; break; }
-          if (globaltimer_ns() - t0 > budget) {
-            set_error(st, (int32_t)CSS_ERR_TIMEOUT, where);
-            ok = 0;
-            break;
-          }
+    *epoch += 1u;
+    const uint32_t target = *epoch * (uint32_t)ncta;
+    red_release_add_u32(bar, 1u);
+    uint64_t t0 = globaltimer_ns();
+    const uint64_t budget = st->spin_budget_ns;
+    uint32_t spins = 0;
+    while ((int32_t)(ld_acquire_u32(bar) - target) < 0) {
+      if ((++spins & 63u) == 0u) {
+        if (ld_volatile_i32(&st->code) != 0) { ok = 0; break; }
+        if (globaltimer_ns() - t0 > budget) {
+          set_error(st, (int32_t)CSS_ERR_TIMEOUT, where);
+          ok = 0;
+          break;
         }
-        if (spins > 256u) __nanosleep(64);
       }
+      if (spins > 256u) __nanosleep(64);
     }
     if (ok && ld_volatile_i32(&st->code) != 0) ok = 0;
     s_ok = ok;
@@ -156,21 +160,63 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-// (value, index) ordering of the argmax: larger value wins, equal values go
-// to the lower index; index < 0 means "no candidate".
-__device__ __forceinline__ bool better(double v1, int i1, double v2, int i2) {
-  if (i1 < 0) return false;
-  if (i2 < 0) return true;
-  return (v1 > v2) || (v1 == v2 && i1 < i2);
+// Exact float -> double by integer operations: conversions to FP64 issue at
+// the FP64 rate on this part, integer operations at the full rate.  Subnormal
+// floats (rare) take the hardware conversion.
+__device__ __forceinline__ double to_f64(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  const uint32_t frac = u & 0x7fffffu;
+  const uint64_t sign = (uint64_t)(u >> 31) << 63;
+  if (e == 0u) {
+    if (frac == 0u) return __longlong_as_double((long long)sign);
+    return (double)f;
+  }
+  const uint64_t ex = (e == 0xffu) ? 0x7ffull : (uint64_t)(e + 896u);   // 1023 - 127
+  return __longlong_as_double((long long)(sign | (ex << 52) | ((uint64_t)frac << 29)));
+}
+__device__ __forceinline__ double to_f64(double d) { return d; }
+
+// Candidate scores are non-negative doubles, whose IEEE-754 bit patterns
+// (sign cleared, so that -0 and +0 agree) order like the values: the argmax
+// compares these keys with integer instructions, because FP64 compares issue
+// at a small fraction of the integer rate on this part.
+__device__ __forceinline__ long long score_key(double v) {
+  return __double_as_longlong(v) & 0x7fffffffffffffffLL;
 }
 
-__device__ __forceinline__ void warp_argmax(double& v, int& i) {
+// (key, index) ordering of the argmax: larger key wins, equal keys go to the
+// lower index; index < 0 means "no candidate".
+__device__ __forceinline__ bool better(long long k1, int i1, long long k2, int i2) {
+  if (i1 < 0) return false;
+  if (i2 < 0) return true;
+  return (k1 > k2) || (k1 == k2 && i1 < i2);
+}
+
+__device__ __forceinline__ void warp_argmax(long long& k, int& i) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+    long long k2 = __shfl_xor_sync(0xffffffffu, k, o);
     int i2 = __shfl_xor_sync(0xffffffffu, i, o);
-    if (better(v2, i2, v, i)) { v = v2; i = i2; }
+    if (better(k2, i2, k, i)) { k = k2; i = i2; }
   }
+}
+
+// Block-wide FP64 sum in thread 0 only: the threads' values go through shared
+// memory and warp 0 adds them (NW + 5 FP64 adds in one warp, instead of five
+// in every warp).  `red` holds blockDim.x values; fixed order.
+template <typename T>
+__device__ __forceinline__ T block_sum_to0(T v, T* red) {
+  const int lane = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  red[threadIdx.x] = v;
+  __syncthreads();
+  T s = T(0);
+  if (threadIdx.x < 32) {
+    for (int w = 0; w < nw; ++w) s += red[w * 32 + lane];
+    s = warp_sum(s);
+  }
+  return s;
 }
 
 // Block-wide sum; every thread gets the result.  `red` holds >= 32 values.

@@ -43,6 +43,7 @@ struct Ctx {
   double* scoef; // coefficients (FP64)
   Acc* sups;     // upsilon in Acc precision
   double* sred;  // NS * RB partials
+  uint32_t* epoch;  // thread 0: barriers of the team passed so far
 };
 
 // ------------------------------------------------------------- transpose ----
@@ -113,13 +114,19 @@ __device__ __forceinline__ void lds_vec(const Acc* p, Acc (&a)[V]) {
 }
 
 // ------------------------------------------------------------- row GEMV -----
-// For every row i < m of the team's rows: fin(i, sum_{j<nj} M[i + j ldm] c[j])
-// with c in shared memory.  Rows are split in tiles of RB rows, dealt round-robin
-// to the team's CTAs; inside a CTA the j-range of a tile is split over half-warp
-// streams when the CTA has few tiles.  Deterministic for a fixed team size.
-template <typename TS, typename TM, typename TC, typename Acc, typename Fin>
+// For every row i < m of the team's rows: fin(i, sum_{j<nj} M[i + j ldm] c[j], pv)
+// with c in shared memory and pv = pre(i), which the finishing thread calls
+// before the products so that the loads it makes overlap them.  Rows are split
+// in tiles of RB rows, dealt round-robin to the team's CTAs; inside a CTA the
+// j-range of a tile is split over half-warp streams when the CTA has few
+// tiles.  Deterministic for a fixed team size.
+struct NoPre {
+  __device__ int operator()(int) const { return 0; }
+};
+
+template <typename TS, typename TM, typename TC, typename Acc, typename Pre, typename Fin>
 __device__ void row_gemv(const Ctx<Acc>& x, int m, int nj, const TM* M, long long ldm,
-                         const TC* c, Fin fin) {
+                         const TC* c, Pre pre, Fin fin) {
   const int G = (m + RB - 1) / RB;
   const int my_tiles = (G > x.rank) ? (G - x.rank + x.ncta - 1) / x.ncta : 0;
   const int TP = (G + x.ncta - 1) / x.ncta;
@@ -132,38 +139,35 @@ __device__ void row_gemv(const Ctx<Acc>& x, int m, int nj, const TM* M, long lon
   TS* red = reinterpret_cast<TS*>(x.sred);
   for (int base = 0; base < my_tiles; base += slots) {
     const int ti = base + slot;
+    // the finishing thread of this round and its row
+    const int sl = x.tid / RB, rr = x.tid % RB;
+    const int tj = base + sl;
+    const int frow = (x.tid < slots * RB && tj < my_tiles) ? (x.rank + tj * x.ncta) * RB + rr : m;
+    decltype(pre(0)) pv{};
+    if (frow < m) pv = pre(frow);
     TS acc = TS(0);
     if (ti < my_tiles) {
       const int row = (x.rank + ti * x.ncta) * RB + r16;
       if (row < m) {
         const TM* mp = M + row;
         int j = sub;
-        for (; j + 3 * SP < nj; j += 4 * SP) {
-          TS a0 = (TS)ld_cg(mp + (long long)j * ldm);
-          TS a1 = (TS)ld_cg(mp + (long long)(j + SP) * ldm);
-          TS a2 = (TS)ld_cg(mp + (long long)(j + 2 * SP) * ldm);
-          TS a3 = (TS)ld_cg(mp + (long long)(j + 3 * SP) * ldm);
-          acc += a0 * (TS)c[j];
-          acc += a1 * (TS)c[j + SP];
-          acc += a2 * (TS)c[j + 2 * SP];
-          acc += a3 * (TS)c[j + 3 * SP];
+        // eight loads in flight per trip: these phases are bound by L2 latency
+        for (; j + 7 * SP < nj; j += 8 * SP) {
+          TS a[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) a[q] = (TS)ld_cg(mp + (long long)(j + q * SP) * ldm);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) acc += a[q] * (TS)c[j + q * SP];
         }
         for (; j < nj; j += SP) acc += (TS)ld_cg(mp + (long long)j * ldm) * (TS)c[j];
       }
     }
     red[s * RB + r16] = acc;
     __syncthreads();
-    if (x.tid < slots * RB) {
-      const int sl = x.tid / RB, rr = x.tid % RB;
-      const int tj = base + sl;
-      if (tj < my_tiles) {
-        const int row = (x.rank + tj * x.ncta) * RB + rr;
-        if (row < m) {
-          TS sum = TS(0);
-          for (int q = 0; q < SP; ++q) sum += red[(sl * SP + q) * RB + rr];
-          fin(row, (double)sum);
-        }
-      }
+    if (frow < m) {
+      TS sum = TS(0);
+      for (int q = 0; q < SP; ++q) sum += red[(sl * SP + q) * RB + rr];
+      fin(frow, (double)sum, pv);
     }
     __syncthreads();
   }
@@ -179,7 +183,7 @@ __device__ void col_dots(const Ctx<Acc>& x, int len, int nj, const TM* M, long l
     for (int j = x.rank * NW + x.warp; j < nj; j += x.ncta * NW) {
       const TM* col = M + (long long)j * ldm;
       TS acc = TS(0);
-#pragma unroll 4
+#pragma unroll 8
       for (int i = x.lane; i < len; i += 32) acc += (TS)ld_cg(col + i) * (TS)v[i];
       acc = warp_sum(acc);
       if (x.lane == 0) fin(j, (double)acc);
@@ -188,9 +192,9 @@ __device__ void col_dots(const Ctx<Acc>& x, int len, int nj, const TM* M, long l
     for (int j = x.rank; j < nj; j += x.ncta) {
       const TM* col = M + (long long)j * ldm;
       TS acc = TS(0);
-#pragma unroll 4
+#pragma unroll 8
       for (int i = x.tid; i < len; i += NT) acc += (TS)ld_cg(col + i) * (TS)v[i];
-      acc = block_sum(acc, reinterpret_cast<TS*>(x.sred));
+      acc = block_sum_to0(acc, reinterpret_cast<TS*>(x.sred));
       if (x.tid == 0) fin(j, (double)acc);
     }
   }
@@ -198,18 +202,18 @@ __device__ void col_dots(const Ctx<Acc>& x, int len, int nj, const TM* M, long l
 
 // ------------------------------------------------------------- CTA argmax ---
 template <typename Acc>
-__device__ void cta_argmax_publish(const Ctx<Acc>& x, double bv, int bi) {
-  __shared__ double s_v[NW];
+__device__ void cta_argmax_publish(const Ctx<Acc>& x, long long bv, int bi) {
+  __shared__ long long s_v[NW];
   __shared__ int s_i[NW];
   warp_argmax(bv, bi);
   if (x.lane == 0) { s_v[x.warp] = bv; s_i[x.warp] = bi; }
   __syncthreads();
   if (x.warp == 0) {
-    double v = (x.lane < NW) ? s_v[x.lane] : -1.0;
+    long long v = (x.lane < NW) ? s_v[x.lane] : -1LL;
     int i = (x.lane < NW) ? s_i[x.lane] : -1;
     warp_argmax(v, i);
     if (x.lane == 0) {
-      x.team->cand_val[x.rank] = v;
+      x.team->cand_val[x.rank] = __longlong_as_double(v);
       x.team->cand_idx[x.rank] = i;
     }
   }
@@ -220,10 +224,10 @@ template <typename Acc>
 __device__ int team_argmax(const Ctx<Acc>& x) {
   __shared__ int s_p;
   if (x.warp == 0) {
-    double v = -1.0;
+    long long v = -1;
     int i = -1;
     for (int r = x.lane; r < x.ncta; r += 32) {
-      double v2 = ld_cg(x.team->cand_val + r);
+      long long v2 = __double_as_longlong(ld_cg(x.team->cand_val + r));
       int i2 = ld_cg(x.team->cand_idx + r);
       if (better(v2, i2, v, i)) { v = v2; i = i2; }
     }
@@ -265,7 +269,7 @@ __device__ double team_sum(const Ctx<Acc>& x, int slot) {
 // and the warp applies the update to 32 columns at once, every 32 / CW tiles.
 template <typename TA, int CW>
 __device__ void fused_step(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc& u, int t,
-                           int p, double s, uint64_t pol, double& bv, int& bi) {
+                           int p, double s, uint64_t pol, long long& bv, int& bi) {
   using Acc = typename AccOf<TA>::type;
   constexpr int V = Vec<TA>::V;
   constexpr int NV = 2 * CW;
@@ -388,7 +392,8 @@ __device__ void fused_step(const Ctx<typename AccOf<TA>::type>& x, const UnitDes
         if (col == p) { u.selmask[col] = 1; selected = true; }
         if (!selected && g0 > 0.0 && gi > u.tau * g0) {
           const double sc = u.score_mode ? gi : fmax(fi, 0.0) / gi;
-          if (better(sc, col, bv, bi)) { bv = sc; bi = col; }
+          const long long sk = score_key(sc);
+          if (better(sk, col, bv, bi)) { bv = sk; bi = col; }
         }
       }
       slot = 0;
@@ -402,7 +407,7 @@ __device__ void fused_step(const Ctx<typename AccOf<TA>::type>& x, const UnitDes
 // non-finite check, F^(0) partial sums and the first argmax.
 template <typename TA>
 __device__ void init_pass(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc& u,
-                          uint64_t pol, double& bv, int& bi, double& fsum, int& bad) {
+                          uint64_t pol, long long& bv, int& bi, double& fsum, int& bad) {
   using Acc = typename AccOf<TA>::type;
   constexpr int V = Vec<TA>::V;
   const int n = u.n, m = u.m;
@@ -434,7 +439,8 @@ __device__ void init_pass(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc
       if (u.mode == 0) fsum += g0;
       if (g0 > 0.0) {
         const double sc = u.score_mode ? g0 : fmax(f0, 0.0) / g0;
-        if (better(sc, col, bv, bi)) { bv = sc; bi = col; }
+        const long long sk = score_key(sc);
+          if (better(sk, col, bv, bi)) { bv = sk; bi = col; }
       }
     }
   }
@@ -465,7 +471,8 @@ __device__ void run_unit(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc&
   const int m = u.m, n = u.n;
 
   // ---- initialisation: g^(0), F^(0), first argmax
-  double bv = -1.0, fsum = 0.0;
+  long long bv = -1;
+  double fsum = 0.0;
   int bi = -1, bad = 0;
   init_pass<TA>(x, u, pol_stream, bv, bi, fsum, bad);
   if (__syncthreads_or(bad)) set_error(x.st, (int32_t)CSS_ERR_NONFINITE, 100);
@@ -478,7 +485,7 @@ __device__ void run_unit(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc&
     tm.tile_ctr[1] = 0u;
   }
   cta_argmax_publish(x, bv, bi);
-  if (!team_barrier(tm.bar, x.ncta, x.st, 1)) return;
+  if (!team_barrier(tm.bar, x.ncta, x.st, 1, x.epoch)) return;
 
   double F = team_sum(x, 2);  // meaningful in rank 0, thread 0
   if (x.rank == 0 && x.tid == 0) u.trace[0] = F;
@@ -506,38 +513,49 @@ __device__ void run_unit(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc&
       u.trace[t + 1] = F;
     }
     const TA* ap = reinterpret_cast<const TA*>(u.A) + (long long)p * u.lda;
-#pragma unroll 4
-    for (int i = x.tid; i < m; i += NT) x.se64[i] = (double)load_elem<TA>(ap + i);
+#pragma unroll 8
+    for (int i = x.tid; i < m; i += NT) x.se64[i] = to_f64(load_elem<TA>(ap + i));
     __syncthreads();
     col_dots<double>(x, m, t, u.Q, (long long)m, x.se64, [&](int j, double v) { u.coef[j] = v; });
     mark(2);
-    if (!team_barrier(tm.bar, x.ncta, x.st, 2)) return;
+    if (!team_barrier(tm.bar, x.ncta, x.st, 2, x.epoch)) return;
     mark(3);
 
     // ---- Phase C: e = a_p - Q_t c, ||e||^2 partials (delta_p of Eq. delta_omega)
     for (int j = x.tid; j < t; j += NT) x.scoef[j] = ld_cg(u.coef + j);
     __syncthreads();
     double nrm_part = 0.0;
-    row_gemv<double>(x, m, t, u.Q, (long long)m, x.scoef, [&](int i, double sum) {
-      const double ei = (double)load_elem<TA>(ap + i) - sum;
+    Acc* e_acc = reinterpret_cast<Acc*>(u.e1);   // e in Acc precision, converted once
+    row_gemv<double>(x, m, t, u.Q, (long long)m, x.scoef, NoPre{}, [&](int i, double sum, int) {
+      const double ei = x.se64[i] - sum;   // a_p is still staged in se64
       u.e[i] = ei;
+      e_acc[i] = (Acc)ei;
       nrm_part += ei * ei;
     });
     mark(4);
-    nrm_part = block_sum(nrm_part, x.sred);
+    nrm_part = block_sum_to0(nrm_part, x.sred);
     if (x.tid == 0) tm.part[x.rank * 4 + 0] = nrm_part;
-    if (!team_barrier(tm.bar, x.ncta, x.st, 4)) return;
+    if (!team_barrier(tm.bar, x.ncta, x.st, 4, x.epoch)) return;
     mark(5);
 
     // ---- Phase D: y_un = C e (CSS) or B (B^T e) (GCSS); d = Z^T e
-    const double nrm2 = team_sum(x, 0);
-#pragma unroll 4
+    // stage e and reduce ||e||^2 over the team's partials (the same order as
+    // team_sum) with both sets of loads in flight together
+    double nrm_acc = 0.0;
+    if (x.warp == 0)
+      for (int r = x.lane; r < x.ncta; r += 32) nrm_acc += ld_cg(tm.part + r * 4 + 0);
+#pragma unroll 8
     for (int i = x.tid; i < m; i += NT) {
-      const double ei = ld_cg(u.e + i);
-      x.se64[i] = ei;
-      x.seacc[i] = (Acc)ei;
+      x.se64[i] = ld_cg(u.e + i);
+      x.seacc[i] = ld_cg(e_acc + i);
+    }
+    if (x.warp == 0) {
+      nrm_acc = warp_sum(nrm_acc);
+      // 1 / ||e||, once per CTA (FP64 square roots and divisions are slow)
+      if (x.lane == 0) { s_scal[0] = nrm_acc; s_scal[1] = 1.0 / sqrt(nrm_acc); }
     }
     __syncthreads();
+    const double nrm2 = s_scal[0];
     mark(6);
     double s_un = 0.0;
     if (u.mode == 0) {
@@ -545,8 +563,14 @@ __device__ void run_unit(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc&
       constexpr int VC = 16 / sizeof(Acc);
       const int m_vec = u.t_vec_ok ? (m / VC) * VC : 0;
       double ey = 0.0;
-      constexpr int UC = 8;   // 16-byte loads in flight per lane
-      for (int i = x.rank * NW + x.warp; i < m; i += x.ncta * NW) {
+      constexpr int UC = 16;  // 16-byte loads in flight per lane
+      // the CTA's row results go through shared memory so that one warp, not
+      // all sixteen, issues their FP64 conversions and the FP64 dot e^T y
+      Acc* srow = reinterpret_cast<Acc*>(x.sred);
+      const int rows_per_warp = (m + x.ncta * NW - 1) / (x.ncta * NW);
+      const bool gather = rows_per_warp * NW <= NS * RB * (int)(sizeof(double) / sizeof(Acc));
+      int kr = 0;
+      for (int i = x.rank * NW + x.warp; i < m; i += x.ncta * NW, ++kr) {
         const Acc* cp = C + (long long)i * u.ldt;
         Acc accs[UC];
 #pragma unroll
@@ -580,54 +604,81 @@ __device__ void run_unit(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc&
         for (int l2 = m_vec + x.lane; l2 < m; l2 += 32) acc = fma(__ldg(cp + l2), x.seacc[l2], acc);
         acc = warp_sum(acc);
         if (x.lane == 0) {
-          u.y[i] = (double)acc;
-          ey += x.se64[i] * (double)acc;
+          if (gather) {
+            srow[kr * NW + x.warp] = acc;
+          } else {
+            u.y[i] = (double)acc;
+            ey += x.se64[i] * (double)acc;
+          }
+        }
+      }
+      if (gather) {
+        __syncthreads();
+        if (x.warp == 0) {
+          for (int idx = x.lane; idx < rows_per_warp * NW; idx += 32) {
+            const int i = x.rank * NW + (idx % NW) + (idx / NW) * x.ncta * NW;
+            if (i < m) {
+              const double yi = (double)srow[idx];
+              u.y[i] = yi;
+              ey += x.se64[i] * yi;
+            }
+          }
         }
       }
       mark(7);
       col_dots<double>(x, m, t, u.Z, (long long)m, x.se64, [&](int j, double v) { u.coef[j] = v; });
       mark(8);
-      ey = block_sum(ey, x.sred);
+      ey = block_sum_to0(ey, x.sred);
       if (x.tid == 0) tm.part[x.rank * 4 + 1] = ey;
-      if (!team_barrier(tm.bar, x.ncta, x.st, 5)) return;
+      if (!team_barrier(tm.bar, x.ncta, x.st, 5, x.epoch)) return;
       mark(9);
     } else {
       const Acc* B = reinterpret_cast<const Acc*>(u.T);
       col_dots<Acc>(x, m, u.r, B, u.ldt, x.seacc, [&](int j, double v) { u.ups[j] = v; });
-      if (!team_barrier(tm.bar, x.ncta, x.st, 5)) return;
+      if (!team_barrier(tm.bar, x.ncta, x.st, 5, x.epoch)) return;
       for (int j = x.tid; j < u.r; j += NT) {
         const double v = ld_cg(u.ups + j);
         x.scoef[j] = v;
         x.sups[j] = (Acc)v;
       }
       __syncthreads();
-      row_gemv<Acc>(x, m, u.r, B, u.ldt, x.sups, [&](int i, double sum) { u.y[i] = sum; });
+      row_gemv<Acc>(x, m, u.r, B, u.ldt, x.sups, NoPre{}, [&](int i, double sum, int) { u.y[i] = sum; });
       col_dots<double>(x, u.r, t, u.Z, (long long)u.r, x.scoef, [&](int j, double v) { u.coef[j] = v; });
       double ss = 0.0;
       for (int j = x.tid; j < u.r; j += NT) ss += x.scoef[j] * x.scoef[j];
-      s_un = block_sum(ss, x.sred);
+      s_un = block_sum_to0(ss, x.sred);
+      if (x.tid == 0) s_scal[2] = s_un / nrm2;   // Theorem 4's ||upsilon||^2 for unit q
       if (x.rank == 0) {
         // upsilon^(t) = B^T q, column t of Z (read by later iterations only)
-        const double inv = 1.0 / sqrt(nrm2);
+        const double inv = s_scal[1];
         for (int j = x.tid; j < u.r; j += NT) u.Z[(long long)t * u.r + j] = x.scoef[j] * inv;
       }
-      if (!team_barrier(tm.bar, x.ncta, x.st, 6)) return;
+      if (!team_barrier(tm.bar, x.ncta, x.st, 6, x.epoch)) return;
       mark(9);
     }
 
     // ---- Phase E: q, y = y_un / ||e||, y' = y - Q (Q^T y), s
     double s;
     {
-      const double ey_all = (u.mode == 0) ? team_sum(x, 1) : 0.0;
+      // CSS: s = e^T y / ||e||^2 from the team's partials (team_sum's order),
+      // by one thread; the coefficient loads are in flight meanwhile
+      double ey_acc = 0.0;
+      if (u.mode == 0 && x.warp == 0)
+        for (int r = x.lane; r < x.ncta; r += 32) ey_acc += ld_cg(tm.part + r * 4 + 1);
       for (int j = x.tid; j < t; j += NT) x.scoef[j] = ld_cg(u.coef + j);
+      if (u.mode == 0 && x.warp == 0) {
+        ey_acc = warp_sum(ey_acc);
+        if (x.lane == 0) s_scal[2] = ey_acc / nrm2;
+      }
       __syncthreads();
-      const double inv = 1.0 / sqrt(nrm2);
-      s = (u.mode == 0) ? ey_all / nrm2 : s_un / nrm2;
+      const double inv = s_scal[1];
+      s = s_scal[2];
       Acc* qv = reinterpret_cast<Acc*>(u.qv);
       Acc* ypv = reinterpret_cast<Acc*>(u.ypv);
-      row_gemv<double>(x, m, t, u.Q, (long long)m, x.scoef, [&](int i, double sum) {
-        const double yi = ld_cg(u.y + i) * inv;
-        const double qi = ld_cg(u.e + i) * inv;
+      auto pre = [&](int i) { return make_double2(ld_cg(u.y + i), ld_cg(u.e + i)); };
+      row_gemv<double>(x, m, t, u.Q, (long long)m, x.scoef, pre, [&](int i, double sum, double2 ye) {
+        const double yi = ye.x * inv;
+        const double qi = ye.y * inv;
         u.Q[(long long)t * m + i] = qi;
         if (u.mode == 0) u.Z[(long long)t * m + i] = yi;
         qv[i] = (Acc)qi;
@@ -635,7 +686,7 @@ __device__ void run_unit(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc&
       });
     }
     mark(10);
-    if (!team_barrier(tm.bar, x.ncta, x.st, 7)) return;
+    if (!team_barrier(tm.bar, x.ncta, x.st, 7, x.epoch)) return;
     mark(11);
 
     // ---- fused step over A
@@ -649,13 +700,14 @@ __device__ void run_unit(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc&
       }
       __syncthreads();
       mark(12);
-      double bv2 = -1.0;
+      long long bv2 = -1;
       int bi2 = -1;
       fused_step<TA, CW>(x, u, t, p, s, pol_stream, bv2, bi2);
       mark(13);
       cta_argmax_publish(x, bv2, bi2);
+      mark(15);
     }
-    if (!team_barrier(tm.bar, x.ncta, x.st, 8)) return;
+    if (!team_barrier(tm.bar, x.ncta, x.st, 8, x.epoch)) return;
     mark(14);
   }
 
@@ -669,7 +721,7 @@ __device__ void run_unit(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc&
       u.diag_g[i] = ld_cg(u.g + i);
     }
   }
-  team_barrier(tm.bar, x.ncta, x.st, 9);
+  team_barrier(tm.bar, x.ncta, x.st, 9, x.epoch);
 }
 
 template <typename TA, int CW>
@@ -702,6 +754,9 @@ __global__ void __launch_bounds__(NT, 1) greedy_kernel(GreedyLaunch L) {
   x.sups = reinterpret_cast<Acc*>(p);
   p += ((size_t)L.r_max * sizeof(Acc) + 15) & ~(size_t)15;
   x.sred = reinterpret_cast<double*>(p);
+  __shared__ uint32_t s_epoch;
+  if (threadIdx.x == 0) s_epoch = 0u;   // used by thread 0 only
+  x.epoch = &s_epoch;
 
   for (int ui = tm.u_begin; ui < tm.u_end; ++ui) {
     const UnitDesc u = L.units[L.order[ui]];

@@ -47,7 +47,7 @@ struct UnitDesc {
 
 struct TeamDesc {
   int cta0, ncta, u_begin, u_end;   // units order[u_begin .. u_end)
-  uint32_t* bar;                    // 2 words
+  uint32_t* bar;                    // word 0: the team barrier's arrival count
   double* part;                     // ncta * 4
   double* cand_val;                 // ncta
   int* cand_idx;                    // ncta

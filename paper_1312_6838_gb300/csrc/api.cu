@@ -40,7 +40,7 @@ double tau_of(const css_opts& o, int dt) {
 
 // Per-problem device state (see UnitDesc in greedy.cuh).
 struct UnitState {
-  double *f = nullptr, *g = nullptr, *g0 = nullptr;
+  double *f = nullptr, *g = nullptr, *thr = nullptr;
   unsigned char* selmask = nullptr;
   double *Q = nullptr, *Z = nullptr, *W = nullptr;
   void *qv = nullptr, *ypv = nullptr;
@@ -50,7 +50,7 @@ struct UnitState {
 void carve_scores(WsCarver& c, int n, UnitState& s) {
   s.f = c.take<double>(n);
   s.g = c.take<double>(n);
-  s.g0 = c.take<double>(n);
+  s.thr = c.take<double>(n);
   s.selmask = c.take<unsigned char>(n);
 }
 
@@ -401,7 +401,7 @@ UnitDesc make_unit(const void* A, int dt, int64_t m, int64_t n, int64_t lda, int
   u.tau = tau_of(o, dt);
   u.f = s.f;
   u.g = s.g;
-  u.g0 = s.g0;
+  u.thr = s.thr;
   u.selmask = s.selmask;
   u.Q = s.Q;
   u.Z = s.Z;
@@ -673,7 +673,7 @@ __global__ void map_sel_kernel(const int* __restrict__ local, const int* __restr
 
 struct DistLayout {
   Header h;
-  UnitState sc;            // f, g, g0, selmask over all n columns
+  UnitState sc;            // f, g, thr, selmask over all n columns
   double* f0_saved;
   std::vector<UnitState> blk;
   int* bsel;
@@ -792,7 +792,7 @@ css_status gcss_distributed(const void* A, css_dtype dtype, int64_t m, int64_t n
     UnitState st = L.blk[b];
     st.f = L.sc.f + off;
     st.g = L.sc.g + off;
-    st.g0 = L.sc.g0 + off;
+    st.thr = L.sc.thr + off;
     st.selmask = L.sc.selmask + off;
     const void* Ab = (const char*)A + off * lda * (int64_t)esize(dtype);
     units.push_back(make_unit(Ab, dtype, m, w, lda, kb, 1, B, ldb, r, st, nullptr,

@@ -201,10 +201,12 @@ __device__ void col_dots(const Ctx<Acc>& x, int len, int nj, const TM* M, long l
 }
 
 // ------------------------------------------------------------- CTA argmax ---
+// Publishes the CTA's best candidate and returns its index (every thread).
 template <typename Acc>
-__device__ void cta_argmax_publish(const Ctx<Acc>& x, long long bv, int bi) {
+__device__ int cta_argmax_publish(const Ctx<Acc>& x, long long bv, int bi) {
   __shared__ long long s_v[NW];
   __shared__ int s_i[NW];
+  __shared__ int s_best;
   warp_argmax(bv, bi);
   if (x.lane == 0) { s_v[x.warp] = bv; s_i[x.warp] = bi; }
   __syncthreads();
@@ -215,9 +217,21 @@ __device__ void cta_argmax_publish(const Ctx<Acc>& x, long long bv, int bi) {
     if (x.lane == 0) {
       x.team->cand_val[x.rank] = __longlong_as_double(v);
       x.team->cand_idx[x.rank] = i;
+      s_best = i;
     }
   }
   __syncthreads();
+  return s_best;
+}
+
+// Warms L2 with column `col` of A: the team's next pivot is one of its CTAs'
+// candidates, and the pivot phase reads that column first.
+template <typename TA>
+__device__ __forceinline__ void prefetch_column(const UnitDesc& u, int col) {
+  const unsigned bytes = (unsigned)((size_t)u.m * sizeof(TA)) & ~15u;
+  if (col < 0 || !u.vec_ok || bytes == 0u) return;
+  const TA* p = reinterpret_cast<const TA*>(u.A) + (long long)col * u.lda;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 template <typename Acc>
@@ -380,9 +394,9 @@ __device__ void fused_step(const Ctx<typename AccOf<TA>::type>& x, const UnitDes
       if (bcol >= 0) {
         const int col = bcol;
         double fi = ld_cg(u.f + col), gi = ld_cg(u.g + col);
-        const double g0 = ld_cg(u.g0 + col);
+        const double thr = ld_cg(u.thr + col);
         bool selected = __ldcg(u.selmask + col) != 0;
-        const double w = (double)bw, h = (double)bh;
+        const double w = to_f64(bw), h = to_f64(bh);
         // Theorem 2 / Theorem 4: f - 2 omega o x + s (omega o omega), g - omega o omega
         fi = fi - 2.0 * w * h + s * (w * w);
         gi = gi - w * w;
@@ -390,7 +404,7 @@ __device__ void fused_step(const Ctx<typename AccOf<TA>::type>& x, const UnitDes
         u.g[col] = gi;
         if (u.W) u.W[(long long)t * n + col] = w;
         if (col == p) { u.selmask[col] = 1; selected = true; }
-        if (!selected && g0 > 0.0 && gi > u.tau * g0) {
+        if (!selected && gi > thr) {
           const double sc = u.score_mode ? gi : fmax(fi, 0.0) / gi;
           const long long sk = score_key(sc);
           if (better(sk, col, bv, bi)) { bv = sk; bi = col; }
@@ -430,9 +444,10 @@ __device__ void init_pass(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc
     }
     acc = warp_sum(acc);
     if (x.lane == 0) {
-      const double g0 = (double)acc;
+      const double g0 = to_f64(acc);
       const double f0 = ld_cg(u.f + col);
-      u.g0[col] = g0;
+      // columns with g_i <= tau g_i^(0) are no longer candidates
+      u.thr[col] = (g0 > 0.0) ? u.tau * g0 : __longlong_as_double(0x7ff0000000000000LL);
       u.g[col] = g0;
       u.selmask[col] = 0;
       if (!isfinite(g0) || !isfinite(f0)) bad = 1;
@@ -484,7 +499,8 @@ __device__ void run_unit(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc&
     tm.tile_ctr[0] = 0u;
     tm.tile_ctr[1] = 0u;
   }
-  cta_argmax_publish(x, bv, bi);
+  const int cb0 = cta_argmax_publish(x, bv, bi);
+  if (x.tid == 0) prefetch_column<TA>(u, cb0);
   if (!team_barrier(tm.bar, x.ncta, x.st, 1, x.epoch)) return;
 
   double F = team_sum(x, 2);  // meaningful in rank 0, thread 0
@@ -704,7 +720,8 @@ __device__ void run_unit(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc&
       int bi2 = -1;
       fused_step<TA, CW>(x, u, t, p, s, pol_stream, bv2, bi2);
       mark(13);
-      cta_argmax_publish(x, bv2, bi2);
+      const int cb = cta_argmax_publish(x, bv2, bi2);
+      if (x.tid == 0) prefetch_column<TA>(u, cb);
       mark(15);
     }
     if (!team_barrier(tm.bar, x.ncta, x.st, 8, x.epoch)) return;

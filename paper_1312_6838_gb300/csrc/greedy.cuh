@@ -18,7 +18,7 @@ struct UnitDesc {
   // state
   double* f;          // numerator of the criterion, Theorem 2/4
   double* g;          // denominator (residual column norms)
-  double* g0;         // initial norms (candidate threshold)
+  double* thr;        // candidate threshold tau * g_i^(0) (+inf where g_i^(0) = 0)
   unsigned char* selmask;
   double* Q;          // m x k orthonormal basis of the selected columns
   double* Z;          // CSS: C Q (m x k, ld m).  GCSS: B^T Q (r x k, ld r)

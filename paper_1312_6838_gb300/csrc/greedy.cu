@@ -200,6 +200,173 @@ __device__ void col_dots(const Ctx<Acc>& x, int len, int nj, const TM* M, long l
   }
 }
 
+// ------------------------------------------------ double-float products ----
+// The Gram-Schmidt products of the BF16/FP32 path (Q^T a_p, Q c, Z^T e, Q d:
+// m x t multiply-adds each) run in double-float arithmetic: every FP64 value
+// of Q, Z, e and the coefficients is held as an unevaluated sum hi + lo of two
+// floats (48 significant bits), products are made exact with an FMA (Dekker's
+// product) and the running sum keeps its rounding errors (Knuth's TwoSum) --
+// the compensated dot product of Ogita, Rump and Oishi, as accurate as an
+// evaluation in twice the float precision.  About eleven FP32 operations per
+// term instead of one FP64 multiply-add, which issues some fifty times slower
+// on this part.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+// (sh, sl) += (xh + xl) * (yh + yl)
+__device__ __forceinline__ void df_fma(float& sh, float& sl, float xh, float xl, float yh, float yl) {
+  const float p = xh * yh;
+  float e = fmaf(xh, yh, -p);
+  e = fmaf(xh, yl, e);
+  e = fmaf(xl, yh, e);
+  float s, err;
+  two_sum(sh, p, s, err);
+  sh = s;
+  sl += err + e;
+}
+// (ah, al) += (bh, bl), renormalised
+__device__ __forceinline__ void df_add(float& ah, float& al, float bh, float bl) {
+  float s, e;
+  two_sum(ah, bh, s, e);
+  e += al + bl;
+  ah = s + e;
+  al = e - (ah - s);
+}
+__device__ __forceinline__ float2 df_norm(float h, float l) {
+  float s, e;
+  two_sum(h, l, s, e);
+  return make_float2(s, e);
+}
+__device__ __forceinline__ double df_to_f64(float2 v) { return to_f64(v.x) + to_f64(v.y); }
+// FP64 -> hi + lo (three FP64 operations; only where a vector element is formed)
+__device__ __forceinline__ float2 f64_to_df(double v) {
+  const float h = __double2float_rn(v);
+  return make_float2(h, __double2float_rn(v - to_f64(h)));
+}
+__device__ __forceinline__ float2 df_of(float v) { return make_float2(v, 0.f); }
+__device__ __forceinline__ float2 df_of(float2 v) { return v; }
+
+__device__ __forceinline__ void warp_df_sum(float& h, float& l) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float bh = __shfl_xor_sync(0xffffffffu, h, o);
+    const float bl = __shfl_xor_sync(0xffffffffu, l, o);
+    df_add(h, l, bh, bl);
+  }
+}
+
+// row_gemv in double-float: fin(i, sum_j M[i, j] c[j] as hi + lo, pre(i)),
+// M and c held as float2 (hi, lo).  Same row and stream split as row_gemv.
+template <typename Acc, typename Pre, typename Fin>
+__device__ void row_gemv_df(const Ctx<Acc>& x, int m, int nj, const float2* M, long long ldm,
+                            const float2* c, Pre pre, Fin fin) {
+  const int G = (m + RB - 1) / RB;
+  const int my_tiles = (G > x.rank) ? (G - x.rank + x.ncta - 1) / x.ncta : 0;
+  const int TP = (G + x.ncta - 1) / x.ncta;
+  int SP = NS;
+  while (SP > 1 && SP * TP > NS) SP >>= 1;
+  const int slots = NS / SP;
+  const int s = x.warp * 2 + (x.lane >> 4);
+  const int slot = s / SP, sub = s % SP;
+  const int r16 = x.lane & (RB - 1);
+  float2* red = reinterpret_cast<float2*>(x.sred);
+  for (int base = 0; base < my_tiles; base += slots) {
+    const int ti = base + slot;
+    const int sl = x.tid / RB, rr = x.tid % RB;
+    const int tj = base + sl;
+    const int frow = (x.tid < slots * RB && tj < my_tiles) ? (x.rank + tj * x.ncta) * RB + rr : m;
+    decltype(pre(0)) pv{};
+    if (frow < m) pv = pre(frow);
+    float ah = 0.f, al = 0.f;
+    if (ti < my_tiles) {
+      const int row = (x.rank + ti * x.ncta) * RB + r16;
+      if (row < m) {
+        const float2* mp = M + row;
+        int j = sub;
+        for (; j + 7 * SP < nj; j += 8 * SP) {
+          float2 a[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) a[q] = ld_cg(mp + (long long)(j + q * SP) * ldm);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const float2 cv = c[j + q * SP];
+            df_fma(ah, al, a[q].x, a[q].y, cv.x, cv.y);
+          }
+        }
+        for (; j < nj; j += SP) {
+          const float2 a = ld_cg(mp + (long long)j * ldm);
+          const float2 cv = c[j];
+          df_fma(ah, al, a.x, a.y, cv.x, cv.y);
+        }
+      }
+    }
+    red[s * RB + r16] = df_norm(ah, al);
+    __syncthreads();
+    if (frow < m) {
+      float h = 0.f, l = 0.f;
+      for (int q = 0; q < SP; ++q) {
+        const float2 v = red[(sl * SP + q) * RB + rr];
+        df_add(h, l, v.x, v.y);
+      }
+      fin(frow, make_float2(h, l), pv);
+    }
+    __syncthreads();
+  }
+}
+
+// col_dots in double-float: fin(j, sum_i M[i, j] v[i] as hi + lo), M as float2,
+// v as float (exact values) or float2, in shared memory.
+template <typename Acc, typename TV, typename Fin>
+__device__ void col_dots_df(const Ctx<Acc>& x, int len, int nj, const float2* M, long long ldm,
+                            const TV* v, Fin fin) {
+  const int per_cta = (nj + x.ncta - 1) / x.ncta;
+  if (per_cta >= NW / 2) {
+    for (int j = x.rank * NW + x.warp; j < nj; j += x.ncta * NW) {
+      const float2* col = M + (long long)j * ldm;
+      float h = 0.f, l = 0.f;
+#pragma unroll 8
+      for (int i = x.lane; i < len; i += 32) {
+        const float2 a = ld_cg(col + i);
+        const float2 b = df_of(v[i]);
+        df_fma(h, l, a.x, a.y, b.x, b.y);
+      }
+      const float2 n0 = df_norm(h, l);
+      h = n0.x;
+      l = n0.y;
+      warp_df_sum(h, l);
+      if (x.lane == 0) fin(j, make_float2(h, l));
+    }
+  } else {
+    float2* red = reinterpret_cast<float2*>(x.sred);
+    for (int j = x.rank; j < nj; j += x.ncta) {
+      const float2* col = M + (long long)j * ldm;
+      float h = 0.f, l = 0.f;
+#pragma unroll 8
+      for (int i = x.tid; i < len; i += NT) {
+        const float2 a = ld_cg(col + i);
+        const float2 b = df_of(v[i]);
+        df_fma(h, l, a.x, a.y, b.x, b.y);
+      }
+      const float2 n0 = df_norm(h, l);
+      h = n0.x;
+      l = n0.y;
+      warp_df_sum(h, l);
+      __syncthreads();
+      if (x.lane == 0) red[x.warp] = make_float2(h, l);
+      __syncthreads();
+      if (x.warp == 0) {
+        float2 w = (x.lane < NW) ? red[x.lane] : make_float2(0.f, 0.f);
+        h = w.x;
+        l = w.y;
+        warp_df_sum(h, l);
+        if (x.lane == 0) fin(j, make_float2(h, l));
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------- CTA argmax ---
 // Publishes the CTA's best candidate and returns its index (every thread).
 template <typename Acc>
@@ -479,11 +646,20 @@ __device__ void init_pass(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc
 template <typename TA, int CW>
 __device__ void run_unit(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc& u) {
   using Acc = typename AccOf<TA>::type;
+  // BF16/FP32 input: Q, Z (CSS), e and the coefficients are held as float
+  // pairs and their products run in double-float (see row_gemv_df)
+  constexpr bool kDF = sizeof(Acc) == 4;
   __shared__ double s_scal[4];
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_keep = policy_evict_last();
   const TeamDesc& tm = *x.team;
   const int m = u.m, n = u.n;
+  float2* const Q2 = reinterpret_cast<float2*>(u.Q);
+  float2* const Z2 = reinterpret_cast<float2*>(u.Z);
+  float2* const coef2 = reinterpret_cast<float2*>(u.coef);
+  float2* const e2 = reinterpret_cast<float2*>(u.e1);
+  float2* const scoef2 = reinterpret_cast<float2*>(x.scoef);
+  float2* const se2 = reinterpret_cast<float2*>(x.se64);
 
   // ---- initialisation: g^(0), F^(0), first argmax
   long long bv = -1;
@@ -519,35 +695,58 @@ __device__ void run_unit(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc&
     const int p_arg = p;
     if (t < u.n_forced) p = u.forced[t];
     if (p < 0) break;
+    // f_p, g_p for the error trace: loaded now, used after the staging below
+    double fp = 0.0, gp = 1.0;
     if (x.rank == 0 && x.tid == 0) {
+      fp = ld_cg(u.f + p);
+      gp = ld_cg(u.g + p);
       // counter of the next iteration's fused step; its last user finished
       // before the previous iteration's final barrier
       tm.tile_ctr[(t + 1) & 1] = 0u;
       if (u.diag_argmax) u.diag_argmax[t] = p_arg;
       u.sel[t] = p;
-      F = F - ld_cg(u.f + p) / ld_cg(u.g + p);   // Theorem 1 / Theorem 3
-      u.trace[t + 1] = F;
     }
     const TA* ap = reinterpret_cast<const TA*>(u.A) + (long long)p * u.lda;
+    if constexpr (kDF) {
+      // a_p is exact in float
 #pragma unroll 8
-    for (int i = x.tid; i < m; i += NT) x.se64[i] = to_f64(load_elem<TA>(ap + i));
-    __syncthreads();
-    col_dots<double>(x, m, t, u.Q, (long long)m, x.se64, [&](int j, double v) { u.coef[j] = v; });
+      for (int i = x.tid; i < m; i += NT) x.seacc[i] = load_elem<TA>(ap + i);
+      __syncthreads();
+      col_dots_df(x, m, t, Q2, (long long)m, x.seacc, [&](int j, float2 v) { coef2[j] = v; });
+    } else {
+#pragma unroll 8
+      for (int i = x.tid; i < m; i += NT) x.se64[i] = to_f64(load_elem<TA>(ap + i));
+      __syncthreads();
+      col_dots<double>(x, m, t, u.Q, (long long)m, x.se64, [&](int j, double v) { u.coef[j] = v; });
+    }
+    if (x.rank == 0 && x.tid == 0) {
+      F = F - fp / gp;   // Theorem 1 / Theorem 3
+      u.trace[t + 1] = F;
+    }
     mark(2);
     if (!team_barrier(tm.bar, x.ncta, x.st, 2, x.epoch)) return;
     mark(3);
 
     // ---- Phase C: e = a_p - Q_t c, ||e||^2 partials (delta_p of Eq. delta_omega)
-    for (int j = x.tid; j < t; j += NT) x.scoef[j] = ld_cg(u.coef + j);
-    __syncthreads();
     double nrm_part = 0.0;
-    Acc* e_acc = reinterpret_cast<Acc*>(u.e1);   // e in Acc precision, converted once
-    row_gemv<double>(x, m, t, u.Q, (long long)m, x.scoef, NoPre{}, [&](int i, double sum, int) {
-      const double ei = x.se64[i] - sum;   // a_p is still staged in se64
-      u.e[i] = ei;
-      e_acc[i] = (Acc)ei;
-      nrm_part += ei * ei;
-    });
+    if constexpr (kDF) {
+      for (int j = x.tid; j < t; j += NT) scoef2[j] = ld_cg(coef2 + j);
+      __syncthreads();
+      row_gemv_df(x, m, t, Q2, (long long)m, scoef2, NoPre{}, [&](int i, float2 sum, int) {
+        const double ei = to_f64(x.seacc[i]) - df_to_f64(sum);   // a_p is still staged
+        u.e[i] = ei;
+        e2[i] = f64_to_df(ei);   // e as hi + lo, formed once
+        nrm_part += ei * ei;
+      });
+    } else {
+      for (int j = x.tid; j < t; j += NT) x.scoef[j] = ld_cg(u.coef + j);
+      __syncthreads();
+      row_gemv<double>(x, m, t, u.Q, (long long)m, x.scoef, NoPre{}, [&](int i, double sum, int) {
+        const double ei = x.se64[i] - sum;   // a_p is still staged in se64
+        u.e[i] = ei;
+        nrm_part += ei * ei;
+      });
+    }
     mark(4);
     nrm_part = block_sum_to0(nrm_part, x.sred);
     if (x.tid == 0) tm.part[x.rank * 4 + 0] = nrm_part;
@@ -560,10 +759,20 @@ __device__ void run_unit(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc&
     double nrm_acc = 0.0;
     if (x.warp == 0)
       for (int r = x.lane; r < x.ncta; r += 32) nrm_acc += ld_cg(tm.part + r * 4 + 0);
+    if constexpr (kDF) {
 #pragma unroll 8
-    for (int i = x.tid; i < m; i += NT) {
-      x.se64[i] = ld_cg(u.e + i);
-      x.seacc[i] = ld_cg(e_acc + i);
+      for (int i = x.tid; i < m; i += NT) {
+        const float2 ev = ld_cg(e2 + i);
+        se2[i] = ev;
+        x.seacc[i] = ev.x;
+      }
+    } else {
+#pragma unroll 8
+      for (int i = x.tid; i < m; i += NT) {
+        const double ei = ld_cg(u.e + i);
+        x.se64[i] = ei;
+        x.seacc[i] = (Acc)ei;
+      }
     }
     if (x.warp == 0) {
       nrm_acc = warp_sum(nrm_acc);
@@ -624,7 +833,7 @@ __device__ void run_unit(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc&
             srow[kr * NW + x.warp] = acc;
           } else {
             u.y[i] = (double)acc;
-            ey += x.se64[i] * (double)acc;
+            ey += (kDF ? df_to_f64(se2[i]) : x.se64[i]) * (double)acc;
           }
         }
       }
@@ -636,13 +845,16 @@ __device__ void run_unit(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc&
             if (i < m) {
               const double yi = (double)srow[idx];
               u.y[i] = yi;
-              ey += x.se64[i] * yi;
+              ey += (kDF ? df_to_f64(se2[i]) : x.se64[i]) * yi;
             }
           }
         }
       }
       mark(7);
-      col_dots<double>(x, m, t, u.Z, (long long)m, x.se64, [&](int j, double v) { u.coef[j] = v; });
+      if constexpr (kDF)
+        col_dots_df(x, m, t, Z2, (long long)m, se2, [&](int j, float2 v) { coef2[j] = v; });
+      else
+        col_dots<double>(x, m, t, u.Z, (long long)m, x.se64, [&](int j, double v) { u.coef[j] = v; });
       mark(8);
       ey = block_sum_to0(ey, x.sred);
       if (x.tid == 0) tm.part[x.rank * 4 + 1] = ey;
@@ -659,7 +871,10 @@ __device__ void run_unit(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc&
       }
       __syncthreads();
       row_gemv<Acc>(x, m, u.r, B, u.ldt, x.sups, NoPre{}, [&](int i, double sum, int) { u.y[i] = sum; });
-      col_dots<double>(x, u.r, t, u.Z, (long long)u.r, x.scoef, [&](int j, double v) { u.coef[j] = v; });
+      col_dots<double>(x, u.r, t, u.Z, (long long)u.r, x.scoef, [&](int j, double v) {
+        if constexpr (kDF) coef2[j] = f64_to_df(v);
+        else u.coef[j] = v;
+      });
       double ss = 0.0;
       for (int j = x.tid; j < u.r; j += NT) ss += x.scoef[j] * x.scoef[j];
       s_un = block_sum_to0(ss, x.sred);
@@ -681,7 +896,11 @@ __device__ void run_unit(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc&
       double ey_acc = 0.0;
       if (u.mode == 0 && x.warp == 0)
         for (int r = x.lane; r < x.ncta; r += 32) ey_acc += ld_cg(tm.part + r * 4 + 1);
-      for (int j = x.tid; j < t; j += NT) x.scoef[j] = ld_cg(u.coef + j);
+      if constexpr (kDF) {
+        for (int j = x.tid; j < t; j += NT) scoef2[j] = ld_cg(coef2 + j);
+      } else {
+        for (int j = x.tid; j < t; j += NT) x.scoef[j] = ld_cg(u.coef + j);
+      }
       if (u.mode == 0 && x.warp == 0) {
         ey_acc = warp_sum(ey_acc);
         if (x.lane == 0) s_scal[2] = ey_acc / nrm2;
@@ -692,14 +911,26 @@ __device__ void run_unit(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc&
       Acc* qv = reinterpret_cast<Acc*>(u.qv);
       Acc* ypv = reinterpret_cast<Acc*>(u.ypv);
       auto pre = [&](int i) { return make_double2(ld_cg(u.y + i), ld_cg(u.e + i)); };
-      row_gemv<double>(x, m, t, u.Q, (long long)m, x.scoef, pre, [&](int i, double sum, double2 ye) {
-        const double yi = ye.x * inv;
-        const double qi = ye.y * inv;
-        u.Q[(long long)t * m + i] = qi;
-        if (u.mode == 0) u.Z[(long long)t * m + i] = yi;
-        qv[i] = (Acc)qi;
-        ypv[i] = (Acc)(yi - sum * inv);
-      });
+      if constexpr (kDF) {
+        row_gemv_df(x, m, t, Q2, (long long)m, scoef2, pre, [&](int i, float2 sum, double2 ye) {
+          const double yi = ye.x * inv;
+          const double qi = ye.y * inv;
+          const float2 q2 = f64_to_df(qi);
+          Q2[(long long)t * m + i] = q2;
+          if (u.mode == 0) Z2[(long long)t * m + i] = f64_to_df(yi);
+          qv[i] = q2.x;
+          ypv[i] = (Acc)(yi - df_to_f64(sum) * inv);
+        });
+      } else {
+        row_gemv<double>(x, m, t, u.Q, (long long)m, x.scoef, pre, [&](int i, double sum, double2 ye) {
+          const double yi = ye.x * inv;
+          const double qi = ye.y * inv;
+          u.Q[(long long)t * m + i] = qi;
+          if (u.mode == 0) u.Z[(long long)t * m + i] = yi;
+          qv[i] = (Acc)qi;
+          ypv[i] = (Acc)(yi - sum * inv);
+        });
+      }
     }
     mark(10);
     if (!team_barrier(tm.bar, x.ncta, x.st, 7, x.epoch)) return;

@@ -390,11 +390,12 @@ def main():
     per_iter = a_bytes + c_bytes + 48 * n
     achieved = per_iter * res.n_sel / (statistics.mean(loop_ms) / 1e3) / 1e9
     # DRAM traffic per launch from the ncu capture summarised in
-    # profiles/greedy_kernel_decay_4096x65536.md: 1.015 x the bytes of A per
-    # A pass (C stays in L2), scaled by the A passes of this launch
+    # profiles/greedy_kernel_decay_4096x65536.md (4096 x 32768, 17 A passes):
+    # reads 1.0163 x the bytes of A and writes 63.2 B per column per A pass
+    # (C stays in L2), scaled by the A passes of this launch
     traffic = None
     if args.workload == WORKLOAD and args.dtype == "bf16":
-        traffic = (res.n_sel + 1) * a_bytes * 1.015
+        traffic = (res.n_sel + 1) * (a_bytes * 1.0163 + 63.2 * n)
     peak, peak_kind = peaks()
     out = {
         "metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": ws,

@@ -53,6 +53,10 @@ struct Params {
   long long lda_col;
   int* err;
   unsigned long long spin_ns;
+  // symmetric use of C = A A^T: mode 2 computes only the tiles that touch
+  // the lower triangle (rows >= columns); mode 3 multiplies by the upper
+  // triangle U' of C (diagonal halved), so M-tile J starts at K = 128 J
+  int tri;
 };
 
 // ------------------------------------------------------------- PTX glue -----
@@ -176,6 +180,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (P.mode >= 2) {
     ntile0 = blockIdx.y * P.n_tile;
   }
+  // strictly upper tile of C: not needed (the lower triangle is mirrored)
+  if (P.tri && P.mode == 2 && tile0 + BM - 1 < ntile0) return;
+  // U' rows of this tile are zero left of column tile0
+  if (P.tri && P.mode == 3) kb_begin = tile0 / BK;
   const int parts = P.nparts;
   const int n_it = max(0, kb_end - kb_begin) * parts;
 
@@ -359,13 +367,17 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // B (FP32, m x r, ldb) -> three BF16 parts B1 + B2 + B3 (m x rpad each, ld mpad),
 // laid out side by side: part p, column j at Bp[(p * rpad + j) * mpad + i].
+// tri: B is the symmetric C with only its lower triangle valid, and the parts
+// hold U' (column j, row i: C[i, j] for i > j, C[j, j] / 2 on the diagonal,
+// 0 above), so that a_i^T C a_i = 2 a_i^T U' a_i.
 __global__ void split3_kernel(const float* __restrict__ B, long long ldb, int m, int r, int mpad,
-                              int rpad, __nv_bfloat16* __restrict__ Bp) {
+                              int rpad, __nv_bfloat16* __restrict__ Bp, int tri) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long tot = (long long)mpad * rpad;
   if (idx >= tot) return;
   const int i = (int)(idx % mpad), j = (int)(idx / mpad);
-  float v = (i < m && j < r) ? B[(long long)j * ldb + i] : 0.f;
+  float v = (i < m && j < r && (!tri || i >= j)) ? B[(long long)j * ldb + i] : 0.f;
+  if (tri && i == j) v *= 0.5f;
   __nv_bfloat16 b1 = __float2bfloat16_rn(v);
   v -= __bfloat162float(b1);
   __nv_bfloat16 b2 = __float2bfloat16_rn(v);
@@ -471,7 +483,7 @@ cudaError_t colnorms(const void* A, long long lda, int m, int n, const float* B,
   const int rpad = (r + 15) / 16 * 16;
   __nv_bfloat16* Bp = (__nv_bfloat16*)scratch;
   const long long tot = (long long)mpad * rpad;
-  split3_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(B, ldb, m, r, mpad, rpad, Bp);
+  split3_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(B, ldb, m, r, mpad, rpad, Bp, 0);
   CUtensorMap ta, tb;
   int n_half, halves;
   halves_for(r, n_half, halves);
@@ -501,12 +513,31 @@ cudaError_t colnorms(const void* A, long long lda, int m, int n, const float* B,
 }
 
 __global__ void sum_rows_kernel(const double* __restrict__ partial, int nblk, int n,
-                                double* __restrict__ out) {
+                                double* __restrict__ out, double scale) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double s = 0.0;
   for (int b = 0; b < nblk; ++b) s += partial[(long long)b * n + i];
-  out[i] = s;
+  out[i] = scale * s;
+}
+
+// Upper triangle of the m x m matrix C (ld m) from its lower triangle, through
+// 32 x 32 shared-memory tiles (coalesced reads and writes).
+__global__ void mirror_lower_kernel(float* __restrict__ C, int m) {
+  __shared__ float tile[32][33];
+  const int bi = blockIdx.x, bj = blockIdx.y;   // source tile: rows bi*32.., columns bj*32..
+  if (bi < bj) return;                          // only tiles on or below the diagonal
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int k = ty; k < 32; k += blockDim.y) {
+    const int r = bi * 32 + tx, c = bj * 32 + k;
+    if (r < m && c < m) tile[k][tx] = C[(long long)c * m + r];
+  }
+  __syncthreads();
+  // C[c, r] = C[r, c] for r > c
+  for (int k = ty; k < 32; k += blockDim.y) {
+    const int c = bj * 32 + tx, r = bi * 32 + k;
+    if (r < m && c < m && r > c) C[(long long)r * m + c] = tile[tx][k];
+  }
 }
 
 size_t css_f0_scratch_bytes(int m, int n) {
@@ -532,6 +563,7 @@ cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, do
     if (!make_map(&ta, A, (uint64_t)m, (uint64_t)n, (uint64_t)lda, BK)) return cudaErrorInvalidValue;
     Params P{};
     P.mode = 2;
+    P.tri = 1;
     P.M = m;
     P.N = m;
     P.n_half = 256;
@@ -551,18 +583,23 @@ cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, do
     tc_kernel<true, true><<<grid, kThreads, smem, s>>>(ta, ta, P);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  // C = C1 + C2 + C3 in BF16
+  // the greedy iterations read whole rows of C: fill its upper triangle
+  mirror_lower_kernel<<<dim3((m + 31) / 32, (m + 31) / 32), dim3(32, 8), 0, s>>>(C, m);
+  // U' (upper triangle of C, diagonal halved) = U1 + U2 + U3 in BF16
   {
     const long long tot = (long long)mpad * rpad;
-    split3_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(C, m, m, m, mpad, rpad, Cp);
+    split3_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(C, m, m, m, mpad, rpad, Cp, 1);
   }
-  // partial[M-tile][i] = sum over the tile's rows r of A[r, i] (C A)[r, i]
+  // partial[M-tile][i] = sum over the tile's rows r of A[r, i] (U' A)[r, i];
+  // U' is zero left of the diagonal, so M-tile J contracts over K >= 128 J only
+  // (half of the products of C A)
   {
     CUtensorMap ta, tb;
     if (!make_map(&ta, Cp, (uint64_t)mpad, (uint64_t)(3 * rpad), (uint64_t)mpad, BM)) return cudaErrorInvalidValue;
     if (!make_map(&tb, A, (uint64_t)m, (uint64_t)n, (uint64_t)lda, 256)) return cudaErrorInvalidValue;
     Params P{};
     P.mode = 3;
+    P.tri = 1;
     P.M = m;
     P.N = n;
     P.n_half = 256;
@@ -586,7 +623,8 @@ cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, do
     tc_kernel<false, false><<<grid, kThreads, smem, s>>>(ta, tb, P);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  sum_rows_kernel<<<(n + 255) / 256, 256, 0, s>>>(partial, (m + BM - 1) / BM, n, f);
+  // f_i = a_i^T C a_i = 2 a_i^T U' a_i
+  sum_rows_kernel<<<(n + 255) / 256, 256, 0, s>>>(partial, (m + BM - 1) / BM, n, f, 2.0);
   return cudaGetLastError();
 }
 

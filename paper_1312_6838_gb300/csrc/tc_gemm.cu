@@ -23,6 +23,7 @@
 #include <cudaTypedefs.h>
 
 #include "tc.cuh"
+#include "css_common.cuh"
 
 namespace css {
 namespace tc {
@@ -30,7 +31,7 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BK = 64;        // K elements per stage: one 128-byte swizzle row
-constexpr int STAGES = 3;
+constexpr int STAGES = 3;     // ring depth, at most (Params::stages picks 1..3)
 constexpr int kThreads = 192;
 constexpr int kTmemCols = 512;
 
@@ -57,6 +58,11 @@ struct Params {
   // the lower triangle (rows >= columns); mode 3 multiplies by the upper
   // triangle U' of C (diagonal halved), so M-tile J starts at K = 128 J
   int tri;
+  // group: one ring stage holds the distinct tiles of every part for one K
+  // block (a tile shared by all parts is loaded once), and the parts' MMAs
+  // run back to back on it; otherwise each (K block, part) is its own stage
+  int group;
+  int stages;        // ring depth (1..STAGES)
 };
 
 // ------------------------------------------------------------- PTX glue -----
@@ -143,6 +149,31 @@ __device__ __forceinline__ void fence_before() {
 __device__ __forceinline__ void fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
+// Double-float sums for the epilogues: products of two floats are exact as
+// p + e (Dekker, by FMA) and sums keep their rounding error (Knuth's TwoSum),
+// 48 significant bits without FP64 instructions (which issue ~50x slower than
+// FP32 on this part).
+__device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void df_add2(float& ah, float& al, float bh, float bl) {
+  float s, e;
+  df_two_sum(ah, bh, s, e);
+  e += al + bl;
+  ah = s + e;
+  al = e - (ah - s);
+}
+__device__ __forceinline__ void df_acc_prod(float& sh, float& sl, float a, float b) {
+  const float p = a * b;
+  const float e = fmaf(a, b, -p);
+  float s, err;
+  df_two_sum(sh, p, s, err);
+  sh = s;
+  sl += err + e;
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
   asm volatile(
@@ -163,7 +194,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int a_bytes = BM * BK * 2;
-  uint8_t* bars_base = smem + STAGES * P.stage_bytes;
+  const int NSTG = P.stages;
+  uint8_t* bars_base = smem + NSTG * P.stage_bytes;
   uint64_t* full = (uint64_t*)bars_base;
   uint64_t* empty = full + STAGES;
   uint64_t* done = empty + STAGES;
@@ -185,10 +217,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   // U' rows of this tile are zero left of column tile0
   if (P.tri && P.mode == 3) kb_begin = tile0 / BK;
   const int parts = P.nparts;
-  const int n_it = max(0, kb_end - kb_begin) * parts;
+  // group mode: tiles per stage (a part stride of 0 means one shared tile)
+  const int nA = (P.group && P.a_part_stride != 0) ? parts : 1;
+  const int nB = (P.group && P.b_part_stride != 0) ? parts : 1;
+  const int b_tile_bytes = P.halves * P.n_half * BK * 2;
+  const int n_it = max(0, kb_end - kb_begin) * (P.group ? 1 : parts);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < NSTG; ++s) {
       mbar_init(smem_u32(&full[s]), 1);
       mbar_init(smem_u32(&empty[s]), 1);
     }
@@ -210,58 +246,72 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------------------ producer
     int issued = 0;
     for (int it = 0; it < n_it; ++it) {
-      const int s = it % STAGES;
-      const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+      const int s = it % NSTG;
+      const uint32_t ph = (uint32_t)((it / NSTG) & 1);
       if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u, P.err, P.spin_ns)) break;
-      const int kb = kb_begin + it / parts, part = it % parts;
+      const int kb = kb_begin + (P.group ? it : it / parts);
+      const int part0 = P.group ? 0 : it % parts;
       const int k0 = kb * BK;
       uint8_t* sa = smem + s * P.stage_bytes;
-      uint8_t* sb = sa + a_bytes;
+      uint8_t* sb = sa + nA * a_bytes;
       const uint32_t fb = smem_u32(&full[s]);
-      mbar_expect_tx(fb, (uint32_t)(a_bytes + P.halves * P.n_half * BK * 2));
-      if (A_MN) {
-        tma_load_2d(smem_u32(sa), &tmA, fb, tile0, k0);
-        tma_load_2d(smem_u32(sa + 64 * BK * 2), &tmA, fb, tile0 + 64, k0);
-      } else {
-        tma_load_2d(smem_u32(sa), &tmA, fb, k0, part * P.a_part_stride + tile0);
+      mbar_expect_tx(fb, (uint32_t)(nA * a_bytes + nB * b_tile_bytes));
+      for (int pa = 0; pa < nA; ++pa) {
+        const int part = part0 + pa;
+        uint8_t* ta = sa + pa * a_bytes;
+        if (A_MN) {
+          tma_load_2d(smem_u32(ta), &tmA, fb, tile0, k0);
+          tma_load_2d(smem_u32(ta + 64 * BK * 2), &tmA, fb, tile0 + 64, k0);
+        } else {
+          tma_load_2d(smem_u32(ta), &tmA, fb, k0, part * P.a_part_stride + tile0);
+        }
       }
-      if (B_MN) {
-        // N-major B: 64-row boxes stacked 8 KB apart (the descriptor's LBO)
-        for (int q = 0; q < P.halves * P.n_half / 64; ++q)
-          tma_load_2d(smem_u32(sb + q * 64 * BK * 2), &tmB, fb, ntile0 + 64 * q, k0);
-      } else {
-        for (int h = 0; h < P.halves; ++h)
-          tma_load_2d(smem_u32(sb + h * P.n_half * BK * 2), &tmB, fb, k0,
-                      ntile0 + part * P.b_part_stride + h * P.n_half);
+      for (int pb = 0; pb < nB; ++pb) {
+        const int part = part0 + pb;
+        uint8_t* tb = sb + pb * b_tile_bytes;
+        if (B_MN) {
+          // N-major B: 64-row boxes stacked 8 KB apart (the descriptor's LBO)
+          for (int q = 0; q < P.halves * P.n_half / 64; ++q)
+            tma_load_2d(smem_u32(tb + q * 64 * BK * 2), &tmB, fb, ntile0 + 64 * q, k0);
+        } else {
+          for (int h = 0; h < P.halves; ++h)
+            tma_load_2d(smem_u32(tb + h * P.n_half * BK * 2), &tmB, fb, k0,
+                        ntile0 + part * P.b_part_stride + h * P.n_half);
+        }
       }
       issued = it + 1;
     }
     // on failure: let the copies already issued land before the CTA exits
     if (issued < n_it) {
-      for (int it = max(0, issued - STAGES); it < issued; ++it) {
-        const int s = it % STAGES;
-        mbar_wait(smem_u32(&full[s]), (uint32_t)((it / STAGES) & 1), P.err, P.spin_ns);
+      for (int it = max(0, issued - NSTG); it < issued; ++it) {
+        const int s = it % NSTG;
+        mbar_wait(smem_u32(&full[s]), (uint32_t)((it / NSTG) & 1), P.err, P.spin_ns);
       }
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------------------------------------------------- MMA issuer
     const uint32_t idesc = make_idesc(P.n_half, BM, A_MN, B_MN);
+    const int pg = P.group ? parts : 1;   // parts whose MMAs share one stage
     for (int it = 0; it < n_it; ++it) {
-      const int s = it % STAGES;
-      const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+      const int s = it % NSTG;
+      const uint32_t ph = (uint32_t)((it / NSTG) & 1);
       if (!mbar_wait(smem_u32(&full[s]), ph, P.err, P.spin_ns)) break;
       fence_after();
-      const uint32_t sa = smem_u32(smem + s * P.stage_bytes);
-      const uint32_t sb = sa + a_bytes;
+      const uint32_t sa0 = smem_u32(smem + s * P.stage_bytes);
+      const uint32_t sb0 = sa0 + nA * a_bytes;
 #pragma unroll
       for (int ks = 0; ks < BK / 16; ++ks) {
-        // A: M-major -> 16 K rows of 128 bytes per step; K-major -> 32 bytes
-        const uint64_t ad = A_MN ? make_desc(sa + ks * 2048, 64 * BK * 2, 1024)
-                                 : make_desc(sa + ks * 32, 16, 1024);
-        for (int h = 0; h < P.halves; ++h) {
-          const uint64_t bd = B_MN ? make_desc(sb + h * P.n_half * BK * 2 + ks * 2048, 64 * BK * 2, 1024)
-                                   : make_desc(sb + h * P.n_half * BK * 2 + ks * 32, 16, 1024);
-          umma(tmem + h * P.n_half, ad, bd, idesc, (it > 0 || ks > 0) ? 1u : 0u);
+        for (int pp = 0; pp < pg; ++pp) {
+          const uint32_t sa = sa0 + (nA > 1 ? pp : 0) * a_bytes;
+          const uint32_t sb = sb0 + (nB > 1 ? pp : 0) * b_tile_bytes;
+          // A: M-major -> 16 K rows of 128 bytes per step; K-major -> 32 bytes
+          const uint64_t ad = A_MN ? make_desc(sa + ks * 2048, 64 * BK * 2, 1024)
+                                   : make_desc(sa + ks * 32, 16, 1024);
+          for (int h = 0; h < P.halves; ++h) {
+            const uint64_t bd = B_MN ? make_desc(sb + h * P.n_half * BK * 2 + ks * 2048, 64 * BK * 2, 1024)
+                                     : make_desc(sb + h * P.n_half * BK * 2 + ks * 32, 16, 1024);
+            umma(tmem + h * P.n_half, ad, bd, idesc, (it > 0 || ks > 0 || pp > 0) ? 1u : 0u);
+          }
         }
       }
       umma_commit(smem_u32(&empty[s]));
@@ -294,19 +344,23 @@ __global__ void __launch_bounds__(kThreads, 1)
       // column dots: partial[M-tile][c] = sum over this tile's rows r of
       // Acol[r, c] * D[r, c]; rows are TMEM lanes, so each 16-column chunk is
       // reduced across the warp (transpose reduction) and then across warps
-      __shared__ double cred[4][16];
+      // (products exact as hi + lo, sums in double-float, one FP64 add per
+      // column at the end)
+      __shared__ float2 cred[4][16];
       const int ncols = P.halves * P.n_half;
       for (int j0 = 0; j0 < ncols; j0 += 16) {
         float v[16];
         tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)j0, v);
-        double pr[16];
+        float ph[16], pl[16];
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj) {
           const int c = ntile0 + j0 + jj;
-          pr[jj] = 0.0;
+          ph[jj] = 0.f;
+          pl[jj] = 0.f;
           if (row < P.M && c < P.N) {
             const float a = __bfloat162float(P.Acol[(long long)c * P.lda_col + row]);
-            pr[jj] = (double)a * (double)v[jj];
+            ph[jj] = a * v[jj];
+            pl[jj] = fmaf(a, v[jj], -ph[jj]);
           }
         }
         // 16 values over 32 lanes: lane L ends with the warp sum of index L >> 1
@@ -316,23 +370,34 @@ __global__ void __launch_bounds__(kThreads, 1)
           const bool up = (lane & mask) != 0;
 #pragma unroll
           for (int jj = 0; jj < half; ++jj) {
-            const double send = up ? pr[jj] : pr[jj + half];
-            const double keep = up ? pr[jj + half] : pr[jj];
-            pr[jj] = keep + __shfl_xor_sync(0xffffffffu, send, mask);
+            const float sh = up ? ph[jj] : ph[jj + half], sl = up ? pl[jj] : pl[jj + half];
+            const float kh = up ? ph[jj + half] : ph[jj], kl = up ? pl[jj + half] : pl[jj];
+            const float oh = __shfl_xor_sync(0xffffffffu, sh, mask);
+            const float ol = __shfl_xor_sync(0xffffffffu, sl, mask);
+            ph[jj] = kh;
+            pl[jj] = kl;
+            df_add2(ph[jj], pl[jj], oh, ol);
           }
         }
-        double tot = pr[0] + __shfl_xor_sync(0xffffffffu, pr[0], 1);
-        if ((lane & 1) == 0) cred[q][lane >> 1] = tot;
+        {
+          const float oh = __shfl_xor_sync(0xffffffffu, ph[0], 1);
+          const float ol = __shfl_xor_sync(0xffffffffu, pl[0], 1);
+          df_add2(ph[0], pl[0], oh, ol);
+        }
+        if ((lane & 1) == 0) cred[q][lane >> 1] = make_float2(ph[0], pl[0]);
         asm volatile("bar.sync 1, 128;" ::: "memory");
         if (q == 0 && lane < 16) {
           const int c = ntile0 + j0 + lane;
-          if (c < P.N)
-            P.f[(long long)blockIdx.x * P.N + c] = cred[0][lane] + cred[1][lane] + cred[2][lane] + cred[3][lane];
+          if (c < P.N) {
+            float h = cred[0][lane].x, l = cred[0][lane].y;
+            for (int w = 1; w < 4; ++w) df_add2(h, l, cred[w][lane].x, cred[w][lane].y);
+            P.f[(long long)blockIdx.x * P.N + c] = to_f64(h) + to_f64(l);
+          }
         }
         asm volatile("bar.sync 1, 128;" ::: "memory");
       }
     } else if (ok) {
-      double acc = 0.0;
+      float sh = 0.f, sl = 0.f;   // mode 1: sum of squares in double-float
       const int ncols = P.halves * P.n_half;
       for (int j0 = 0; j0 < ncols; j0 += 16) {
         float v[16];
@@ -348,12 +413,12 @@ __global__ void __launch_bounds__(kThreads, 1)
               if (P.mode == 0)
                 P.out[(long long)blockIdx.y * P.M * P.N + (long long)j * P.M + row] = v[jj];
               else
-                acc += (double)v[jj] * (double)v[jj];
+                df_acc_prod(sh, sl, v[jj], v[jj]);
             }
           }
         }
       }
-      if (P.mode == 1 && row < P.M) P.f[row] = acc;
+      if (P.mode == 1 && row < P.M) P.f[row] = to_f64(sh) + to_f64(sl);
     }
     fence_before();
   }
@@ -426,7 +491,7 @@ void halves_for(int r, int& n_half, int& halves) {
   }
 }
 
-size_t smem_for(int stage_bytes) { return (size_t)STAGES * stage_bytes + 256 + 1024; }
+size_t smem_for(int stage_bytes, int stages = STAGES) { return (size_t)stages * stage_bytes + 256 + 1024; }
 
 }  // namespace
 
@@ -459,6 +524,7 @@ cudaError_t project_partials(const void* A, long long lda, int m, int n, const v
   P.kb_total = (n + BK - 1) / BK;
   P.kb_per_cta = (P.kb_total + slices - 1) / slices;
   P.nparts = 1;
+  P.stages = STAGES;
   P.stage_bytes = BM * BK * 2 + halves * n_half * BK * 2;
   P.out = partial;
   P.err = err;
@@ -499,6 +565,7 @@ cudaError_t colnorms(const void* A, long long lda, int m, int n, const float* B,
   P.kb_total = (m + BK - 1) / BK;
   P.kb_per_cta = P.kb_total;
   P.nparts = 3;
+  P.stages = STAGES;
   P.b_part_stride = rpad;
   P.stage_bytes = BM * BK * 2 + halves * n_half * BK * 2;
   P.f = f;
@@ -572,6 +639,7 @@ cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, do
     P.kb_total = (n + BK - 1) / BK;
     P.kb_per_cta = P.kb_total;
     P.nparts = 1;
+    P.stages = STAGES;
     P.stage_bytes = BM * BK * 2 + 256 * BK * 2;
     P.out = C;
     P.err = err;
@@ -602,24 +670,29 @@ cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, do
     P.tri = 1;
     P.M = m;
     P.N = n;
+    // 512 columns per CTA (two MMAs of N = 256, the whole TMEM) and one stage
+    // per K block holding the three U' parts and the single shared A tile:
+    // 112 KB per stage, two stages
     P.n_half = 256;
-    P.halves = 1;
-    P.n_tile = 256;
+    P.halves = 2;
+    P.n_tile = 512;
+    P.group = 1;
     P.kb_total = (m + BK - 1) / BK;
     P.kb_per_cta = P.kb_total;
     P.nparts = 3;
+    P.stages = 2;
     P.a_part_stride = rpad;
     P.b_part_stride = 0;
-    P.stage_bytes = BM * BK * 2 + 256 * BK * 2;
+    P.stage_bytes = 3 * BM * BK * 2 + 512 * BK * 2;
     P.f = partial;
     P.Acol = (const __nv_bfloat16*)A;
     P.lda_col = lda;
     P.err = err;
     P.spin_ns = spin_ns;
-    const size_t smem = smem_for(P.stage_bytes);
+    const size_t smem = smem_for(P.stage_bytes, P.stages);
     if ((e = cudaFuncSetAttribute(tc_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
       return e;
-    dim3 grid((m + BM - 1) / BM, (n + 255) / 256);
+    dim3 grid((m + BM - 1) / BM, (n + 511) / 512);
     tc_kernel<false, false><<<grid, kThreads, smem, s>>>(ta, tb, P);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }

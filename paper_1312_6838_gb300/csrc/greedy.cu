@@ -7,12 +7,14 @@
 // one cooperative launch.  A single large problem uses one team = the grid.
 //
 // Per iteration t (p = column picked at t):
-//   pivot     e = (I - Q Q^T) a_p by two Gram-Schmidt passes (FP64), the first
-//             with the coefficients Q^T a_p = omega^(r)_p already held in W;
-//             delta_p = ||e||^2, q = e / ||e|| (Eq. delta_omega: omega = A^T q).
+//   pivot     e = (I - Q Q^T) a_p, one Gram-Schmidt pass with the coefficients
+//             c = Q^T a_p formed exactly (FP64, or double-float for BF16/FP32
+//             input); delta_p = ||e||^2, q = e / ||e|| (Eq. delta_omega:
+//             omega = A^T q).
 //   target    CSS:  y = C q with C = A A^T;  GCSS: upsilon = B^T q, y = B upsilon.
 //             s = q^T y (= ||omega||^2, Theorem 2) or ||upsilon||^2 (Theorem 4).
-//             y' = (I - Q Q^T) y, so that A^T y' = G omega (CSS) or
+//             y' = (I - Q Q^T) y = (y - Q d) with d = Z^T e / ||e||, Z = C Q,
+//             so that A^T y' = G omega (CSS) or
 //             A^T B upsilon - sum_r (upsilon^(r)^T upsilon) omega^(r) (GCSS).
 //   fused     one pass over A: omega_i = a_i . q and h_i = a_i . y' per column,
 //             f_i <- f_i - 2 omega_i h_i + s omega_i^2, g_i <- g_i - omega_i^2,

@@ -14,7 +14,9 @@
  *                       then GCSS on the union of the blocks' selections.
  *   css_project         B = A Omega, the random projection of Sec. 5.1
  *                       (Algorithm 2: per-block partial sums, then row sums).
- *   css_select_batched  many independent Algorithm 1 instances in one launch.
+ *   css_select_batched  many independent Algorithm 1 instances in one launch;
+ *                       css_select_batched_prepare / _run split it so that
+ *                       the device work can be captured in a CUDA graph.
  *   css_residual_backward
  *                       loss ||A - P^(S) A||_F^2 (Problem 1's criterion,
  *                       Eq. Projection of Sec. 3.1) and its gradient with
@@ -281,6 +283,39 @@ size_t css_batched_workspace_size(const css_problem* probs, int32_t count,
 css_status css_select_batched(const css_problem* probs, int32_t count,
                               css_dtype dtype, void* ws, size_t ws_bytes,
                               const css_opts* opts, css_stream_t stream);
+
+/*
+ * The same batch in two steps, so that the device work can be repeated or
+ * captured in a CUDA graph (no implementation detail of the paper; this is
+ * how a batch is replayed without host work):
+ *
+ *   css_select_batched_prepare  validates, plans the teams and writes every
+ *       descriptor into the workspace; returns after the copies finished
+ *       (it synchronises `stream`).  Not capturable.
+ *   css_select_batched_run      resets the status, barriers and counters
+ *       from device-side values and enqueues the initial scores (three
+ *       launches) and the persistent launch on `stream`: device work only,
+ *       with no host copy and no synchronisation, so it may be captured and
+ *       replayed.  It reads the problems' A and writes sel, trace, n_sel
+ *       (and W) through the DEVICE pointers given to prepare, which must stay
+ *       valid; the status is read afterwards with css_read_status(ws).
+ *
+ * `plan` is HOST memory owned by the caller, filled by prepare and read by
+ * run; it belongs to `ws` (run rejects another workspace with
+ * CSS_ERR_INVALID_ARG).  Runs on the same workspace must not overlap on the
+ * GPU.  opts as for css_select_batched except timing_ms and sync, which
+ * only css_select_batched uses.
+ */
+typedef struct {
+    uint64_t opaque[64];
+} css_batched_plan;
+
+css_status css_select_batched_prepare(const css_problem* probs, int32_t count,
+                                      css_dtype dtype, void* ws, size_t ws_bytes,
+                                      const css_opts* opts, css_batched_plan* plan,
+                                      css_stream_t stream);
+css_status css_select_batched_run(const css_batched_plan* plan, void* ws,
+                                  css_stream_t stream);
 
 /*
  * Loss and gradient of the reconstruction error at a fixed selected set S

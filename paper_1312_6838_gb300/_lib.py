@@ -68,6 +68,11 @@ I64 = C.c_int64
 SZ = C.c_size_t
 DBL = C.c_double
 
+class css_batched_plan(C.Structure):
+    """Opaque host record of a prepared batch (css_select_batched_prepare)."""
+    _fields_ = [("opaque", C.c_uint64 * 64)]
+
+
 _SIGS = {
     "css_opts_default": (None, [C.POINTER(css_opts)]),
     "css_status_string": (C.c_char_p, [I32]),
@@ -83,6 +88,9 @@ _SIGS = {
                           C.POINTER(css_opts), P]),
     "css_batched_workspace_size": (SZ, [C.POINTER(css_problem), I32, I32, C.POINTER(css_opts)]),
     "css_select_batched": (I32, [C.POINTER(css_problem), I32, I32, P, SZ, C.POINTER(css_opts), P]),
+    "css_select_batched_prepare": (I32, [C.POINTER(css_problem), I32, I32, P, SZ, C.POINTER(css_opts),
+                                         C.POINTER(css_batched_plan), P]),
+    "css_select_batched_run": (I32, [C.POINTER(css_batched_plan), P, P]),
     "css_residual_backward": (I32, [P, I32, I64, I64, I64, P, I32, DBL, P, I64, P, P, SZ,
                                     C.POINTER(css_opts), P]),
     "css_select_host": (I32, [P, I32, I64, I64, I64, I32, P, P, P, P, P, SZ,

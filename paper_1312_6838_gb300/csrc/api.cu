@@ -73,6 +73,7 @@ void carve_rest(WsCarver& c, int dt, int m, int n, int k, int r, int mode, bool 
 // Launch-wide descriptor region.
 struct Header {
   DevStatus* st;
+  DevStatus* st_init;   // the status a launch starts from (copied into st)
   UnitDesc* units;
   TeamDesc* teams;
   int* order;
@@ -98,6 +99,7 @@ int split_slots_for(int64_t split_cols) {
 
 void carve_header(WsCarver& c, int max_units, Header& h, int64_t split_cols) {
   h.st = c.take<DevStatus>(1);
+  h.st_init = c.take<DevStatus>(1);
   h.units = c.take<UnitDesc>(max_units);
   h.teams = c.take<TeamDesc>(kMaxCtas);
   h.order = c.take<int>(max_units);
@@ -207,9 +209,23 @@ Plan make_plan(const std::vector<double>& work, int grid) {
   return P;
 }
 
-// Copy descriptors, clear the status, launch the persistent kernel.
-css_status launch_units(const Header& h, std::vector<UnitDesc>& units, const std::vector<double>& work,
-                        int dt, int grid_max, int tile_cols, uint64_t spin_ns, cudaStream_t s) {
+// A persistent launch in two parts: prepare_units plans the teams and copies
+// every descriptor into the workspace; start_units resets the status, the
+// barriers and the counters from device-side values and launches, so that
+// it can be repeated (or captured in a CUDA graph) without host data.
+struct LaunchInfo {
+  GreedyLaunch L;
+  int split_used;
+  uint32_t* bars;
+  uint32_t* tile_ctr;
+  uint32_t* split_done;
+  DevStatus* st;
+  DevStatus* st_init;
+};
+
+css_status prepare_units(const Header& h, std::vector<UnitDesc>& units, const std::vector<double>& work,
+                         int dt, int grid_max, int tile_cols, uint64_t spin_ns, cudaStream_t s,
+                         LaunchInfo& info) {
   int m_max = 1, k_max = 1, r_max = 1;
   for (auto& u : units) {
     m_max = std::max(m_max, u.m);
@@ -245,16 +261,11 @@ css_status launch_units(const Header& h, std::vector<UnitDesc>& units, const std
   DevStatus st{};
   st.spin_budget_ns = spin_ns ? spin_ns : kDefaultSpinNs;
   cudaError_t e;
-  if ((e = cudaMemcpyAsync(h.st, &st, sizeof(st), cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_status(e);
+  if ((e = cudaMemcpyAsync(h.st_init, &st, sizeof(st), cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_status(e);
   if ((e = cudaMemcpyAsync(h.units, units.data(), units.size() * sizeof(UnitDesc), cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_status(e);
   if ((e = cudaMemcpyAsync(h.teams, P.teams.data(), P.teams.size() * sizeof(TeamDesc), cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_status(e);
   if ((e = cudaMemcpyAsync(h.order, P.order.data(), P.order.size() * sizeof(int), cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_status(e);
   if ((e = cudaMemcpyAsync(h.cta_team, P.cta_team.data(), P.cta_team.size() * sizeof(int), cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_status(e);
-  if ((e = cudaMemsetAsync(h.bars, 0, 2 * sizeof(uint32_t) * P.grid, s)) != cudaSuccess) return cuda_status(e);
-  if ((e = cudaMemsetAsync(h.tile_ctr, 0, 2 * sizeof(uint32_t) * P.grid, s)) != cudaSuccess) return cuda_status(e);
-  if (split_used > 0 &&
-      (e = cudaMemsetAsync(h.split_done, 0, sizeof(uint32_t) * split_used, s)) != cudaSuccess)
-    return cuda_status(e);
   GreedyLaunch L{};
   L.units = h.units;
   L.order = h.order;
@@ -269,7 +280,35 @@ css_status launch_units(const Header& h, std::vector<UnitDesc>& units, const std
   L.grid = P.grid;
   L.threads = kGreedyThreads;
   L.smem = smem;
-  return cuda_status(greedy_launch(L, s));
+  info.L = L;
+  info.split_used = split_used;
+  info.bars = h.bars;
+  info.tile_ctr = h.tile_ctr;
+  info.split_done = h.split_done;
+  info.st = h.st;
+  info.st_init = h.st_init;
+  return CSS_OK;
+}
+
+css_status start_units(const LaunchInfo& info, cudaStream_t s) {
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(info.st, info.st_init, sizeof(DevStatus), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+    return cuda_status(e);
+  if ((e = cudaMemsetAsync(info.bars, 0, 2 * sizeof(uint32_t) * info.L.grid, s)) != cudaSuccess) return cuda_status(e);
+  if ((e = cudaMemsetAsync(info.tile_ctr, 0, 2 * sizeof(uint32_t) * info.L.grid, s)) != cudaSuccess)
+    return cuda_status(e);
+  if (info.split_used > 0 &&
+      (e = cudaMemsetAsync(info.split_done, 0, sizeof(uint32_t) * info.split_used, s)) != cudaSuccess)
+    return cuda_status(e);
+  return cuda_status(greedy_launch(info.L, s));
+}
+
+css_status launch_units(const Header& h, std::vector<UnitDesc>& units, const std::vector<double>& work,
+                        int dt, int grid_max, int tile_cols, uint64_t spin_ns, cudaStream_t s) {
+  LaunchInfo info{};
+  css_status cs = prepare_units(h, units, work, dt, grid_max, tile_cols, spin_ns, s, info);
+  if (cs != CSS_OK) return cs;
+  return start_units(info, s);
 }
 
 css_status finish(const Header& h, const css_opts& o, cudaStream_t s) {
@@ -442,33 +481,6 @@ cudaError_t gcss_f0(int dt, const void* A, int64_t lda, int64_t m, int64_t n, co
     return tc::colnorms(A, lda, (int)m, (int)n, (const float*)B, ldb, (int)r, tc_scratch, f, h.aux_err,
                         o.spin_budget_ns ? o.spin_budget_ns : kDefaultSpinNs, s);
   return gcss_f0_simt(dt, A, lda, (int)m, (int)n, B, ldb, (int)r, partial, f, s);
-}
-
-// Streams for the per-problem initial-score kernels of a batch, so that the
-// small GEMMs of different problems run side by side.  Created once per device
-// and kept for the life of the process.
-constexpr int kPoolStreams = 16;
-struct StreamPool {
-  cudaStream_t st[kPoolStreams];
-  cudaEvent_t ev[kPoolStreams + 1];
-  bool ok = false;
-};
-
-StreamPool* stream_pool() {
-  static std::mutex mu;
-  static StreamPool pools[64];
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  std::lock_guard<std::mutex> lock(mu);
-  StreamPool& P = pools[dev];
-  if (!P.ok) {
-    for (int i = 0; i < kPoolStreams; ++i)
-      if (cudaStreamCreateWithFlags(&P.st[i], cudaStreamNonBlocking) != cudaSuccess) return nullptr;
-    for (int i = 0; i <= kPoolStreams; ++i)
-      if (cudaEventCreateWithFlags(&P.ev[i], cudaEventDisableTiming) != cudaSuccess) return nullptr;
-    P.ok = true;
-  }
-  return &P;
 }
 
 int team_ctas_for(int64_t n, int64_t m) {
@@ -862,6 +874,8 @@ struct BatchLayout {
   std::vector<UnitState> st;
   std::vector<void*> C;
   std::vector<double*> partial;
+  F0Item* items;   // initial-score work list, count entries
+  int* starts;     // 3 * (count + 1) first blocks (css_f0_grouped_starts)
   size_t bytes;
 };
 
@@ -881,8 +895,86 @@ BatchLayout batch_layout(void* ws, size_t cap, const css_problem* probs, int cou
     L.C[i] = c.take<char>((size_t)p.m * p.m * accsize(dt));
     L.partial[i] = c.take<double>(css_f0_partial_doubles(dt, (int)p.m, (int)p.n));
   }
+  L.items = c.take<F0Item>(std::max(count, 1));
+  L.starts = c.take<int>(3 * (std::max(count, 1) + 1));
   L.bytes = c.off;
   return L;
+}
+
+// Host side of a prepared batch, kept in the caller's css_batched_plan.
+struct BatchedPlanImpl {
+  uint64_t magic;
+  void* ws;
+  int count, dtype;
+  F0Grid grid;
+  const F0Item* items;
+  const int* starts;
+  int* aux_err;
+  LaunchInfo info;
+};
+constexpr uint64_t kPlanMagic = 0x43535342504c414eull;   // "CSSBPLAN"
+static_assert(sizeof(BatchedPlanImpl) <= sizeof(css_batched_plan), "css_batched_plan too small");
+
+css_status batched_prepare(const css_problem* probs, int32_t count, css_dtype dtype, void* ws,
+                           size_t ws_bytes, const css_opts& o, BatchedPlanImpl& P, cudaStream_t s) {
+  if (!probs || count < 1 || !valid_dtype(dtype)) return CSS_ERR_INVALID_ARG;
+  if (o.n_forced || o.diag_argmax || o.diag_f || o.trace_ns) return CSS_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i) {
+    const css_problem& p = probs[i];
+    if (!p.A || !p.sel || !p.trace || !p.n_sel) return CSS_ERR_INVALID_ARG;
+    if (p.m < 1 || p.n < 1 || p.lda < p.m || p.k < 1 || p.k > kMaxK || p.k > p.m || p.k > p.n)
+      return CSS_ERR_INVALID_ARG;
+  }
+  if (!ws || ((uintptr_t)ws % kWsAlign) != 0) return CSS_ERR_WORKSPACE;
+  BatchLayout L = batch_layout(ws, ws_bytes, probs, count, dtype);
+  if (L.bytes > ws_bytes) return CSS_ERR_WORKSPACE;
+  if (!device_ok()) return CSS_ERR_UNSUPPORTED;
+  std::vector<UnitDesc> units;
+  std::vector<double> work;
+  std::vector<F0Item> items(count);
+  std::vector<int> ms(count), ns(count), starts(3 * (count + 1));
+  for (int i = 0; i < count; ++i) {
+    const css_problem& p = probs[i];
+    items[i] = F0Item{p.A, p.lda, (int)p.m, (int)p.n, L.C[i], L.partial[i], L.st[i].f};
+    ms[i] = (int)p.m;
+    ns[i] = (int)p.n;
+    units.push_back(make_unit(p.A, dtype, p.m, p.n, p.lda, p.k, 0, L.C[i], p.m, 0, L.st[i], p.W,
+                              p.sel, p.trace, p.n_sel, o));
+    work.push_back((double)p.k * p.m * p.n + 4.0 * p.m * p.k * p.k);
+  }
+  P = BatchedPlanImpl{};
+  P.grid = css_f0_grouped_starts(dtype, ms.data(), ns.data(), count, starts.data());
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(L.items, items.data(), sizeof(F0Item) * count, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_status(e);
+  if ((e = cudaMemcpyAsync(L.starts, starts.data(), sizeof(int) * starts.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_status(e);
+  const int tile = pick_tile(o, dtype, 0);
+  css_status cs = prepare_units(L.h, units, work, dtype, o.grid_ctas, tile, o.spin_budget_ns, s, P.info);
+  if (cs != CSS_OK) return cs;
+  // the descriptors come from host vectors that end with this call
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_status(e);
+  P.magic = kPlanMagic;
+  P.ws = ws;
+  P.count = count;
+  P.dtype = dtype;
+  P.items = L.items;
+  P.starts = L.starts;
+  P.aux_err = L.h.aux_err;
+  return CSS_OK;
+}
+
+// Initial scores of every problem (three grouped launches), then the
+// persistent launch: device work only, so the sequence can be captured.
+css_status batched_run(const BatchedPlanImpl& P, cudaStream_t s, PhaseTimer* tm) {
+  if (cudaMemsetAsync(P.aux_err, 0, sizeof(int), s) != cudaSuccess) return CSS_ERR_CUDA;
+  if (tm) tm->mark(0, s);
+  cudaError_t e = css_f0_grouped(P.dtype, P.items, P.starts, P.grid, P.count, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (tm) tm->mark(1, s);
+  css_status cs = start_units(P.info, s);
+  if (tm) tm->mark(2, s);
+  return cs;
 }
 
 }  // namespace
@@ -902,54 +994,37 @@ css_status css_select_batched(const css_problem* probs, int32_t count, css_dtype
                               size_t ws_bytes, const css_opts* opts, css_stream_t stream) {
   const css_opts o = opts ? *opts : defaults();
   cudaStream_t s = (cudaStream_t)stream;
-  if (!probs || count < 1 || !valid_dtype(dtype)) return CSS_ERR_INVALID_ARG;
-  if (o.n_forced || o.diag_argmax || o.diag_f || o.trace_ns) return CSS_ERR_INVALID_ARG;
-  for (int i = 0; i < count; ++i) {
-    const css_problem& p = probs[i];
-    if (!p.A || !p.sel || !p.trace || !p.n_sel) return CSS_ERR_INVALID_ARG;
-    if (p.m < 1 || p.n < 1 || p.lda < p.m || p.k < 1 || p.k > kMaxK || p.k > p.m || p.k > p.n)
-      return CSS_ERR_INVALID_ARG;
-  }
-  if (!ws || ((uintptr_t)ws % kWsAlign) != 0) return CSS_ERR_WORKSPACE;
-  BatchLayout L = batch_layout(ws, ws_bytes, probs, count, dtype);
-  if (L.bytes > ws_bytes) return CSS_ERR_WORKSPACE;
-  if (!device_ok()) return CSS_ERR_UNSUPPORTED;
-  PhaseTimer tm(o);
-  tm.mark(0, s);
-  if (cudaMemsetAsync(L.h.aux_err, 0, sizeof(int), s) != cudaSuccess) return CSS_ERR_CUDA;
-  std::vector<UnitDesc> units;
-  std::vector<double> work;
-  // initial scores of every problem: spread over the stream pool (after the
-  // caller's stream), joined back before the persistent launch
-  StreamPool* pool = count > 1 ? stream_pool() : nullptr;
-  if (pool) {
-    if (cudaEventRecord(pool->ev[kPoolStreams], s) != cudaSuccess) return CSS_ERR_CUDA;
-    for (int j = 0; j < kPoolStreams; ++j)
-      if (cudaStreamWaitEvent(pool->st[j], pool->ev[kPoolStreams], 0) != cudaSuccess) return CSS_ERR_CUDA;
-  }
-  for (int i = 0; i < count; ++i) {
-    const css_problem& p = probs[i];
-    cudaStream_t si = pool ? pool->st[i % kPoolStreams] : s;
-    cudaError_t e = css_f0_simt(dtype, p.A, p.lda, (int)p.m, (int)p.n, L.C[i], L.partial[i], L.st[i].f, si);
-    if (e != cudaSuccess) return cuda_status(e);
-    units.push_back(make_unit(p.A, dtype, p.m, p.n, p.lda, p.k, 0, L.C[i], p.m, 0, L.st[i], p.W,
-                              p.sel, p.trace, p.n_sel, o));
-    work.push_back((double)p.k * p.m * p.n + 4.0 * p.m * p.k * p.k);
-  }
-  if (pool) {
-    for (int j = 0; j < kPoolStreams; ++j) {
-      if (cudaEventRecord(pool->ev[j], pool->st[j]) != cudaSuccess) return CSS_ERR_CUDA;
-      if (cudaStreamWaitEvent(s, pool->ev[j], 0) != cudaSuccess) return CSS_ERR_CUDA;
-    }
-  }
-  tm.mark(1, s);
-  const int tile = pick_tile(o, dtype, 0);
-  css_status cs = launch_units(L.h, units, work, dtype, o.grid_ctas, tile, o.spin_budget_ns, s);
+  BatchedPlanImpl P;
+  css_status cs = batched_prepare(probs, count, dtype, ws, ws_bytes, o, P, s);
   if (cs != CSS_OK) return cs;
-  tm.mark(2, s);
-  cs = finish(L.h, o, s);
+  PhaseTimer tm(o);
+  cs = batched_run(P, s, &tm);
+  if (cs != CSS_OK) return cs;
+  cs = finish(batch_layout(ws, ws_bytes, probs, count, dtype).h, o, s);
   tm.report(o);
   return cs;
+}
+
+css_status css_select_batched_prepare(const css_problem* probs, int32_t count, css_dtype dtype,
+                                      void* workspace, size_t workspace_bytes, const css_opts* opts,
+                                      css_batched_plan* plan, css_stream_t stream) {
+  if (!plan) return CSS_ERR_INVALID_ARG;
+  const css_opts o = opts ? *opts : defaults();
+  std::memset(plan, 0, sizeof(*plan));
+  BatchedPlanImpl P;
+  css_status cs = batched_prepare(probs, count, dtype, workspace, workspace_bytes, o, P,
+                                  (cudaStream_t)stream);
+  if (cs != CSS_OK) return cs;
+  std::memcpy(plan, &P, sizeof(P));
+  return CSS_OK;
+}
+
+css_status css_select_batched_run(const css_batched_plan* plan, void* workspace, css_stream_t stream) {
+  if (!plan) return CSS_ERR_INVALID_ARG;
+  BatchedPlanImpl P;
+  std::memcpy(&P, plan, sizeof(P));
+  if (P.magic != kPlanMagic || P.ws != workspace || !workspace) return CSS_ERR_INVALID_ARG;
+  return batched_run(P, (cudaStream_t)stream, nullptr);
 }
 
 }  // extern "C"

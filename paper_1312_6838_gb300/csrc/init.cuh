@@ -14,6 +14,27 @@ size_t gcss_f0_partial_doubles(int dtype, int r, int n);
 cudaError_t css_f0_simt(int dtype, const void* A, long long lda, int m, int n, void* C,
                         double* partial, double* f, cudaStream_t s);
 
+// Many CSS problems at once (css_select_batched): the same computation as
+// css_f0_simt for every item, in three launches whose blocks run over the
+// concatenated tiles of all items.
+struct F0Item {
+  const void* A;
+  long long lda;
+  int m, n;
+  void* C;           // m x m, Acc type
+  double* partial;   // css_f0_partial_doubles(dtype, m, n)
+  double* f;         // n
+};
+struct F0Grid {
+  int syrk = 0, colreduce = 0, sums = 0;   // blocks of the three launches
+};
+// Host: the first block of every item in each launch, three arrays of
+// count + 1 ints back to back in `starts`; returns the grid sizes.
+F0Grid css_f0_grouped_starts(int dtype, const int* m, const int* n, int count, int* starts);
+// Device arrays: items[count], starts[3 * (count + 1)].
+cudaError_t css_f0_grouped(int dtype, const F0Item* items, const int* starts, const F0Grid& grid,
+                           int count, cudaStream_t s);
+
 // GCSS: f[i] = ||B^T A_:i||^2, B (m x r, leading dimension ldb, Acc type).
 cudaError_t gcss_f0_simt(int dtype, const void* A, long long lda, int m, int n, const void* B,
                          long long ldb, int r, double* partial, double* f, cudaStream_t s);

@@ -24,15 +24,15 @@ template <> __device__ __forceinline__ float cvt_in<__nv_bfloat16>(__nv_bfloat16
 // computed; the lower tile is written by mirroring.  TT x TT outputs per
 // thread, 16 x 16 threads, K chunks of KC columns of A.
 template <typename TA, int TT, int KC>
-__global__ void __launch_bounds__(256) syrk_kernel(const TA* __restrict__ A, long long lda, int m,
-                                                   int n, typename AccOf<TA>::type* __restrict__ C) {
+__device__ __forceinline__ void syrk_tile(const TA* __restrict__ A, long long lda, int m, int n,
+                                          typename AccOf<TA>::type* __restrict__ C, int tile) {
   using Acc = typename AccOf<TA>::type;
   constexpr int BT = 16 * TT;
   __shared__ __align__(16) Acc As[KC][BT];
   __shared__ __align__(16) Acc Bs[KC][BT];
   const int nt = (m + BT - 1) / BT;
   // decode the linear index into (bi, bj), bi <= bj
-  int idx = blockIdx.x, bi = 0;
+  int idx = tile, bi = 0;
   while (idx >= nt - bi) { idx -= nt - bi; ++bi; }
   const int bj = bi + idx;
   const int i0 = bi * BT, j0 = bj * BT;
@@ -76,21 +76,26 @@ __global__ void __launch_bounds__(256) syrk_kernel(const TA* __restrict__ A, lon
   }
 }
 
+template <typename TA, int TT, int KC>
+__global__ void __launch_bounds__(256) syrk_kernel(const TA* __restrict__ A, long long lda, int m,
+                                                   int n, typename AccOf<TA>::type* __restrict__ C) {
+  syrk_tile<TA, TT, KC>(A, lda, m, n, C, blockIdx.x);
+}
+
 // ------------------------------------------------------ column reduction ----
 // D = X^T Y with X (K x M, ldx) and Y (K x N, ldy) both K-contiguous.
 // partial[mb * n + i] = sum over the rows r of M-tile mb of
 //     EPI == 0 :  D[r, i] * Y[r, i]       (CSS: C A dotted with A, needs M == K)
 //     EPI == 1 :  D[r, i]^2               (GCSS: ||B^T a_i||^2)
 template <typename TX, typename TA, int TT, int KC, int EPI>
-__global__ void __launch_bounds__(256) colreduce_kernel(const TX* __restrict__ X, long long ldx,
-                                                       const TA* __restrict__ Y, long long ldy, int K,
-                                                       int M, int N, double* __restrict__ partial) {
+__device__ __forceinline__ void colreduce_tile(const TX* __restrict__ X, long long ldx,
+                                               const TA* __restrict__ Y, long long ldy, int K, int M,
+                                               int N, double* __restrict__ partial, int mb, int nb) {
   using Acc = typename AccOf<TA>::type;
   constexpr int BT = 16 * TT;
   __shared__ __align__(16) Acc Xs[KC][BT + 1];
   __shared__ __align__(16) Acc Ys[KC][BT + 1];
   __shared__ double red[16][BT];
-  const int mb = blockIdx.y, nb = blockIdx.x;
   const int r0 = mb * BT, c0 = nb * BT;
   const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
   Acc acc[TT][TT];
@@ -143,6 +148,13 @@ __global__ void __launch_bounds__(256) colreduce_kernel(const TX* __restrict__ X
   }
 }
 
+template <typename TX, typename TA, int TT, int KC, int EPI>
+__global__ void __launch_bounds__(256) colreduce_kernel(const TX* __restrict__ X, long long ldx,
+                                                       const TA* __restrict__ Y, long long ldy, int K,
+                                                       int M, int N, double* __restrict__ partial) {
+  colreduce_tile<TX, TA, TT, KC, EPI>(X, ldx, Y, ldy, K, M, N, partial, blockIdx.y, blockIdx.x);
+}
+
 __global__ void sum_partials_kernel(const double* __restrict__ partial, int nblk, int n,
                                     double* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -184,7 +196,98 @@ cudaError_t gcss_f0_simt_t(const void* A_, long long lda, int m, int n, const vo
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ grouped -------
+// One launch for the initial scores of many CSS problems: blockIdx.x runs
+// over the concatenated tiles of all problems; start[g] is the first block of
+// problem g (start[count] = grid).
+__device__ __forceinline__ int group_of(const int* __restrict__ start, int count, int b) {
+  int lo = 0, hi = count;   // start[lo] <= b < start[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (start[mid] <= b) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <typename TA, int TT, int KC>
+__global__ void __launch_bounds__(256) syrk_grouped(const F0Item* __restrict__ items,
+                                                    const int* __restrict__ start, int count) {
+  using Acc = typename AccOf<TA>::type;
+  const int g = group_of(start, count, blockIdx.x);
+  const F0Item it = items[g];
+  syrk_tile<TA, TT, KC>(reinterpret_cast<const TA*>(it.A), it.lda, it.m, it.n,
+                        reinterpret_cast<Acc*>(it.C), blockIdx.x - start[g]);
+}
+
+template <typename TA, int TT, int KC>
+__global__ void __launch_bounds__(256) colreduce_grouped(const F0Item* __restrict__ items,
+                                                         const int* __restrict__ start, int count) {
+  using Acc = typename AccOf<TA>::type;
+  constexpr int BT = 16 * TT;
+  const int g = group_of(start, count, blockIdx.x);
+  const F0Item it = items[g];
+  const int local = blockIdx.x - start[g];
+  const int nbs = (it.n + BT - 1) / BT;
+  colreduce_tile<Acc, TA, TT, KC, 0>(reinterpret_cast<const Acc*>(it.C), (long long)it.m,
+                                     reinterpret_cast<const TA*>(it.A), it.lda, it.m, it.m, it.n,
+                                     it.partial, local / nbs, local % nbs);
+}
+
+template <int BT>
+__global__ void sum_partials_grouped(const F0Item* __restrict__ items, const int* __restrict__ start,
+                                     int count) {
+  const int g = group_of(start, count, blockIdx.x);
+  const F0Item it = items[g];
+  const int i = (blockIdx.x - start[g]) * blockDim.x + threadIdx.x;
+  if (i >= it.n) return;
+  const int nblk = (it.m + BT - 1) / BT;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += it.partial[(long long)b * it.n + i];
+  it.f[i] = s;
+}
+
+template <typename TA>
+cudaError_t css_f0_grouped_t(const F0Item* items, const int* starts, const F0Grid& grid, int count,
+                             cudaStream_t s) {
+  constexpr int TT = Tiles<TA>::TT, KC = Tiles<TA>::KC, BT = 16 * TT;
+  syrk_grouped<TA, TT, KC><<<grid.syrk, 256, 0, s>>>(items, starts, count);
+  colreduce_grouped<TA, TT, KC><<<grid.colreduce, 256, 0, s>>>(items, starts + (count + 1), count);
+  sum_partials_grouped<BT><<<grid.sums, 256, 0, s>>>(items, starts + 2 * (count + 1), count);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+F0Grid css_f0_grouped_starts(int dtype, const int* m, const int* n, int count, int* starts) {
+  const int BT = (dtype == CSS_F64) ? 64 : 128;
+  F0Grid G{};
+  int* s0 = starts;
+  int* s1 = starts + (count + 1);
+  int* s2 = starts + 2 * (count + 1);
+  for (int g = 0; g < count; ++g) {
+    const int nt = (m[g] + BT - 1) / BT;
+    s0[g] = G.syrk;
+    s1[g] = G.colreduce;
+    s2[g] = G.sums;
+    G.syrk += nt * (nt + 1) / 2;
+    G.colreduce += nt * ((n[g] + BT - 1) / BT);
+    G.sums += (n[g] + 255) / 256;
+  }
+  s0[count] = G.syrk;
+  s1[count] = G.colreduce;
+  s2[count] = G.sums;
+  return G;
+}
+
+cudaError_t css_f0_grouped(int dtype, const F0Item* items, const int* starts, const F0Grid& grid,
+                           int count, cudaStream_t s) {
+  switch (dtype) {
+    case CSS_F64: return css_f0_grouped_t<double>(items, starts, grid, count, s);
+    case CSS_F32: return css_f0_grouped_t<float>(items, starts, grid, count, s);
+    default: return css_f0_grouped_t<__nv_bfloat16>(items, starts, grid, count, s);
+  }
+}
 
 size_t css_f0_partial_doubles(int dtype, int m, int n) {
   const int BT = (dtype == CSS_F64) ? 64 : 128;

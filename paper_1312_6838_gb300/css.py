@@ -305,6 +305,59 @@ def select_batched(As: Sequence[torch.Tensor], ks: Sequence[int], *, grid_ctas=0
     return [Selection(s, t, int(ns), code) for (s, t, _), ns in zip(outs, nsels)]
 
 
+class BatchedPlan:
+    """A batch prepared once (css_select_batched_prepare) whose device work,
+    run(), can be repeated or captured in a CUDA graph: it reads the matrices
+    given here (their storage must stay allocated; their values may change
+    between runs) and writes the selections into the tensors held here."""
+
+    def __init__(self, As: Sequence[torch.Tensor], ks: Sequence[int], *, grid_ctas=0,
+                 tile_cols=0, tau_rel=None, stream=None):
+        if len(As) != len(ks) or not As:
+            raise ValueError("need one k per matrix")
+        dtype = As[0].dtype
+        dev = As[0].device
+        dt = _DT[dtype]
+        self._lib = L.load()
+        probs = (L.css_problem * len(As))()
+        self._outs = []
+        for i, (A, k) in enumerate(zip(As, ks)):
+            if A.dtype != dtype:
+                raise TypeError("all matrices must share one dtype")
+            m, n, lda = _colmajor(A)
+            sel = torch.empty(k, dtype=torch.int32, device=dev)
+            trace = torch.empty(k + 1, dtype=torch.float64, device=dev)
+            nsel = torch.zeros(1, dtype=torch.int32, device=dev)
+            probs[i].A = A.data_ptr()
+            probs[i].m, probs[i].n, probs[i].lda, probs[i].k = m, n, lda, int(k)
+            probs[i].sel, probs[i].trace, probs[i].n_sel = sel.data_ptr(), trace.data_ptr(), nsel.data_ptr()
+            probs[i].W = None
+            self._outs.append((sel, trace, nsel))
+        self._As = list(As)
+        o = _opts(tau_rel, None, 0, grid_ctas, tile_cols)
+        nbytes = self._lib.css_batched_workspace_size(probs, len(As), dt, C.byref(o))
+        if nbytes == 0:
+            raise ValueError("invalid batch")
+        self._keep, self._ws = _workspace(nbytes, dev)
+        self._plan = L.css_batched_plan()
+        code = self._lib.css_select_batched_prepare(probs, len(As), dt, _ptr(self._ws), nbytes,
+                                                    C.byref(o), C.byref(self._plan), _stream(stream))
+        _check(code, "css_select_batched_prepare")
+
+    def run(self, stream=None):
+        """Enqueue the initial scores and the persistent launch (device work only)."""
+        code = self._lib.css_select_batched_run(C.byref(self._plan), _ptr(self._ws), _stream(stream))
+        _check(code, "css_select_batched_run")
+
+    def status(self, stream=None):
+        """Status of the last run (synchronises the stream)."""
+        return self._lib.css_read_status(_ptr(self._ws), _stream(stream))
+
+    def results(self):
+        nsels = torch.cat([x[2] for x in self._outs]).tolist()
+        return [Selection(s, t, int(ns), 0) for (s, t, _), ns in zip(self._outs, nsels)]
+
+
 def select_host(A_host: torch.Tensor, k: int, A_dev: torch.Tensor, *, ws=None, stream=None):
     """Algorithm 1 from host memory: copies A_host (column-major, ideally pinned)
     into the device staging tensor A_dev, selects, copies the results back.

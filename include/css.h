@@ -318,6 +318,37 @@ css_status css_select_batched_run(const css_batched_plan* plan, void* ws,
                                   css_stream_t stream);
 
 /*
+ * Tile-width autotuner of the fused streaming step (no counterpart in the
+ * paper; a tuning aid).  The fused step hands out tiles of 2, 4 or 8 columns;
+ * css_select, gcss_select, gcss_distributed and css_select_batched with
+ * opts->tile_cols == 0 use the width recorded for the current device, the
+ * dtype and the shape's bucket (floor(log2 m), floor(log2 n)), else 8.
+ *
+ *   css_autotune_select  runs css_select on the caller's problem (arguments
+ *       as css_select; the outputs hold the last run's selection) once per
+ *       width untimed and once timed, records the fastest and returns it in
+ *       *best_tile (HOST int32); times_ms is a HOST double[3] or NULL (greedy
+ *       iterations in ms for widths 2, 4, 8).  Synchronises `stream`.
+ *   css_tile_record / css_tile_lookup  set / read an entry for a device
+ *       name (HOST string, as cudaDeviceProp::name); lookup returns 0 when
+ *       there is none.  Host only.
+ *   css_tile_cache_save / css_tile_cache_load  write / merge the table as a
+ *       flat JSON object {"<device>|<dtype>|m<b>|n<b>": <width>, ...};
+ *       CSS_ERR_INVALID_ARG on an unreadable file or a malformed entry (the
+ *       table is then unchanged).  Host only.
+ * The table is process-wide and guarded by a mutex.
+ */
+css_status css_autotune_select(const void* A, css_dtype dtype, int64_t m, int64_t n,
+                               int64_t lda, int32_t k, int32_t* sel, double* trace,
+                               int32_t* n_sel, void* ws, size_t ws_bytes,
+                               int32_t* best_tile, double* times_ms, css_stream_t stream);
+css_status css_tile_record(const char* device_name, css_dtype dtype, int64_t m, int64_t n,
+                           int32_t tile_cols);
+int32_t css_tile_lookup(const char* device_name, css_dtype dtype, int64_t m, int64_t n);
+css_status css_tile_cache_save(const char* path);
+css_status css_tile_cache_load(const char* path);
+
+/*
  * Loss and gradient of the reconstruction error at a fixed selected set S
  * (Problem 1's criterion; P^(S) = A_S (A_S^T A_S)^-1 A_S^T, Eq. Projection).
  *

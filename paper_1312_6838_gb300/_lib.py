@@ -91,6 +91,12 @@ _SIGS = {
     "css_select_batched_prepare": (I32, [C.POINTER(css_problem), I32, I32, P, SZ, C.POINTER(css_opts),
                                          C.POINTER(css_batched_plan), P]),
     "css_select_batched_run": (I32, [C.POINTER(css_batched_plan), P, P]),
+    "css_autotune_select": (I32, [P, I32, I64, I64, I64, I32, P, P, P, P, SZ, C.POINTER(C.c_int32),
+                                  P, P]),
+    "css_tile_record": (I32, [C.c_char_p, I32, I64, I64, I32]),
+    "css_tile_lookup": (I32, [C.c_char_p, I32, I64, I64]),
+    "css_tile_cache_save": (I32, [C.c_char_p]),
+    "css_tile_cache_load": (I32, [C.c_char_p]),
     "css_residual_backward": (I32, [P, I32, I64, I64, I64, P, I32, DBL, P, I64, P, P, SZ,
                                     C.POINTER(css_opts), P]),
     "css_select_host": (I32, [P, I32, I64, I64, I64, I32, P, P, P, P, P, SZ,

@@ -11,6 +11,7 @@
 #include "init.cuh"
 #include "tc.cuh"
 #include "project.cuh"
+#include "tune.cuh"
 #include "backward.cuh"
 
 using namespace css;
@@ -354,11 +355,14 @@ struct PhaseTimer {
 // Columns per fused-step tile: 8 keeps the most 16-byte loads in flight per
 // warp (measured fastest for BF16 and FP32 at m = 4096); the split tail keeps
 // the last, long tiles from idling the team.
-int pick_tile(const css_opts& o, int dt, int m) {
+// Columns per fused-step tile: the caller's choice, else the autotuner's
+// (css_autotune_select, css_tile_cache_load) for this device and shape
+// bucket, else 8, which keeps the most 16-byte loads in flight per warp and
+// measured fastest for BF16 and FP32 at m = 4096.
+int pick_tile(const css_opts& o, int dt, int64_t m, int64_t n) {
   if (o.tile_cols == 2 || o.tile_cols == 4 || o.tile_cols == 8) return o.tile_cols;
-  (void)dt;
-  (void)m;
-  return 8;
+  const int t = tuned_tile(dt, m, n);
+  return t ? t : 8;
 }
 
 css_status check_forced(const css_opts& o, int n, int k) {
@@ -570,7 +574,7 @@ css_status css_select(const void* A, css_dtype dtype, int64_t m, int64_t n, int6
   tm.mark(1, s);
   std::vector<UnitDesc> units{make_unit(A, dtype, m, n, lda, k, 0, L.C, m, 0, L.s, W, sel, trace,
                                         n_sel, o)};
-  const int tile = pick_tile(o, dtype, (int)m);
+  const int tile = pick_tile(o, dtype, m, n);
   int gmax = o.grid_ctas > 0 ? o.grid_ctas : team_ctas_for(n, m);
   cs = launch_units(L.h, units, {1.0}, dtype, gmax, tile, o.spin_budget_ns, s);
   if (cs != CSS_OK) return cs;
@@ -603,7 +607,7 @@ css_status gcss_select(const void* A, css_dtype dtype, int64_t m, int64_t n, int
   tm.mark(1, s);
   std::vector<UnitDesc> units{make_unit(A, dtype, m, n, lda, k, 1, B, ldb, r, L.s, W, sel, trace,
                                         n_sel, o)};
-  const int tile = pick_tile(o, dtype, (int)m);
+  const int tile = pick_tile(o, dtype, m, n);
   int gmax = o.grid_ctas > 0 ? o.grid_ctas : team_ctas_for(n, m);
   cs = launch_units(L.h, units, {1.0}, dtype, gmax, tile, o.spin_budget_ns, s);
   if (cs != CSS_OK) return cs;
@@ -812,7 +816,7 @@ css_status gcss_distributed(const void* A, css_dtype dtype, int64_t m, int64_t n
                               L.bnsel + b, ob));
     work.push_back((double)w * kb);
   }
-  const int tile = pick_tile(o, dtype, (int)m);
+  const int tile = pick_tile(o, dtype, m, n);
   css_status cs = launch_units(L.h, units, work, dtype, o.grid_ctas, tile, o.spin_budget_ns, s);
   if (cs != CSS_OK) return cs;
   // reduce phase: union of the blocks' selections, block order then selection order
@@ -949,7 +953,10 @@ css_status batched_prepare(const css_problem* probs, int32_t count, css_dtype dt
     return cuda_status(e);
   if ((e = cudaMemcpyAsync(L.starts, starts.data(), sizeof(int) * starts.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return cuda_status(e);
-  const int tile = pick_tile(o, dtype, 0);
+  int64_t m_big = 0, n_big = 0;
+  for (int i = 0; i < count; ++i)
+    if (probs[i].m * probs[i].n > m_big * n_big) { m_big = probs[i].m; n_big = probs[i].n; }
+  const int tile = pick_tile(o, dtype, m_big, n_big);
   css_status cs = prepare_units(L.h, units, work, dtype, o.grid_ctas, tile, o.spin_budget_ns, s, P.info);
   if (cs != CSS_OK) return cs;
   // the descriptors come from host vectors that end with this call

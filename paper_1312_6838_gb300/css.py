@@ -358,6 +358,29 @@ class BatchedPlan:
         return [Selection(s, t, int(ns), 0) for (s, t, _), ns in zip(self._outs, nsels)]
 
 
+def autotune(A: torch.Tensor, k: int, *, stream=None):
+    """Time the fused step's tile widths (2, 4, 8) on A and record the fastest
+    for this device and shape bucket (css_autotune_select).  Returns
+    (best width, {width: greedy-iteration ms})."""
+    m, n, lda = _colmajor(A)
+    dt = _DT[A.dtype]
+    lib = L.load()
+    dev = A.device
+    sel = torch.empty(k, dtype=torch.int32, device=dev)
+    trace = torch.empty(k + 1, dtype=torch.float64, device=dev)
+    nsel = torch.zeros(1, dtype=torch.int32, device=dev)
+    o = L.default_opts()
+    nbytes = lib.css_workspace_size(L.CSS_OP_SELECT, dt, m, n, 0, k, 0, C.byref(o))
+    _keep, ws = _workspace(nbytes, dev)
+    best = C.c_int32(0)
+    times = (C.c_double * 3)()
+    code = lib.css_autotune_select(_ptr(A), dt, m, n, lda, k, _ptr(sel), _ptr(trace), _ptr(nsel),
+                                   _ptr(ws), nbytes, C.byref(best), C.cast(times, C.c_void_p),
+                                   _stream(stream))
+    _check(code, "css_autotune_select")
+    return best.value, {2: times[0], 4: times[1], 8: times[2]}
+
+
 def select_host(A_host: torch.Tensor, k: int, A_dev: torch.Tensor, *, ws=None, stream=None):
     """Algorithm 1 from host memory: copies A_host (column-major, ideally pinned)
     into the device staging tensor A_dev, selects, copies the results back.

@@ -28,6 +28,13 @@ Functions and the passages they follow:
   for a given selected prefix (used to check sampled outputs at large sizes).
 * ``residual_gradient``      -- d||A - P^(S)A||_F^2 / dA at fixed S, derived from
   Eq. (Projection) by differentiating P^(S) (restated in the docstring).
+* ``philox4x32_10``,
+  ``random_omega``           -- the random matrix Omega of Sec. 5.1 drawn from a
+  counter-based generator, Philox4x32-10 (Salmon, Moraes, Dror and Shaw,
+  "Parallel random numbers: as easy as 1, 2, 3", SC 2011), written from that
+  definition: the dense Gaussian matrix and the sparse random sign matrix
+  (entries +-1 with probability 1/(2 sqrt n) each, 0 otherwise) that Sec. 5.1
+  cites and Sec. 7 uses ("rnd" and "ssgn").
 
 Readings where the paper is silent (the same readings the CUDA path takes):
 
@@ -59,6 +66,10 @@ __all__ = [
     "exact_scores",
     "exact_gcss_scores",
     "residual_gradient",
+    "philox4x32_10",
+    "random_omega",
+    "OMEGA_GAUSSIAN",
+    "OMEGA_SPARSE_SIGN",
     "GreedyResult",
 ]
 
@@ -315,6 +326,67 @@ def greedy_gcss(A, B, l, tau_rel=1e-12, forced=None, keep_scores=False):
     res.W = omegas
     res.f, res.g = f, g
     return res
+
+
+# --------------------------------------------------------------------------- #
+# Omega (Sec. 5.1) from a counter-based generator.
+# --------------------------------------------------------------------------- #
+OMEGA_GAUSSIAN = 0
+OMEGA_SPARSE_SIGN = 1
+
+_PHILOX_M0, _PHILOX_M1 = 0xD2511F53, 0xCD9E8D57      # round multipliers
+_PHILOX_W0, _PHILOX_W1 = 0x9E3779B9, 0xBB67AE85      # key increments (Weyl)
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 (Salmon et al., SC 2011): ten rounds on a 4 x 32-bit
+    counter with a 2 x 32-bit key.  Each round multiplies words 0 and 2 by the
+    two constants (64-bit products split into high and low halves) and forms
+    (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0); the key is bumped by the Weyl
+    constants between rounds.  ``ctr`` is four uint32 arrays (broadcast), ``key``
+    two ints; returns four uint32 arrays."""
+    mask = np.uint64(0xFFFFFFFF)
+    c0, c1, c2, c3 = (np.asarray(c, dtype=np.uint64) & mask for c in ctr)
+    k0, k1 = np.uint64(key[0] & 0xFFFFFFFF), np.uint64(key[1] & 0xFFFFFFFF)
+    for _ in range(10):
+        p0 = np.uint64(_PHILOX_M0) * c0
+        p1 = np.uint64(_PHILOX_M1) * c2
+        hi0, lo0 = p0 >> np.uint64(32), p0 & mask
+        hi1, lo1 = p1 >> np.uint64(32), p1 & mask
+        c0, c1, c2, c3 = hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0
+        k0 = (k0 + np.uint64(_PHILOX_W0)) & mask
+        k1 = (k1 + np.uint64(_PHILOX_W1)) & mask
+    return tuple(x.astype(np.uint32) for x in (c0, c1, c2, c3))
+
+
+def sparse_sign_threshold(n):
+    """A draw x0 (uniform 32-bit) marks a nonzero when x0 < floor(2^32 / sqrt n),
+    i.e. with probability 1/sqrt(n) (the sparse random sign matrix of Sec. 5.1)."""
+    return min(0xFFFFFFFF, int(np.floor(4294967296.0 / np.sqrt(float(n)))))
+
+
+def random_omega(n, r, seed, dist):
+    """Omega (n x r) of Sec. 5.1; entry (i, j) comes from the Philox block of
+    counter (i, j, 0, 0) under key (seed mod 2^32, seed >> 32):
+      Gaussian:    u1 = (x0 + 1) / 2^32, u2 = x1 / 2^32,
+                   Omega_ij = sqrt(-2 ln u1) cos(2 pi u2) / sqrt(r)   (Box-Muller,
+                   variance 1/r; the selection is invariant to the scale of B)
+      sparse sign: Omega_ij = 0 unless x0 < floor(2^32 / sqrt n); then +1 if the
+                   lowest bit of x1 is 0, else -1 (unscaled: the selection is
+                   invariant to the scale of B)."""
+    i = np.arange(n, dtype=np.uint64)[:, None]
+    j = np.arange(r, dtype=np.uint64)[None, :]
+    zero = np.zeros((1, 1), dtype=np.uint64)
+    x0, x1, _, _ = philox4x32_10((i, j, zero, zero), (seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF))
+    if dist == OMEGA_GAUSSIAN:
+        u1 = (x0.astype(np.float64) + 1.0) / 4294967296.0
+        u2 = x1.astype(np.float64) / 4294967296.0
+        return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2) / np.sqrt(float(r))
+    if dist == OMEGA_SPARSE_SIGN:
+        nz = x0.astype(np.uint64) < np.uint64(sparse_sign_threshold(n))
+        sign = np.where((x1 & np.uint32(1)) == 0, 1.0, -1.0)
+        return np.where(nz, sign, 0.0)
+    raise ValueError("unknown distribution")
 
 
 # --------------------------------------------------------------------------- #

@@ -327,3 +327,63 @@ def test_bf16_rounding():
     # 1 + 1.5 * 2^-8 rounds up to 1 + 2^-7
     np.testing.assert_array_equal(b[:4], np.array([1.0, 1.0, 1.0078125, -2.5], np.float32))
     assert abs(b[4] - 3.140625) == 0
+
+
+# --------------------------------------------------------------------------- #
+# Omega from Philox4x32-10 (Sec. 5.1's random matrices)
+# --------------------------------------------------------------------------- #
+# Known-answer vectors published with the generator (Salmon et al., SC 2011,
+# Random123 distribution): (counter, key) -> output.
+PHILOX_KAT = [
+    ((0, 0, 0, 0), (0, 0), (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)),
+    ((0xFFFFFFFF,) * 4, (0xFFFFFFFF, 0xFFFFFFFF), (0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD)),
+    ((0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344), (0xA4093822, 0x299F31D0),
+     (0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1)),
+]
+
+
+@pytest.mark.parametrize("ctr,key,out", PHILOX_KAT)
+def test_philox_known_answers(ctr, key, out):
+    got = O.philox4x32_10(tuple(np.uint32(c) for c in ctr), key)
+    assert tuple(int(x) for x in got) == out
+
+
+def test_gaussian_omega_moments_and_independence():
+    n, r = 4000, 50
+    W = O.random_omega(n, r, 2024, O.OMEGA_GAUSSIAN)
+    N = W.size
+    # N(0, 1/r): mean within 5 standard errors, variance within 5 s.e. of 1/r
+    assert abs(W.mean()) < 5 / np.sqrt(N * r)
+    var_se = np.sqrt(2.0 / N) / r
+    assert abs(W.var() - 1.0 / r) < 5 * var_se
+    # fourth moment of a Gaussian: 3 sigma^4
+    k4 = np.mean((W * np.sqrt(r)) ** 4)
+    assert abs(k4 - 3.0) < 0.15
+    # columns uncorrelated
+    Cc = np.corrcoef(W[:, :8].T)
+    assert np.max(np.abs(Cc - np.eye(8))) < 5 / np.sqrt(n)
+
+
+def test_omega_entries_depend_only_on_position_and_seed():
+    A = O.random_omega(300, 20, 7, O.OMEGA_GAUSSIAN)
+    B = O.random_omega(500, 30, 7, O.OMEGA_GAUSSIAN)
+    # the same draws; only the 1/sqrt(r) scale differs
+    np.testing.assert_allclose(A * np.sqrt(20.0), B[:300, :20] * np.sqrt(30.0), rtol=1e-14, atol=0)
+    C = O.random_omega(300, 20, 8, O.OMEGA_GAUSSIAN)
+    assert np.mean(A == C) < 1e-3
+    D = O.random_omega(300, 20, 7 + (1 << 32), O.OMEGA_GAUSSIAN)   # high key word matters
+    assert np.mean(A == D) < 1e-3
+
+
+def test_sparse_sign_omega():
+    n, r = 40000, 60
+    S = O.random_omega(n, r, 99, O.OMEGA_SPARSE_SIGN)
+    assert set(np.unique(S)) <= {-1.0, 0.0, 1.0}
+    p = 1.0 / np.sqrt(n)
+    nnz = np.count_nonzero(S)
+    assert abs(nnz - p * S.size) < 5 * np.sqrt(S.size * p * (1 - p))
+    plus = np.count_nonzero(S > 0)
+    assert abs(plus - nnz / 2) < 5 * np.sqrt(nnz / 4)
+    # the threshold is floor(2^32 / sqrt n): for n = 4 exactly half of the draws
+    assert O.sparse_sign_threshold(4) == 1 << 31
+    assert O.sparse_sign_threshold(1) == 0xFFFFFFFF

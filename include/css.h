@@ -88,7 +88,8 @@ typedef enum {
     CSS_OP_DISTRIBUTED = 2,
     CSS_OP_PROJECT = 3,
     CSS_OP_BACKWARD = 4,
-    CSS_OP_HOST_SELECT = 5
+    CSS_OP_HOST_SELECT = 5,
+    CSS_OP_PROJECT_RANDOM = 6
 } css_op;
 
 /* Options.  Fill with css_opts_default() and change fields as needed;
@@ -257,6 +258,47 @@ css_status css_project(const void* A, css_dtype dtype, int64_t m, int64_t n,
                        int64_t lda, const void* Omega, int64_t r, int64_t ldo,
                        void* Bout, int64_t ldb, void* ws, size_t ws_bytes,
                        const css_opts* opts, css_stream_t stream);
+
+/*
+ * Omega drawn on the device from the counter-based generator Philox4x32-10
+ * (Salmon, Moraes, Dror and Shaw, SC 2011): entry (i, j) is a function of
+ * (i, j, seed) alone -- the Philox block at counter (i, j, 0, 0) under key
+ * (seed mod 2^32, seed >> 32) -- so the same seed gives the same matrix at
+ * any size, on any device.
+ *   CSS_OMEGA_GAUSSIAN     N(0, 1/r) by Box-Muller on the first two words
+ *                          (u1 = (w0 + 1) / 2^32, u2 = w1 / 2^32); FP32
+ *                          arithmetic for BF16/FP32 output, FP64 for FP64.
+ *   CSS_OMEGA_SPARSE_SIGN  the sparse random sign matrix of Sec. 5.1: +1 or
+ *                          -1 (lowest bit of w1) where w0 < floor(2^32/sqrt n),
+ *                          i.e. with probability 1/sqrt(n); 0 elsewhere.
+ *                          Unscaled (the selection does not depend on B's
+ *                          scale).
+ */
+typedef enum {
+    CSS_OMEGA_GAUSSIAN = 0,
+    CSS_OMEGA_SPARSE_SIGN = 1
+} css_omega;
+
+/*
+ * css_random_omega: write Omega (n x r, DEVICE, leading dimension ldo >= n,
+ * dtype BF16/FP32/FP64) on `stream`.
+ *
+ * css_project_random: B = A Omega (Algorithm 2) with Omega drawn as above.
+ *   Gaussian: Omega is written into the workspace in A's dtype and multiplied
+ *   as in css_project (tensor cores for BF16).  Sparse sign: Omega is never
+ *   formed; each column of B adds the +-columns of A its column of Omega
+ *   selects, in increasing row order (FP32 sums for BF16/FP32 A, FP64 for
+ *   FP64), and the workspace is unused (ws may be NULL).  The workspace size
+ *   is css_workspace_size(CSS_OP_PROJECT_RANDOM, dtype, m, n, r, 0, 0, opts).
+ *   Other arguments as css_project.
+ */
+css_status css_random_omega(int64_t n, int64_t r, uint64_t seed, css_omega dist,
+                            css_dtype dtype, void* Omega, int64_t ldo,
+                            css_stream_t stream);
+css_status css_project_random(const void* A, css_dtype dtype, int64_t m, int64_t n,
+                              int64_t lda, int64_t r, uint64_t seed, css_omega dist,
+                              void* Bout, int64_t ldb, void* ws, size_t ws_bytes,
+                              const css_opts* opts, css_stream_t stream);
 
 /* One independent greedy CSS problem of a batch (HOST struct; the pointers
    inside are DEVICE pointers with the meaning they have in css_select). */

@@ -539,6 +539,9 @@ size_t css_workspace_size(css_op op, css_dtype dtype, int64_t m, int64_t n, int6
     case CSS_OP_PROJECT:
       if (r <= 0) return 0;
       return project_workspace_bytes(dtype, m, n, r);
+    case CSS_OP_PROJECT_RANDOM:
+      if (r <= 0) return 0;
+      return project_random_workspace_bytes(dtype, m, n, r);
     case CSS_OP_BACKWARD:
       if (k <= 0) return 0;
       return backward_workspace_bytes(dtype, m, n, k);

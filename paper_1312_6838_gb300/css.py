@@ -265,6 +265,39 @@ def project(A: torch.Tensor, Omega: torch.Tensor, *, out=None, stream=None, sync
     return B
 
 
+OMEGA = {"gaussian": L.CSS_OMEGA_GAUSSIAN, "sparse_sign": L.CSS_OMEGA_SPARSE_SIGN}
+
+
+def random_omega(n: int, r: int, seed: int, dist="gaussian", dtype=torch.float32, device="cuda",
+                 stream=None) -> torch.Tensor:
+    """Omega (n x r, column-major) drawn on the device from Philox4x32-10
+    (css_random_omega): "gaussian" N(0, 1/r) or "sparse_sign"."""
+    lib = L.load()
+    Om = empty_colmajor(n, r, dtype, device)
+    _, _, ldo = _colmajor(Om, "Omega")
+    code = lib.css_random_omega(n, r, int(seed), OMEGA[dist], _DT[dtype], _ptr(Om), ldo, _stream(stream))
+    _check(code, "css_random_omega")
+    return Om
+
+
+def project_random(A: torch.Tensor, r: int, seed: int, dist="gaussian", *, out=None, stream=None,
+                   sync=True, init_path=0):
+    """B = A Omega with Omega drawn on the device (css_project_random)."""
+    m, n, lda = _colmajor(A)
+    dev = A.device
+    dt = _DT[A.dtype]
+    lib = L.load()
+    B = out if out is not None else empty_colmajor(m, r, _ACC[A.dtype], dev)
+    _, _, ldb = _colmajor(B, "B")
+    o = _opts(sync=sync, init_path=init_path)
+    nbytes = lib.css_workspace_size(L.CSS_OP_PROJECT_RANDOM, dt, m, n, r, 0, 0, C.byref(o))
+    _keep, ws = _workspace(nbytes, dev)
+    code = lib.css_project_random(_ptr(A), dt, m, n, lda, r, int(seed), OMEGA[dist], _ptr(B), ldb,
+                                  _ptr(ws), nbytes, C.byref(o), _stream(stream))
+    _check(code, "css_project_random")
+    return B
+
+
 def select_batched(As: Sequence[torch.Tensor], ks: Sequence[int], *, grid_ctas=0, tile_cols=0,
                    tau_rel=None, stream=None, timing=None):
     """Independent greedy CSS problems in one persistent launch.  Returns a list

@@ -35,6 +35,11 @@ Functions and the passages they follow:
   definition: the dense Gaussian matrix and the sparse random sign matrix
   (entries +-1 with probability 1/(2 sqrt n) each, 0 otherwise) that Sec. 5.1
   cites and Sec. 7 uses ("rnd" and "ssgn").
+* ``rnd_greedy_css``         -- RndGreedyCSS of Sec. 7: Algorithm 3 with the
+  target B = A Omega of Sec. 5.1, Omega n x l (r = l).
+* ``relative_accuracy``      -- the evaluation measure of Sec. 7: the
+  reconstruction error of a selection placed between that of uniform column
+  sampling (0 %) and that of the best rank-l approximation by SVD (100 %).
 
 Readings where the paper is silent (the same readings the CUDA path takes):
 
@@ -67,6 +72,8 @@ __all__ = [
     "exact_gcss_scores",
     "residual_gradient",
     "philox4x32_10",
+    "rnd_greedy_css",
+    "relative_accuracy",
     "random_omega",
     "OMEGA_GAUSSIAN",
     "OMEGA_SPARSE_SIGN",
@@ -387,6 +394,24 @@ def random_omega(n, r, seed, dist):
         sign = np.where((x1 & np.uint32(1)) == 0, 1.0, -1.0)
         return np.where(nz, sign, 0.0)
     raise ValueError("unknown distribution")
+
+
+def rnd_greedy_css(A, l, seed, dist=OMEGA_GAUSSIAN, tau_rel=1e-12):
+    """RndGreedyCSS (Sec. 7): greedy generalized CSS (Algorithm 3) of the
+    columns of A for the random target B = A Omega with Omega = random_omega(
+    n, l, seed, dist) -- the random projection of Sec. 5.1 with r = l."""
+    A = _as64(A)
+    B = random_projection(A, random_omega(A.shape[1], l, seed, dist))
+    return greedy_gcss(A, B, l, tau_rel=tau_rel)
+
+
+def relative_accuracy(err_S, err_uniform, err_svd):
+    """Relative accuracy of Sec. 7 in percent, from Frobenius reconstruction
+    errors (not squared): (||A - A_U|| - ||A - A_S||) / (||A - A_U|| - ||A - A_l||)
+    x 100, where A_U is the approximation from a uniform random subset of l
+    columns, A_S the one from the selected subset and A_l the best rank-l
+    approximation (SVD)."""
+    return 100.0 * (err_uniform - err_S) / (err_uniform - err_svd)
 
 
 # --------------------------------------------------------------------------- #

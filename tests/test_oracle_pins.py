@@ -387,3 +387,20 @@ def test_sparse_sign_omega():
     # the threshold is floor(2^32 / sqrt n): for n = 4 exactly half of the draws
     assert O.sparse_sign_threshold(4) == 1 << 31
     assert O.sparse_sign_threshold(1) == 0xFFFFFFFF
+
+
+def test_rnd_greedy_recovers_the_column_space_of_a_rank_l_matrix():
+    """With r = l = rank(A), B = A Omega spans range(A) (almost surely), so the
+    l columns RndGreedyCSS picks reconstruct A exactly (Theorem 3's trace
+    reaches 0), for both random matrices of Sec. 5.1."""
+    A = ci.lowrank_uv(40, 120, 6, 0.0, 3)
+    for dist in (O.OMEGA_GAUSSIAN, O.OMEGA_SPARSE_SIGN):
+        res = O.rnd_greedy_css(A, 6, seed=11, dist=dist)
+        assert len(res.S) == 6
+        assert O.reconstruction_error(A, res.S) <= 1e-18 * np.linalg.norm(A) ** 2
+
+
+def test_relative_accuracy_end_points():
+    assert O.relative_accuracy(5.0, 5.0, 2.0) == 0.0       # as good as uniform sampling
+    assert O.relative_accuracy(2.0, 5.0, 2.0) == 100.0     # as good as the SVD
+    assert O.relative_accuracy(3.5, 5.0, 2.0) == 50.0

@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "decay_4096x32768", "dist_2048x262144", "dist_2048x65536",
-                             "batched_1024"],
+                             "batched_1024", "relative_accuracy"],
                     help="decay_4096x32768 is the small profiling case of the headline model; "
                          "dist_* run the distributed pipeline (Algorithms 2 and 4), batched_1024 "
                          "the batched independent problems")
@@ -246,6 +246,21 @@ def run_distributed(args):
     clk = clocks.stop()
     tot = [a.elapsed_time(b) for a, b in ev]
     proj = [a.elapsed_time(b) for a, b in evp]
+    # the projection with Omega drawn on the device instead of read from HBM:
+    # Gaussian (generated, then the tensor-core product) and the sparse random
+    # sign matrix (no Omega formed), Sec. 5.1 / Sec. 7's "rnd" and "ssgn"
+    def t_ms(f, reps=5):
+        f()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            f()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+    proj_gen = t_ms(lambda: css.project_random(A, r, c["omega_seed"], "gaussian"))
+    proj_ssgn = t_ms(lambda: css.project_random(A, r, c["omega_seed"], "sparse_sign"))
     block_iters = int((res.block_sel >= 0).sum().item())
     iters = block_iters + res.n_sel
     ms = statistics.mean(tot)
@@ -265,6 +280,8 @@ def run_distributed(args):
         "config": {"workload": args.workload, "m": m, "n": n, "r": r, "blocks": len(offs) - 1,
                    "l_block": c["l_block"], "k": c["k"], "block_iterations": block_iters},
         "projection_ms": pms,
+        "projection_generated_gaussian_ms": proj_gen,
+        "projection_sparse_sign_ms": proj_ssgn,
         "roofline": {"bound": "tensor", "achieved": tf, "peak": peak_tf, "unit": "TFLOP/s",
                      "frac": tf / peak_tf, "traffic": None, "kernel": "tc_kernel (B = A Omega)"},
         "gpu_launches": None, "clocks": clk}), flush=True)
@@ -320,6 +337,65 @@ def run_batched(args):
         "clocks": clk}), flush=True)
 
 
+def run_relative_accuracy(args):
+    """The evaluation measure of Sec. 7 on a synthetic matrix with a decaying
+    spectrum (2048 x 16384 BF16, rank 400 + 1e-3 noise): GreedyCSS,
+    RndGreedyCSS (Gaussian and sparse sign Omega) and the distributed
+    selection (Algorithms 2 and 4, 16 blocks) against uniform sampling without
+    replacement (mean error over 10 seeds, 0 %) and the best rank-l
+    approximation (FP64 SVD of the same BF16 values, 100 %).  Errors
+    ||A - P_S A||_F come from the device (css_residual_backward, loss only)."""
+    import torch
+    from paper_1312_6838_gb300 import css
+    m, n, rank = 2048, 16384, 400
+    A32 = ci.lowrank_decaying(m, n, rank, 1e-3, 3, dtype=np.float32)
+    A = torch.from_numpy(np.ascontiguousarray(A32.T)).cuda().to(torch.bfloat16).t()
+    vals = A.float().cpu().numpy().astype(np.float64)
+    del A32
+    # best rank-l errors from the eigenvalues of A A^T (FP64)
+    ev = np.sort(np.clip(np.linalg.eigvalsh(vals @ vals.T), 0.0, None))[::-1]
+    fro2 = float(np.sum(vals * vals))
+
+    def err(S):
+        return float(np.sqrt(max(css.residual(A, list(S)).item(), 0.0)))
+
+    def timed(f):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = f()
+        torch.cuda.synchronize()
+        return out, (time.perf_counter() - t0) * 1e3
+
+    offs = [int(x) for x in np.linspace(0, n, 17)]
+    rows = {}
+    for l in (16, 64, 128):
+        e_svd = float(np.sqrt(max(fro2 - ev[:l].sum(), 0.0)))
+        rng = np.random.default_rng(100 + l)
+        e_uni = float(np.mean([err(rng.choice(n, l, replace=False)) for _ in range(10)]))
+        css.select(A, l)                                   # first launches outside timing
+        methods = {
+            "GreedyCSS": lambda: css.select(A, l).indices.cpu().tolist(),
+            "RndGreedyCSS (rnd)": lambda: css.select_randomized(A, l, 5, "gaussian").indices.cpu().tolist(),
+            "RndGreedyCSS (ssgn)": lambda: css.select_randomized(A, l, 5, "sparse_sign").indices.cpu().tolist(),
+            "DistGreedyCSS (rnd, 16 blocks)": lambda: css.distributed(
+                A, css.project_random(A, l, 5, "gaussian"), offs, max(1, l // 4), l).indices.cpu().tolist(),
+        }
+        row = {"l": l, "svd_error": e_svd, "uniform_error": e_uni}
+        for name, f in methods.items():
+            S, ms = timed(f)
+            e = err(S)
+            row[name] = {"relative_accuracy_pct": 100.0 * (e_uni - e) / (e_uni - e_svd), "error": e,
+                         "ms": ms}
+        rows[str(l)] = row
+    best = rows["64"]["GreedyCSS"]["relative_accuracy_pct"]
+    print(json.dumps({
+        "metric": "relative accuracy (%) of GreedyCSS at l = 64 (Sec. 7's measure)", "value": best,
+        "unit": "%", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+        "config": {"workload": "relative_accuracy", "m": m, "n": n, "rank": rank, "noise": 1e-3,
+                   "dtype": "bf16", "uniform_seeds": 10},
+        "results": rows}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -330,6 +406,9 @@ def main():
         return
     if args.workload == "batched_1024":
         run_batched(args)
+        return
+    if args.workload == "relative_accuracy":
+        run_relative_accuracy(args)
         return
     import torch
     ws, rank, local = dist_env()

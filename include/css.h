@@ -89,7 +89,8 @@ typedef enum {
     CSS_OP_PROJECT = 3,
     CSS_OP_BACKWARD = 4,
     CSS_OP_HOST_SELECT = 5,
-    CSS_OP_PROJECT_RANDOM = 6
+    CSS_OP_PROJECT_RANDOM = 6,
+    CSS_OP_RANDOMIZED = 7
 } css_op;
 
 /* Options.  Fill with css_opts_default() and change fields as needed;
@@ -299,6 +300,18 @@ css_status css_project_random(const void* A, css_dtype dtype, int64_t m, int64_t
                               int64_t lda, int64_t r, uint64_t seed, css_omega dist,
                               void* Bout, int64_t ldb, void* ws, size_t ws_bytes,
                               const css_opts* opts, css_stream_t stream);
+
+/*
+ * RndGreedyCSS (Sec. 7): the greedy generalized CSS of Algorithm 3 for the
+ * random target B = A Omega, Omega n x l drawn on the device as in
+ * css_project_random (r = l).  Selects l columns; outputs as css_select
+ * (sel int32[l], trace double[l+1] with trace[0] = ||B||_F^2).  Workspace:
+ * css_workspace_size(CSS_OP_RANDOMIZED, dtype, m, n, 0, l, 0, opts).
+ */
+css_status css_select_randomized(const void* A, css_dtype dtype, int64_t m, int64_t n,
+                                 int64_t lda, int32_t l, uint64_t seed, css_omega dist,
+                                 int32_t* sel, double* trace, int32_t* n_sel, void* ws,
+                                 size_t ws_bytes, const css_opts* opts, css_stream_t stream);
 
 /* One independent greedy CSS problem of a batch (HOST struct; the pointers
    inside are DEVICE pointers with the meaning they have in css_select). */

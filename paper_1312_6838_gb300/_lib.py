@@ -24,7 +24,7 @@ CSS_ERR_UNSUPPORTED = -7
 
 CSS_F64, CSS_F32, CSS_BF16 = 0, 1, 2
 (CSS_OP_SELECT, CSS_OP_GCSS, CSS_OP_DISTRIBUTED, CSS_OP_PROJECT, CSS_OP_BACKWARD,
- CSS_OP_HOST_SELECT, CSS_OP_PROJECT_RANDOM) = range(7)
+ CSS_OP_HOST_SELECT, CSS_OP_PROJECT_RANDOM, CSS_OP_RANDOMIZED) = range(8)
 CSS_OMEGA_GAUSSIAN, CSS_OMEGA_SPARSE_SIGN = 0, 1
 
 
@@ -101,6 +101,8 @@ _SIGS = {
     "css_random_omega": (I32, [I64, I64, C.c_uint64, I32, I32, P, I64, P]),
     "css_project_random": (I32, [P, I32, I64, I64, I64, I64, C.c_uint64, I32, P, I64, P, SZ,
                                  C.POINTER(css_opts), P]),
+    "css_select_randomized": (I32, [P, I32, I64, I64, I64, I32, C.c_uint64, I32, P, P, P, P, SZ,
+                                    C.POINTER(css_opts), P]),
     "css_residual_backward": (I32, [P, I32, I64, I64, I64, P, I32, DBL, P, I64, P, P, SZ,
                                     C.POINTER(css_opts), P]),
     "css_select_host": (I32, [P, I32, I64, I64, I64, I32, P, P, P, P, P, SZ,

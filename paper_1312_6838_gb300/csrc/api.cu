@@ -494,6 +494,15 @@ int team_ctas_for(int64_t n, int64_t m) {
   return (int)std::max<int64_t>(1, std::max(a, b));
 }
 
+// RndGreedyCSS (Sec. 7): B = A Omega with Omega n x l drawn on the device,
+// then Algorithm 3 for the target B.  Workspace: gcss_select's first (so that
+// css_read_status reads its status), then B, then css_project_random's.
+size_t randomized_parts(int dtype, int64_t m, int64_t n, int32_t l, size_t& g, size_t& bb) {
+  g = align_up(gcss_layout(nullptr, (size_t)-1, dtype, m, n, l, l, true).bytes);
+  bb = align_up((size_t)m * l * accsize(dtype));
+  return g + bb + project_random_workspace_bytes(dtype, m, n, l);
+}
+
 }  // namespace
 
 extern "C" {
@@ -542,6 +551,11 @@ size_t css_workspace_size(css_op op, css_dtype dtype, int64_t m, int64_t n, int6
     case CSS_OP_PROJECT_RANDOM:
       if (r <= 0) return 0;
       return project_random_workspace_bytes(dtype, m, n, r);
+    case CSS_OP_RANDOMIZED: {
+      if (k <= 0) return 0;
+      size_t g = 0, bb = 0;
+      return randomized_parts(dtype, m, n, k, g, bb);
+    }
     case CSS_OP_BACKWARD:
       if (k <= 0) return 0;
       return backward_workspace_bytes(dtype, m, n, k);
@@ -618,6 +632,25 @@ css_status gcss_select(const void* A, css_dtype dtype, int64_t m, int64_t n, int
   cs = finish(L.h, o, s);
   tm.report(o);
   return cs;
+}
+
+css_status css_select_randomized(const void* A, css_dtype dtype, int64_t m, int64_t n, int64_t lda, int32_t l,
+                                 uint64_t seed, css_omega dist, int32_t* sel, double* trace, int32_t* n_sel,
+                                 void* ws, size_t ws_bytes, const css_opts* opts, css_stream_t stream) {
+  if (!A || !sel || !trace || !n_sel || !valid_dtype(dtype)) return CSS_ERR_INVALID_ARG;
+  if (m < 1 || n < 1 || lda < m || l < 1 || l > kMaxK || l > m || l > n) return CSS_ERR_INVALID_ARG;
+  if (!ws || ((uintptr_t)ws % kWsAlign) != 0) return CSS_ERR_WORKSPACE;
+  size_t g = 0, bb = 0;
+  const size_t need = randomized_parts(dtype, m, n, l, g, bb);
+  if (ws_bytes < need) return CSS_ERR_WORKSPACE;
+  css_opts po = opts ? *opts : defaults();
+  po.sync = 0;            // the selection below reports the status
+  po.timing_ms = nullptr;
+  void* B = (char*)ws + g;
+  css_status cs = css_project_random(A, dtype, m, n, lda, l, seed, dist, B, m, (char*)B + bb, ws_bytes - g - bb,
+                                     &po, stream);
+  if (cs != CSS_OK) return cs;
+  return gcss_select(A, dtype, m, n, lda, B, l, m, l, sel, trace, n_sel, nullptr, ws, g, opts, stream);
 }
 
 css_status css_read_status(const void* ws, css_stream_t stream) {

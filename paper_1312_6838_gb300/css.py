@@ -298,6 +298,27 @@ def project_random(A: torch.Tensor, r: int, seed: int, dist="gaussian", *, out=N
     return B
 
 
+def select_randomized(A: torch.Tensor, l: int, seed: int, dist="gaussian", *, tau_rel=None,
+                      stream=None) -> Selection:
+    """RndGreedyCSS (Sec. 7): Algorithm 3 for the target B = A Omega with Omega
+    n x l drawn on the device (css_select_randomized)."""
+    m, n, lda = _colmajor(A)
+    dev = A.device
+    dt = _DT[A.dtype]
+    lib = L.load()
+    sel = torch.empty(l, dtype=torch.int32, device=dev)
+    trace = torch.empty(l + 1, dtype=torch.float64, device=dev)
+    nsel = torch.zeros(1, dtype=torch.int32, device=dev)
+    o = _opts(tau_rel)
+    nbytes = lib.css_workspace_size(L.CSS_OP_RANDOMIZED, dt, m, n, 0, l, 0, C.byref(o))
+    _keep, ws = _workspace(nbytes, dev)
+    code = lib.css_select_randomized(_ptr(A), dt, m, n, lda, l, int(seed), OMEGA[dist], _ptr(sel),
+                                     _ptr(trace), _ptr(nsel), _ptr(ws), nbytes, C.byref(o),
+                                     _stream(stream))
+    _check(code, "css_select_randomized")
+    return Selection(sel, trace, int(nsel.item()), code)
+
+
 def select_batched(As: Sequence[torch.Tensor], ks: Sequence[int], *, grid_ctas=0, tile_cols=0,
                    tau_rel=None, stream=None, timing=None):
     """Independent greedy CSS problems in one persistent launch.  Returns a list

@@ -40,6 +40,10 @@ Functions and the passages they follow:
 * ``relative_accuracy``      -- the evaluation measure of Sec. 7: the
   reconstruction error of a selection placed between that of uniform column
   sampling (0 %) and that of the best rank-l approximation by SVD (100 %).
+* ``embedding``              -- Q = orth(A_:S) and W = Q^T A, Sec. 3.2
+  (Eq. CSS_LowDim).
+* ``rank_k_approximation``   -- the column-based rank-k approximation
+  A~_{S,k} = Q W~_k and the approximate SVD of Eq. (ApproxSVD), Sec. 3.2.
 
 Readings where the paper is silent (the same readings the CUDA path takes):
 
@@ -558,3 +562,50 @@ def residual_gradient(A, S):
     G = 2.0 * R
     G[:, S] = -2.0 * (R @ T.T)
     return float(np.sum(R * R)), G
+
+
+# --------------------------------------------------------------------------- #
+# Sec. 3.2: embedding into the span of the selected columns, the column-based
+# rank-k approximation and the approximate SVD (Eq. CSS_LowDim, Eq. ApproxSVD).
+# --------------------------------------------------------------------------- #
+def embedding(A, S):
+    """Q = orth(A_:S) and W = Q^T A (Eq. CSS_LowDim).
+
+    orth() is the thin QR factorisation A_:S = Q R (Householder, LAPACK) with
+    each column of Q signed so that diag(R) > 0.  With that sign Q is the one
+    orthonormal basis that Gram-Schmidt produces on the columns of A_:S taken
+    in selection order: q_t is the normalised part of column S[t] outside the
+    span of the earlier ones, the direction whose A^T q_t is the omega of
+    iteration t (Eq. delta_omega).  Returns (Q m x l, W l x n, R l x l).
+    """
+    A = _as64(A)
+    S = list(S)
+    Q, R = np.linalg.qr(A[:, S], mode="reduced")
+    sgn = np.where(np.diag(R) < 0.0, -1.0, 1.0)
+    Q = Q * sgn
+    R = R * sgn[:, None]
+    return Q, Q.T @ A, R
+
+
+def rank_k_approximation(Q, W, k):
+    """Column-based rank-k approximation of Sec. 3.2 and the approximate SVD of
+    Eq. (ApproxSVD), from an orthonormal Q (m x l) and W = Q^T A (l x n).
+
+    1. Thin SVD W = U^(W) Sigma^(W) V^(W)^T (LAPACK), singular values
+       descending; the best rank-k approximation of W is
+       W~_k = U^(W)_k Sigma^(W)_k V^(W)_k^T.
+    2. A~_{S,k} = Q W~_k.
+    3. Eq. (ApproxSVD): U~ = Q U^(W)_k, Sigma~ = Sigma^(W)_k, V~ = V^(W)_k.
+
+    Returns a dict: ``U`` (m x k), ``sigma`` (k), ``V`` (n x k), ``Uw``
+    (l x k, U^(W)_k), ``Wk`` (l x n), ``sigma_all`` (all singular values of W)
+    and ``tail`` = sum_{i >= k} sigma_i^2 = ||W - W~_k||_F^2.  A~_{S,k} itself
+    is ``Q @ Wk``.
+    """
+    Q = _as64(Q)
+    W = _as64(W)
+    Uw, sw, Vwt = np.linalg.svd(W, full_matrices=False)
+    Uk, sk, Vk = Uw[:, :k], sw[:k], Vwt[:k, :].T
+    Wk = (Uk * sk) @ Vk.T
+    return {"U": Q @ Uk, "sigma": sk, "V": Vk, "Uw": Uk, "Wk": Wk,
+            "sigma_all": sw, "tail": float(np.sum(sw[k:] ** 2))}

@@ -404,3 +404,107 @@ def test_relative_accuracy_end_points():
     assert O.relative_accuracy(5.0, 5.0, 2.0) == 0.0       # as good as uniform sampling
     assert O.relative_accuracy(2.0, 5.0, 2.0) == 100.0     # as good as the SVD
     assert O.relative_accuracy(3.5, 5.0, 2.0) == 50.0
+
+
+# ------------------------------------------- Sec. 3.2: embedding, rank k ---
+def test_embedding_rows_are_the_greedy_omegas():
+    """W = Q^T A with Q from a Householder QR equals the omega history the
+    greedy recursion builds (Eq. delta_omega): two unrelated computations of
+    the same rows; W[:, S] is the upper-triangular R with a positive
+    diagonal (the Q-less QR structure of the selection)."""
+    A = ci.lowrank_uv(30, 50, 5, 0.05, 11)
+    r = O.greedy_css(A, 8)
+    Q, W, R = O.embedding(A, r.S)
+    np.testing.assert_allclose(W, r.W, atol=1e-10 * np.abs(r.W).max())
+    np.testing.assert_allclose(W[:, r.S], R, atol=1e-12 * np.abs(R).max())
+    assert np.all(np.diag(R) > 0)
+    assert np.allclose(np.tril(W[:, r.S], -1), 0.0, atol=1e-12 * np.abs(R).max())
+    np.testing.assert_allclose(Q.T @ Q, np.eye(len(r.S)), atol=1e-13)
+
+
+def test_embedding_projection_is_the_normal_equations_projection():
+    """Q Q^T A = A_S (A_S^T A_S)^-1 A_S^T A (Eq. Projection), and
+    ||A||^2 - ||W||^2 = F(S) from the normal equations."""
+    A = ci.lowrank_uv(40, 70, 6, 0.1, 12)
+    S = [3, 17, 5, 60, 41, 22, 9]
+    Q, W, _ = O.embedding(A, S)
+    AS = A[:, S]
+    PA = AS @ np.linalg.solve(AS.T @ AS, AS.T @ A)
+    np.testing.assert_allclose(Q @ W, PA, atol=1e-11 * np.abs(A).max())
+    F = O.reconstruction_error_normal_eq(A, S)
+    assert abs(np.sum(A * A) - np.sum(W * W) - F) <= 1e-10 * np.sum(A * A)
+
+
+@pytest.mark.parametrize("k", [1, 3, 7])
+def test_rank_k_is_the_best_rank_k_of_the_projection(k):
+    """A~_{S,k} = Q W~_k is the best rank-k approximation of P^(S) A (Q has
+    orthonormal columns), computed here by an SVD of the m x n matrix P^(S) A
+    formed through the normal equations -- a different path -- and the error
+    splits as ||A - A~_{S,k}||^2 = F(S) + sum_{i>=k} sigma_i(W)^2."""
+    A = ci.lowrank_uv(35, 60, 8, 0.05, 13)
+    S = O.greedy_css(A, 7).S
+    Q, W, _ = O.embedding(A, S)
+    out = O.rank_k_approximation(Q, W, k)
+    AS = A[:, S]
+    PA = AS @ np.linalg.solve(AS.T @ AS, AS.T @ A)
+    U, s, Vt = np.linalg.svd(PA, full_matrices=False)
+    best = (U[:, :k] * s[:k]) @ Vt[:k]
+    Ak = Q @ out["Wk"]
+    np.testing.assert_allclose(Ak, best, atol=1e-10 * np.abs(A).max())
+    np.testing.assert_allclose(out["sigma"], s[:k], rtol=1e-12)
+    err = np.sum((A - Ak) ** 2)
+    assert abs(err - (O.reconstruction_error(A, S) + out["tail"])) <= 1e-10 * np.sum(A * A)
+
+
+def test_rank_k_is_locally_optimal_over_rank_k_coefficients():
+    """No rank-k coefficient matrix T near the optimum gives a smaller
+    ||A - A_S T||_F (the minimisation Sec. 3.2 states): perturbations of T*
+    kept at rank k by truncation never improve on it."""
+    rng = np.random.default_rng(14)
+    A = ci.lowrank_uv(20, 30, 6, 0.1, 14)
+    S = [0, 4, 9, 13, 21]
+    k = 2
+    Q, W, _ = O.embedding(A, S)
+    out = O.rank_k_approximation(Q, W, k)
+    AS = A[:, S]
+    T_star = np.linalg.lstsq(AS, Q @ out["Wk"], rcond=None)[0]
+    best = np.sum((A - AS @ T_star) ** 2)
+    for _ in range(200):
+        T = T_star + 1e-3 * rng.standard_normal(T_star.shape)
+        u, s, vt = np.linalg.svd(T, full_matrices=False)
+        Tk = (u[:, :k] * s[:k]) @ vt[:k]
+        assert np.sum((A - AS @ Tk) ** 2) >= best * (1 - 1e-12)
+
+
+def test_approximate_svd_is_exact_when_the_selection_spans_A():
+    """A of exact rank 4 and a selection spanning its range: P^(S) A = A, so
+    Eq. (ApproxSVD) returns A's own leading singular triplets and
+    A~_{S,k} is A's best rank-k approximation (Eckart-Young)."""
+    U0 = np.linalg.qr(np.random.default_rng(15).standard_normal((25, 4)))[0]
+    V0 = np.linalg.qr(np.random.default_rng(16).standard_normal((40, 4)))[0]
+    A = (U0 * np.array([5.0, 3.0, 2.0, 0.5])) @ V0.T
+    S = O.greedy_css(A, 4).S
+    Q, W, _ = O.embedding(A, S)
+    s_true = np.linalg.svd(A, compute_uv=False)
+    for k in (2, 4):
+        out = O.rank_k_approximation(Q, W, k)
+        np.testing.assert_allclose(out["sigma"], s_true[:k], rtol=1e-12)
+        Ua, sa, Vta = np.linalg.svd(A)
+        best = (Ua[:, :k] * sa[:k]) @ Vta[:k]
+        recon = (out["U"] * out["sigma"]) @ out["V"].T
+        np.testing.assert_allclose(recon, best, atol=1e-12 * 5.0)
+        np.testing.assert_allclose(out["U"].T @ out["U"], np.eye(k), atol=1e-13)
+        np.testing.assert_allclose(out["V"].T @ out["V"], np.eye(k), atol=1e-13)
+
+
+def test_approximate_singular_values_interlace():
+    """W = Q^T A compresses A, so sigma_i(W) <= sigma_i(A) for every i
+    (Cauchy interlacing); with k = l, A~_{S,l} = P^(S) A."""
+    A = ci.lowrank_uv(30, 45, 10, 0.2, 17)
+    S = O.greedy_css(A, 6).S
+    Q, W, _ = O.embedding(A, S)
+    out = O.rank_k_approximation(Q, W, len(S))
+    sA = np.linalg.svd(A, compute_uv=False)
+    assert np.all(out["sigma_all"] <= sA[:len(S)] * (1 + 1e-12))
+    np.testing.assert_allclose(Q @ out["Wk"], Q @ (Q.T @ A), atol=1e-12 * np.abs(A).max())
+    assert out["tail"] == 0.0 or out["tail"] < 1e-20

@@ -21,6 +21,12 @@
  *                       loss ||A - P^(S) A||_F^2 (Problem 1's criterion,
  *                       Eq. Projection of Sec. 3.1) and its gradient with
  *                       respect to A at a fixed selected set S.
+ *   css_embed           Q = orth(A_:S) and the embedding W = Q^T A of all
+ *                       columns into the span of a selection (Sec. 3.2,
+ *                       Eq. CSS_LowDim).
+ *   css_lowrank         the column-based rank-k approximation
+ *                       A~_{S,k} = Q W~_k and the approximate SVD of
+ *                       Eq. (ApproxSVD) from Q and W (Sec. 3.2).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -76,8 +82,10 @@ typedef enum {
     CSS_ERR_WORKSPACE = -4,   /* ws NULL, misaligned or smaller than required */
     CSS_ERR_TIMEOUT = -5,     /* a bounded device-side wait ran out */
     CSS_ERR_NONFINITE = -6,   /* A (or B) holds a NaN or an infinity */
-    CSS_ERR_UNSUPPORTED = -7  /* no sm_103a device, or a dtype combination
+    CSS_ERR_UNSUPPORTED = -7, /* no sm_103a device, or a dtype combination
                                  the entry point does not take */
+    CSS_ERR_NOT_CONVERGED = -8 /* css_lowrank: the eigenvalue iteration did
+                                  not converge within its sweep limit */
 } css_status;
 
 typedef enum { CSS_F64 = 0, CSS_F32 = 1, CSS_BF16 = 2 } css_dtype;
@@ -90,7 +98,9 @@ typedef enum {
     CSS_OP_BACKWARD = 4,
     CSS_OP_HOST_SELECT = 5,
     CSS_OP_PROJECT_RANDOM = 6,
-    CSS_OP_RANDOMIZED = 7
+    CSS_OP_RANDOMIZED = 7,
+    CSS_OP_EMBED = 8,
+    CSS_OP_LOWRANK = 9
 } css_op;
 
 /* Options.  Fill with css_opts_default() and change fields as needed;
@@ -151,6 +161,13 @@ typedef struct {
        15 the CTA's argmax candidate published, 14 after the last barrier.
        Unused entries are 0. */
     uint64_t* trace_ns;
+    /* DEVICE double[m * k] or NULL (css_select, gcss_select): the orthonormal
+       basis Q of the selected columns, column t (basis[t * m + i]) = q_t,
+       the normalised part of the t-th selected column outside the span of
+       the earlier ones (Gram-Schmidt in selection order; W = Q^T A).
+       FP32/BF16 input: the basis is held as double-float pairs and returned
+       as their FP64 sum.  Columns t >= *n_sel are set to zero. */
+    double* basis;
 } css_opts;
 
 /* Fill *opts with the defaults. */
@@ -166,8 +183,9 @@ const char* css_version(void);
    (m rows, n columns, r target columns for GCSS/projection, k columns to
    select; unused sizes may be 0).  For CSS_OP_DISTRIBUTED, n is the total
    column count and r the target width; the per-block limit l_block must be
-   passed in k_block.  For CSS_OP_BACKWARD, k is |S|.  Returns 0 when the
-   sizes are invalid. */
+   passed in k_block.  For CSS_OP_BACKWARD and CSS_OP_EMBED, k is |S|.  For
+   CSS_OP_LOWRANK, r is the embedding dimension l and k the rank.  Returns 0
+   when the sizes are invalid. */
 size_t css_workspace_size(css_op op, css_dtype dtype, int64_t m, int64_t n,
                           int64_t r, int32_t k, int32_t k_block,
                           const css_opts* opts);
@@ -430,6 +448,80 @@ css_status css_residual_backward(const void* A, css_dtype dtype, int64_t m,
                                  int64_t ldda, double* loss, void* ws,
                                  size_t ws_bytes, const css_opts* opts,
                                  css_stream_t stream);
+
+/*
+ * Embedding into the span of a selection (Sec. 3.2, Eq. CSS_LowDim):
+ *
+ *   Q = orth(A_:S)   m x l: the thin QR factor of A_:S whose R has a positive
+ *                    diagonal, i.e. the Gram-Schmidt basis of the selected
+ *                    columns in the order of `sel` (the basis css_select
+ *                    builds, opts->basis)
+ *   W = Q^T A        l x n: row t at W[t * ldw + j] (the layout of
+ *                    css_select's omega rows), W[:, sel] = R
+ *
+ *   sel       DEVICE int32[l], distinct column indices (checked on the host
+ *             through a small synchronous copy).
+ *   Q         DEVICE double, m x l, leading dimension ldq >= m, or NULL.
+ *   W         DEVICE double, l rows of stride ldw >= n, or NULL (not both).
+ * Q comes from CholeskyQR2 in FP64 (Fukaya, Nakatsukasa, Yanagisawa and
+ * Yamamoto, 2014: Q1 = A_S L1^-T from A_S^T A_S = L1 L1^T, then the same once
+ * more on Q1), orthonormal to working precision while the condition number of
+ * A_S stays below about 1e7.  A pivot at or below 1e-12 of its column's
+ * squared norm (dependent columns) gives CSS_ERR_INVALID_ARG (sync mode).
+ * W: FP64 products for FP64 input; FP32/BF16 input runs in double-float
+ * arithmetic (FP32 pairs with error-free products and sums).  l <= 1024,
+ * l <= min(m, n).  Workspace: css_workspace_size(CSS_OP_EMBED, dtype, m, n,
+ * 0, l, 0, opts).
+ */
+css_status css_embed(const void* A, css_dtype dtype, int64_t m, int64_t n,
+                     int64_t lda, const int32_t* sel, int32_t l, double* Q,
+                     int64_t ldq, double* W, int64_t ldw, void* ws,
+                     size_t ws_bytes, const css_opts* opts,
+                     css_stream_t stream);
+
+/*
+ * Rank-k approximation and approximate SVD from an embedding (Sec. 3.2):
+ *
+ *   W = U^(W) Sigma^(W) V^(W)^T          SVD of the l x n embedding
+ *   W~_k = U^(W)_k Sigma^(W)_k V^(W)_k^T  its best rank-k approximation
+ *   A~_{S,k} = Q W~_k = U~ Sigma~ V~^T    the column-based rank-k
+ *                                        approximation of A
+ *   U~ = Q U^(W)_k,  Sigma~ = Sigma^(W)_k,  V~ = V^(W)_k   (Eq. ApproxSVD)
+ *
+ * Inputs (DEVICE, FP64):
+ *   W         l rows of stride ldw >= n (W[t * ldw + j]), e.g. css_select's
+ *             omega rows or css_embed's output.
+ *   Q         m x l, leading dimension ldq >= m, orthonormal columns, or
+ *             NULL when U is not requested.
+ * Outputs (DEVICE, FP64; every one but sigma may be NULL):
+ *   sigma     double[k]: sigma_1 >= ... >= sigma_k >= 0.
+ *   U         m x k, leading dimension ldu >= m: U~ (needs Q).
+ *   V         n x k, leading dimension ldv >= n: V~ = W^T U^(W)_k
+ *             Sigma_k^-1.  A column whose sigma_i^2 is at or below
+ *             (n + l) * 2^-52 * ||W||_F^2 -- below what the method resolves,
+ *             e.g. W of rank < k -- is returned as zeros.
+ *   Uw        l x k, leading dimension l: U^(W)_k.
+ *   tail      double[1]: sum_{i >= k} sigma_i^2 = ||W - W~_k||_F^2.  With
+ *             W = Q^T A, ||A - A~_{S,k}||_F^2 = ||A - P^(S) A||_F^2 + tail,
+ *             the first term being css_select's final error trace entry.
+ * Each singular vector is signed so that the entry of largest magnitude of
+ * its U^(W) column (lowest index on ties) is positive.
+ * Method: G = W W^T (FP64), its eigendecomposition by cyclic Jacobi
+ * rotations in FP64 (parallel round-robin ordering, one cooperative
+ * kernel), sigma_i^2 = lambda_i, then U~ and V~ as FP64 products.  The
+ * eigenvalues carry an absolute error of about (n + l) 2^-53 ||W||_F^2 (the
+ * Gram matrix's rounding): sigma_i is accurate relative to sigma_1^2 /
+ * sigma_i, not to sigma_i.  CSS_ERR_NOT_CONVERGED if the rotations have not
+ * converged after 60 sweeps; CSS_ERR_NONFINITE for NaN/Inf in W.
+ * 1 <= k <= l <= 1024.  Workspace: css_workspace_size(CSS_OP_LOWRANK,
+ * CSS_F64, m, n, l, k, 0, opts).
+ */
+css_status css_lowrank(const double* W, int64_t ldw, const double* Q,
+                       int64_t ldq, int64_t m, int64_t n, int32_t l, int32_t k,
+                       double* sigma, double* U, int64_t ldu, double* V,
+                       int64_t ldv, double* Uw, double* tail, void* ws,
+                       size_t ws_bytes, const css_opts* opts,
+                       css_stream_t stream);
 
 /*
  * css_select from HOST buffers: copies A (HOST, m x n, lda; pinned memory

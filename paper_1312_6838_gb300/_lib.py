@@ -21,10 +21,12 @@ CSS_ERR_WORKSPACE = -4
 CSS_ERR_TIMEOUT = -5
 CSS_ERR_NONFINITE = -6
 CSS_ERR_UNSUPPORTED = -7
+CSS_ERR_NOT_CONVERGED = -8
 
 CSS_F64, CSS_F32, CSS_BF16 = 0, 1, 2
 (CSS_OP_SELECT, CSS_OP_GCSS, CSS_OP_DISTRIBUTED, CSS_OP_PROJECT, CSS_OP_BACKWARD,
- CSS_OP_HOST_SELECT, CSS_OP_PROJECT_RANDOM, CSS_OP_RANDOMIZED) = range(8)
+ CSS_OP_HOST_SELECT, CSS_OP_PROJECT_RANDOM, CSS_OP_RANDOMIZED, CSS_OP_EMBED,
+ CSS_OP_LOWRANK) = range(10)
 CSS_OMEGA_GAUSSIAN, CSS_OMEGA_SPARSE_SIGN = 0, 1
 
 
@@ -45,6 +47,7 @@ class css_opts(C.Structure):
         ("init_path", C.c_int32),
         ("reserved", C.c_int32 * 7),
         ("trace_ns", C.c_void_p),
+        ("basis", C.c_void_p),
     ]
 
 
@@ -103,6 +106,9 @@ _SIGS = {
                                  C.POINTER(css_opts), P]),
     "css_select_randomized": (I32, [P, I32, I64, I64, I64, I32, C.c_uint64, I32, P, P, P, P, SZ,
                                     C.POINTER(css_opts), P]),
+    "css_embed": (I32, [P, I32, I64, I64, I64, P, I32, P, I64, P, I64, P, SZ, C.POINTER(css_opts), P]),
+    "css_lowrank": (I32, [P, I64, P, I64, I64, I64, I32, I32, P, P, I64, P, I64, P, P, P, SZ,
+                          C.POINTER(css_opts), P]),
     "css_residual_backward": (I32, [P, I32, I64, I64, I64, P, I32, DBL, P, I64, P, P, SZ,
                                     C.POINTER(css_opts), P]),
     "css_select_host": (I32, [P, I32, I64, I64, I64, I32, P, P, P, P, P, SZ,

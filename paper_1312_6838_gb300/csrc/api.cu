@@ -13,6 +13,7 @@
 #include "project.cuh"
 #include "tune.cuh"
 #include "backward.cuh"
+#include "lowrank.cuh"
 
 using namespace css;
 
@@ -522,6 +523,7 @@ const char* css_status_string(css_status s) {
     case CSS_ERR_TIMEOUT: return "CSS_ERR_TIMEOUT: a bounded device wait ran out";
     case CSS_ERR_NONFINITE: return "CSS_ERR_NONFINITE: input holds NaN or Inf";
     case CSS_ERR_UNSUPPORTED: return "CSS_ERR_UNSUPPORTED";
+    case CSS_ERR_NOT_CONVERGED: return "CSS_ERR_NOT_CONVERGED: the eigenvalue iteration hit its sweep limit";
   }
   return "unknown css_status";
 }
@@ -531,6 +533,11 @@ const char* css_version(void) { return "libcss 0.1 (sm_103a)"; }
 size_t css_workspace_size(css_op op, css_dtype dtype, int64_t m, int64_t n, int64_t r, int32_t k,
                           int32_t k_block, const css_opts* opts) {
   (void)opts;
+  if (op == CSS_OP_LOWRANK) {
+    // m may be 0 here (U not requested); r is the embedding dimension l
+    if (n <= 0 || n > (int64_t)INT32_MAX || r < 1 || r > 1024 || k < 1 || k > r) return 0;
+    return lowrank_workspace_bytes(n, (int32_t)r, k);
+  }
   if (!valid_dtype(dtype) || m <= 0 || n <= 0) return 0;
   switch (op) {
     case CSS_OP_SELECT:
@@ -559,6 +566,11 @@ size_t css_workspace_size(css_op op, css_dtype dtype, int64_t m, int64_t n, int6
     case CSS_OP_BACKWARD:
       if (k <= 0) return 0;
       return backward_workspace_bytes(dtype, m, n, k);
+    case CSS_OP_EMBED:
+      if (k <= 0 || k > 1024 || k > m || k > n) return 0;
+      return embed_workspace_bytes(m, k);
+    default:
+      break;
   }
   return 0;
 }
@@ -596,6 +608,8 @@ css_status css_select(const void* A, css_dtype dtype, int64_t m, int64_t n, int6
   cs = launch_units(L.h, units, {1.0}, dtype, gmax, tile, o.spin_budget_ns, s);
   if (cs != CSS_OK) return cs;
   tm.mark(2, s);
+  if (o.basis && (e = export_basis(dtype, L.s.Q, (int)m, k, n_sel, o.basis, s)) != cudaSuccess)
+    return cuda_status(e);
   cs = finish(L.h, o, s);
   tm.report(o);
   return cs;
@@ -629,6 +643,8 @@ css_status gcss_select(const void* A, css_dtype dtype, int64_t m, int64_t n, int
   cs = launch_units(L.h, units, {1.0}, dtype, gmax, tile, o.spin_budget_ns, s);
   if (cs != CSS_OK) return cs;
   tm.mark(2, s);
+  if (o.basis && (e = export_basis(dtype, L.s.Q, (int)m, k, n_sel, o.basis, s)) != cudaSuccess)
+    return cuda_status(e);
   cs = finish(L.h, o, s);
   tm.report(o);
   return cs;

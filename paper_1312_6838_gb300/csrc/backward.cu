@@ -1,5 +1,8 @@
-// Loss and gradient of the reconstruction error at a fixed selected set S.
+// Reconstruction at a fixed selected set S: the embedding Q = orth(A_S),
+// W = Q^T A of Sec. 3.2 (css_embed), and the loss and gradient of the
+// reconstruction error (css_residual_backward).
 //
+// Loss and gradient:
 //   L(A) = ||A - P^(S) A||_F^2,  P^(S) = A_S (A_S^T A_S)^-1 A_S^T   (Eq. Projection)
 //   T = (A_S^T A_S)^-1 A_S^T A,  R = A - A_S T
 //   dL/dA = 2 R  (columns outside S),  dL/dA_S = -2 R T^T
@@ -158,12 +161,14 @@ __global__ void q_kernel(const double* __restrict__ AS, const double* __restrict
 
 // --------------------------------------------------- W = Q^T A  (k x n) -----
 // 32 (k) x 64 (n) outputs per block, 2 x 4 per thread, K = m in chunks of 16.
+// Element (j, c) of W goes to W[j * wj + c * wc]; the double-float split to
+// Wh / Wl (same positions) when those are not null.
 template <typename TA>
 __global__ void __launch_bounds__(256) w_kernel(const float* __restrict__ Qh, const float* __restrict__ Ql,
                                                 const double* __restrict__ Q, const TA* __restrict__ A,
                                                 long long lda, int m, int n, int k,
-                                                double* __restrict__ W, float* __restrict__ Wh,
-                                                float* __restrict__ Wl) {
+                                                double* __restrict__ W, long long wj, long long wc,
+                                                float* __restrict__ Wh, float* __restrict__ Wl) {
   constexpr int BK = 16;
   __shared__ float qh[BK][33], ql[BK][33];
   __shared__ double qd[BK][33];
@@ -213,12 +218,14 @@ __global__ void __launch_bounds__(256) w_kernel(const float* __restrict__ Qh, co
       const int j = j0 + ty * 2 + a, c = c0 + tx * 4 + b;
       if (j < k && c < n) {
         const double v = F64 ? accd[a][b] : (double)acc[a][b].s + (double)acc[a][b].c;
-        const long long o = (long long)c * k + j;
+        const long long o = (long long)j * wj + (long long)c * wc;
         W[o] = v;
-        float h, lo;
-        df_split(v, h, lo);
-        Wh[o] = h;
-        Wl[o] = lo;
+        if (Wh) {
+          float h, lo;
+          df_split(v, h, lo);
+          Wh[o] = h;
+          Wl[o] = lo;
+        }
       }
     }
 }
@@ -424,7 +431,7 @@ css_status run_backward(const TA* A, int dt, int m, int n, long long lda, const 
   chol_inv_kernel<<<1, 1024, 0, s>>>(L.G, k, L.Linv, L.status);
   q_kernel<<<(unsigned)((mk + 255) / 256), 256, 0, s>>>(L.AS, L.Linv, m, k, L.Q, L.Qh, L.Ql);
   w_kernel<TA><<<dim3((n + 63) / 64, (k + 31) / 32), 256, 0, s>>>(L.Qh, L.Ql, L.Q, A, lda, m, n, k, L.W,
-                                                                L.Wh, L.Wl);
+                                                                1, k, L.Wh, L.Wl);
   const dim3 rg((m + 63) / 64, (n + 63) / 64);
   r_kernel<TA><<<rg, 256, 0, s>>>(L.Qh, L.Ql, L.Q, L.Wh, L.Wl, L.W, A, lda, m, n, k, dA ? L.R : nullptr,
                                   dA, ldda, 2.0 * grad_out, L.loss_part);
@@ -447,7 +454,114 @@ css_status run_backward(const TA* A, int dt, int m, int n, long long lda, const 
   return CSS_OK;
 }
 
+// ------------------------------------------------ embedding (Sec. 3.2) -----
+// Copy of an m x l FP64 matrix to a caller buffer with leading dimension ld.
+__global__ void copy_cols_kernel(const double* __restrict__ src, int m, int l, double* __restrict__ dst,
+                                 long long ld) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)m * l) return;
+  const int i = (int)(idx % m), j = (int)(idx / m);
+  dst[(long long)j * ld + i] = src[idx];
+}
+
+struct EmbLayout {
+  int* status;
+  double *AS, *G, *Linv, *Q1, *Q;
+  float *Qh, *Ql;
+  size_t bytes;
+};
+
+EmbLayout emb_layout(void* ws, size_t cap, int64_t m, int32_t l) {
+  WsCarver c(ws, cap);
+  EmbLayout L{};
+  L.status = c.take<int>(64);
+  L.AS = c.take<double>((size_t)m * l);
+  L.G = c.take<double>((size_t)l * l);
+  L.Linv = c.take<double>((size_t)l * l);
+  L.Q1 = c.take<double>((size_t)m * l);
+  L.Q = c.take<double>((size_t)m * l);
+  L.Qh = c.take<float>((size_t)m * l);
+  L.Ql = c.take<float>((size_t)m * l);
+  L.bytes = c.off;
+  return L;
+}
+
+// CholeskyQR2: A_S^T A_S = L1 L1^T, Q1 = A_S L1^-T; Q1^T Q1 = L2 L2^T,
+// Q = Q1 L2^-T.  Then W = Q^T A (row t at W + t * ldw).
+template <typename TA>
+css_status run_embed(const TA* A, int m, int n, long long lda, const int* sel, int l, double* Qout,
+                     long long ldq, double* W, long long ldw, const EmbLayout& L, const css_opts& o,
+                     cudaStream_t s) {
+  cudaMemsetAsync(L.status, 0, sizeof(int), s);
+  const long long ml = (long long)m * l;
+  const unsigned gb = (unsigned)((ml + 255) / 256);
+  const dim3 gg((l + 15) / 16, (l + 15) / 16);
+  gather_cols_kernel<TA><<<gb, 256, 0, s>>>(A, lda, m, sel, l, L.AS);
+  gram_kernel<<<gg, 256, 0, s>>>(L.AS, m, l, L.G);
+  chol_inv_kernel<<<1, 1024, 0, s>>>(L.G, l, L.Linv, L.status);
+  q_kernel<<<gb, 256, 0, s>>>(L.AS, L.Linv, m, l, L.Q1, L.Qh, L.Ql);
+  gram_kernel<<<gg, 256, 0, s>>>(L.Q1, m, l, L.G);
+  chol_inv_kernel<<<1, 1024, 0, s>>>(L.G, l, L.Linv, L.status);
+  q_kernel<<<gb, 256, 0, s>>>(L.Q1, L.Linv, m, l, L.Q, L.Qh, L.Ql);
+  if (W)
+    w_kernel<TA><<<dim3((n + 63) / 64, (l + 31) / 32), 256, 0, s>>>(L.Qh, L.Ql, L.Q, A, lda, m, n, l, W, ldw,
+                                                                  1, nullptr, nullptr);
+  if (Qout) copy_cols_kernel<<<gb, 256, 0, s>>>(L.Q, m, l, Qout, ldq);
+  if (cudaGetLastError() != cudaSuccess) return CSS_ERR_CUDA;
+  if (o.sync) {
+    int st = 0;
+    if (cudaMemcpyAsync(&st, L.status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return CSS_ERR_CUDA;
+    if (st) return CSS_ERR_INVALID_ARG;   // A_S is rank deficient
+  }
+  return CSS_OK;
+}
+
+css_status check_selection(const int32_t* sel, int32_t k, int64_t n) {
+  std::vector<int32_t> h(k);
+  if (cudaMemcpy(h.data(), sel, sizeof(int32_t) * k, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return CSS_ERR_CUDA;
+  std::vector<char> seen(n, 0);
+  for (int32_t v : h) {
+    if (v < 0 || v >= n || seen[v]) return CSS_ERR_INVALID_ARG;
+    seen[v] = 1;
+  }
+  return CSS_OK;
+}
+
 }  // namespace
+
+size_t embed_workspace_bytes(int64_t m, int32_t l) { return emb_layout(nullptr, (size_t)-1, m, l).bytes; }
+
+extern "C" css_status css_embed(const void* A, css_dtype dtype, int64_t m, int64_t n, int64_t lda,
+                                const int32_t* sel, int32_t l, double* Q, int64_t ldq, double* W,
+                                int64_t ldw, void* ws, size_t ws_bytes, const css_opts* opts,
+                                css_stream_t stream) {
+  css_opts o;
+  css_opts_default(&o);
+  if (opts) o = *opts;
+  if (!A || !sel || (!Q && !W)) return CSS_ERR_INVALID_ARG;
+  if (dtype != CSS_F64 && dtype != CSS_F32 && dtype != CSS_BF16) return CSS_ERR_INVALID_ARG;
+  if (m < 1 || n < 1 || lda < m || l < 1 || l > 1024 || l > m || l > n) return CSS_ERR_INVALID_ARG;
+  if (m > INT32_MAX || n > INT32_MAX) return CSS_ERR_INVALID_ARG;
+  if ((Q && ldq < m) || (W && ldw < n)) return CSS_ERR_INVALID_ARG;
+  if (!ws || ((uintptr_t)ws % kWsAlign) != 0) return CSS_ERR_WORKSPACE;
+  EmbLayout L = emb_layout(ws, ws_bytes, m, l);
+  if (L.bytes > ws_bytes) return CSS_ERR_WORKSPACE;
+  css_status cs = check_selection(sel, l, n);
+  if (cs != CSS_OK) return cs;
+  cudaStream_t s = (cudaStream_t)stream;
+  switch (dtype) {
+    case CSS_F64:
+      return run_embed<double>((const double*)A, (int)m, (int)n, lda, sel, l, Q, ldq, W, ldw, L, o, s);
+    case CSS_F32:
+      return run_embed<float>((const float*)A, (int)m, (int)n, lda, sel, l, Q, ldq, W, ldw, L, o, s);
+    default:
+      return run_embed<__nv_bfloat16>((const __nv_bfloat16*)A, (int)m, (int)n, lda, sel, l, Q, ldq, W, ldw,
+                                      L, o, s);
+  }
+}
 
 size_t backward_workspace_bytes(int dtype, int64_t m, int64_t n, int32_t k) {
   return bw_layout(nullptr, (size_t)-1, dtype, m, n, k, true).bytes;
@@ -470,14 +584,8 @@ extern "C" css_status css_residual_backward(const void* A, css_dtype dtype, int6
   BwLayout L = bw_layout(ws, ws_bytes, dtype, m, n, k, dA != nullptr);
   if (L.bytes > ws_bytes) return CSS_ERR_WORKSPACE;
   // the selected indices: in range and distinct (a small synchronous copy)
-  std::vector<int32_t> h(k);
-  if (cudaMemcpy(h.data(), sel, sizeof(int32_t) * k, cudaMemcpyDeviceToHost) != cudaSuccess)
-    return CSS_ERR_CUDA;
-  std::vector<char> seen(n, 0);
-  for (int32_t v : h) {
-    if (v < 0 || v >= n || seen[v]) return CSS_ERR_INVALID_ARG;
-    seen[v] = 1;
-  }
+  const css_status cs = check_selection(sel, k, n);
+  if (cs != CSS_OK) return cs;
   cudaStream_t s = (cudaStream_t)stream;
   switch (dtype) {
     case CSS_F64:

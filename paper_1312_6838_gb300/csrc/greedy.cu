@@ -1065,4 +1065,31 @@ cudaError_t greedy_launch(const GreedyLaunch& L, cudaStream_t stream) {
   return cudaLaunchCooperativeKernel(k, dim3(L.grid), dim3(NT), args, L.smem, stream);
 }
 
+// Q (FP64, or double-float pairs for FP32/BF16 input) to a caller buffer as
+// FP64; columns at or beyond the number selected become zero.
+__global__ void export_basis_kernel(const double* __restrict__ Q, int df, int m, int k,
+                                    const int* __restrict__ n_sel, double* __restrict__ out) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)m * k) return;
+  const int t = (int)(idx / m);
+  double v = 0.0;
+  if (t < *n_sel) {
+    if (df) {
+      const float2 q2 = reinterpret_cast<const float2*>(Q)[idx];
+      v = (double)q2.x + (double)q2.y;
+    } else {
+      v = Q[idx];
+    }
+  }
+  out[idx] = v;
+}
+
+cudaError_t export_basis(int dtype, const double* Q, int m, int k, const int* n_sel, double* out,
+                         cudaStream_t stream) {
+  const long long total = (long long)m * k;
+  export_basis_kernel<<<(unsigned)((total + 255) / 256), 256, 0, stream>>>(Q, dtype != CSS_F64, m, k, n_sel,
+                                                                           out);
+  return cudaGetLastError();
+}
+
 }  // namespace css

@@ -86,5 +86,9 @@ size_t greedy_smem_bytes(int dtype, int m_max, int k_max, int r_max);
 int greedy_occupancy(int dtype, int tile_cols, size_t smem);
 // Enqueue the persistent kernel (cooperative launch).  Returns a cudaError_t.
 cudaError_t greedy_launch(const GreedyLaunch& L, cudaStream_t stream);
+// Copies the basis Q of one unit (m x k, FP64 or double-float pairs) to `out`
+// as FP64, zeroing columns t >= *n_sel (opts->basis).
+cudaError_t export_basis(int dtype, const double* Q, int m, int k, const int* n_sel, double* out,
+                         cudaStream_t stream);
 
 }  // namespace css

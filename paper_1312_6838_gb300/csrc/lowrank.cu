@@ -1,0 +1,496 @@
+// Rank-k approximation and approximate SVD from an embedding (Sec. 3.2):
+//
+//   W = U^(W) Sigma^(W) V^(W)^T,   A~_{S,k} = Q W~_k,
+//   U~ = Q U^(W)_k,  Sigma~ = Sigma^(W)_k,  V~ = V^(W)_k   (Eq. ApproxSVD).
+//
+// W is short and wide (l x n, l <= 1024), so its SVD goes through the l x l
+// Gram matrix G = W W^T = U^(W) (Sigma^(W))^2 U^(W)^T:
+//   1. gram_rows_kernel: G in FP64 over lower 32 x 32 tiles, the n columns cut
+//      into slices whose partial tiles gram_reduce_kernel adds in a fixed
+//      order (bitwise reproducible).
+//   2. jacobi_kernel: the eigendecomposition of G by two-sided cyclic Jacobi
+//      rotations (Golub and Van Loan, Matrix Computations, Sec. 8.5) in the
+//      parallel round-robin ordering of Brent and Luk (1985): each round
+//      rotates l/2 disjoint index pairs at once.  One cooperative kernel on a
+//      g x g grid of CTAs, one grid barrier per round; CTA (x, y) updates the
+//      2 x 2 blocks whose row pair lies in pair chunk x and column pair in
+//      chunk y, so it needs the rotations of two chunks only.
+//   3. order_kernel: eigenvalues sorted descending, U^(W)_k with a sign rule,
+//      sigma, the tail sum and the 1 / sigma scaling of V~.
+//   4. gemm_nn_kernel: U~ = Q U^(W)_k and V~ = W^T U^(W)_k Sigma_k^-1 in FP64.
+//
+// Everything is FP64: on this part FP64 runs at 1/64 of the FP32 rate, so
+// the Gram matrix and V~ (2 l^2 n / 2 and l k n multiply-adds) are bound by
+// the FP64 pipe, and the Jacobi rounds by their grid barrier.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "css_common.cuh"
+#include "lowrank.cuh"
+
+using namespace css;
+
+namespace {
+
+constexpr int kGT = 32;          // Gram tile
+constexpr int kGK = 32;          // columns per staged chunk
+constexpr int kMaxL = 1024;
+constexpr int kMaxSweeps = 60;
+constexpr int kJacobiThreads = 256;
+constexpr int kMaxGridDim = 12;  // at most 12 x 12 = 144 CTAs (<= one per SM)
+
+// ----------------------------------------------------------- 1. G = W W^T --
+// Block (pair, slice): output tile (ti, tj), ti >= tj, over the columns of one
+// slice; 2 x 2 outputs per thread.
+__global__ void __launch_bounds__(256) gram_rows_kernel(const double* __restrict__ W, long long ldw, int l,
+                                                        int n, int slice, int npairs,
+                                                        double* __restrict__ part) {
+  __shared__ double xa[kGT][kGK + 1], xb[kGT][kGK + 1];
+  const int pidx = blockIdx.x, sl = blockIdx.y;
+  int ti = (int)((sqrtf(8.f * pidx + 1.f) - 1.f) * 0.5f);
+  while (ti * (ti + 1) / 2 > pidx) --ti;
+  while ((ti + 1) * (ti + 2) / 2 <= pidx) ++ti;
+  const int tj = pidx - ti * (ti + 1) / 2;
+  const int a0 = ti * kGT, b0 = tj * kGT;
+  const int cb = sl * slice, ce = min(n, cb + slice);
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc00 = 0.0, acc01 = 0.0, acc10 = 0.0, acc11 = 0.0;
+  for (int c0 = cb; c0 < ce; c0 += kGK) {
+    for (int e = threadIdx.x; e < kGT * kGK; e += 256) {
+      const int row = e / kGK, col = e % kGK;
+      const bool okc = c0 + col < ce;
+      xa[row][col] = (okc && a0 + row < l) ? W[(long long)(a0 + row) * ldw + c0 + col] : 0.0;
+      xb[row][col] = (okc && b0 + row < l) ? W[(long long)(b0 + row) * ldw + c0 + col] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < kGK; ++kk) {
+      const double u0 = xa[ty * 2][kk], u1 = xa[ty * 2 + 1][kk];
+      const double v0 = xb[tx * 2][kk], v1 = xb[tx * 2 + 1][kk];
+      acc00 = fma(u0, v0, acc00);
+      acc01 = fma(u0, v1, acc01);
+      acc10 = fma(u1, v0, acc10);
+      acc11 = fma(u1, v1, acc11);
+    }
+    __syncthreads();
+  }
+  double* out = part + ((long long)sl * npairs + pidx) * (kGT * kGT);
+  out[(ty * 2) * kGT + tx * 2] = acc00;
+  out[(ty * 2) * kGT + tx * 2 + 1] = acc01;
+  out[(ty * 2 + 1) * kGT + tx * 2] = acc10;
+  out[(ty * 2 + 1) * kGT + tx * 2 + 1] = acc11;
+}
+
+// G (lp x lp, column-major, zero padding row/column when l is odd) from the
+// slices' partial tiles, added in slice order; V = I.
+__global__ void gram_reduce_kernel(const double* __restrict__ part, int nslices, int npairs, int l, int lp,
+                                   double* __restrict__ G, double* __restrict__ V) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)lp * lp) return;
+  const int r = (int)(idx % lp), c = (int)(idx / lp);
+  V[idx] = (r == c) ? 1.0 : 0.0;
+  if (r >= l || c >= l) {
+    G[idx] = 0.0;
+    return;
+  }
+  const int a = max(r, c), b = min(r, c);
+  const int ti = a / kGT, tj = b / kGT;
+  const int pidx = ti * (ti + 1) / 2 + tj;
+  const int off = (a % kGT) * kGT + (b % kGT);
+  double s = 0.0;
+  for (int q = 0; q < nslices; ++q) s += part[((long long)q * npairs + pidx) * (kGT * kGT) + off];
+  G[idx] = s;
+}
+
+// ------------------------------------------------------------- 2. Jacobi --
+struct JacobiArgs {
+  double* G0;
+  double* G1;
+  double* V;
+  int lp;
+  int gdim;
+  int chunk;          // pairs per chunk
+  uint32_t* bar;
+  int* flags;         // [kMaxSweeps]: a rotation happened in sweep s
+  int* info;          // [0] sweeps, [1] buffer holding the final G
+  DevStatus* st;
+};
+
+// Pair j of round r of the round-robin tournament on lp indices: index lp-1
+// stays, the others turn one step per round (every pair meets once in lp-1
+// rounds).
+__device__ __forceinline__ void rr_pair(int r, int j, int lp, int& p, int& q) {
+  int a, b;
+  if (j == 0) {
+    a = r;
+    b = lp - 1;
+  } else {
+    a = (r + j) % (lp - 1);
+    b = (r + lp - 1 - j) % (lp - 1);
+  }
+  p = min(a, b);
+  q = max(a, b);
+}
+
+// One plane rotation applied to a pair (a, b): (c a - s b, s a + c b), in one
+// fixed instruction order so that mirrored elements come out bitwise equal.
+__device__ __forceinline__ void rot(double c, double s, double a, double b, double& x, double& y) {
+  x = fma(c, a, -(s * b));
+  y = fma(s, a, c * b);
+}
+
+__global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(JacobiArgs A) {
+  __shared__ double s_c[kMaxL / 2], s_s[kMaxL / 2];
+  __shared__ int s_p[kMaxL / 2], s_q[kMaxL / 2];
+  __shared__ double s_red[32];
+  __shared__ uint32_t s_epoch;
+  __shared__ int s_rot, s_any;
+  const int lp = A.lp, h = lp / 2, NT = kJacobiThreads, tid = threadIdx.x;
+  const int cx = blockIdx.x % A.gdim, cy = blockIdx.x / A.gdim;
+  const int xb = cx * A.chunk, xe = min(h, xb + A.chunk);
+  const int yb = cy * A.chunk, ye = min(h, yb + A.chunk);
+  const int ncta = gridDim.x;
+  if (tid == 0) s_epoch = 0u;
+  // trace(G) = ||W||_F^2, the same sum in every CTA
+  double tr = 0.0;
+  for (int i = tid; i < lp; i += NT) tr += A.G0[(long long)i * lp + i];
+  tr = block_sum(tr, s_red);
+  if (!isfinite(tr)) {
+    if (blockIdx.x == 0 && tid == 0) set_error(A.st, (int32_t)CSS_ERR_NONFINITE, 0);
+    return;
+  }
+  // A pair is left alone when |g_pq| <= 1e-15 sqrt(g_pp g_qq) (the relative
+  // test of Demmel and Veselic) or when |g_pq| <= 1e-17 trace(G), far below
+  // the Gram matrix's own rounding.
+  const double tiny = 1e-17 * tr;
+  const double tol2 = 1e-30;
+  int cur = 0, sweep = 0;
+  bool conv = false;
+  const int nx = xe - xb, ny = ye - yb;
+  for (sweep = 0; sweep < kMaxSweeps && !conv; ++sweep) {
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    for (int r = 0; r < lp - 1; ++r) {
+      const double* Gc = cur ? A.G1 : A.G0;
+      double* Gn = cur ? A.G0 : A.G1;
+      // rotations of the pairs in chunks x and y
+      const int nang = nx + (cx == cy ? 0 : ny);
+      for (int e = tid; e < nang; e += NT) {
+        const int j = e < nx ? xb + e : yb + (e - nx);
+        int p, q;
+        rr_pair(r, j, lp, p, q);
+        const double gpp = __ldcg(Gc + (long long)p * lp + p);
+        const double gqq = __ldcg(Gc + (long long)q * lp + q);
+        const double gpq = __ldcg(Gc + (long long)q * lp + p);
+        double c = 1.0, sn = 0.0;
+        if (fabs(gpq) > tiny && gpq * gpq > tol2 * fabs(gpp * gqq)) {
+          // t = tan(theta), the smaller root of t^2 + 2 tau t - 1 = 0 with
+          // tau = (g_qq - g_pp) / (2 g_pq):  t = sgn(d) 2 g_pq / (|d| +
+          // sqrt(d^2 + 4 g_pq^2)), d = g_qq - g_pp, formed in FP32 after a
+          // common power-of-two scaling (t only has to be close; the
+          // rotation stays orthogonal to FP64 precision because c is then
+          // formed from t in FP64).
+          const double d = gqq - gpp, g2 = 2.0 * gpq;
+          int ex;
+          frexp(fmax(fabs(d), fabs(g2)), &ex);
+          const float df = (float)ldexp(d, -ex), gf = (float)ldexp(g2, -ex);
+          const float tf = copysignf(1.f, df) * gf / (fabsf(df) + sqrtf(df * df + gf * gf));
+          const double t = (double)tf;
+          c = rsqrt(fma(t, t, 1.0));
+          sn = t * c;
+          s_rot = 1;
+        }
+        s_c[j] = c;
+        s_s[j] = sn;
+        s_p[j] = p;
+        s_q[j] = q;
+      }
+      __syncthreads();
+      // 2 x 2 blocks: rows of pair jr (chunk x), columns of pair jc (chunk y).
+      // The rotation of the lower-numbered pair is applied first, so the
+      // blocks (jr, jc) and (jc, jr) give mirror-equal values.
+      for (int e = tid; e < nx * ny; e += NT) {
+        const int jr = xb + e % nx, jc = yb + e / nx;
+        const int r0 = s_p[jr], r1 = s_q[jr], c0 = s_p[jc], c1 = s_q[jc];
+        const double cr = s_c[jr], sr = s_s[jr], cc = s_c[jc], sc = s_s[jc];
+        const double b00 = __ldcg(Gc + (long long)c0 * lp + r0), b10 = __ldcg(Gc + (long long)c0 * lp + r1);
+        const double b01 = __ldcg(Gc + (long long)c1 * lp + r0), b11 = __ldcg(Gc + (long long)c1 * lp + r1);
+        double o00, o01, o10, o11;
+        if (jr <= jc) {
+          double x00, x10, x01, x11;
+          rot(cr, sr, b00, b10, x00, x10);   // rows first
+          rot(cr, sr, b01, b11, x01, x11);
+          rot(cc, sc, x00, x01, o00, o01);
+          rot(cc, sc, x10, x11, o10, o11);
+          if (jr == jc) o10 = o01;           // the block's own g_pq = g_qp
+        } else {
+          double y00, y01, y10, y11;
+          rot(cc, sc, b00, b01, y00, y01);   // columns first
+          rot(cc, sc, b10, b11, y10, y11);
+          rot(cr, sr, y00, y10, o00, o10);
+          rot(cr, sr, y01, y11, o01, o11);
+        }
+        Gn[(long long)c0 * lp + r0] = o00;
+        Gn[(long long)c1 * lp + r0] = o01;
+        Gn[(long long)c0 * lp + r1] = o10;
+        Gn[(long long)c1 * lp + r1] = o11;
+      }
+      // V <- V J for the column pairs of chunk y, the rows of slice x
+      {
+        const int rb = (int)((long long)lp * cx / A.gdim), re = (int)((long long)lp * (cx + 1) / A.gdim);
+        const int nr = re - rb;
+        for (int e = tid; e < nr * ny; e += NT) {
+          const int i = rb + e % nr, jc = yb + e / nr;
+          const int p = s_p[jc], q = s_q[jc];
+          // other CTAs rotated these columns in earlier rounds: read from L2
+          const double vp = __ldcg(A.V + (long long)p * lp + i), vq = __ldcg(A.V + (long long)q * lp + i);
+          double x, y;
+          rot(s_c[jc], s_s[jc], vp, vq, x, y);
+          A.V[(long long)p * lp + i] = x;
+          A.V[(long long)q * lp + i] = y;
+        }
+      }
+      if (!team_barrier(A.bar, ncta, A.st, 40, &s_epoch)) return;
+      cur ^= 1;
+    }
+    // every pair of the sweep was seen by the CTA on the diagonal of its chunk
+    if (tid == 0 && s_rot) atomicOr(A.flags + sweep, 1);
+    if (!team_barrier(A.bar, ncta, A.st, 41, &s_epoch)) return;
+    if (tid == 0) s_any = __ldcg(A.flags + sweep);
+    __syncthreads();
+    conv = (s_any == 0);
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+    A.info[0] = sweep;
+    A.info[1] = cur;
+    if (!conv) set_error(A.st, (int32_t)CSS_ERR_NOT_CONVERGED, 42);
+  }
+}
+
+// --------------------------------------------------- 3. order and signs --
+// One block.  lam_i = G_ii; rank by (lambda descending, index ascending).
+__global__ void __launch_bounds__(1024) order_kernel(const double* __restrict__ G0, const double* __restrict__ G1,
+                                                     const double* __restrict__ V, const int* __restrict__ info,
+                                                     int l, int lp, int k, long long n, double* __restrict__ sigma,
+                                                     double* __restrict__ Uw, double* __restrict__ scale,
+                                                     double* __restrict__ tail) {
+  __shared__ double lam[kMaxL];
+  __shared__ int ord[kMaxL];
+  __shared__ double red[32];
+  const double* G = info[1] ? G1 : G0;
+  for (int i = threadIdx.x; i < l; i += blockDim.x) lam[i] = G[(long long)i * lp + i];
+  __syncthreads();
+  double tr = 0.0;
+  for (int i = threadIdx.x; i < l; i += blockDim.x) {
+    const double v = lam[i];
+    int rk = 0;
+    for (int j = 0; j < l; ++j) rk += (lam[j] > v) || (lam[j] == v && j < i);
+    ord[rk] = i;
+    tr += fmax(v, 0.0);
+  }
+  tr = block_sum(tr, red);   // ||W||_F^2
+  double tl = 0.0;
+  for (int r = k + threadIdx.x; r < l; r += blockDim.x) tl += fmax(lam[ord[r]], 0.0);
+  tl = block_sum(tl, red);
+  if (threadIdx.x == 0 && tail) tail[0] = tl;
+  // resolution of the Gram route: (n + l) 2^-52 ||W||_F^2
+  const double thr = (double)(n + l) * 0x1p-52 * tr;
+  for (int r = threadIdx.x; r < k; r += blockDim.x) {
+    const double lv = fmax(lam[ord[r]], 0.0);
+    const double sv = sqrt(lv);
+    sigma[r] = sv;
+    scale[r] = (lv > thr && sv > 0.0) ? 1.0 / sv : 0.0;
+  }
+  // U^(W)_k: column r = eigenvector ord[r], signed so that its entry of
+  // largest magnitude (lowest index on ties) is positive; one warp a column
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r = wid; r < k; r += nw) {
+    const double* v = V + (long long)ord[r] * lp;
+    double best = -1.0;
+    int bi = l;
+    for (int i = lane; i < l; i += 32) {
+      const double a = fabs(v[i]);
+      if (a > best) { best = a; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    const double sg = (bi < l && v[bi] < 0.0) ? -1.0 : 1.0;
+    for (int i = lane; i < l; i += 32) Uw[(long long)r * l + i] = sg * v[i];
+  }
+}
+
+// ------------------------------------------- 4. C = A B diag(scale), FP64 --
+// A: M x K (lda), B: K x N (ldb), C: M x N (ldc), all column-major.  64 x 64
+// outputs per block, 4 x 4 per thread (rows tx + 16 a, columns ty + 16 b).
+__global__ void __launch_bounds__(256) gemm_nn_kernel(const double* __restrict__ A, long long lda,
+                                                      const double* __restrict__ B, long long ldb,
+                                                      const double* __restrict__ scale, double* __restrict__ C,
+                                                      long long ldc, long long M, int N, int K) {
+  constexpr int BK = 16;
+  __shared__ double as[BK][64], bs[BK][65];
+  const long long m0 = (long long)blockIdx.x * 64;
+  const int n0 = blockIdx.y * 64;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    for (int e = threadIdx.x; e < BK * 64; e += 256) {
+      const int i = e % 64, kk = e / 64;
+      as[kk][i] = (m0 + i < M && k0 + kk < K) ? A[(long long)(k0 + kk) * lda + m0 + i] : 0.0;
+      const int kk2 = e % BK, j = e / BK;
+      bs[kk2][j] = (n0 + j < N && k0 + kk2 < K) ? B[(long long)(n0 + j) * ldb + k0 + kk2] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < BK; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = as[kk][tx + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = bs[kk][ty + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const int j = n0 + ty + 16 * b;
+    if (j >= N) continue;
+    const double sc = scale ? scale[j] : 1.0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const long long i = m0 + tx + 16 * a;
+      if (i < M) C[(long long)j * ldc + i] = acc[a][b] * sc;
+    }
+  }
+}
+
+// ------------------------------------------------------------ host side --
+struct LrLayout {
+  DevStatus* st;
+  int* info;
+  int* flags;
+  uint32_t* bar;
+  double *part, *G0, *G1, *V, *Uw, *scale;
+  int nslices, npairs, slice;
+  size_t bytes;
+};
+
+int gram_tiles(int l) { return (l + kGT - 1) / kGT; }
+
+LrLayout lr_layout(void* ws, size_t cap, int64_t n, int32_t l, int32_t k, int sms) {
+  WsCarver c(ws, cap);
+  LrLayout L{};
+  L.st = (DevStatus*)c.take<char>(kStatusBytes);   // first: css_read_status reads it
+  L.info = c.take<int>(64);
+  L.flags = c.take<int>(kMaxSweeps + 4);
+  L.bar = c.take<uint32_t>(64);
+  const int t = gram_tiles(l);
+  L.npairs = t * (t + 1) / 2;
+  // enough (pair, slice) blocks for about two waves, slices of >= 256 columns
+  const int want = std::max(1, (2 * std::max(sms, 1) + L.npairs - 1) / L.npairs);
+  const int cap_slices = (int)std::max<int64_t>(1, (n + 255) / 256);
+  L.nslices = std::min({want, cap_slices, 64});
+  L.slice = (int)((n + L.nslices - 1) / L.nslices);
+  L.part = c.take<double>((size_t)L.nslices * L.npairs * kGT * kGT);
+  const int lp = l + (l & 1);
+  L.G0 = c.take<double>((size_t)lp * lp);
+  L.G1 = c.take<double>((size_t)lp * lp);
+  L.V = c.take<double>((size_t)lp * lp);
+  L.Uw = c.take<double>((size_t)l * k);
+  L.scale = c.take<double>(k);
+  L.bytes = c.off;
+  return L;
+}
+
+int device_sms() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return n;
+}
+
+// The Gram slices are sized for 152 SMs whatever the device, so that
+// css_workspace_size needs no device and the launch carves the same layout.
+constexpr int kLayoutSms = 152;
+
+}  // namespace
+
+size_t lowrank_workspace_bytes(int64_t n, int32_t l, int32_t k) {
+  return lr_layout(nullptr, (size_t)-1, n, l, k, kLayoutSms).bytes;
+}
+
+extern "C" css_status css_lowrank(const double* W, int64_t ldw, const double* Q, int64_t ldq, int64_t m,
+                                  int64_t n, int32_t l, int32_t k, double* sigma, double* U, int64_t ldu,
+                                  double* V, int64_t ldv, double* Uw, double* tail, void* ws, size_t ws_bytes,
+                                  const css_opts* opts, css_stream_t stream) {
+  css_opts o;
+  css_opts_default(&o);
+  if (opts) o = *opts;
+  if (!W || !sigma) return CSS_ERR_INVALID_ARG;
+  if (n < 1 || n > INT32_MAX || ldw < n || l < 1 || l > kMaxL || k < 1 || k > l) return CSS_ERR_INVALID_ARG;
+  if (U && (!Q || m < 1 || m > INT32_MAX || ldq < m || ldu < m)) return CSS_ERR_INVALID_ARG;
+  if (V && ldv < n) return CSS_ERR_INVALID_ARG;
+  if (!ws || ((uintptr_t)ws % kWsAlign) != 0) return CSS_ERR_WORKSPACE;
+  LrLayout L = lr_layout(ws, ws_bytes, n, l, k, kLayoutSms);
+  if (L.bytes > ws_bytes) return CSS_ERR_WORKSPACE;
+  int dev = 0, major = 0, minor = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CSS_ERR_CUDA;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (major != 10 || minor != 3 || !coop) return CSS_ERR_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int lp = l + (l & 1), h = lp / 2;
+  // Jacobi grid: g x g CTAs, chunks of about 8+ pairs, g <= 12, g^2 <= SMs
+  int gdim = std::max(1, std::min(kMaxGridDim, h / 8));
+  const int sms = device_sms();
+  while (gdim > 1 && gdim * gdim > sms) --gdim;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_kernel, kJacobiThreads, 0) != cudaSuccess ||
+      occ < 1)
+    return CSS_ERR_CUDA;
+  const int chunk = (h + gdim - 1) / gdim;
+
+  DevStatus hs{};
+  hs.spin_budget_ns = o.spin_budget_ns ? o.spin_budget_ns : 2000000000ull;
+  cudaError_t e = cudaMemcpyAsync(L.st, &hs, sizeof(hs), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(L.flags, 0, sizeof(int) * (kMaxSweeps + 4), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(L.bar, 0, sizeof(uint32_t) * 64, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(L.info, 0, sizeof(int) * 64, s);
+  if (e != cudaSuccess) return CSS_ERR_CUDA;
+  gram_rows_kernel<<<dim3(L.npairs, L.nslices), 256, 0, s>>>(W, ldw, l, (int)n, L.slice, L.npairs, L.part);
+  gram_reduce_kernel<<<(unsigned)(((long long)lp * lp + 255) / 256), 256, 0, s>>>(L.part, L.nslices, L.npairs,
+                                                                                   l, lp, L.G0, L.V);
+  if (cudaGetLastError() != cudaSuccess) return CSS_ERR_CUDA;
+  JacobiArgs ja{L.G0, L.G1, L.V, lp, gdim, chunk, L.bar, L.flags, L.info, L.st};
+  void* args[] = {&ja};
+  e = cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(gdim * gdim), dim3(kJacobiThreads), args, 0,
+                                  s);
+  if (e != cudaSuccess) return CSS_ERR_CUDA;
+  double* uw = Uw ? Uw : L.Uw;
+  order_kernel<<<1, 1024, 0, s>>>(L.G0, L.G1, L.V, L.info, l, lp, k, (long long)n, sigma, uw, L.scale, tail);
+  if (U)
+    gemm_nn_kernel<<<dim3((unsigned)((m + 63) / 64), (k + 63) / 64), 256, 0, s>>>(Q, ldq, uw, l, nullptr, U, ldu,
+                                                                                   m, k, l);
+  if (V)
+    gemm_nn_kernel<<<dim3((unsigned)((n + 63) / 64), (k + 63) / 64), 256, 0, s>>>(W, ldw, uw, l, L.scale, V, ldv,
+                                                                                   n, k, l);
+  if (cudaGetLastError() != cudaSuccess) return CSS_ERR_CUDA;
+  if (!o.sync) return CSS_OK;
+  DevStatus st{};
+  e = cudaMemcpyAsync(&st, L.st, sizeof(st), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return CSS_ERR_CUDA;
+  return st.code != 0 ? (css_status)st.code : CSS_OK;
+}

@@ -92,6 +92,7 @@ class Selection:
     diag_g: Optional[torch.Tensor] = None
     timing_ms: Optional[tuple] = None       # (initial scores, greedy iterations)
     trace_ns: Optional[torch.Tensor] = None  # int64[k, 16] phase timestamps
+    basis: Optional[torch.Tensor] = None    # float64 (m, k) column-major: Q, W = Q^T A
 
     @property
     def indices(self):
@@ -128,7 +129,7 @@ def _prep_forced(forced, device):
 
 def select(A: torch.Tensor, k: int, *, tau_rel=None, forced=None, return_W=False, diag=False,
            score_mode=0, grid_ctas=0, tile_cols=0, spin_budget_ns=0, stream=None,
-           timing=False, phase_trace=False, init_path=0) -> Selection:
+           timing=False, phase_trace=False, init_path=0, return_basis=False) -> Selection:
     """Greedy CSS (Algorithm 1) of the columns of A (column-major, on the GPU)."""
     m, n, lda = _colmajor(A)
     dev = A.device
@@ -151,6 +152,9 @@ def select(A: torch.Tensor, k: int, *, tau_rel=None, forced=None, return_W=False
     tr = torch.zeros((k, 16), dtype=torch.int64, device=dev) if phase_trace else None
     if tr is not None:
         o.trace_ns = tr.data_ptr()
+    Qb = torch.empty((k, m), dtype=torch.float64, device=dev).t() if return_basis else None
+    if Qb is not None:
+        o.basis = Qb.data_ptr()
     nbytes = lib.css_workspace_size(L.CSS_OP_SELECT, dt, m, n, 0, k, 0, C.byref(o))
     if nbytes == 0:
         raise ValueError("invalid sizes for css_select")
@@ -163,12 +167,13 @@ def select(A: torch.Tensor, k: int, *, tau_rel=None, forced=None, return_W=False
     if tms is not None:
         res.timing_ms = (tms[0], tms[1])
     res.trace_ns = tr
+    res.basis = Qb
     return res
 
 
 def gcss_select(A: torch.Tensor, B: torch.Tensor, k: int, *, tau_rel=None, forced=None,
                 return_W=False, diag=False, grid_ctas=0, tile_cols=0, spin_budget_ns=0,
-                stream=None, init_path=0) -> Selection:
+                stream=None, init_path=0, return_basis=False) -> Selection:
     """Greedy generalized CSS (Algorithm 3): columns of A reconstructing B.
     B must be float64 when A is float64, float32 otherwise (column-major)."""
     m, n, lda = _colmajor(A)
@@ -191,6 +196,9 @@ def gcss_select(A: torch.Tensor, B: torch.Tensor, k: int, *, tau_rel=None, force
               torch.empty(n, dtype=torch.float64, device=dev),
               torch.empty(n, dtype=torch.float64, device=dev))
     o = _opts(tau_rel, fz, 0, grid_ctas, tile_cols, spin_budget_ns, True, dg, init_path)
+    Qb = torch.empty((k, m), dtype=torch.float64, device=dev).t() if return_basis else None
+    if Qb is not None:
+        o.basis = Qb.data_ptr()
     nbytes = lib.css_workspace_size(L.CSS_OP_GCSS, dt, m, n, r, k, 0, C.byref(o))
     if nbytes == 0:
         raise ValueError("invalid sizes for gcss_select")
@@ -198,7 +206,78 @@ def gcss_select(A: torch.Tensor, B: torch.Tensor, k: int, *, tau_rel=None, force
     code = lib.gcss_select(_ptr(A), dt, m, n, lda, _ptr(B), r, ldb, k, _ptr(sel), _ptr(trace),
                            _ptr(nsel), _ptr(W), _ptr(ws), nbytes, C.byref(o), _stream(stream))
     _check(code, "gcss_select")
-    return Selection(sel, trace, int(nsel.item()), code, W, *(dg if dg else (None, None, None)))
+    res = Selection(sel, trace, int(nsel.item()), code, W, *(dg if dg else (None, None, None)))
+    res.basis = Qb
+    return res
+
+
+@dataclass
+class Embedding:
+    Q: torch.Tensor      # float64 (m, l), column-major: orth(A_:S)
+    W: torch.Tensor      # float64 (l, n), row t contiguous: Q^T A
+
+
+def embed(A: torch.Tensor, S, *, stream=None) -> Embedding:
+    """Q = orth(A_:S) and W = Q^T A (Sec. 3.2, Eq. CSS_LowDim) on the GPU."""
+    m, n, lda = _colmajor(A)
+    dev = A.device
+    dt = _DT[A.dtype]
+    lib = L.load()
+    sel = torch.as_tensor(list(S) if not torch.is_tensor(S) else S, dtype=torch.int32).to(dev).contiguous()
+    l = int(sel.numel())
+    Q = torch.empty((l, m), dtype=torch.float64, device=dev).t()
+    W = torch.empty((l, n), dtype=torch.float64, device=dev)
+    o = L.default_opts()
+    nbytes = lib.css_workspace_size(L.CSS_OP_EMBED, dt, m, n, 0, l, 0, C.byref(o))
+    if nbytes == 0:
+        raise ValueError("invalid sizes for css_embed")
+    _keep, ws = _workspace(nbytes, dev)
+    code = lib.css_embed(_ptr(A), dt, m, n, lda, _ptr(sel), l, _ptr(Q), m, _ptr(W), n, _ptr(ws), nbytes,
+                         C.byref(o), _stream(stream))
+    _check(code, "css_embed")
+    return Embedding(Q, W)
+
+
+@dataclass
+class LowRank:
+    sigma: torch.Tensor                  # float64 (k,), descending
+    Uw: torch.Tensor                     # float64 (l, k) column-major: U^(W)_k
+    tail: float                          # sum_{i >= k} sigma_i(W)^2
+    U: Optional[torch.Tensor] = None     # float64 (m, k) column-major: Q U^(W)_k
+    V: Optional[torch.Tensor] = None     # float64 (n, k) column-major: V^(W)_k
+
+
+def lowrank(W: torch.Tensor, k: int, Q: Optional[torch.Tensor] = None, *, want_V=True,
+            stream=None) -> LowRank:
+    """Rank-k approximation / approximate SVD from an embedding (Sec. 3.2,
+    Eq. ApproxSVD).  W: float64 (l, n) with unit column stride; Q: float64
+    (m, l) column-major or None (then U is not formed)."""
+    if W.dtype != torch.float64 or W.dim() != 2 or W.stride(1) != 1 or not W.is_cuda:
+        raise TypeError("W must be a CUDA float64 (l, n) tensor with unit column stride")
+    l, n = W.shape
+    ldw = W.stride(0) if l > 1 else n
+    dev = W.device
+    m, ldq = 0, 1
+    if Q is not None:
+        m, lq, ldq = _colmajor(Q, "Q")
+        if Q.dtype != torch.float64 or lq != l:
+            raise TypeError("Q must be float64 (m, l) column-major")
+    lib = L.load()
+    sigma = torch.empty(k, dtype=torch.float64, device=dev)
+    Uw = torch.empty((k, l), dtype=torch.float64, device=dev).t()
+    tail = torch.empty(1, dtype=torch.float64, device=dev)
+    U = torch.empty((k, m), dtype=torch.float64, device=dev).t() if Q is not None else None
+    V = torch.empty((k, n), dtype=torch.float64, device=dev).t() if want_V else None
+    o = L.default_opts()
+    nbytes = lib.css_workspace_size(L.CSS_OP_LOWRANK, L.CSS_F64, m, n, l, k, 0, C.byref(o))
+    if nbytes == 0:
+        raise ValueError("invalid sizes for css_lowrank")
+    _keep, ws = _workspace(nbytes, dev)
+    code = lib.css_lowrank(_ptr(W), ldw, _ptr(Q), ldq, m, n, l, k, _ptr(sigma), _ptr(U), max(m, 1),
+                           _ptr(V), n, _ptr(Uw), _ptr(tail), _ptr(ws), nbytes, C.byref(o),
+                           _stream(stream))
+    _check(code, "css_lowrank")
+    return LowRank(sigma, Uw, float(tail.item()), U, V)
 
 
 @dataclass

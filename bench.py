@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "decay_4096x32768", "dist_2048x262144", "dist_2048x65536",
-                             "batched_1024", "relative_accuracy"],
+                             "batched_1024", "relative_accuracy", "lowrank"],
                     help="decay_4096x32768 is the small profiling case of the headline model; "
                          "dist_* run the distributed pipeline (Algorithms 2 and 4), batched_1024 "
                          "the batched independent problems")
@@ -396,6 +396,71 @@ def run_relative_accuracy(args):
         "results": rows}), flush=True)
 
 
+FP64_TFLOPS = 1.20   # FP64 FMA throughput of this part, measured with a dependent-free FMA loop
+
+
+def run_lowrank(args):
+    """Sec. 3.2 after the headline selection: the greedy run on the
+    4096 x 65536 BF16 workload (k = 256, basis and omega rows kept), then the
+    rank-128 approximation and approximate SVD from that embedding
+    (css_lowrank: Gram matrix, Jacobi eigendecomposition, U~ and V~).  Each
+    timed step is one css_lowrank call; W (134 MB) is larger than L2."""
+    import torch
+    from paper_1312_6838_gb300 import css
+    c, A32 = workload_array(WORKLOAD)
+    m, n, k = c["m"], c["n"], c["k"]
+    kr = 128
+    A = css.to_colmajor(torch.from_numpy(A32).cuda().to(torch.bfloat16))
+    del A32
+    res = css.select(A, k, return_W=True, return_basis=True)
+    W, Q = res.W, res.basis
+    l = res.n_sel
+    for _ in range(max(args.warmup, 3)):
+        css.lowrank(W, kr, Q)
+    phases = css.lowrank(W, kr, Q, timing=True).timing_ms
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(0)
+    clk.start()
+    ev0.record()
+    for _ in range(args.steps):
+        out = css.lowrank(W, kr, Q)
+    ev1.record()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    # the dominant kernel: the Gram matrix W W^T, l (l + 1) / 2 n FP64 FMAs
+    gram_flop = 2.0 * (l * (l + 1) / 2) * n
+    gram_tf = gram_flop / (phases[0] * 1e-3) / 1e12
+    v_flop = 2.0 * n * l * kr + 2.0 * m * l * kr
+    line = {
+        "metric": "rank-k approximation and approximate SVD from the embedding (Sec. 3.2)",
+        "value": ms, "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3),
+        "ms_per_step": ms, "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"lowrank_{WORKLOAD}", "m": m, "n": n, "l": l, "k": kr,
+                   "selection_dtype": "bf16", "l2": "W (134 MB) larger than L2"},
+        "phases_ms": {"gram": phases[0], "eigendecomposition": phases[1], "products": phases[2]},
+        "jacobi_sweeps": int(phases[3]),
+        "fp64_tflops": {"gram": gram_tf,
+                        "products": v_flop / (phases[2] * 1e-3) / 1e12},
+        "roofline": {"bound": "alu", "achieved": gram_tf, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
+                     "frac": gram_tf / FP64_TFLOPS, "traffic": None,
+                     "kernel": "gram_rows_kernel (FP64)"},
+        "sigma_1": float(out.sigma[0]), "tail": out.tail, "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        from oracle import css_oracle as O
+        Wn, Qn = W.cpu().numpy(), Q.cpu().numpy()
+        t0 = time.perf_counter()
+        ref = O.rank_k_approximation(Qn, Wn, kr)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": dt * 1e3, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": "the whole problem once (numpy/LAPACK thin SVD of W)"}
+        line["max_sigma_rel_diff_vs_oracle"] = float(
+            np.max(np.abs(out.sigma.cpu().numpy() - ref["sigma"]) / ref["sigma"]))
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -409,6 +474,9 @@ def main():
         return
     if args.workload == "relative_accuracy":
         run_relative_accuracy(args)
+        return
+    if args.workload == "lowrank":
+        run_lowrank(args)
         return
     import torch
     ws, rank, local = dist_env()

@@ -139,7 +139,7 @@ typedef struct {
     int32_t* diag_argmax;
     /* HOST double[2] or NULL (sync mode only): milliseconds of the
        initial-score phase and of the greedy iterations, from CUDA events on
-       `stream`. */
+       `stream` (css_lowrank: double[4], see there). */
     double* timing_ms;
     double* diag_f;
     double* diag_g;
@@ -512,9 +512,11 @@ css_status css_embed(const void* A, css_dtype dtype, int64_t m, int64_t n,
  * eigenvalues carry an absolute error of about (n + l) 2^-53 ||W||_F^2 (the
  * Gram matrix's rounding): sigma_i is accurate relative to sigma_1^2 /
  * sigma_i, not to sigma_i.  CSS_ERR_NOT_CONVERGED if the rotations have not
- * converged after 60 sweeps; CSS_ERR_NONFINITE for NaN/Inf in W.
+ * converged after 40 sweeps; CSS_ERR_NONFINITE for NaN/Inf in W.
  * 1 <= k <= l <= 1024.  Workspace: css_workspace_size(CSS_OP_LOWRANK,
- * CSS_F64, m, n, l, k, 0, opts).
+ * CSS_F64, m, n, l, k, 0, opts).  opts->timing_ms (sync mode) is HOST
+ * double[4] here: milliseconds of the Gram matrix, of the eigendecomposition
+ * and of the ordering and products, then the number of Jacobi sweeps.
  */
 css_status css_lowrank(const double* W, int64_t ldw, const double* Q,
                        int64_t ldq, int64_t m, int64_t n, int32_t l, int32_t k,

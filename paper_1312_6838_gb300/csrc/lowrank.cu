@@ -8,13 +8,16 @@
 //   1. gram_rows_kernel: G in FP64 over lower 32 x 32 tiles, the n columns cut
 //      into slices whose partial tiles gram_reduce_kernel adds in a fixed
 //      order (bitwise reproducible).
-//   2. jacobi_kernel: the eigendecomposition of G by two-sided cyclic Jacobi
+//   2. jacobi_kernel: the eigenvalues of G by two-sided cyclic Jacobi
 //      rotations (Golub and Van Loan, Matrix Computations, Sec. 8.5) in the
 //      parallel round-robin ordering of Brent and Luk (1985): each round
 //      rotates l/2 disjoint index pairs at once.  One cooperative kernel on a
 //      g x g grid of CTAs, one grid barrier per round; CTA (x, y) updates the
 //      2 x 2 blocks whose row pair lies in pair chunk x and column pair in
-//      chunk y, so it needs the rotations of two chunks only.
+//      chunk y, so it needs the rotations of two chunks only.  The rounds'
+//      rotations are logged, and replay_rotations_kernel forms the
+//      eigenvectors V = J_1 J_2 ... afterwards, one row of V per block, off
+//      the barrier-bound path.
 //   3. order_kernel: eigenvalues sorted descending, U^(W)_k with a sign rule,
 //      sigma, the tail sum and the 1 / sigma scaling of V~.
 //   4. gemm_nn_kernel: U~ = Q U^(W)_k and V~ = W^T U^(W)_k Sigma_k^-1 in FP64.
@@ -36,7 +39,7 @@ namespace {
 constexpr int kGT = 32;          // Gram tile
 constexpr int kGK = 32;          // columns per staged chunk
 constexpr int kMaxL = 1024;
-constexpr int kMaxSweeps = 60;
+constexpr int kMaxSweeps = 40;
 constexpr int kJacobiThreads = 256;
 constexpr int kMaxGridDim = 12;  // at most 12 x 12 = 144 CTAs (<= one per SM)
 
@@ -83,13 +86,12 @@ __global__ void __launch_bounds__(256) gram_rows_kernel(const double* __restrict
 }
 
 // G (lp x lp, column-major, zero padding row/column when l is odd) from the
-// slices' partial tiles, added in slice order; V = I.
+// slices' partial tiles, added in slice order.
 __global__ void gram_reduce_kernel(const double* __restrict__ part, int nslices, int npairs, int l, int lp,
-                                   double* __restrict__ G, double* __restrict__ V) {
+                                   double* __restrict__ G) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)lp * lp) return;
   const int r = (int)(idx % lp), c = (int)(idx / lp);
-  V[idx] = (r == c) ? 1.0 : 0.0;
   if (r >= l || c >= l) {
     G[idx] = 0.0;
     return;
@@ -107,13 +109,14 @@ __global__ void gram_reduce_kernel(const double* __restrict__ part, int nslices,
 struct JacobiArgs {
   double* G0;
   double* G1;
-  double* V;
+  double2* rotlog;    // (c, s) of every pair of every round, for the V replay
+  long long max_rounds;
   int lp;
   int gdim;
   int chunk;          // pairs per chunk
   uint32_t* bar;
-  int* flags;         // [kMaxSweeps]: a rotation happened in sweep s
-  int* info;          // [0] sweeps, [1] buffer holding the final G
+  int* flags;         // [kMaxSweeps + 1]: some pair still needs a rotation
+  int* info;          // [0] sweeps, [1] buffer holding the final G, [2] rounds
   DevStatus* st;
 };
 
@@ -140,12 +143,35 @@ __device__ __forceinline__ void rot(double c, double s, double a, double b, doub
   y = fma(s, a, c * b);
 }
 
+// A pair is rotated unless |g_pq| <= 1e-15 sqrt(g_pp g_qq) (the relative test
+// of Demmel and Veselic) or |g_pq| <= 1e-17 trace(G), far below the Gram
+// matrix's own rounding.
+__device__ __forceinline__ bool needs_rot(double gpp, double gqq, double gpq, double tiny) {
+  return fabs(gpq) > tiny && gpq * gpq > 1e-30 * fabs(gpp * gqq);
+}
+
+// The rotation that annihilates g_pq: t = tan(theta), the smaller root of
+// t^2 + 2 tau t - 1 = 0 with tau = (g_qq - g_pp) / (2 g_pq), i.e.
+// t = sgn(d) 2 g_pq / (|d| + sqrt(d^2 + 4 g_pq^2)), d = g_qq - g_pp, formed in
+// FP32 after a common power-of-two scaling; c = 1 / sqrt(1 + t^2) and s = t c
+// then come from that t in FP64, so the rotation is orthogonal to FP64
+// precision (t itself only has to be close).
+__device__ __forceinline__ void rot_angle(double gpp, double gqq, double gpq, double& c, double& sn) {
+  const double d = gqq - gpp, g2 = 2.0 * gpq;
+  int ex;
+  frexp(fmax(fabs(d), fabs(g2)), &ex);
+  const float df = (float)ldexp(d, -ex), gf = (float)ldexp(g2, -ex);
+  const float tf = copysignf(1.f, df) * gf / (fabsf(df) + sqrtf(df * df + gf * gf));
+  const double t = (double)tf;
+  c = rsqrt(fma(t, t, 1.0));
+  sn = t * c;
+}
+
 __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(JacobiArgs A) {
   __shared__ double s_c[kMaxL / 2], s_s[kMaxL / 2];
-  __shared__ int s_p[kMaxL / 2], s_q[kMaxL / 2];
   __shared__ double s_red[32];
   __shared__ uint32_t s_epoch;
-  __shared__ int s_rot, s_any;
+  __shared__ int s_any;
   const int lp = A.lp, h = lp / 2, NT = kJacobiThreads, tid = threadIdx.x;
   const int cx = blockIdx.x % A.gdim, cy = blockIdx.x / A.gdim;
   const int xb = cx * A.chunk, xe = min(h, xb + A.chunk);
@@ -160,22 +186,53 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(JacobiArgs A) {
     if (blockIdx.x == 0 && tid == 0) set_error(A.st, (int32_t)CSS_ERR_NONFINITE, 0);
     return;
   }
-  // A pair is left alone when |g_pq| <= 1e-15 sqrt(g_pp g_qq) (the relative
-  // test of Demmel and Veselic) or when |g_pq| <= 1e-17 trace(G), far below
-  // the Gram matrix's own rounding.
   const double tiny = 1e-17 * tr;
-  const double tol2 = 1e-30;
-  int cur = 0, sweep = 0;
-  bool conv = false;
   const int nx = xe - xb, ny = ye - yb;
-  for (sweep = 0; sweep < kMaxSweeps && !conv; ++sweep) {
-    if (tid == 0) s_rot = 0;
-    __syncthreads();
-    for (int r = 0; r < lp - 1; ++r) {
+  const int nang = nx + (cx == cy ? 0 : ny);
+  const long long tot = (long long)lp * lp;
+  const long long per = (tot + ncta - 1) / ncta;
+  const long long cbeg = (long long)blockIdx.x * per, cend = min(tot, cbeg + per);
+  int cur = 0, sweep = 0;
+  long long rg = 0;
+  bool conv = false;
+  for (sweep = 0; sweep <= kMaxSweeps; ++sweep) {
+    // Does any pair of the current G still need a rotation?  (Checked on
+    // the whole matrix, so no sweep without rotations is needed to stop.)
+    {
+      const double* Gc = cur ? A.G1 : A.G0;
+      int bad = 0;
+      for (long long idx = cbeg + tid; idx < cend; idx += NT) {
+        const int p = (int)(idx % lp), q = (int)(idx / lp);
+        if (p >= q) continue;
+        const double gpq = __ldcg(Gc + idx);
+        const double gpp = __ldcg(Gc + (long long)p * lp + p), gqq = __ldcg(Gc + (long long)q * lp + q);
+        bad |= needs_rot(gpp, gqq, gpq, tiny) ? 1 : 0;
+      }
+      if (__syncthreads_or(bad) && tid == 0) atomicOr(A.flags + sweep, 1);
+      if (!team_barrier(A.bar, ncta, A.st, 40, &s_epoch)) return;
+      if (tid == 0) s_any = __ldcg(A.flags + sweep);
+      __syncthreads();
+      if (!s_any) {
+        conv = true;
+        break;
+      }
+      if (sweep == kMaxSweeps || rg + (lp - 1) > A.max_rounds) break;
+    }
+    for (int r = 0; r < lp - 1; ++r, ++rg) {
       const double* Gc = cur ? A.G1 : A.G0;
       double* Gn = cur ? A.G0 : A.G1;
-      // rotations of the pairs in chunks x and y
-      const int nang = nx + (cx == cy ? 0 : ny);
+      // this thread's first 2 x 2 block: its loads go out together with the
+      // rotations' inputs (both only need the round's pairs)
+      int f_r0 = 0, f_r1 = 0, f_c0 = 0, f_c1 = 0;
+      double f00 = 0.0, f10 = 0.0, f01 = 0.0, f11 = 0.0;
+      if (tid < nx * ny) {
+        rr_pair(r, xb + tid % nx, lp, f_r0, f_r1);
+        rr_pair(r, yb + tid / nx, lp, f_c0, f_c1);
+        f00 = __ldcg(Gc + (long long)f_c0 * lp + f_r0);
+        f10 = __ldcg(Gc + (long long)f_c0 * lp + f_r1);
+        f01 = __ldcg(Gc + (long long)f_c1 * lp + f_r0);
+        f11 = __ldcg(Gc + (long long)f_c1 * lp + f_r1);
+      }
       for (int e = tid; e < nang; e += NT) {
         const int j = e < nx ? xb + e : yb + (e - nx);
         int p, q;
@@ -184,27 +241,11 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(JacobiArgs A) {
         const double gqq = __ldcg(Gc + (long long)q * lp + q);
         const double gpq = __ldcg(Gc + (long long)q * lp + p);
         double c = 1.0, sn = 0.0;
-        if (fabs(gpq) > tiny && gpq * gpq > tol2 * fabs(gpp * gqq)) {
-          // t = tan(theta), the smaller root of t^2 + 2 tau t - 1 = 0 with
-          // tau = (g_qq - g_pp) / (2 g_pq):  t = sgn(d) 2 g_pq / (|d| +
-          // sqrt(d^2 + 4 g_pq^2)), d = g_qq - g_pp, formed in FP32 after a
-          // common power-of-two scaling (t only has to be close; the
-          // rotation stays orthogonal to FP64 precision because c is then
-          // formed from t in FP64).
-          const double d = gqq - gpp, g2 = 2.0 * gpq;
-          int ex;
-          frexp(fmax(fabs(d), fabs(g2)), &ex);
-          const float df = (float)ldexp(d, -ex), gf = (float)ldexp(g2, -ex);
-          const float tf = copysignf(1.f, df) * gf / (fabsf(df) + sqrtf(df * df + gf * gf));
-          const double t = (double)tf;
-          c = rsqrt(fma(t, t, 1.0));
-          sn = t * c;
-          s_rot = 1;
-        }
+        if (needs_rot(gpp, gqq, gpq, tiny)) rot_angle(gpp, gqq, gpq, c, sn);
         s_c[j] = c;
         s_s[j] = sn;
-        s_p[j] = p;
-        s_q[j] = q;
+        // the CTA on the diagonal of chunk x logs the chunk's rotations
+        if (cx == cy) A.rotlog[rg * h + j] = make_double2(c, sn);
       }
       __syncthreads();
       // 2 x 2 blocks: rows of pair jr (chunk x), columns of pair jc (chunk y).
@@ -212,10 +253,20 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(JacobiArgs A) {
       // blocks (jr, jc) and (jc, jr) give mirror-equal values.
       for (int e = tid; e < nx * ny; e += NT) {
         const int jr = xb + e % nx, jc = yb + e / nx;
-        const int r0 = s_p[jr], r1 = s_q[jr], c0 = s_p[jc], c1 = s_q[jc];
+        int r0, r1, c0, c1;
+        double b00, b10, b01, b11;
+        if (e == tid) {
+          r0 = f_r0; r1 = f_r1; c0 = f_c0; c1 = f_c1;
+          b00 = f00; b10 = f10; b01 = f01; b11 = f11;
+        } else {
+          rr_pair(r, jr, lp, r0, r1);
+          rr_pair(r, jc, lp, c0, c1);
+          b00 = __ldcg(Gc + (long long)c0 * lp + r0);
+          b10 = __ldcg(Gc + (long long)c0 * lp + r1);
+          b01 = __ldcg(Gc + (long long)c1 * lp + r0);
+          b11 = __ldcg(Gc + (long long)c1 * lp + r1);
+        }
         const double cr = s_c[jr], sr = s_s[jr], cc = s_c[jc], sc = s_s[jc];
-        const double b00 = __ldcg(Gc + (long long)c0 * lp + r0), b10 = __ldcg(Gc + (long long)c0 * lp + r1);
-        const double b01 = __ldcg(Gc + (long long)c1 * lp + r0), b11 = __ldcg(Gc + (long long)c1 * lp + r1);
         double o00, o01, o10, o11;
         if (jr <= jc) {
           double x00, x10, x01, x11;
@@ -236,36 +287,47 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(JacobiArgs A) {
         Gn[(long long)c0 * lp + r1] = o10;
         Gn[(long long)c1 * lp + r1] = o11;
       }
-      // V <- V J for the column pairs of chunk y, the rows of slice x
-      {
-        const int rb = (int)((long long)lp * cx / A.gdim), re = (int)((long long)lp * (cx + 1) / A.gdim);
-        const int nr = re - rb;
-        for (int e = tid; e < nr * ny; e += NT) {
-          const int i = rb + e % nr, jc = yb + e / nr;
-          const int p = s_p[jc], q = s_q[jc];
-          // other CTAs rotated these columns in earlier rounds: read from L2
-          const double vp = __ldcg(A.V + (long long)p * lp + i), vq = __ldcg(A.V + (long long)q * lp + i);
-          double x, y;
-          rot(s_c[jc], s_s[jc], vp, vq, x, y);
-          A.V[(long long)p * lp + i] = x;
-          A.V[(long long)q * lp + i] = y;
-        }
-      }
-      if (!team_barrier(A.bar, ncta, A.st, 40, &s_epoch)) return;
+      if (!team_barrier(A.bar, ncta, A.st, 41, &s_epoch)) return;
       cur ^= 1;
     }
-    // every pair of the sweep was seen by the CTA on the diagonal of its chunk
-    if (tid == 0 && s_rot) atomicOr(A.flags + sweep, 1);
-    if (!team_barrier(A.bar, ncta, A.st, 41, &s_epoch)) return;
-    if (tid == 0) s_any = __ldcg(A.flags + sweep);
-    __syncthreads();
-    conv = (s_any == 0);
   }
   if (blockIdx.x == 0 && tid == 0) {
     A.info[0] = sweep;
     A.info[1] = cur;
+    A.info[2] = (int)rg;
     if (!conv) set_error(A.st, (int32_t)CSS_ERR_NOT_CONVERGED, 42);
   }
+}
+
+// V = J_1 J_2 ... J_R, the product of every round's rotations, replayed from
+// the log: row i of V evolves on its own (V <- V J only mixes its entries p
+// and q), so one block per row keeps it in shared memory and applies the
+// rounds in order, the next round's (c, s) loaded ahead of the current one.
+__global__ void __launch_bounds__(512) replay_rotations_kernel(const double2* __restrict__ rotlog,
+                                                               const int* __restrict__ info, int lp,
+                                                               double* __restrict__ V) {
+  extern __shared__ double row[];
+  const int i = blockIdx.x, h = lp / 2;
+  for (int c = threadIdx.x; c < lp; c += blockDim.x) row[c] = (c == i) ? 1.0 : 0.0;
+  __syncthreads();
+  const long long R = info[2];
+  const int j = threadIdx.x;   // blockDim.x == h
+  int r = 0;
+  double2 cs = R > 0 ? __ldcg(rotlog + j) : make_double2(1.0, 0.0);
+  for (long long g = 0; g < R; ++g) {
+    const double2 nxt = (g + 1 < R) ? __ldcg(rotlog + (g + 1) * h + j) : make_double2(1.0, 0.0);
+    int p, q;
+    rr_pair(r, j, lp, p, q);
+    const double x = row[p], y = row[q];
+    double u, v;
+    rot(cs.x, cs.y, x, y, u, v);
+    row[p] = u;
+    row[q] = v;
+    __syncthreads();
+    cs = nxt;
+    if (++r == lp - 1) r = 0;
+  }
+  for (int c = threadIdx.x; c < lp; c += blockDim.x) V[(long long)c * lp + i] = row[c];
 }
 
 // --------------------------------------------------- 3. order and signs --
@@ -382,6 +444,8 @@ struct LrLayout {
   int* flags;
   uint32_t* bar;
   double *part, *G0, *G1, *V, *Uw, *scale;
+  double2* rotlog;
+  long long max_rounds;
   int nslices, npairs, slice;
   size_t bytes;
 };
@@ -397,16 +461,19 @@ LrLayout lr_layout(void* ws, size_t cap, int64_t n, int32_t l, int32_t k, int sm
   L.bar = c.take<uint32_t>(64);
   const int t = gram_tiles(l);
   L.npairs = t * (t + 1) / 2;
-  // enough (pair, slice) blocks for about two waves, slices of >= 256 columns
-  const int want = std::max(1, (2 * std::max(sms, 1) + L.npairs - 1) / L.npairs);
+  // about twelve (pair, slice) blocks per SM, so that the uneven last share
+  // of blocks costs little; slices of >= 256 columns
+  const int want = std::max(1, (12 * std::max(sms, 1) + L.npairs - 1) / L.npairs);
   const int cap_slices = (int)std::max<int64_t>(1, (n + 255) / 256);
-  L.nslices = std::min({want, cap_slices, 64});
+  L.nslices = std::min({want, cap_slices, 256});
   L.slice = (int)((n + L.nslices - 1) / L.nslices);
   L.part = c.take<double>((size_t)L.nslices * L.npairs * kGT * kGT);
   const int lp = l + (l & 1);
   L.G0 = c.take<double>((size_t)lp * lp);
   L.G1 = c.take<double>((size_t)lp * lp);
   L.V = c.take<double>((size_t)lp * lp);
+  L.max_rounds = (long long)kMaxSweeps * (lp - 1);
+  L.rotlog = c.take<double2>((size_t)L.max_rounds * (lp / 2));
   L.Uw = c.take<double>((size_t)l * k);
   L.scale = c.take<double>(k);
   L.bytes = c.off;
@@ -469,17 +536,34 @@ extern "C" css_status css_lowrank(const double* W, int64_t ldw, const double* Q,
   if (e == cudaSuccess) e = cudaMemsetAsync(L.bar, 0, sizeof(uint32_t) * 64, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(L.info, 0, sizeof(int) * 64, s);
   if (e != cudaSuccess) return CSS_ERR_CUDA;
+  // opts->timing_ms (sync mode): Gram, eigendecomposition, products, sweeps
+  const bool timed = o.timing_ms != nullptr && o.sync;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  if (timed)
+    for (auto& x : ev)
+      if (cudaEventCreate(&x) != cudaSuccess) return CSS_ERR_CUDA;
+  struct EvGuard {
+    cudaEvent_t* e;
+    ~EvGuard() {
+      for (int i = 0; i < 4; ++i)
+        if (e[i]) cudaEventDestroy(e[i]);
+    }
+  } guard{ev};
+  if (timed) cudaEventRecord(ev[0], s);
   gram_rows_kernel<<<dim3(L.npairs, L.nslices), 256, 0, s>>>(W, ldw, l, (int)n, L.slice, L.npairs, L.part);
   gram_reduce_kernel<<<(unsigned)(((long long)lp * lp + 255) / 256), 256, 0, s>>>(L.part, L.nslices, L.npairs,
-                                                                                   l, lp, L.G0, L.V);
+                                                                                   l, lp, L.G0);
   if (cudaGetLastError() != cudaSuccess) return CSS_ERR_CUDA;
-  JacobiArgs ja{L.G0, L.G1, L.V, lp, gdim, chunk, L.bar, L.flags, L.info, L.st};
+  if (timed) cudaEventRecord(ev[1], s);
+  JacobiArgs ja{L.G0, L.G1, L.rotlog, L.max_rounds, lp, gdim, chunk, L.bar, L.flags, L.info, L.st};
   void* args[] = {&ja};
   e = cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(gdim * gdim), dim3(kJacobiThreads), args, 0,
                                   s);
   if (e != cudaSuccess) return CSS_ERR_CUDA;
+  replay_rotations_kernel<<<l, h, lp * sizeof(double), s>>>(L.rotlog, L.info, lp, L.V);
   double* uw = Uw ? Uw : L.Uw;
   order_kernel<<<1, 1024, 0, s>>>(L.G0, L.G1, L.V, L.info, l, lp, k, (long long)n, sigma, uw, L.scale, tail);
+  if (timed) cudaEventRecord(ev[2], s);
   if (U)
     gemm_nn_kernel<<<dim3((unsigned)((m + 63) / 64), (k + 63) / 64), 256, 0, s>>>(Q, ldq, uw, l, nullptr, U, ldu,
                                                                                    m, k, l);
@@ -487,10 +571,19 @@ extern "C" css_status css_lowrank(const double* W, int64_t ldw, const double* Q,
     gemm_nn_kernel<<<dim3((unsigned)((n + 63) / 64), (k + 63) / 64), 256, 0, s>>>(W, ldw, uw, l, L.scale, V, ldv,
                                                                                    n, k, l);
   if (cudaGetLastError() != cudaSuccess) return CSS_ERR_CUDA;
+  if (timed) cudaEventRecord(ev[3], s);
   if (!o.sync) return CSS_OK;
   DevStatus st{};
+  int info[2] = {0, 0};
   e = cudaMemcpyAsync(&st, L.st, sizeof(st), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(info, L.info, sizeof(info), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return CSS_ERR_CUDA;
+  if (timed) {
+    float ms[3] = {0.f, 0.f, 0.f};
+    for (int i = 0; i < 3; ++i) cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
+    for (int i = 0; i < 3; ++i) o.timing_ms[i] = ms[i];
+    o.timing_ms[3] = info[0];
+  }
   return st.code != 0 ? (css_status)st.code : CSS_OK;
 }

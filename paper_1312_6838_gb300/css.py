@@ -245,10 +245,11 @@ class LowRank:
     tail: float                          # sum_{i >= k} sigma_i(W)^2
     U: Optional[torch.Tensor] = None     # float64 (m, k) column-major: Q U^(W)_k
     V: Optional[torch.Tensor] = None     # float64 (n, k) column-major: V^(W)_k
+    timing_ms: Optional[tuple] = None    # (Gram, eigendecomposition, products, sweeps)
 
 
 def lowrank(W: torch.Tensor, k: int, Q: Optional[torch.Tensor] = None, *, want_V=True,
-            stream=None) -> LowRank:
+            stream=None, timing=False) -> LowRank:
     """Rank-k approximation / approximate SVD from an embedding (Sec. 3.2,
     Eq. ApproxSVD).  W: float64 (l, n) with unit column stride; Q: float64
     (m, l) column-major or None (then U is not formed)."""
@@ -269,6 +270,9 @@ def lowrank(W: torch.Tensor, k: int, Q: Optional[torch.Tensor] = None, *, want_V
     U = torch.empty((k, m), dtype=torch.float64, device=dev).t() if Q is not None else None
     V = torch.empty((k, n), dtype=torch.float64, device=dev).t() if want_V else None
     o = L.default_opts()
+    tms = (C.c_double * 4)() if timing else None
+    if tms is not None:
+        o.timing_ms = C.cast(tms, C.c_void_p)
     nbytes = lib.css_workspace_size(L.CSS_OP_LOWRANK, L.CSS_F64, m, n, l, k, 0, C.byref(o))
     if nbytes == 0:
         raise ValueError("invalid sizes for css_lowrank")
@@ -277,7 +281,7 @@ def lowrank(W: torch.Tensor, k: int, Q: Optional[torch.Tensor] = None, *, want_V
                            _ptr(V), n, _ptr(Uw), _ptr(tail), _ptr(ws), nbytes, C.byref(o),
                            _stream(stream))
     _check(code, "css_lowrank")
-    return LowRank(sigma, Uw, float(tail.item()), U, V)
+    return LowRank(sigma, Uw, float(tail.item()), U, V, tuple(tms) if tms is not None else None)
 
 
 @dataclass

@@ -112,3 +112,45 @@ def test_opts_layout_matches_header(lib):
     from paper_1312_6838_gb300 import _lib as L
     o = L.default_opts()
     assert o.tau_rel < 0 and o.sync == 1 and o.n_forced == 0 and o.grid_ctas == 0
+
+
+def test_embed_and_lowrank_host_checks(lib):
+    """Sec. 3.2 entry points: workspace sizes need no device, and argument
+    errors are found on the host before anything is enqueued."""
+    from paper_1312_6838_gb300 import _lib as L
+    o = L.default_opts()
+    P = C.c_void_p
+    fake = P(0x10000)
+    assert lib.css_workspace_size(L.CSS_OP_EMBED, L.CSS_BF16, 4096, 65536, 0, 256, 0, None) > 0
+    assert lib.css_workspace_size(L.CSS_OP_EMBED, L.CSS_BF16, 100, 65536, 0, 101, 0, None) == 0
+    assert lib.css_workspace_size(L.CSS_OP_EMBED, L.CSS_F64, 4096, 65536, 0, 1025, 0, None) == 0
+    a = lib.css_workspace_size(L.CSS_OP_LOWRANK, L.CSS_F64, 4096, 65536, 256, 128, 0, None)
+    b = lib.css_workspace_size(L.CSS_OP_LOWRANK, L.CSS_F64, 0, 65536, 256, 128, 0, None)
+    assert a > 0 and a == b                       # m is not needed for the workspace
+    assert lib.css_workspace_size(L.CSS_OP_LOWRANK, L.CSS_F64, 0, 65536, 256, 257, 0, None) == 0
+    assert lib.css_workspace_size(L.CSS_OP_LOWRANK, L.CSS_F64, 0, 65536, 1025, 10, 0, None) == 0
+    # css_embed: NULL A, no output requested, l > m, repeated check needs a device (not here)
+    r = lib.css_embed(P(0), L.CSS_F32, 10, 20, 10, fake, 3, fake, 10, fake, 20, fake, 1 << 20, C.byref(o), P(0))
+    assert r == L.CSS_ERR_INVALID_ARG
+    r = lib.css_embed(fake, L.CSS_F32, 10, 20, 10, fake, 3, P(0), 10, P(0), 20, fake, 1 << 20, C.byref(o), P(0))
+    assert r == L.CSS_ERR_INVALID_ARG
+    r = lib.css_embed(fake, L.CSS_F32, 10, 20, 10, fake, 11, fake, 10, fake, 20, fake, 1 << 20, C.byref(o), P(0))
+    assert r == L.CSS_ERR_INVALID_ARG
+    r = lib.css_embed(fake, L.CSS_F32, 10, 20, 10, fake, 3, fake, 9, P(0), 20, fake, 1 << 20, C.byref(o), P(0))
+    assert r == L.CSS_ERR_INVALID_ARG              # ldq < m
+    # css_lowrank: NULL W, k > l, ldw < n, U without Q, workspace too small
+    r = lib.css_lowrank(P(0), 20, P(0), 0, 0, 20, 4, 2, fake, P(0), 1, P(0), 20, P(0), P(0), fake, 1 << 30,
+                        C.byref(o), P(0))
+    assert r == L.CSS_ERR_INVALID_ARG
+    r = lib.css_lowrank(fake, 20, P(0), 0, 0, 20, 4, 5, fake, P(0), 1, P(0), 20, P(0), P(0), fake, 1 << 30,
+                        C.byref(o), P(0))
+    assert r == L.CSS_ERR_INVALID_ARG
+    r = lib.css_lowrank(fake, 19, P(0), 0, 0, 20, 4, 2, fake, P(0), 1, P(0), 20, P(0), P(0), fake, 1 << 30,
+                        C.byref(o), P(0))
+    assert r == L.CSS_ERR_INVALID_ARG
+    r = lib.css_lowrank(fake, 20, P(0), 0, 10, 20, 4, 2, fake, fake, 10, P(0), 20, P(0), P(0), fake, 1 << 30,
+                        C.byref(o), P(0))
+    assert r == L.CSS_ERR_INVALID_ARG
+    r = lib.css_lowrank(fake, 20, P(0), 0, 0, 20, 4, 2, fake, P(0), 1, P(0), 20, P(0), P(0), fake, 64,
+                        C.byref(o), P(0))
+    assert r == L.CSS_ERR_WORKSPACE

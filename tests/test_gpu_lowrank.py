@@ -60,6 +60,32 @@ def test_embed_matches_oracle(css, dtype, shape):
     assert np.all(np.diag(W[:, S]) > 0)
 
 
+def test_embed_with_padded_leading_dimension(css):
+    m, n, l = 100, 900, 12
+    A, vals = dev_matrix(ci.lowrank_uv(m, n, 30, 0.05, 77), torch.float32, ld=136)
+    assert A.stride(1) == 136
+    S = _sel(n, l, 5)
+    emb = css.embed(A, S)
+    Qr, Wr, _ = O.embedding(vals, S)
+    np.testing.assert_allclose(emb.Q.cpu().numpy(), Qr, atol=1e-10)
+    colnorm = np.linalg.norm(vals, axis=0)
+    assert np.all(np.abs(emb.W.cpu().numpy() - Wr) <= 1e-10 * colnorm[None, :])
+
+
+def test_gcss_basis_is_the_embedding_of_its_selection(css):
+    """gcss_select's basis (opts.basis) and omega rows: W = Q^T A also for
+    Algorithm 3 (omega = A^T q whatever the target)."""
+    m, n, r, k = 150, 1200, 20, 16
+    A, vals = dev_matrix(ci.lowrank_uv(m, n, 2 * k, 0.05, 61), torch.float64)
+    B = torch.from_numpy(ci.lowrank_uv(m, r, r, 0.0, 62)).cuda().t().contiguous().t()
+    res = css.gcss_select(A, B, k, return_W=True, return_basis=True)
+    S = res.indices.cpu().tolist()
+    Qr, Wr, _ = O.embedding(vals, S)
+    np.testing.assert_allclose(res.basis.cpu().numpy()[:, :len(S)], Qr, atol=1e-9)
+    colnorm = np.linalg.norm(vals, axis=0)
+    assert np.all(np.abs(res.W.cpu().numpy()[:len(S)] - Wr) <= 1e-9 * colnorm[None, :])
+
+
 def test_embed_rejects_dependent_and_repeated_columns(css):
     A_np = ci.lowrank_uv(50, 80, 3, 0.0, 5)        # rank 3
     A, _ = dev_matrix(A_np, torch.float64)
@@ -222,6 +248,16 @@ def test_lowrank_rejects_nonfinite(css):
     with pytest.raises(CssError) as ei:
         css.lowrank(torch.from_numpy(W).cuda(), 4)
     assert ei.value.code == CSS_ERR_NONFINITE
+
+
+def test_lowrank_without_U_or_V(css):
+    W = np.random.default_rng(4).standard_normal((30, 2000)) * (1.0 / np.arange(1, 31))[:, None]
+    Wd = torch.from_numpy(W).cuda()
+    full = css.lowrank(Wd, 10)
+    bare = css.lowrank(Wd, 10, want_V=False)
+    assert bare.U is None and bare.V is None
+    assert torch.equal(full.sigma, bare.sigma) and torch.equal(full.Uw, bare.Uw)
+    assert full.tail == bare.tail
 
 
 def test_lowrank_is_deterministic(css):

@@ -76,10 +76,194 @@ __device__ __forceinline__ void syrk_tile(const TA* __restrict__ A, long long ld
   }
 }
 
+// ------------------------------------------- FP32-accumulating tiles -------
+// FP32 or BF16 A: 128 x 128 outputs per block, 8 x 8 per thread as two 4 x 4
+// quadrants (rows ty*4 + {0..3} and 64 + ty*4 + {0..3}, columns likewise with
+// tx), so that each K step reads four 16-byte vectors from shared memory for
+// 64 FMAs without bank conflicts.  K advances in chunks of 16 through two
+// shared-memory buffers: the next chunk's global loads are in registers while
+// the current chunk is multiplied.
+constexpr int kFT = 128;            // tile edge
+constexpr int kFK = 16;             // K chunk
+constexpr int kFP = kFT + 4;        // row stride of the K-major operands (16-byte aligned)
+constexpr int kFV = kFT * kFK / 256;  // elements each thread stages per operand
+
+struct F32Acc {
+  float v[8][8];
+};
+
+__device__ __forceinline__ void f32_zero(F32Acc& a) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+#pragma unroll
+    for (int w = 0; w < 8; ++w) a.v[q][w] = 0.f;
+}
+
+// acc += X[kk][rows] (x) Y[kk][cols] for the kFK steps of one staged chunk
+template <int LD>
+__device__ __forceinline__ void f32_chunk(const float* __restrict__ X, const float* __restrict__ Y, int ty,
+                                          int tx, F32Acc& acc) {
+#pragma unroll
+  for (int kk = 0; kk < kFK; ++kk) {
+    const float4 a0 = *reinterpret_cast<const float4*>(X + kk * LD + ty * 4);
+    const float4 a1 = *reinterpret_cast<const float4*>(X + kk * LD + 64 + ty * 4);
+    const float4 b0 = *reinterpret_cast<const float4*>(Y + kk * LD + tx * 4);
+    const float4 b1 = *reinterpret_cast<const float4*>(Y + kk * LD + 64 + tx * 4);
+    const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+#pragma unroll
+      for (int w = 0; w < 8; ++w) acc.v[q][w] = fmaf(a[q], b[w], acc.v[q][w]);
+  }
+}
+
+// row (or column) index of this thread's q-th output within the tile
+__device__ __forceinline__ int f32_idx(int t, int q) { return (q < 4 ? 0 : 64) + t * 4 + (q & 3); }
+
+// C = A A^T for tile pair (bi, bj), bi <= bj (see syrk_tile).  The staged
+// operands are A's rows i0.., j0.. over 16 consecutive columns: column-major
+// A makes each of them a contiguous run.
+template <typename TA>
+__device__ __forceinline__ void syrk_tile_f32(const TA* __restrict__ A, long long lda, int m, int n,
+                                              float* __restrict__ C, int tile) {
+  __shared__ __align__(16) float sm[2][2][kFK][kFT];
+  const int nt = (m + kFT - 1) / kFT;
+  int idx = tile, bi = 0;
+  while (idx >= nt - bi) { idx -= nt - bi; ++bi; }
+  const int bj = bi + idx;
+  const int i0 = bi * kFT, j0 = bj * kFT;
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  F32Acc acc;
+  f32_zero(acc);
+  float ra[kFV], rb[kFV];
+  // thread tid stages row rr = tid % 128 of columns l0 + tid / 128 + 2 v
+  const int rr = tid % kFT, kk0 = tid / kFT;
+  const bool oka = i0 + rr < m, okb = j0 + rr < m;
+  const TA* pa = A + (long long)kk0 * lda + i0 + rr;
+  const TA* pb = A + (long long)kk0 * lda + j0 + rr;
+  const long long step = 2 * lda;
+  auto fetch = [&](int l0) {
+    const long long off = (long long)l0 * lda;
+#pragma unroll
+    for (int v = 0; v < kFV; ++v) {
+      const bool okl = l0 + kk0 + 2 * v < n;
+      ra[v] = (okl && oka) ? cvt_in<TA>(pa[off + v * step]) : 0.f;
+      rb[v] = (okl && okb) ? cvt_in<TA>(pb[off + v * step]) : 0.f;
+    }
+  };
+  auto stage = [&](int buf) {
+#pragma unroll
+    for (int v = 0; v < kFV; ++v) {
+      sm[buf][0][kk0 + 2 * v][rr] = ra[v];
+      sm[buf][1][kk0 + 2 * v][rr] = rb[v];
+    }
+  };
+  fetch(0);
+  stage(0);
+  __syncthreads();
+  int buf = 0;
+  for (int l0 = 0; l0 < n; l0 += kFK) {
+    const bool more = l0 + kFK < n;
+    if (more) fetch(l0 + kFK);
+    f32_chunk<kFT>(&sm[buf][0][0][0], &sm[buf][1][0][0], ty, tx, acc);
+    if (more) stage(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int i = i0 + f32_idx(ty, q);
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      const int j = j0 + f32_idx(tx, w);
+      if (i < m && j < m) {
+        C[(long long)j * m + i] = acc.v[q][w];
+        if (bi != bj) C[(long long)i * m + j] = acc.v[q][w];
+      }
+    }
+  }
+}
+
+// Column reduction (see colreduce_tile) with FP32 accumulation.  X and Y are
+// K-contiguous, so 16 consecutive threads read 16 consecutive K entries of
+// one row and write them transposed into the K-major staging buffers (row
+// stride kFP keeps those writes to two-way bank conflicts).
+template <typename TX, typename TA, int EPI>
+__device__ __forceinline__ void colreduce_tile_f32(const TX* __restrict__ X, long long ldx,
+                                                   const TA* __restrict__ Y, long long ldy, int K, int M,
+                                                   int N, double* __restrict__ partial, int mb, int nb) {
+  __shared__ __align__(16) float sm[2][2][kFK][kFP];
+  const int r0 = mb * kFT, c0 = nb * kFT;
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  F32Acc acc;
+  f32_zero(acc);
+  float rx[kFV], ry[kFV];
+  // thread tid stages K entry kk = tid % 16 of rows rr0 + 16 v, rr0 = tid / 16
+  const int kk = tid % kFK, rr0 = tid / kFK;
+  const int vx = (M - r0 - rr0 + kFK - 1) / kFK, vy = (N - c0 - rr0 + kFK - 1) / kFK;   // valid rows
+  const TX* px = X + (long long)(r0 + rr0) * ldx + kk;
+  const TA* py = Y + (long long)(c0 + rr0) * ldy + kk;
+  const long long sx = kFK * ldx, sy = kFK * ldy;
+  auto fetch = [&](int k0) {
+    const bool okk = k0 + kk < K;
+#pragma unroll
+    for (int v = 0; v < kFV; ++v) {
+      rx[v] = (okk && v < vx) ? (float)px[k0 + v * sx] : 0.f;
+      ry[v] = (okk && v < vy) ? cvt_in<TA>(py[k0 + v * sy]) : 0.f;
+    }
+  };
+  auto stage = [&](int buf) {
+#pragma unroll
+    for (int v = 0; v < kFV; ++v) {
+      sm[buf][0][kk][rr0 + kFK * v] = rx[v];
+      sm[buf][1][kk][rr0 + kFK * v] = ry[v];
+    }
+  };
+  fetch(0);
+  stage(0);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < K; k0 += kFK) {
+    const bool more = k0 + kFK < K;
+    if (more) fetch(k0 + kFK);
+    f32_chunk<kFP>(&sm[buf][0][0][0], &sm[buf][1][0][0], ty, tx, acc);
+    if (more) stage(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+  // epilogue: per column, this thread's 8 rows summed in FP64, then the 16
+  // row groups added in a fixed order (the staging buffers are free now)
+  double* red = reinterpret_cast<double*>(&sm[0][0][0][0]);   // [16][kFT]
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    const int cl = f32_idx(tx, w), i = c0 + cl;
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int r = r0 + f32_idx(ty, q);
+      if (r < M && i < N) {
+        const double d = (double)acc.v[q][w];
+        if (EPI == 0) s += d * (double)cvt_in<TA>(Y[(long long)i * ldy + r]);
+        else s += d * d;
+      }
+    }
+    red[ty * kFT + cl] = s;
+  }
+  __syncthreads();
+  for (int c = tid; c < kFT; c += 256) {
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) s += red[q * kFT + c];
+    if (c0 + c < N) partial[(long long)mb * N + c0 + c] = s;
+  }
+}
+
 template <typename TA, int TT, int KC>
-__global__ void __launch_bounds__(256) syrk_kernel(const TA* __restrict__ A, long long lda, int m,
+__global__ void __launch_bounds__(256, 2) syrk_kernel(const TA* __restrict__ A, long long lda, int m,
                                                    int n, typename AccOf<TA>::type* __restrict__ C) {
-  syrk_tile<TA, TT, KC>(A, lda, m, n, C, blockIdx.x);
+  if constexpr (sizeof(typename AccOf<TA>::type) == 4) syrk_tile_f32<TA>(A, lda, m, n, C, blockIdx.x);
+  else syrk_tile<TA, TT, KC>(A, lda, m, n, C, blockIdx.x);
 }
 
 // ------------------------------------------------------ column reduction ----
@@ -152,7 +336,10 @@ template <typename TX, typename TA, int TT, int KC, int EPI>
 __global__ void __launch_bounds__(256) colreduce_kernel(const TX* __restrict__ X, long long ldx,
                                                        const TA* __restrict__ Y, long long ldy, int K,
                                                        int M, int N, double* __restrict__ partial) {
-  colreduce_tile<TX, TA, TT, KC, EPI>(X, ldx, Y, ldy, K, M, N, partial, blockIdx.y, blockIdx.x);
+  if constexpr (sizeof(typename AccOf<TA>::type) == 4)
+    colreduce_tile_f32<TX, TA, EPI>(X, ldx, Y, ldy, K, M, N, partial, blockIdx.y, blockIdx.x);
+  else
+    colreduce_tile<TX, TA, TT, KC, EPI>(X, ldx, Y, ldy, K, M, N, partial, blockIdx.y, blockIdx.x);
 }
 
 __global__ void sum_partials_kernel(const double* __restrict__ partial, int nblk, int n,
@@ -211,13 +398,17 @@ __device__ __forceinline__ int group_of(const int* __restrict__ start, int count
 }
 
 template <typename TA, int TT, int KC>
-__global__ void __launch_bounds__(256) syrk_grouped(const F0Item* __restrict__ items,
+__global__ void __launch_bounds__(256, 2) syrk_grouped(const F0Item* __restrict__ items,
                                                     const int* __restrict__ start, int count) {
   using Acc = typename AccOf<TA>::type;
   const int g = group_of(start, count, blockIdx.x);
   const F0Item it = items[g];
-  syrk_tile<TA, TT, KC>(reinterpret_cast<const TA*>(it.A), it.lda, it.m, it.n,
-                        reinterpret_cast<Acc*>(it.C), blockIdx.x - start[g]);
+  if constexpr (sizeof(Acc) == 4)
+    syrk_tile_f32<TA>(reinterpret_cast<const TA*>(it.A), it.lda, it.m, it.n, reinterpret_cast<Acc*>(it.C),
+                      blockIdx.x - start[g]);
+  else
+    syrk_tile<TA, TT, KC>(reinterpret_cast<const TA*>(it.A), it.lda, it.m, it.n,
+                          reinterpret_cast<Acc*>(it.C), blockIdx.x - start[g]);
 }
 
 template <typename TA, int TT, int KC>
@@ -229,9 +420,14 @@ __global__ void __launch_bounds__(256) colreduce_grouped(const F0Item* __restric
   const F0Item it = items[g];
   const int local = blockIdx.x - start[g];
   const int nbs = (it.n + BT - 1) / BT;
-  colreduce_tile<Acc, TA, TT, KC, 0>(reinterpret_cast<const Acc*>(it.C), (long long)it.m,
-                                     reinterpret_cast<const TA*>(it.A), it.lda, it.m, it.m, it.n,
-                                     it.partial, local / nbs, local % nbs);
+  if constexpr (sizeof(Acc) == 4)
+    colreduce_tile_f32<Acc, TA, 0>(reinterpret_cast<const Acc*>(it.C), (long long)it.m,
+                                   reinterpret_cast<const TA*>(it.A), it.lda, it.m, it.m, it.n, it.partial,
+                                   local / nbs, local % nbs);
+  else
+    colreduce_tile<Acc, TA, TT, KC, 0>(reinterpret_cast<const Acc*>(it.C), (long long)it.m,
+                                       reinterpret_cast<const TA*>(it.A), it.lda, it.m, it.m, it.n,
+                                       it.partial, local / nbs, local % nbs);
 }
 
 template <int BT>

@@ -118,13 +118,14 @@ def _as64(X):
 # --------------------------------------------------------------------------- #
 # Problem 1 / Eq. (Projection): the criterion evaluated directly.
 # --------------------------------------------------------------------------- #
-def reconstruction_error(A, S, B=None):
+def reconstruction_error(A, S, B=None, chunk=None):
     """F(S) = ||T - P^(S) T||_F^2 with T = A (CSS) or T = B (GCSS, Problem 4).
 
     P^(S) projects onto span(A_:S) (Eq. Projection, Sec. 3.1).  It is applied
     through a Householder QR of A_:S (numpy/LAPACK), which spans the same space
     and stays accurate when A_:S is ill-conditioned; the residual is formed
-    explicitly so that no cancellation against ||T||^2 occurs.
+    explicitly so that no cancellation against ||T||^2 occurs.  ``chunk``
+    forms it ``chunk`` columns of T at a time (large inputs; same quantity).
     """
     A = _as64(A)
     T = A if B is None else _as64(B)
@@ -132,8 +133,13 @@ def reconstruction_error(A, S, B=None):
     if len(S) == 0:
         return float(np.sum(T * T))
     Q, _ = np.linalg.qr(A[:, S], mode="reduced")
-    R = T - Q @ (Q.T @ T)
-    return float(np.sum(R * R))
+    step = T.shape[1] if chunk is None else int(chunk)
+    total = 0.0
+    for c0 in range(0, T.shape[1], step):
+        Tc = T[:, c0:c0 + step]
+        R = Tc - Q @ (Q.T @ Tc)
+        total += float(np.sum(R * R))
+    return total
 
 
 def reconstruction_error_normal_eq(A, S, B=None):

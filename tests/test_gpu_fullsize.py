@@ -1,0 +1,136 @@
+"""Parity at the benchmark's full sizes, in the configuration bench.py times
+(default options), against the FP64 oracle on the same values:
+
+* the headline selection, 4096 x 65536 (1/i spectrum of rank 256 + 1e-3
+  noise), k = 256, streamed in BF16 and in FP32: step-by-step index parity
+  with teacher-forced replay where the oracle's top-two gap is below the
+  path's tolerance, the final error of the device's own selection, and
+  Theorem 1's recursive trace against the direct error at sampled steps;
+* the distributed pipeline (Algorithm 4), 2048 x 262144 BF16, 64 log-normal
+  blocks, l_block = 100, k = 100, on the oracle's own target B;
+* the batched form, all 1024 problems of the batched workload in one launch,
+  a seeded sample of 24 of them against the oracle and every one checked for
+  its invariants.
+"""
+import numpy as np
+import pytest
+import torch
+
+import css_inputs as ci
+from oracle import css_oracle as O
+from tests.gpu_helpers import GAP_TOL, dev_matrix, first_mismatch, score_error_bound, teacher_forced_parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def css():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1312_6838_gb300 import build, css as mod
+    build.build()
+    return mod
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float32])
+def test_headline_selection_full_size(css, dtype):
+    c = ci.CONFIGS["decay_4096x65536"]
+    m, n, k = c["m"], c["n"], c["k"]
+    A32 = ci.lowrank_decaying(m, n, c["rank"], c["noise"], c["seed"], dtype=np.float32)
+    A, vals = dev_matrix(A32, dtype)
+    del A32
+    ref = O.greedy_css(vals, k, tau_rel=1e-6, keep_scores=True)
+    assert len(ref.S) == k
+    restarts = teacher_forced_parity(
+        lambda forced: css.select(A, k, forced=forced if forced else None).indices.cpu().tolist(),
+        ref, m=m, dtype=dtype, max_rounds=k)
+    res = css.select(A, k)
+    S = res.indices.cpu().tolist()
+    tr = res.trace.cpu().numpy()
+    # the error trace never increases and starts at ||A||_F^2
+    assert np.all(np.diff(tr) <= 1e-9 * tr[0])
+    assert abs(tr[0] - float(np.sum(vals * vals))) <= 1e-6 * tr[0]
+    # final error of the device's own selection against the oracle's
+    e_gpu = O.reconstruction_error(vals, S, chunk=8192)
+    e_ref = O.reconstruction_error(vals, ref.S, chunk=8192)
+    if restarts == 0:
+        assert abs(e_gpu - e_ref) <= 1e-4 * e_ref
+    else:
+        assert e_gpu <= e_ref * 1.01
+    # Theorem 1's recursion against the direct error of the same prefix
+    for t in (1, 2, 4, 16, 64, 256):
+        direct = O.reconstruction_error(vals, S[:t], chunk=8192)
+        assert abs(tr[t] - direct) <= 1e-4 * direct, (t, tr[t], direct)
+
+
+def test_distributed_pipeline_full_size(css):
+    c = ci.CONFIGS["dist_2048x262144"]
+    m, n, r = c["m"], c["n"], c["r"]
+    A32 = ci.lowrank_decaying(m, n, c["rank"], c["noise"], c["seed"], dtype=np.float32)
+    A, vals = dev_matrix(A32, torch.bfloat16)
+    del A32
+    Om = ci.gaussian_omega(n, r, c["omega_seed"]).astype(np.float64)
+    B64 = O.random_projection(vals, Om)
+    del Om
+    offs = ci.lognormal_blocks(n, c["blocks"], c["block_median"], c["block_sigma"], c["block_seed"])
+    final, per_block, _ = O.distributed_css(vals, B64, offs, c["l_block"], c["k"], tau_rel=1e-6)
+    # the device runs on the same target, rounded once to FP32
+    B = torch.from_numpy(B64.astype(np.float32)).cuda().t().contiguous().t()
+    got = css.distributed(A, B, offs, c["l_block"], c["k"])
+    S = got.indices.cpu().tolist()
+    assert len(S) == c["k"] and len(set(S)) == c["k"]
+    # the final GCSS error (Problem 4) of the device's selection against the
+    # oracle's, both evaluated in FP64 on the same B
+    e_gpu = O.reconstruction_error(vals, S, B64)
+    e_ref = O.reconstruction_error(vals, final, B64)
+    if S == list(final):
+        assert abs(e_gpu - e_ref) <= 1e-4 * e_ref, (e_gpu, e_ref)
+    else:
+        assert e_gpu <= e_ref * 1.01, (e_gpu, e_ref)
+    # every block's selection: where the device's and the oracle's picks part
+    # (near-ties under the mixed path's score error), the block's GCSS error
+    # of the device's picks is as good to 1 percent
+    bsel = got.block_sel.cpu().numpy()
+    for b, ids in enumerate(per_block):
+        dev = [int(v) for v in bsel[b] if v >= 0]
+        assert len(dev) == len(ids), b
+        if dev != ids:
+            lo, hi = offs[b], offs[b + 1]
+            e_d = O.reconstruction_error(vals[:, lo:hi], [j - lo for j in dev], B64)
+            e_o = O.reconstruction_error(vals[:, lo:hi], [j - lo for j in ids], B64)
+            assert e_d <= e_o * 1.01, (b, e_d, e_o)
+
+
+def test_batched_workload_full_size(css):
+    c = ci.CONFIGS["batched_1024"]
+    specs = ci.batched_specs(c["count"], c["seed"])
+    As, ks, insts = [], [], []
+    for i, (m, n, k) in enumerate(specs):
+        A = ci.batched_instance(m, n, k, c["seed"] + i, noise=c["noise"])
+        insts.append(A)
+        As.append(torch.from_numpy(np.ascontiguousarray(A.T)).cuda().t())
+        ks.append(k)
+    res = css.select_batched(As, ks)
+    for (m, n, k), rr in zip(specs, res):
+        tr = rr.trace.cpu().numpy()[: rr.n_sel + 1]
+        assert rr.n_sel == k                      # rank k + noise: never exhausted
+        assert np.all(np.diff(tr) <= 1e-9 * tr[0])
+        assert len(set(rr.indices.cpu().tolist())) == k
+    rng = np.random.default_rng(2024)
+    for i in rng.choice(len(specs), size=24, replace=False):
+        vals = insts[i].astype(np.float64)
+        m = vals.shape[0]
+        ref = O.greedy_css(vals, ks[i], tau_rel=1e-6, keep_scores=True)
+        S = res[i].indices.cpu().tolist()
+        # up to the first step where the two part, the picks are identical;
+        # there the oracle's gap must be within the FP32 path's score error
+        t = first_mismatch(S, list(ref.S))
+        if t is not None:
+            tol = max(GAP_TOL, score_error_bound(ref, t, m, torch.float32))
+            assert ref.gaps[t] <= tol, (i, t, ref.gaps[t], tol)
+        e_gpu = O.reconstruction_error(vals, S)
+        e_ref = O.reconstruction_error(vals, ref.S)
+        if t is None:
+            assert abs(e_gpu - e_ref) <= 1e-4 * e_ref, (i, e_gpu, e_ref)
+        else:
+            assert e_gpu <= e_ref * 1.01, (i, e_gpu, e_ref)

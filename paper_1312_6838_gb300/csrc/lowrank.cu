@@ -11,10 +11,11 @@
 //   2. jacobi_kernel: the eigenvalues of G by two-sided cyclic Jacobi
 //      rotations (Golub and Van Loan, Matrix Computations, Sec. 8.5) in the
 //      parallel round-robin ordering of Brent and Luk (1985): each round
-//      rotates l/2 disjoint index pairs at once.  One cooperative kernel on a
-//      g x g grid of CTAs, one grid barrier per round; CTA (x, y) updates the
-//      2 x 2 blocks whose row pair lies in pair chunk x and column pair in
-//      chunk y, so it needs the rotations of two chunks only.  The rounds'
+//      rotates l/2 disjoint index pairs at once.  One cooperative kernel, one
+//      CTA per chunk pair (x <= y) of a g x g grid, one grid barrier per
+//      round; CTA (x, y) updates the 2 x 2 blocks whose row pair lies in pair
+//      chunk x and column pair in chunk y and writes each to its mirror image
+//      too, so it needs the rotations of two chunks only.  The rounds'
 //      rotations are logged, and replay_rotations_kernel forms the
 //      eigenvectors V = J_1 J_2 ... afterwards, one row of V per block, off
 //      the barrier-bound path.
@@ -41,7 +42,7 @@ constexpr int kGK = 32;          // columns per staged chunk
 constexpr int kMaxL = 1024;
 constexpr int kMaxSweeps = 40;
 constexpr int kJacobiThreads = 256;
-constexpr int kMaxGridDim = 12;  // at most 12 x 12 = 144 CTAs (<= one per SM)
+constexpr int kMaxGridDim = 16;  // at most 16 * 17 / 2 = 136 CTAs (<= one per SM)
 
 // ----------------------------------------------------------- 1. G = W W^T --
 // Block (pair, slice): output tile (ti, tj), ti >= tj, over the columns of one
@@ -158,8 +159,7 @@ __device__ __forceinline__ bool needs_rot(double gpp, double gqq, double gpq, do
 // precision (t itself only has to be close).
 __device__ __forceinline__ void rot_angle(double gpp, double gqq, double gpq, double& c, double& sn) {
   const double d = gqq - gpp, g2 = 2.0 * gpq;
-  int ex;
-  frexp(fmax(fabs(d), fabs(g2)), &ex);
+  const int ex = ilogb(fmax(fabs(d), fabs(g2))) + 1;   // 2^-ex scales both into [1/2, 1)
   const float df = (float)ldexp(d, -ex), gf = (float)ldexp(g2, -ex);
   const float tf = copysignf(1.f, df) * gf / (fabsf(df) + sqrtf(df * df + gf * gf));
   const double t = (double)tf;
@@ -173,7 +173,10 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(JacobiArgs A) {
   __shared__ uint32_t s_epoch;
   __shared__ int s_any;
   const int lp = A.lp, h = lp / 2, NT = kJacobiThreads, tid = threadIdx.x;
-  const int cx = blockIdx.x % A.gdim, cy = blockIdx.x / A.gdim;
+  // CTA -> chunk pair (cx <= cy) of the upper triangle of a gdim x gdim grid
+  int cx = 0, cb = blockIdx.x;
+  while (cb >= A.gdim - cx) { cb -= A.gdim - cx; ++cx; }
+  const int cy = cx + cb;
   const int xb = cx * A.chunk, xe = min(h, xb + A.chunk);
   const int yb = cy * A.chunk, ye = min(h, yb + A.chunk);
   const int ncta = gridDim.x;
@@ -189,6 +192,19 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(JacobiArgs A) {
   const double tiny = 1e-17 * tr;
   const int nx = xe - xb, ny = ye - yb;
   const int nang = nx + (cx == cy ? 0 : ny);
+  // blocks (jr, jc), jr in chunk x, jc in chunk y; on a diagonal chunk pair
+  // only jr <= jc (the other half is the mirror image)
+  const bool diag = cx == cy;
+  const int nblk = diag ? nx * (nx + 1) / 2 : nx * ny;
+  auto block_of = [diag, xb, yb, nx](int e) -> int2 {
+    if (diag) {
+      int b = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
+      while (b * (b + 1) / 2 > e) --b;
+      while ((b + 1) * (b + 2) / 2 <= e) ++b;
+      return make_int2(xb + (e - b * (b + 1) / 2), xb + b);
+    }
+    return make_int2(xb + e % nx, yb + e / nx);
+  };
   const long long tot = (long long)lp * lp;
   const long long per = (tot + ncta - 1) / ncta;
   const long long cbeg = (long long)blockIdx.x * per, cend = min(tot, cbeg + per);
@@ -225,9 +241,10 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(JacobiArgs A) {
       // rotations' inputs (both only need the round's pairs)
       int f_r0 = 0, f_r1 = 0, f_c0 = 0, f_c1 = 0;
       double f00 = 0.0, f10 = 0.0, f01 = 0.0, f11 = 0.0;
-      if (tid < nx * ny) {
-        rr_pair(r, xb + tid % nx, lp, f_r0, f_r1);
-        rr_pair(r, yb + tid / nx, lp, f_c0, f_c1);
+      if (tid < nblk) {
+        const int2 fj = block_of(tid);
+        rr_pair(r, fj.x, lp, f_r0, f_r1);
+        rr_pair(r, fj.y, lp, f_c0, f_c1);
         f00 = __ldcg(Gc + (long long)f_c0 * lp + f_r0);
         f10 = __ldcg(Gc + (long long)f_c0 * lp + f_r1);
         f01 = __ldcg(Gc + (long long)f_c1 * lp + f_r0);
@@ -248,11 +265,12 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(JacobiArgs A) {
         if (cx == cy) A.rotlog[rg * h + j] = make_double2(c, sn);
       }
       __syncthreads();
-      // 2 x 2 blocks: rows of pair jr (chunk x), columns of pair jc (chunk y).
-      // The rotation of the lower-numbered pair is applied first, so the
-      // blocks (jr, jc) and (jc, jr) give mirror-equal values.
-      for (int e = tid; e < nx * ny; e += NT) {
-        const int jr = xb + e % nx, jc = yb + e / nx;
+      // 2 x 2 blocks: rows of pair jr, columns of pair jc, jr <= jc; each is
+      // written to both its own place and its mirror image, so G stays
+      // exactly symmetric and half the rotations' FP64 work is saved.
+      for (int e = tid; e < nblk; e += NT) {
+        const int2 jj = block_of(e);
+        const int jr = jj.x, jc = jj.y;
         int r0, r1, c0, c1;
         double b00, b10, b01, b11;
         if (e == tid) {
@@ -267,25 +285,27 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(JacobiArgs A) {
           b11 = __ldcg(Gc + (long long)c1 * lp + r1);
         }
         const double cr = s_c[jr], sr = s_s[jr], cc = s_c[jc], sc = s_s[jc];
-        double o00, o01, o10, o11;
-        if (jr <= jc) {
-          double x00, x10, x01, x11;
-          rot(cr, sr, b00, b10, x00, x10);   // rows first
-          rot(cr, sr, b01, b11, x01, x11);
-          rot(cc, sc, x00, x01, o00, o01);
-          rot(cc, sc, x10, x11, o10, o11);
-          if (jr == jc) o10 = o01;           // the block's own g_pq = g_qp
+        double x00, x10, x01, x11, o00, o01, o10, o11;
+        rot(cr, sr, b00, b10, x00, x10);     // rows
+        rot(cr, sr, b01, b11, x01, x11);
+        rot(cc, sc, x00, x01, o00, o01);     // columns
+        rot(cc, sc, x10, x11, o10, o11);
+        if (jr == jc) {
+          // the pair's own 2 x 2 block: g_pq = g_qp
+          Gn[(long long)r0 * lp + r0] = o00;
+          Gn[(long long)r1 * lp + r0] = o01;
+          Gn[(long long)r0 * lp + r1] = o01;
+          Gn[(long long)r1 * lp + r1] = o11;
         } else {
-          double y00, y01, y10, y11;
-          rot(cc, sc, b00, b01, y00, y01);   // columns first
-          rot(cc, sc, b10, b11, y10, y11);
-          rot(cr, sr, y00, y10, o00, o10);
-          rot(cr, sr, y01, y11, o01, o11);
+          Gn[(long long)c0 * lp + r0] = o00;
+          Gn[(long long)c1 * lp + r0] = o01;
+          Gn[(long long)c0 * lp + r1] = o10;
+          Gn[(long long)c1 * lp + r1] = o11;
+          Gn[(long long)r0 * lp + c0] = o00;
+          Gn[(long long)r0 * lp + c1] = o01;
+          Gn[(long long)r1 * lp + c0] = o10;
+          Gn[(long long)r1 * lp + c1] = o11;
         }
-        Gn[(long long)c0 * lp + r0] = o00;
-        Gn[(long long)c1 * lp + r0] = o01;
-        Gn[(long long)c0 * lp + r1] = o10;
-        Gn[(long long)c1 * lp + r1] = o11;
       }
       if (!team_barrier(A.bar, ncta, A.st, 41, &s_epoch)) return;
       cur ^= 1;
@@ -519,10 +539,11 @@ extern "C" css_status css_lowrank(const double* W, int64_t ldw, const double* Q,
   if (major != 10 || minor != 3 || !coop) return CSS_ERR_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
   const int lp = l + (l & 1), h = lp / 2;
-  // Jacobi grid: g x g CTAs, chunks of about 8+ pairs, g <= 12, g^2 <= SMs
+  // Jacobi grid: the g (g + 1) / 2 chunk pairs of the upper triangle,
+  // chunks of about 8 pairs, g <= 16, no more CTAs than SMs
   int gdim = std::max(1, std::min(kMaxGridDim, h / 8));
   const int sms = device_sms();
-  while (gdim > 1 && gdim * gdim > sms) --gdim;
+  while (gdim > 1 && gdim * (gdim + 1) / 2 > sms) --gdim;
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobi_kernel, kJacobiThreads, 0) != cudaSuccess ||
       occ < 1)
@@ -557,8 +578,8 @@ extern "C" css_status css_lowrank(const double* W, int64_t ldw, const double* Q,
   if (timed) cudaEventRecord(ev[1], s);
   JacobiArgs ja{L.G0, L.G1, L.rotlog, L.max_rounds, lp, gdim, chunk, L.bar, L.flags, L.info, L.st};
   void* args[] = {&ja};
-  e = cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(gdim * gdim), dim3(kJacobiThreads), args, 0,
-                                  s);
+  e = cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(gdim * (gdim + 1) / 2), dim3(kJacobiThreads),
+                                  args, 0, s);
   if (e != cudaSuccess) return CSS_ERR_CUDA;
   replay_rotations_kernel<<<l, h, lp * sizeof(double), s>>>(L.rotlog, L.info, lp, L.V);
   double* uw = Uw ? Uw : L.Uw;

@@ -199,11 +199,15 @@ __device__ __forceinline__ void colreduce_tile_f32(const TX* __restrict__ X, lon
   F32Acc acc;
   f32_zero(acc);
   float rx[kFV], ry[kFV];
-  // thread tid stages K entry kk of rows rr0 + 16 v: in a warp, 8 lanes read 8
-  // consecutive K entries of one of 4 rows, and the transposed writes
-  // (bank 4 kk + rr mod 32 with the kFP stride) fall in 32 distinct banks
+  // thread tid stages K entry kk of rows rr0 + 16 v.  FP32 Y: in a warp, 8
+  // lanes read 8 consecutive K entries (32 bytes) of one of 4 rows, and the
+  // transposed writes (bank 4 kk + rr mod 32 with the kFP stride) fall in 32
+  // distinct banks.  BF16 Y: 16 lanes per row, so that each row's read is
+  // still a whole 32-byte sector (the writes then pair up on banks).
   const int lane = tid & 31, wrp = tid >> 5;
-  const int kk = (lane & 7) + 8 * (wrp & 1), rr0 = (lane >> 3) + 4 * (wrp >> 1);
+  constexpr bool k16 = sizeof(TA) == 2;
+  const int kk = k16 ? tid % kFK : (lane & 7) + 8 * (wrp & 1);
+  const int rr0 = k16 ? tid / kFK : (lane >> 3) + 4 * (wrp >> 1);
   const int vx = (M - r0 - rr0 + kFK - 1) / kFK, vy = (N - c0 - rr0 + kFK - 1) / kFK;   // valid rows
   const TX* px = X + (long long)(r0 + rr0) * ldx + kk;
   const TA* py = Y + (long long)(c0 + rr0) * ldy + kk;

@@ -146,25 +146,32 @@ __device__ __forceinline__ void rot(double c, double s, double a, double b, doub
 
 // A pair is rotated unless |g_pq| <= 1e-15 sqrt(g_pp g_qq) (the relative test
 // of Demmel and Veselic) or |g_pq| <= 1e-17 trace(G), far below the Gram
-// matrix's own rounding.
-__device__ __forceinline__ bool needs_rot(double gpp, double gqq, double gpq, double tiny) {
-  return fabs(gpq) > tiny && gpq * gpq > 1e-30 * fabs(gpp * gqq);
+// matrix's own rounding.  Evaluated in FP32 on the entries scaled by
+// 1 / trace(G) (all of magnitude <= 1 for a PSD G).
+__device__ __forceinline__ bool needs_rot(double gpp, double gqq, double gpq, double inv_tr) {
+  const float ps = (float)(gpp * inv_tr), qs = (float)(gqq * inv_tr), xs = fabsf((float)(gpq * inv_tr));
+  return xs > 1e-17f && xs * xs > 1e-30f * fabsf(ps * qs);
 }
 
 // The rotation that annihilates g_pq: t = tan(theta), the smaller root of
 // t^2 + 2 tau t - 1 = 0 with tau = (g_qq - g_pp) / (2 g_pq), i.e.
-// t = sgn(d) 2 g_pq / (|d| + sqrt(d^2 + 4 g_pq^2)), d = g_qq - g_pp, formed in
-// FP32 after a common power-of-two scaling; c = 1 / sqrt(1 + t^2) and s = t c
-// then come from that t in FP64, so the rotation is orthogonal to FP64
-// precision (t itself only has to be close).
-__device__ __forceinline__ void rot_angle(double gpp, double gqq, double gpq, double& c, double& sn) {
-  const double d = gqq - gpp, g2 = 2.0 * gpq;
-  const int ex = ilogb(fmax(fabs(d), fabs(g2))) + 1;   // 2^-ex scales both into [1/2, 1)
-  const float df = (float)ldexp(d, -ex), gf = (float)ldexp(g2, -ex);
-  const float tf = copysignf(1.f, df) * gf / (fabsf(df) + sqrtf(df * df + gf * gf));
+// t = sgn(d) 2 g_pq / (|d| + sqrt(d^2 + 4 g_pq^2)), d = g_qq - g_pp (taken in
+// FP64, then scaled by 1 / trace(G)), formed in FP32: t only has to be close.
+// c = 1 / sqrt(1 + t^2) then comes from that t to FP64 precision (the FP32
+// reciprocal square root refined by two Newton-Raphson steps
+// y <- y (3/2 - x y^2 / 2)), and s = t c, so the rotation is orthogonal to
+// FP64 precision.
+__device__ __forceinline__ void rot_angle(double gpp, double gqq, double gpq, double inv_tr, double& c,
+                                          double& sn) {
+  const float df = (float)((gqq - gpp) * inv_tr), gf = 2.f * (float)(gpq * inv_tr);
+  const float tf = copysignf(1.f, df) * gf / (fabsf(df) + sqrtf(fmaf(df, df, gf * gf)));
   const double t = (double)tf;
-  c = rsqrt(fma(t, t, 1.0));
-  sn = t * c;
+  const double x = fma(t, t, 1.0), hx = -0.5 * x;
+  double y = (double)rsqrtf((float)x);
+  y = y * fma(hx, y * y, 1.5);
+  y = y * fma(hx, y * y, 1.5);
+  c = y;
+  sn = t * y;
 }
 
 __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(JacobiArgs A) {
@@ -189,7 +196,7 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(JacobiArgs A) {
     if (blockIdx.x == 0 && tid == 0) set_error(A.st, (int32_t)CSS_ERR_NONFINITE, 0);
     return;
   }
-  const double tiny = 1e-17 * tr;
+  const double inv_tr = tr > 0.0 ? 1.0 / tr : 0.0;
   const int nx = xe - xb, ny = ye - yb;
   const int nang = nx + (cx == cy ? 0 : ny);
   // blocks (jr, jc), jr in chunk x, jc in chunk y; on a diagonal chunk pair
@@ -222,7 +229,7 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(JacobiArgs A) {
         if (p >= q) continue;
         const double gpq = __ldcg(Gc + idx);
         const double gpp = __ldcg(Gc + (long long)p * lp + p), gqq = __ldcg(Gc + (long long)q * lp + q);
-        bad |= needs_rot(gpp, gqq, gpq, tiny) ? 1 : 0;
+        bad |= needs_rot(gpp, gqq, gpq, inv_tr) ? 1 : 0;
       }
       if (__syncthreads_or(bad) && tid == 0) atomicOr(A.flags + sweep, 1);
       if (!team_barrier(A.bar, ncta, A.st, 40, &s_epoch)) return;
@@ -258,7 +265,7 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(JacobiArgs A) {
         const double gqq = __ldcg(Gc + (long long)q * lp + q);
         const double gpq = __ldcg(Gc + (long long)q * lp + p);
         double c = 1.0, sn = 0.0;
-        if (needs_rot(gpp, gqq, gpq, tiny)) rot_angle(gpp, gqq, gpq, c, sn);
+        if (needs_rot(gpp, gqq, gpq, inv_tr)) rot_angle(gpp, gqq, gpq, inv_tr, c, sn);
         s_c[j] = c;
         s_s[j] = sn;
         // the CTA on the diagonal of chunk x logs the chunk's rotations

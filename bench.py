@@ -560,10 +560,11 @@ def main():
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "greedy_kernel (persistent: pivot phases + fused step)",
                      "bytes_per_iteration": per_iter, "peak_kind": peak_kind},
-        # per css_select: BF16 -> C = A A^T, split of C, column dots, partial
-        # sums (tensor cores) + the persistent greedy kernel; FP32 -> SYRK,
-        # column-reduction GEMM, partial sums + the greedy kernel
-        "gpu_launches": (5 if args.dtype == "bf16" else 4) * args.steps,
+        # per css_select: BF16 -> C = A A^T (lower tiles), its mirror, the
+        # split of C, column dots, row sums (tensor cores) + the persistent
+        # greedy kernel; FP32 -> SYRK, column-reduction GEMM, partial sums +
+        # the greedy kernel
+        "gpu_launches": (6 if args.dtype == "bf16" else 4) * args.steps,
         "clocks": clk,
     }
     if not args.no_e2e:

@@ -24,8 +24,9 @@
 //   4. gemm_nn_kernel: U~ = Q U^(W)_k and V~ = W^T U^(W)_k Sigma_k^-1 in FP64.
 //
 // Everything is FP64: on this part FP64 runs at 1/64 of the FP32 rate, so
-// the Gram matrix and V~ (2 l^2 n / 2 and l k n multiply-adds) are bound by
-// the FP64 pipe, and the Jacobi rounds by their grid barrier.
+// the Gram matrix and V~ (l^2 n / 2 and l k n multiply-adds) are bound by
+// the FP64 pipe, and each Jacobi round by latency: one dependent L2 trip,
+// a short chain of FP64 arithmetic and a grid barrier.
 #include <algorithm>
 #include <cmath>
 #include <vector>

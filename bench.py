@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "decay_4096x32768", "dist_2048x262144", "dist_2048x65536",
-                             "batched_1024", "relative_accuracy", "lowrank"],
+                             "batched_1024", "relative_accuracy", "lowrank", "adjoint_4096x16384"],
                     help="decay_4096x32768 is the small profiling case of the headline model; "
                          "dist_* run the distributed pipeline (Algorithms 2 and 4), batched_1024 "
                          "the batched independent problems")
@@ -397,6 +397,81 @@ def run_relative_accuracy(args):
 
 
 FP64_TFLOPS = 1.20   # FP64 FMA throughput of this part, measured with a dependent-free FMA loop
+FP32_TFLOPS = 67.9   # FP32 FMA throughput of this part, measured the same way
+
+
+def run_adjoint(args):
+    """The adjoint of the reconstruction error at a fixed selected set: A
+    4096 x 16384 FP32 (rank 128 + 1e-3 noise), S = the device's greedy
+    selection of 128 columns; each timed step is one css_residual_backward
+    call forming the loss and dA (the backward of css.residual).  A (268 MB)
+    and dA are larger than L2."""
+    import torch
+    import ctypes as C
+    from paper_1312_6838_gb300 import css, _lib as L
+    c = ci.CONFIGS["adjoint_4096x16384"]
+    m, n, k = c["m"], c["n"], c["k"]
+    A32 = ci.lowrank_uv(m, n, c["rank"], c["noise"], c["seed"], dtype=np.float32)
+    A = css.to_colmajor(torch.from_numpy(A32).cuda())
+    S = css.select(A, k).indices
+    lib = L.load()
+    dA = css.empty_colmajor(m, n, torch.float32, "cuda")
+    loss = torch.empty(1, dtype=torch.float64, device="cuda")
+    o = L.default_opts()
+    nbytes = lib.css_workspace_size(L.CSS_OP_BACKWARD, L.CSS_F32, m, n, 0, k, 0, C.byref(o))
+    buf = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+    off = (-buf.data_ptr()) % 256
+    ws = buf[off:off + nbytes]
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def step():
+        code = lib.css_residual_backward(C.c_void_p(A.data_ptr()), L.CSS_F32, m, n, m, C.c_void_p(S.data_ptr()), k,
+                                         1.0, C.c_void_p(dA.data_ptr()), m, C.c_void_p(loss.data_ptr()),
+                                         C.c_void_p(ws.data_ptr()), nbytes, C.byref(o), stream)
+        assert code == 0, code
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    clk = ClockSampler(0)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    flop = 6.0 * k * m * n          # Q^T A, A - Q W, R W^T: 2 k m n each
+    tf = flop / (ms * 1e-3) / 1e12
+    line = {
+        "metric": "adjoint of ||A - P_S A||_F^2 at fixed S: loss and dA per call",
+        "value": ms, "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3),
+        "ms_per_step": ms, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "adjoint_4096x16384", "m": m, "n": n, "k": k, "rank": c["rank"],
+                   "noise": c["noise"], "l2": "A and dA (268 MB each) larger than L2"},
+        "roofline": {"bound": "alu", "achieved": tf, "peak": FP32_TFLOPS, "unit": "TFLOP/s",
+                     "frac": tf / FP32_TFLOPS, "traffic": None,
+                     "kernel": "the adjoint's three GEMM-shaped kernels (double-float W and R, FP32 R W^T)",
+                     "note": "algorithmic 6 k m n FLOPs; W and R run in double-float (about 12 FP32 operations "
+                             "per multiply-add), so the FP32 pipe does several times the algorithmic count"},
+        "hbm_bytes_per_call": 3 * m * n * 4, "loss": float(loss.item()), "clocks": clocks,
+        # per call: gather A_S, Gram, Cholesky and inverse, Q, W, R with the
+        # loss partials, loss sum, R W^T slices, dA_S
+        "gpu_launches": 9 * args.steps,
+    }
+    if not args.no_cpu_baseline:
+        from oracle import css_oracle as O
+        vals = A32.astype(np.float64)
+        Sl = S.cpu().tolist()
+        t0 = time.perf_counter()
+        L_ref, _ = O.residual_gradient(vals, Sl)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": dt * 1e3, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": "one full call (closed-form FP64 gradient, numpy on the host)"}
+        line["loss_rel_diff_vs_oracle"] = abs(line["loss"] - L_ref) / L_ref
+    print(json.dumps(line), flush=True)
 
 
 def run_lowrank(args):
@@ -489,6 +564,9 @@ def main():
         return
     if args.workload == "lowrank":
         run_lowrank(args)
+        return
+    if args.workload == "adjoint_4096x16384":
+        run_adjoint(args)
         return
     import torch
     ws, rank, local = dist_env()

@@ -458,8 +458,8 @@ def run_adjoint(args):
                              "per multiply-add), so the FP32 pipe does several times the algorithmic count"},
         "hbm_bytes_per_call": 3 * m * n * 4, "loss": float(loss.item()), "clocks": clocks,
         # per call: gather A_S, Gram, Cholesky and inverse, Q, W, R with the
-        # loss partials, loss sum, R W^T slices, dA_S
-        "gpu_launches": 9 * args.steps,
+        # loss partials, loss sum, R W^T slices, their sum, dA_S
+        "gpu_launches": 10 * args.steps,
     }
     if not args.no_cpu_baseline:
         from oracle import css_oracle as O

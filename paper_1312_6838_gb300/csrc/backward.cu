@@ -367,20 +367,25 @@ __global__ void __launch_bounds__(256) rwt_kernel(const TR* __restrict__ R, cons
     }
 }
 
-// dA[:, S[j]] = -2 g sum_{l >= j} P[i, l] Linv[l, j], P = sum of the slices.
-template <typename TA, typename TR>
-__global__ void das_kernel(const TR* __restrict__ partial, int S, const double* __restrict__ Linv,
-                           int m, int k, const int* __restrict__ sel, double g2, TA* __restrict__ dA,
-                           long long ldda) {
+// P = R W^T (m x k) from the slices, added in slice order, in FP64.
+template <typename TR>
+__global__ void sum_slices_kernel(const TR* __restrict__ partial, int S, long long mk, double* __restrict__ P) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= mk) return;
+  double p = 0.0;
+  for (int s = 0; s < S; ++s) p += (double)partial[(long long)s * mk + idx];
+  P[idx] = p;
+}
+
+// dA[:, S[j]] = -2 g sum_{l >= j} P[i, l] Linv[l, j].
+template <typename TA>
+__global__ void das_kernel(const double* __restrict__ P, const double* __restrict__ Linv, int m, int k,
+                           const int* __restrict__ sel, double g2, TA* __restrict__ dA, long long ldda) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)m * k) return;
   const int i = (int)(idx % m), j = (int)(idx / m);
   double acc = 0.0;
-  for (int l = j; l < k; ++l) {
-    double p = 0.0;
-    for (int s = 0; s < S; ++s) p += (double)partial[(long long)s * m * k + (long long)l * m + i];
-    acc += p * Linv[(long long)j * k + l];
-  }
+  for (int l = j; l < k; ++l) acc += P[(long long)l * m + i] * Linv[(long long)j * k + l];
   dA[(long long)sel[j] * ldda + i] = from_d<TA>(-g2 * acc);
 }
 
@@ -392,6 +397,7 @@ struct BwLayout {
   float *Qh, *Ql, *Wh, *Wl;
   void* R;
   void* P;
+  double* Psum;
   double* loss_part;
   double* loss_tmp;
   size_t bytes;
@@ -413,6 +419,7 @@ BwLayout bw_layout(void* ws, size_t cap, int dt, int64_t m, int64_t n, int32_t k
   const size_t rs = dt == CSS_F64 ? 8 : 4;
   L.R = grad ? (void*)c.take<char>((size_t)m * n * rs) : nullptr;
   L.P = grad ? (void*)c.take<char>((size_t)kSlices * m * k * rs) : nullptr;
+  L.Psum = grad ? c.take<double>((size_t)m * k) : nullptr;
   L.loss_part = c.take<double>((size_t)((m + 63) / 64) * ((n + 63) / 64));
   L.loss_tmp = c.take<double>(1);
   L.bytes = c.off;
@@ -440,8 +447,9 @@ css_status run_backward(const TA* A, int dt, int m, int n, long long lda, const 
     const int slice = (n + kSlices - 1) / kSlices;
     rwt_kernel<TR><<<dim3((m + 63) / 64, (k + 31) / 32, kSlices), 256, 0, s>>>((const TR*)L.R, L.W, m, n,
                                                                               k, slice, (TR*)L.P);
-    das_kernel<TA, TR><<<(unsigned)((mk + 255) / 256), 256, 0, s>>>((const TR*)L.P, kSlices, L.Linv, m,
-                                                                   k, sel, 2.0 * grad_out, dA, ldda);
+    sum_slices_kernel<TR><<<(unsigned)((mk + 255) / 256), 256, 0, s>>>((const TR*)L.P, kSlices, mk, L.Psum);
+    das_kernel<TA><<<(unsigned)((mk + 255) / 256), 256, 0, s>>>(L.Psum, L.Linv, m, k, sel, 2.0 * grad_out, dA,
+                                                               ldda);
   }
   if (cudaGetLastError() != cudaSuccess) return CSS_ERR_CUDA;
   if (o.sync) {

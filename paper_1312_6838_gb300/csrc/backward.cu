@@ -143,6 +143,65 @@ __global__ void chol_inv_kernel(double* __restrict__ G, int k, double* __restric
   if (threadIdx.x == 0 && bad) status[0] = 1;
 }
 
+// The same factorisation with G held in shared memory (k <= kCholSmemK):
+// the k steps of the right-looking update and the substitutions for L^-1
+// then read shared memory instead of L2.
+constexpr int kCholSmemK = 128;
+__global__ void __launch_bounds__(1024) chol_inv_smem_kernel(const double* __restrict__ Gg, int k,
+                                                             double* __restrict__ Linv, int* __restrict__ status) {
+  extern __shared__ double G[];   // k x k, column-major
+  __shared__ int bad;
+  __shared__ double diag0[kCholSmemK];
+  if (threadIdx.x == 0) bad = 0;
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) G[e] = Gg[e];
+  __syncthreads();
+  for (int j = threadIdx.x; j < k; j += blockDim.x) diag0[j] = G[j * k + j];
+  __syncthreads();
+  for (int j = 0; j < k; ++j) {
+    if (threadIdx.x == 0) {
+      // a pivot at or below 1e-12 of its column's squared norm: the selected
+      // columns are linearly dependent to working precision
+      const double d = G[j * k + j];
+      const bool ok = d > 1e-12 * diag0[j];
+      if (!ok) bad = 1;
+      G[j * k + j] = ok ? sqrt(d) : 1.0;
+    }
+    __syncthreads();
+    const double d = G[j * k + j];
+    for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) G[j * k + i] /= d;
+    __syncthreads();
+    const int rem = k - j - 1;
+    for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
+      const int i = j + 1 + e % rem, l = j + 1 + e / rem;
+      if (l <= i) G[l * k + i] -= G[j * k + i] * G[j * k + l];
+    }
+    __syncthreads();
+  }
+  // Linv: forward substitution L x = e_j, one column per thread
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    for (int i = 0; i < j; ++i) Linv[(long long)j * k + i] = 0.0;
+    for (int i = j; i < k; ++i) {
+      double v = (i == j) ? 1.0 : 0.0;
+      for (int l = j; l < i; ++l) v -= G[l * k + i] * Linv[(long long)j * k + l];
+      Linv[(long long)j * k + i] = v / G[i * k + i];
+    }
+  }
+  if (threadIdx.x == 0 && bad) status[0] = 1;
+}
+
+// Cholesky of the k x k matrix in G and L^-1 into Linv (status[0] = 1 for a
+// rank-deficient G); G is overwritten when it does not fit shared memory.
+void chol_inv(double* G, int k, double* Linv, int* status, cudaStream_t s) {
+  if (k <= kCholSmemK) {
+    const size_t smem = (size_t)k * k * sizeof(double);
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(chol_inv_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    chol_inv_smem_kernel<<<1, 1024, smem, s>>>(G, k, Linv, status);
+  } else {
+    chol_inv_kernel<<<1, 1024, 0, s>>>(G, k, Linv, status);
+  }
+}
+
 // Q = A_S L^-T (m x k): Q[i, j] = sum_{l <= j} A_S[i, l] Linv[j, l]; the
 // double-float split of Q is stored alongside.
 __global__ void q_kernel(const double* __restrict__ AS, const double* __restrict__ Linv, int m, int k,
@@ -435,7 +494,7 @@ css_status run_backward(const TA* A, int dt, int m, int n, long long lda, const 
   const long long mk = (long long)m * k;
   gather_cols_kernel<TA><<<(unsigned)((mk + 255) / 256), 256, 0, s>>>(A, lda, m, sel, k, L.AS);
   gram_kernel<<<dim3((k + 15) / 16, (k + 15) / 16), 256, 0, s>>>(L.AS, m, k, L.G);
-  chol_inv_kernel<<<1, 1024, 0, s>>>(L.G, k, L.Linv, L.status);
+  chol_inv(L.G, k, L.Linv, L.status, s);
   q_kernel<<<(unsigned)((mk + 255) / 256), 256, 0, s>>>(L.AS, L.Linv, m, k, L.Q, L.Qh, L.Ql);
   w_kernel<TA><<<dim3((n + 63) / 64, (k + 31) / 32), 256, 0, s>>>(L.Qh, L.Ql, L.Q, A, lda, m, n, k, L.W,
                                                                 1, k, L.Wh, L.Wl);
@@ -506,10 +565,10 @@ css_status run_embed(const TA* A, int m, int n, long long lda, const int* sel, i
   const dim3 gg((l + 15) / 16, (l + 15) / 16);
   gather_cols_kernel<TA><<<gb, 256, 0, s>>>(A, lda, m, sel, l, L.AS);
   gram_kernel<<<gg, 256, 0, s>>>(L.AS, m, l, L.G);
-  chol_inv_kernel<<<1, 1024, 0, s>>>(L.G, l, L.Linv, L.status);
+  chol_inv(L.G, l, L.Linv, L.status, s);
   q_kernel<<<gb, 256, 0, s>>>(L.AS, L.Linv, m, l, L.Q1, L.Qh, L.Ql);
   gram_kernel<<<gg, 256, 0, s>>>(L.Q1, m, l, L.G);
-  chol_inv_kernel<<<1, 1024, 0, s>>>(L.G, l, L.Linv, L.status);
+  chol_inv(L.G, l, L.Linv, L.status, s);
   q_kernel<<<gb, 256, 0, s>>>(L.Q1, L.Linv, m, l, L.Q, L.Qh, L.Ql);
   if (W)
     w_kernel<TA><<<dim3((n + 63) / 64, (l + 31) / 32), 256, 0, s>>>(L.Qh, L.Ql, L.Q, A, lda, m, n, l, W, ldw,

@@ -16,11 +16,11 @@
 //      round; CTA (x, y) updates the 2 x 2 blocks whose row pair lies in pair
 //      chunk x and column pair in chunk y and writes each to its mirror image
 //      too, so it needs the rotations of two chunks only.  The rounds'
-//      rotations are logged, and replay_rotations_kernel forms the
-//      eigenvectors V = J_1 J_2 ... afterwards, one row of V per block, off
-//      the barrier-bound path.
-//   3. order_kernel: eigenvalues sorted descending, U^(W)_k with a sign rule,
-//      sigma, the tail sum and the 1 / sigma scaling of V~.
+//      rotations are logged for the eigenvectors.
+//   3. order_kernel: eigenvalues sorted descending, sigma, the tail sum and
+//      the 1 / sigma scaling of V~; replay_columns_kernel forms only the k
+//      wanted eigenvectors from the rotation log, off the barrier-bound path,
+//      and signs them (U^(W)_k).
 //   4. gemm_nn_kernel: U~ = Q U^(W)_k and V~ = W^T U^(W)_k Sigma_k^-1 in FP64.
 //
 // Everything is FP64: on this part FP64 runs at 1/64 of the FP32 rate, so
@@ -327,44 +327,73 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(JacobiArgs A) {
   }
 }
 
-// V = J_1 J_2 ... J_R, the product of every round's rotations, replayed from
-// the log: row i of V evolves on its own (V <- V J only mixes its entries p
-// and q), so one block per row keeps it in shared memory and applies the
-// rounds in order, the next round's (c, s) loaded ahead of the current one.
-__global__ void __launch_bounds__(512) replay_rotations_kernel(const double2* __restrict__ rotlog,
-                                                               const int* __restrict__ info, int lp,
-                                                               double* __restrict__ V) {
-  extern __shared__ double row[];
-  const int i = blockIdx.x, h = lp / 2;
-  for (int c = threadIdx.x; c < lp; c += blockDim.x) row[c] = (c == i) ? 1.0 : 0.0;
+// Eigenvector ord[r] of G is column ord[r] of V = J_1 J_2 ... J_R, the product
+// of every round's rotations: V e = J_1 (J_2 (... (J_R e))).  Block r replays
+// the logged rounds backwards on that one column, kept in shared memory (the
+// round's pairs are disjoint, so one thread a pair), then signs it so that
+// its entry of largest magnitude (lowest index on ties) is positive and
+// writes it as column r of U^(W)_k.  Only the k wanted columns are formed.
+__global__ void __launch_bounds__(512) replay_columns_kernel(const double2* __restrict__ rotlog,
+                                                             const int* __restrict__ info,
+                                                             const int* __restrict__ ord, int l, int lp,
+                                                             double* __restrict__ Uw) {
+  extern __shared__ double col[];
+  __shared__ double s_best[16];
+  __shared__ int s_bi[16];
+  const int h = lp / 2, j = threadIdx.x;   // blockDim.x: h rounded up to whole warps
+  const int c0 = ord[blockIdx.x];
+  for (int i = threadIdx.x; i < lp; i += blockDim.x) col[i] = (i == c0) ? 1.0 : 0.0;
   __syncthreads();
   const long long R = info[2];
-  const int j = threadIdx.x;   // blockDim.x == h
-  int r = 0;
-  double2 cs = R > 0 ? __ldcg(rotlog + j) : make_double2(1.0, 0.0);
-  for (long long g = 0; g < R; ++g) {
-    const double2 nxt = (g + 1 < R) ? __ldcg(rotlog + (g + 1) * h + j) : make_double2(1.0, 0.0);
-    int p, q;
-    rr_pair(r, j, lp, p, q);
-    const double x = row[p], y = row[q];
-    double u, v;
-    rot(cs.x, cs.y, x, y, u, v);
-    row[p] = u;
-    row[q] = v;
+  const bool act = j < h;
+  int r = R > 0 ? (int)((R - 1) % (lp - 1)) : 0;
+  double2 cs = (act && R > 0) ? __ldcg(rotlog + (R - 1) * h + j) : make_double2(1.0, 0.0);
+  for (long long g = R - 1; g >= 0; --g) {
+    const double2 nxt = (act && g > 0) ? __ldcg(rotlog + (g - 1) * h + j) : make_double2(1.0, 0.0);
+    if (act) {
+      int p, q;
+      rr_pair(r, j, lp, p, q);
+      const double vp = col[p], vq = col[q];
+      // (J v)_p = c v_p + s v_q,  (J v)_q = -s v_p + c v_q
+      col[p] = fma(cs.x, vp, cs.y * vq);
+      col[q] = fma(cs.x, vq, -(cs.y * vp));
+    }
     __syncthreads();
     cs = nxt;
-    if (++r == lp - 1) r = 0;
+    if (--r < 0) r = lp - 2;
   }
-  for (int c = threadIdx.x; c < lp; c += blockDim.x) V[(long long)c * lp + i] = row[c];
+  // sign rule: block-wide argmax of |v_i| (lowest index on ties)
+  double best = -1.0;
+  int bi = l;
+  for (int i = threadIdx.x; i < l; i += blockDim.x) {
+    const double a = fabs(col[i]);
+    if (a > best) { best = a; bi = i; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (lane == 0) { s_best[wid] = best; s_bi[wid] = bi; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < nw; ++w)
+      if (s_best[w] > best || (s_best[w] == best && s_bi[w] < bi)) { best = s_best[w]; bi = s_bi[w]; }
+    s_bi[0] = bi;
+  }
+  __syncthreads();
+  bi = s_bi[0];
+  const double sg = (bi < l && col[bi] < 0.0) ? -1.0 : 1.0;
+  for (int i = threadIdx.x; i < l; i += blockDim.x) Uw[(long long)blockIdx.x * l + i] = sg * col[i];
 }
 
 // --------------------------------------------------- 3. order and signs --
 // One block.  lam_i = G_ii; rank by (lambda descending, index ascending).
 __global__ void __launch_bounds__(1024) order_kernel(const double* __restrict__ G0, const double* __restrict__ G1,
-                                                     const double* __restrict__ V, const int* __restrict__ info,
-                                                     int l, int lp, int k, long long n, double* __restrict__ sigma,
-                                                     double* __restrict__ Uw, double* __restrict__ scale,
-                                                     double* __restrict__ tail) {
+                                                     const int* __restrict__ info, int l, int lp, int k, long long n,
+                                                     double* __restrict__ sigma, double* __restrict__ scale,
+                                                     double* __restrict__ tail, int* __restrict__ ord_out) {
   __shared__ double lam[kMaxL];
   __shared__ int ord[kMaxL];
   __shared__ double red[32];
@@ -391,25 +420,7 @@ __global__ void __launch_bounds__(1024) order_kernel(const double* __restrict__ 
     const double sv = sqrt(lv);
     sigma[r] = sv;
     scale[r] = (lv > thr && sv > 0.0) ? 1.0 / sv : 0.0;
-  }
-  // U^(W)_k: column r = eigenvector ord[r], signed so that its entry of
-  // largest magnitude (lowest index on ties) is positive; one warp a column
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int r = wid; r < k; r += nw) {
-    const double* v = V + (long long)ord[r] * lp;
-    double best = -1.0;
-    int bi = l;
-    for (int i = lane; i < l; i += 32) {
-      const double a = fabs(v[i]);
-      if (a > best) { best = a; bi = i; }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-    }
-    const double sg = (bi < l && v[bi] < 0.0) ? -1.0 : 1.0;
-    for (int i = lane; i < l; i += 32) Uw[(long long)r * l + i] = sg * v[i];
+    ord_out[r] = ord[r];
   }
 }
 
@@ -471,7 +482,8 @@ struct LrLayout {
   int* info;
   int* flags;
   uint32_t* bar;
-  double *part, *G0, *G1, *V, *Uw, *scale;
+  double *part, *G0, *G1, *Uw, *scale;
+  int* ord;
   double2* rotlog;
   long long max_rounds;
   int nslices, npairs, slice;
@@ -499,7 +511,7 @@ LrLayout lr_layout(void* ws, size_t cap, int64_t n, int32_t l, int32_t k, int sm
   const int lp = l + (l & 1);
   L.G0 = c.take<double>((size_t)lp * lp);
   L.G1 = c.take<double>((size_t)lp * lp);
-  L.V = c.take<double>((size_t)lp * lp);
+  L.ord = c.take<int>(k);
   L.max_rounds = (long long)kMaxSweeps * (lp - 1);
   L.rotlog = c.take<double2>((size_t)L.max_rounds * (lp / 2));
   L.Uw = c.take<double>((size_t)l * k);
@@ -589,9 +601,9 @@ extern "C" css_status css_lowrank(const double* W, int64_t ldw, const double* Q,
   e = cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(gdim * (gdim + 1) / 2), dim3(kJacobiThreads),
                                   args, 0, s);
   if (e != cudaSuccess) return CSS_ERR_CUDA;
-  replay_rotations_kernel<<<l, h, lp * sizeof(double), s>>>(L.rotlog, L.info, lp, L.V);
   double* uw = Uw ? Uw : L.Uw;
-  order_kernel<<<1, 1024, 0, s>>>(L.G0, L.G1, L.V, L.info, l, lp, k, (long long)n, sigma, uw, L.scale, tail);
+  order_kernel<<<1, 1024, 0, s>>>(L.G0, L.G1, L.info, l, lp, k, (long long)n, sigma, L.scale, tail, L.ord);
+  replay_columns_kernel<<<k, (h + 31) / 32 * 32, lp * sizeof(double), s>>>(L.rotlog, L.info, L.ord, l, lp, uw);
   if (timed) cudaEventRecord(ev[2], s);
   if (U)
     gemm_nn_kernel<<<dim3((unsigned)((m + 63) / 64), (k + 63) / 64), 256, 0, s>>>(Q, ldq, uw, l, nullptr, U, ldu,

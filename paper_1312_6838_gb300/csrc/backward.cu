@@ -101,10 +101,9 @@ __global__ void gram_kernel(const double* __restrict__ AS, int m, int k, double*
   if (i0 + ty < k && j0 + tx < k) G[(long long)(j0 + tx) * k + i0 + ty] = acc;
 }
 
-// Cholesky G = L L^T in place (lower triangle) and Linv = L^-1, one block.
-// status[0] = 1 when G is not positive definite (A_S rank deficient).
-__global__ void chol_inv_kernel(double* __restrict__ G, int k, double* __restrict__ Linv,
-                                int* __restrict__ status) {
+// Cholesky G = L L^T in place (lower triangle), one block.  status[0] = 1
+// when G is not positive definite (A_S rank deficient).
+__global__ void chol_kernel(double* __restrict__ G, int k, int* __restrict__ status) {
   __shared__ int bad;
   __shared__ double diag0[1024];
   if (threadIdx.x == 0) bad = 0;
@@ -131,16 +130,32 @@ __global__ void chol_inv_kernel(double* __restrict__ G, int k, double* __restric
     }
     __syncthreads();
   }
-  // Linv: forward substitution L x = e_j, one column per thread group
-  for (int j = threadIdx.x; j < k; j += blockDim.x) {
-    for (int i = 0; i < k; ++i) Linv[(long long)j * k + i] = 0.0;
-    for (int i = j; i < k; ++i) {
-      double v = (i == j) ? 1.0 : 0.0;
-      for (int l = j; l < i; ++l) v -= G[(long long)l * k + i] * Linv[(long long)j * k + l];
-      Linv[(long long)j * k + i] = v / G[(long long)i * k + i];
-    }
-  }
   if (threadIdx.x == 0 && bad) status[0] = 1;
+}
+
+// Linv = L^-1 by forward substitution L x = e_j, one warp per column j: the
+// sum over the already known x_l is split across the lanes and the column
+// is kept in shared memory.
+constexpr int kLinvWarps = 8;
+__global__ void __launch_bounds__(kLinvWarps * 32) linv_kernel(const double* __restrict__ G, int k,
+                                                                double* __restrict__ Linv) {
+  extern __shared__ double xs[];   // kLinvWarps x k
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int j = blockIdx.x * kLinvWarps + w;
+  if (j >= k) return;
+  double* x = xs + (size_t)w * k;
+  for (int i = lane; i < j; i += 32) Linv[(long long)j * k + i] = 0.0;
+  for (int i = j; i < k; ++i) {
+    double part = 0.0;
+    for (int l = j + lane; l < i; l += 32) part = fma(G[(long long)l * k + i], x[l], part);
+    part = warp_sum(part);
+    if (lane == 0) {
+      const double v = ((i == j) ? 1.0 : 0.0) - part;
+      x[i] = v / G[(long long)i * k + i];
+    }
+    __syncwarp();
+  }
+  for (int i = j + lane; i < k; i += 32) Linv[(long long)j * k + i] = x[i];
 }
 
 // The same factorisation with G held in shared memory (k <= kCholSmemK):
@@ -198,7 +213,10 @@ void chol_inv(double* G, int k, double* Linv, int* status, cudaStream_t s) {
       cudaFuncSetAttribute(chol_inv_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     chol_inv_smem_kernel<<<1, 1024, smem, s>>>(G, k, Linv, status);
   } else {
-    chol_inv_kernel<<<1, 1024, 0, s>>>(G, k, Linv, status);
+    chol_kernel<<<1, 1024, 0, s>>>(G, k, status);
+    const size_t smem = (size_t)kLinvWarps * k * sizeof(double);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(linv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    linv_kernel<<<(k + kLinvWarps - 1) / kLinvWarps, kLinvWarps * 32, smem, s>>>(G, k, Linv);
   }
 }
 

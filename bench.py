@@ -284,7 +284,11 @@ def run_distributed(args):
         "projection_sparse_sign_ms": proj_ssgn,
         "roofline": {"bound": "tensor", "achieved": tf, "peak": peak_tf, "unit": "TFLOP/s",
                      "frac": tf / peak_tf, "traffic": None, "kernel": "tc_kernel (B = A Omega)"},
-        "gpu_launches": None, "clocks": clk}), flush=True)
+        # per pipeline: projection (tensor-core partials, reduction), the
+        # blocks' initial scores (split of B, tensor-core column norms), the
+        # blocks' greedy launch, union gather of columns and scores, the
+        # union's greedy launch, global ids
+        "gpu_launches": 9 * args.steps, "clocks": clk}), flush=True)
 
 
 def run_batched(args):

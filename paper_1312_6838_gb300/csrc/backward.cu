@@ -307,6 +307,102 @@ __global__ void __launch_bounds__(256) w_kernel(const float* __restrict__ Qh, co
     }
 }
 
+// The FP32/BF16 (double-float) form of w_kernel: 64 x 64 outputs per block,
+// 4 x 4 per thread, so that each K step reads three 16-byte vectors of shared
+// memory for 16 double-float multiply-adds; K chunks of 16 double-buffered
+// through registers.  Each output's terms are added in the same order as in
+// w_kernel, so the result is bit-identical.
+constexpr int kDT = 64, kDK = 16, kDP = kDT + 4;
+
+template <typename TA>
+__global__ void __launch_bounds__(256) w_df_kernel(const float* __restrict__ Qh, const float* __restrict__ Ql,
+                                                   const TA* __restrict__ A, long long lda, int m, int n, int k,
+                                                   double* __restrict__ W, long long wj, long long wc,
+                                                   float* __restrict__ Wh, float* __restrict__ Wl) {
+  __shared__ __align__(16) float sq[2][2][kDK][kDP];   // [buffer][hi, lo][row of the chunk][j]
+  __shared__ __align__(16) float sa[2][kDK][kDP];      // [buffer][row of the chunk][column]
+  const int j0 = blockIdx.y * kDT, c0 = blockIdx.x * kDT;
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  const int rr = tid % kDK, cq = tid / kDK;   // staging: row rr, columns cq + 16 v
+  float rh[4], rl[4], ra[4];
+  DF acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = DF{0.f, 0.f};
+  auto fetch = [&](int r0) {
+    const int r = r0 + rr;
+    const bool okr = r < m;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int x = cq + 16 * v;
+      const bool okq = okr && j0 + x < k, oka = okr && c0 + x < n;
+      rh[v] = okq ? Qh[(long long)(j0 + x) * m + r] : 0.f;
+      rl[v] = okq ? Ql[(long long)(j0 + x) * m + r] : 0.f;
+      ra[v] = oka ? (float)to_d<TA>(A[(long long)(c0 + x) * lda + r]) : 0.f;
+    }
+  };
+  auto stage = [&](int b) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      sq[b][0][rr][cq + 16 * v] = rh[v];
+      sq[b][1][rr][cq + 16 * v] = rl[v];
+      sa[b][rr][cq + 16 * v] = ra[v];
+    }
+  };
+  fetch(0);
+  stage(0);
+  __syncthreads();
+  int buf = 0;
+  for (int r0 = 0; r0 < m; r0 += kDK) {
+    const bool more = r0 + kDK < m;
+    if (more) fetch(r0 + kDK);
+#pragma unroll 4
+    for (int kk = 0; kk < kDK; ++kk) {
+      const float4 qh4 = *reinterpret_cast<const float4*>(&sq[buf][0][kk][ty * 4]);
+      const float4 ql4 = *reinterpret_cast<const float4*>(&sq[buf][1][kk][ty * 4]);
+      const float4 a4 = *reinterpret_cast<const float4*>(&sa[buf][kk][tx * 4]);
+      const float qh[4] = {qh4.x, qh4.y, qh4.z, qh4.w}, ql[4] = {ql4.x, ql4.y, ql4.z, ql4.w};
+      const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) df_fma(acc[a][b], av[b], qh[a], ql[a]);
+    }
+    if (more) stage(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int j = j0 + ty * 4 + a, c = c0 + tx * 4 + b;
+      if (j < k && c < n) {
+        const double v = (double)acc[a][b].s + (double)acc[a][b].c;
+        const long long o = (long long)j * wj + (long long)c * wc;
+        W[o] = v;
+        if (Wh) {
+          float h, lo;
+          df_split(v, h, lo);
+          Wh[o] = h;
+          Wl[o] = lo;
+        }
+      }
+    }
+}
+
+// W = Q^T A launch: FP64 A on w_kernel, FP32/BF16 A on w_df_kernel.
+template <typename TA>
+void launch_w(const float* Qh, const float* Ql, const double* Q, const TA* A, long long lda, int m, int n, int k,
+              double* W, long long wj, long long wc, float* Wh, float* Wl, cudaStream_t s) {
+  if constexpr (sizeof(TA) == 8)
+    w_kernel<TA><<<dim3((n + 63) / 64, (k + 31) / 32), 256, 0, s>>>(Qh, Ql, Q, A, lda, m, n, k, W, wj, wc, Wh, Wl);
+  else
+    w_df_kernel<TA><<<dim3((n + kDT - 1) / kDT, (k + kDT - 1) / kDT), 256, 0, s>>>(Qh, Ql, A, lda, m, n, k, W, wj,
+                                                                                 wc, Wh, Wl);
+}
+
 // ------------------------------------ R = A - Q W (m x n) with epilogues -----
 // 64 x 64 outputs per block, 4 x 4 per thread, K = k in chunks of 16.
 // Writes R (FP32, or FP64 for FP64 input) when Rout != null, dA = 2 g R when
@@ -383,6 +479,104 @@ __global__ void __launch_bounds__(256) r_kernel(const float* __restrict__ Qh, co
     }
   sq = warp_sum(sq);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    loss_part[(long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// The FP32/BF16 (double-float) form of r_kernel: the same 64 x 64 tile and
+// 4 x 4 outputs per thread, with Q and W staged so that each K step reads
+// four 16-byte vectors of shared memory for 16 double-float multiply-adds,
+// and K chunks double-buffered through registers.  Same order of terms and
+// of the loss partial sums as r_kernel, so the results are bit-identical.
+template <typename TA>
+__global__ void __launch_bounds__(256) r_df_kernel(const float* __restrict__ Qh, const float* __restrict__ Ql,
+                                                   const float* __restrict__ Wh, const float* __restrict__ Wl,
+                                                   const TA* __restrict__ A, long long lda, int m, int n, int k,
+                                                   float* __restrict__ Rout, TA* __restrict__ dA, long long ldda,
+                                                   double g2, double* __restrict__ loss_part) {
+  __shared__ __align__(16) float sq[2][2][kDK][kDP];   // [buffer][hi, lo][j of the chunk][row]
+  __shared__ __align__(16) float sw[2][2][kDK][kDP];   // [buffer][hi, lo][j of the chunk][column]
+  __shared__ double red[8];
+  const int i0 = blockIdx.x * kDT, c0 = blockIdx.y * kDT;
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  // staging: Q rows ii = tid % 64 of chunk entries jq + 4 v; W entries jw = tid % 16 of columns cw + 16 v
+  const int ii = tid % kDT, jq = tid / kDT;
+  const int jw = tid % kDK, cw = tid / kDK;
+  float qh_r[4], ql_r[4], wh_r[4], wl_r[4];
+  DF acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = DF{0.f, 0.f};
+  auto fetch = [&](int jb) {
+    const bool oki = i0 + ii < m;
+    const bool okw = jb + jw < k;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int j = jb + jq + 4 * v;
+      const bool okq = oki && j < k;
+      qh_r[v] = okq ? Qh[(long long)j * m + i0 + ii] : 0.f;
+      ql_r[v] = okq ? Ql[(long long)j * m + i0 + ii] : 0.f;
+      const int c = c0 + cw + 16 * v;
+      const bool ok = okw && c < n;
+      wh_r[v] = ok ? Wh[(long long)c * k + jb + jw] : 0.f;
+      wl_r[v] = ok ? Wl[(long long)c * k + jb + jw] : 0.f;
+    }
+  };
+  auto stage = [&](int b) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      sq[b][0][jq + 4 * v][ii] = qh_r[v];
+      sq[b][1][jq + 4 * v][ii] = ql_r[v];
+      sw[b][0][jw][cw + 16 * v] = wh_r[v];
+      sw[b][1][jw][cw + 16 * v] = wl_r[v];
+    }
+  };
+  fetch(0);
+  stage(0);
+  __syncthreads();
+  int buf = 0;
+  for (int jb = 0; jb < k; jb += kDK) {
+    const bool more = jb + kDK < k;
+    if (more) fetch(jb + kDK);
+#pragma unroll 2
+    for (int jj = 0; jj < kDK; ++jj) {
+      const float4 qh4 = *reinterpret_cast<const float4*>(&sq[buf][0][jj][ty * 4]);
+      const float4 ql4 = *reinterpret_cast<const float4*>(&sq[buf][1][jj][ty * 4]);
+      const float4 wh4 = *reinterpret_cast<const float4*>(&sw[buf][0][jj][tx * 4]);
+      const float4 wl4 = *reinterpret_cast<const float4*>(&sw[buf][1][jj][tx * 4]);
+      const float qh[4] = {qh4.x, qh4.y, qh4.z, qh4.w}, ql[4] = {ql4.x, ql4.y, ql4.z, ql4.w};
+      const float wh[4] = {wh4.x, wh4.y, wh4.z, wh4.w}, wl[4] = {wl4.x, wl4.y, wl4.z, wl4.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) df_fma2(acc[a][b], qh[a], ql[a], wh[b], wl[b]);
+    }
+    if (more) stage(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+  double sq_sum = 0.0;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = i0 + ty * 4 + a, c = c0 + tx * 4 + b;
+      if (i < m && c < n) {
+        const double av = to_d<TA>(A[(long long)c * lda + i]);
+        // a - (s + c) in double: the pair carries the product to ~2^-48
+        const double r = (av - (double)acc[a][b].s) - (double)acc[a][b].c;
+        sq_sum += r * r;
+        if (Rout) Rout[(long long)c * m + i] = (float)r;
+        if (dA) dA[(long long)c * ldda + i] = from_d<TA>(g2 * r);
+      }
+    }
+  sq_sum = warp_sum(sq_sum);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq_sum;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
@@ -514,11 +708,14 @@ css_status run_backward(const TA* A, int dt, int m, int n, long long lda, const 
   gram_kernel<<<dim3((k + 15) / 16, (k + 15) / 16), 256, 0, s>>>(L.AS, m, k, L.G);
   chol_inv(L.G, k, L.Linv, L.status, s);
   q_kernel<<<(unsigned)((mk + 255) / 256), 256, 0, s>>>(L.AS, L.Linv, m, k, L.Q, L.Qh, L.Ql);
-  w_kernel<TA><<<dim3((n + 63) / 64, (k + 31) / 32), 256, 0, s>>>(L.Qh, L.Ql, L.Q, A, lda, m, n, k, L.W,
-                                                                1, k, L.Wh, L.Wl);
+  launch_w<TA>(L.Qh, L.Ql, L.Q, A, lda, m, n, k, L.W, 1, k, L.Wh, L.Wl, s);
   const dim3 rg((m + 63) / 64, (n + 63) / 64);
-  r_kernel<TA><<<rg, 256, 0, s>>>(L.Qh, L.Ql, L.Q, L.Wh, L.Wl, L.W, A, lda, m, n, k, dA ? L.R : nullptr,
-                                  dA, ldda, 2.0 * grad_out, L.loss_part);
+  if constexpr (sizeof(TA) == 8)
+    r_kernel<TA><<<rg, 256, 0, s>>>(L.Qh, L.Ql, L.Q, L.Wh, L.Wl, L.W, A, lda, m, n, k, dA ? L.R : nullptr,
+                                    dA, ldda, 2.0 * grad_out, L.loss_part);
+  else
+    r_df_kernel<TA><<<rg, 256, 0, s>>>(L.Qh, L.Ql, L.Wh, L.Wl, A, lda, m, n, k,
+                                       dA ? (float*)L.R : nullptr, dA, ldda, 2.0 * grad_out, L.loss_part);
   if (loss) sum_kernel<<<1, 512, 0, s>>>(L.loss_part, (long long)rg.x * rg.y, 1.0, loss);
   if (dA) {
     const int slice = (n + kSlices - 1) / kSlices;
@@ -589,8 +786,7 @@ css_status run_embed(const TA* A, int m, int n, long long lda, const int* sel, i
   chol_inv(L.G, l, L.Linv, L.status, s);
   q_kernel<<<gb, 256, 0, s>>>(L.Q1, L.Linv, m, l, L.Q, L.Qh, L.Ql);
   if (W)
-    w_kernel<TA><<<dim3((n + 63) / 64, (l + 31) / 32), 256, 0, s>>>(L.Qh, L.Ql, L.Q, A, lda, m, n, l, W, ldw,
-                                                                  1, nullptr, nullptr);
+    launch_w<TA>(L.Qh, L.Ql, L.Q, A, lda, m, n, l, W, ldw, 1, nullptr, nullptr, s);
   if (Qout) copy_cols_kernel<<<gb, 256, 0, s>>>(L.Q, m, l, Qout, ldq);
   if (cudaGetLastError() != cudaSuccess) return CSS_ERR_CUDA;
   if (o.sync) {

@@ -638,6 +638,72 @@ __global__ void __launch_bounds__(256) rwt_kernel(const TR* __restrict__ R, cons
     }
 }
 
+// FP32 form of rwt_kernel: 64 x 64 outputs per block, 4 x 4 per thread, two
+// 16-byte shared-memory reads per K step for 16 FMAs, K chunks
+// double-buffered through registers; same order of terms (bit-identical).
+__global__ void __launch_bounds__(256) rwt_f32_kernel(const float* __restrict__ R, const double* __restrict__ W,
+                                                      int m, int n, int k, int slice, float* __restrict__ partial) {
+  __shared__ __align__(16) float rs[2][kDK][kDP];
+  __shared__ __align__(16) float ws[2][kDK][kDP];
+  const int i0 = blockIdx.x * kDT, j0 = blockIdx.y * kDT, sl = blockIdx.z;
+  const int cb = sl * slice, ce = min(n, cb + slice);
+  const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+  const int xi = tid % kDT, kq = tid / kDT;   // staging: row / entry xi of chunk columns kq + 4 v
+  float rr[4], wr[4];
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+  auto fetch = [&](int c0) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int c = c0 + kq + 4 * v;
+      const bool okc = c < ce;
+      rr[v] = (okc && i0 + xi < m) ? R[(long long)c * m + i0 + xi] : 0.f;
+      wr[v] = (okc && j0 + xi < k) ? (float)W[(long long)c * k + j0 + xi] : 0.f;
+    }
+  };
+  auto stage = [&](int b) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      rs[b][kq + 4 * v][xi] = rr[v];
+      ws[b][kq + 4 * v][xi] = wr[v];
+    }
+  };
+  if (cb < ce) {
+    fetch(cb);
+    stage(0);
+  }
+  __syncthreads();
+  int buf = 0;
+  for (int c0 = cb; c0 < ce; c0 += kDK) {
+    const bool more = c0 + kDK < ce;
+    if (more) fetch(c0 + kDK);
+#pragma unroll 4
+    for (int kk = 0; kk < kDK; ++kk) {
+      const float4 r4 = *reinterpret_cast<const float4*>(&rs[buf][kk][ty * 4]);
+      const float4 w4 = *reinterpret_cast<const float4*>(&ws[buf][kk][tx * 4]);
+      const float ra[4] = {r4.x, r4.y, r4.z, r4.w}, wa[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(ra[a], wa[b], acc[a][b]);
+    }
+    if (more) stage(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+  float* out = partial + (long long)sl * m * k;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = i0 + ty * 4 + a, j = j0 + tx * 4 + b;
+      if (i < m && j < k) out[(long long)j * m + i] = acc[a][b];
+    }
+}
+
 // P = R W^T (m x k) from the slices, added in slice order, in FP64.
 template <typename TR>
 __global__ void sum_slices_kernel(const TR* __restrict__ partial, int S, long long mk, double* __restrict__ P) {
@@ -719,8 +785,12 @@ css_status run_backward(const TA* A, int dt, int m, int n, long long lda, const 
   if (loss) sum_kernel<<<1, 512, 0, s>>>(L.loss_part, (long long)rg.x * rg.y, 1.0, loss);
   if (dA) {
     const int slice = (n + kSlices - 1) / kSlices;
-    rwt_kernel<TR><<<dim3((m + 63) / 64, (k + 31) / 32, kSlices), 256, 0, s>>>((const TR*)L.R, L.W, m, n,
-                                                                              k, slice, (TR*)L.P);
+    if constexpr (sizeof(TR) == 4)
+      rwt_f32_kernel<<<dim3((m + kDT - 1) / kDT, (k + kDT - 1) / kDT, kSlices), 256, 0, s>>>(
+          (const float*)L.R, L.W, m, n, k, slice, (float*)L.P);
+    else
+      rwt_kernel<TR><<<dim3((m + 63) / 64, (k + 31) / 32, kSlices), 256, 0, s>>>((const TR*)L.R, L.W, m, n,
+                                                                                k, slice, (TR*)L.P);
     sum_slices_kernel<TR><<<(unsigned)((mk + 255) / 256), 256, 0, s>>>((const TR*)L.P, kSlices, mk, L.Psum);
     das_kernel<TA><<<(unsigned)((mk + 255) / 256), 256, 0, s>>>(L.Psum, L.Linv, m, k, sel, 2.0 * grad_out, dA,
                                                                ldda);

@@ -81,24 +81,87 @@ __global__ void gather_cols_kernel(const TA* __restrict__ A, long long lda, int 
   AS[idx] = to_d<TA>(A[(long long)sel[j] * lda + i]);
 }
 
-// G = A_S^T A_S (k x k), one 16 x 16 output tile per block.
-__global__ void gram_kernel(const double* __restrict__ AS, int m, int k, double* __restrict__ G) {
-  __shared__ double xs[32][17], ys[32][17];
-  const int i0 = blockIdx.y * 16, j0 = blockIdx.x * 16;
+
+// G = A_S^T A_S split over the m rows: block (pair, slice) forms the 32 x 32
+// tile (ti >= tj) of one row slice, 2 x 2 outputs per thread; gram_fin then
+// adds the slices in order and mirrors (bit-reproducible).  Enough blocks to
+// fill the GPU even for small k, where one block per output tile would not.
+constexpr int kGT = 32, kGK = 32;
+
+struct GramPlan {
+  int tiles, npairs, nslices, slice;
+};
+
+GramPlan gram_plan(int m, int k) {
+  GramPlan g{};
+  g.tiles = (k + kGT - 1) / kGT;
+  g.npairs = g.tiles * (g.tiles + 1) / 2;
+  const int want = std::max(1, (2 * 148 + g.npairs - 1) / g.npairs);
+  g.nslices = std::max(1, std::min(want, (m + 127) / 128));
+  g.slice = (m + g.nslices - 1) / g.nslices;
+  return g;
+}
+
+__global__ void __launch_bounds__(256) gram_part_kernel(const double* __restrict__ AS, int m, int k, int slice,
+                                                        int npairs, double* __restrict__ part) {
+  __shared__ double xa[kGT][kGK + 1], xb[kGT][kGK + 1];
+  const int pidx = blockIdx.x, sl = blockIdx.y;
+  int ti = (int)((sqrtf(8.f * pidx + 1.f) - 1.f) * 0.5f);
+  while (ti * (ti + 1) / 2 > pidx) --ti;
+  while ((ti + 1) * (ti + 2) / 2 <= pidx) ++ti;
+  const int tj = pidx - ti * (ti + 1) / 2;
+  const int a0 = ti * kGT, b0 = tj * kGT;
+  const int rb = sl * slice, re = min(m, rb + slice);
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  double acc = 0.0;
-  for (int r0 = 0; r0 < m; r0 += 32) {
-    for (int e = threadIdx.x; e < 32 * 16; e += 256) {
-      const int rr = e % 32, cc = e / 32;
-      xs[rr][cc] = (r0 + rr < m && i0 + cc < k) ? AS[(long long)(i0 + cc) * m + r0 + rr] : 0.0;
-      ys[rr][cc] = (r0 + rr < m && j0 + cc < k) ? AS[(long long)(j0 + cc) * m + r0 + rr] : 0.0;
+  double acc00 = 0.0, acc01 = 0.0, acc10 = 0.0, acc11 = 0.0;
+  for (int r0 = rb; r0 < re; r0 += kGK) {
+    for (int e = threadIdx.x; e < kGT * kGK; e += 256) {
+      const int col = e / kGK, rr = e % kGK;
+      const bool okr = r0 + rr < re;
+      xa[col][rr] = (okr && a0 + col < k) ? AS[(long long)(a0 + col) * m + r0 + rr] : 0.0;
+      xb[col][rr] = (okr && b0 + col < k) ? AS[(long long)(b0 + col) * m + r0 + rr] : 0.0;
     }
     __syncthreads();
 #pragma unroll 8
-    for (int rr = 0; rr < 32; ++rr) acc = fma(xs[rr][ty], ys[rr][tx], acc);
+    for (int kk = 0; kk < kGK; ++kk) {
+      const double u0 = xa[ty * 2][kk], u1 = xa[ty * 2 + 1][kk];
+      const double v0 = xb[tx * 2][kk], v1 = xb[tx * 2 + 1][kk];
+      acc00 = fma(u0, v0, acc00);
+      acc01 = fma(u0, v1, acc01);
+      acc10 = fma(u1, v0, acc10);
+      acc11 = fma(u1, v1, acc11);
+    }
     __syncthreads();
   }
-  if (i0 + ty < k && j0 + tx < k) G[(long long)(j0 + tx) * k + i0 + ty] = acc;
+  double* out = part + ((long long)sl * npairs + pidx) * (kGT * kGT);
+  out[(ty * 2) * kGT + tx * 2] = acc00;
+  out[(ty * 2) * kGT + tx * 2 + 1] = acc01;
+  out[(ty * 2 + 1) * kGT + tx * 2] = acc10;
+  out[(ty * 2 + 1) * kGT + tx * 2 + 1] = acc11;
+}
+
+__global__ void gram_fin_kernel(const double* __restrict__ part, int nslices, int npairs, int k,
+                                double* __restrict__ G) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)k * k) return;
+  const int r = (int)(idx % k), c = (int)(idx / k);
+  const int a = max(r, c), b = min(r, c);
+  const int pidx = (a / kGT) * (a / kGT + 1) / 2 + b / kGT;
+  const int off = (a % kGT) * kGT + (b % kGT);
+  double s = 0.0;
+  for (int q = 0; q < nslices; ++q) s += part[((long long)q * npairs + pidx) * (kGT * kGT) + off];
+  G[idx] = s;
+}
+
+size_t gram_part_doubles(int m, int k) {
+  const GramPlan g = gram_plan(m, k);
+  return (size_t)g.nslices * g.npairs * kGT * kGT;
+}
+
+void gram(const double* AS, int m, int k, double* part, double* G, cudaStream_t s) {
+  const GramPlan g = gram_plan(m, k);
+  gram_part_kernel<<<dim3(g.npairs, g.nslices), 256, 0, s>>>(AS, m, k, g.slice, g.npairs, part);
+  gram_fin_kernel<<<(unsigned)(((long long)k * k + 255) / 256), 256, 0, s>>>(part, g.nslices, g.npairs, k, G);
 }
 
 // Cholesky G = L L^T in place (lower triangle), one block.  status[0] = 1
@@ -730,7 +793,7 @@ constexpr int kSlices = 16;
 
 struct BwLayout {
   int* status;
-  double *AS, *G, *Linv, *Q, *W;
+  double *AS, *G, *gpart, *Linv, *Q, *W;
   float *Qh, *Ql, *Wh, *Wl;
   void* R;
   void* P;
@@ -746,6 +809,7 @@ BwLayout bw_layout(void* ws, size_t cap, int dt, int64_t m, int64_t n, int32_t k
   L.status = c.take<int>(64);
   L.AS = c.take<double>((size_t)m * k);
   L.G = c.take<double>((size_t)k * k);
+  L.gpart = c.take<double>(gram_part_doubles((int)m, k));
   L.Linv = c.take<double>((size_t)k * k);
   L.Q = c.take<double>((size_t)m * k);
   L.Qh = c.take<float>((size_t)m * k);
@@ -771,7 +835,7 @@ css_status run_backward(const TA* A, int dt, int m, int n, long long lda, const 
   cudaMemsetAsync(L.status, 0, sizeof(int), s);
   const long long mk = (long long)m * k;
   gather_cols_kernel<TA><<<(unsigned)((mk + 255) / 256), 256, 0, s>>>(A, lda, m, sel, k, L.AS);
-  gram_kernel<<<dim3((k + 15) / 16, (k + 15) / 16), 256, 0, s>>>(L.AS, m, k, L.G);
+  gram(L.AS, m, k, L.gpart, L.G, s);
   chol_inv(L.G, k, L.Linv, L.status, s);
   q_kernel<<<(unsigned)((mk + 255) / 256), 256, 0, s>>>(L.AS, L.Linv, m, k, L.Q, L.Qh, L.Ql);
   launch_w<TA>(L.Qh, L.Ql, L.Q, A, lda, m, n, k, L.W, 1, k, L.Wh, L.Wl, s);
@@ -818,7 +882,7 @@ __global__ void copy_cols_kernel(const double* __restrict__ src, int m, int l, d
 
 struct EmbLayout {
   int* status;
-  double *AS, *G, *Linv, *Q1, *Q;
+  double *AS, *G, *gpart, *Linv, *Q1, *Q;
   float *Qh, *Ql;
   size_t bytes;
 };
@@ -829,6 +893,7 @@ EmbLayout emb_layout(void* ws, size_t cap, int64_t m, int32_t l) {
   L.status = c.take<int>(64);
   L.AS = c.take<double>((size_t)m * l);
   L.G = c.take<double>((size_t)l * l);
+  L.gpart = c.take<double>(gram_part_doubles((int)m, l));
   L.Linv = c.take<double>((size_t)l * l);
   L.Q1 = c.take<double>((size_t)m * l);
   L.Q = c.take<double>((size_t)m * l);
@@ -847,12 +912,11 @@ css_status run_embed(const TA* A, int m, int n, long long lda, const int* sel, i
   cudaMemsetAsync(L.status, 0, sizeof(int), s);
   const long long ml = (long long)m * l;
   const unsigned gb = (unsigned)((ml + 255) / 256);
-  const dim3 gg((l + 15) / 16, (l + 15) / 16);
   gather_cols_kernel<TA><<<gb, 256, 0, s>>>(A, lda, m, sel, l, L.AS);
-  gram_kernel<<<gg, 256, 0, s>>>(L.AS, m, l, L.G);
+  gram(L.AS, m, l, L.gpart, L.G, s);
   chol_inv(L.G, l, L.Linv, L.status, s);
   q_kernel<<<gb, 256, 0, s>>>(L.AS, L.Linv, m, l, L.Q1, L.Qh, L.Ql);
-  gram_kernel<<<gg, 256, 0, s>>>(L.Q1, m, l, L.G);
+  gram(L.Q1, m, l, L.gpart, L.G, s);
   chol_inv(L.G, l, L.Linv, L.status, s);
   q_kernel<<<gb, 256, 0, s>>>(L.Q1, L.Linv, m, l, L.Q, L.Qh, L.Ql);
   if (W)

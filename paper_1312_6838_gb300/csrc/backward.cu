@@ -221,12 +221,11 @@ __global__ void __launch_bounds__(kLinvWarps * 32) linv_kernel(const double* __r
   for (int i = j + lane; i < k; i += 32) Linv[(long long)j * k + i] = x[i];
 }
 
-// The same factorisation with G held in shared memory (k <= kCholSmemK):
-// the k steps of the right-looking update and the substitutions for L^-1
-// then read shared memory instead of L2.
+// The same factorisation with G held in shared memory (k <= kCholSmemK): the
+// k steps of the right-looking update read shared memory instead of L2; L
+// is written back over G.
 constexpr int kCholSmemK = 128;
-__global__ void __launch_bounds__(1024) chol_inv_smem_kernel(const double* __restrict__ Gg, int k,
-                                                             double* __restrict__ Linv, int* __restrict__ status) {
+__global__ void __launch_bounds__(1024) chol_smem_kernel(double* __restrict__ Gg, int k, int* __restrict__ status) {
   extern __shared__ double G[];   // k x k, column-major
   __shared__ int bad;
   __shared__ double diag0[kCholSmemK];
@@ -255,32 +254,24 @@ __global__ void __launch_bounds__(1024) chol_inv_smem_kernel(const double* __res
     }
     __syncthreads();
   }
-  // Linv: forward substitution L x = e_j, one column per thread
-  for (int j = threadIdx.x; j < k; j += blockDim.x) {
-    for (int i = 0; i < j; ++i) Linv[(long long)j * k + i] = 0.0;
-    for (int i = j; i < k; ++i) {
-      double v = (i == j) ? 1.0 : 0.0;
-      for (int l = j; l < i; ++l) v -= G[l * k + i] * Linv[(long long)j * k + l];
-      Linv[(long long)j * k + i] = v / G[i * k + i];
-    }
-  }
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) Gg[e] = G[e];
   if (threadIdx.x == 0 && bad) status[0] = 1;
 }
 
-// Cholesky of the k x k matrix in G and L^-1 into Linv (status[0] = 1 for a
-// rank-deficient G); G is overwritten when it does not fit shared memory.
+// Cholesky of the k x k matrix in G (overwritten by L) and L^-1 into Linv
+// (status[0] = 1 for a rank-deficient G).
 void chol_inv(double* G, int k, double* Linv, int* status, cudaStream_t s) {
   if (k <= kCholSmemK) {
     const size_t smem = (size_t)k * k * sizeof(double);
     if (smem > 48 * 1024)
-      cudaFuncSetAttribute(chol_inv_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    chol_inv_smem_kernel<<<1, 1024, smem, s>>>(G, k, Linv, status);
+      cudaFuncSetAttribute(chol_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    chol_smem_kernel<<<1, 1024, smem, s>>>(G, k, status);
   } else {
     chol_kernel<<<1, 1024, 0, s>>>(G, k, status);
-    const size_t smem = (size_t)kLinvWarps * k * sizeof(double);
-    if (smem > 48 * 1024) cudaFuncSetAttribute(linv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    linv_kernel<<<(k + kLinvWarps - 1) / kLinvWarps, kLinvWarps * 32, smem, s>>>(G, k, Linv);
   }
+  const size_t smem = (size_t)kLinvWarps * k * sizeof(double);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(linv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  linv_kernel<<<(k + kLinvWarps - 1) / kLinvWarps, kLinvWarps * 32, smem, s>>>(G, k, Linv);
 }
 
 // Q = A_S L^-T (m x k): Q[i, j] = sum_{l <= j} A_S[i, l] Linv[j, l]; the

@@ -22,6 +22,7 @@ namespace {
 constexpr int kMaxK = 1024;          // columns selected per problem
 constexpr int kMaxCtas = 1024;       // descriptor space reserved per call
 constexpr uint64_t kDefaultSpinNs = 2000000000ull;
+constexpr double kPivotColumnEquiv = 700.0;  // planner: one pivot step in streamed columns
 
 size_t esize(int dt) { return dt == CSS_F64 ? 8 : dt == CSS_F32 ? 4 : 2; }
 size_t accsize(int dt) { return dt == CSS_F64 ? 8 : 4; }
@@ -866,7 +867,10 @@ css_status gcss_distributed(const void* A, css_dtype dtype, int64_t m, int64_t n
     units.push_back(make_unit(Ab, dtype, m, w, lda, kb, 1, B, ldb, r, st, nullptr,
                               bsel + (size_t)b * l_block, L.btrace + (size_t)b * (l_block + 1),
                               L.bnsel + b, ob));
-    work.push_back((double)w * kb);
+    // a block's cost: kb iterations, each a streaming pass over its w columns
+    // plus the pivot, whose latency-bound cost is charged as a fixed number
+    // of column-equivalents (swept on the 2048 x 262144 workload: 700)
+    work.push_back((double)kb * ((double)w + kPivotColumnEquiv));
   }
   const int tile = pick_tile(o, dtype, m, n);
   css_status cs = launch_units(L.h, units, work, dtype, o.grid_ctas, tile, o.spin_budget_ns, s);

@@ -36,7 +36,7 @@ import numpy as np  # noqa: E402
 import css_inputs as ci  # noqa: E402
 
 WORKLOAD = "decay_4096x65536"
-METRIC = "greedy iterations/s (fused streaming step, initial scores excluded)"
+METRIC = "greedy iterations/s and achieved HBM GB/s (fused step), mixed vs plain at equal error"
 
 
 def parse():
@@ -661,6 +661,10 @@ def main():
         "gpu_launches": (6 if args.dtype == "bf16" else 4) * args.steps,
         "clocks": clk,
     }
+    out["hbm_gbs"] = achieved
+    if args.dtype == "bf16" and args.workload in (WORKLOAD, "decay_4096x32768"):
+        del A
+        out.update(plain_comparison(css, At_host, dev, k, c_bytes, n, res.indices.cpu().tolist()))
     if not args.no_e2e:
         out["e2e"] = e2e(css, A32, tdt, m, n, k, dev, args)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -670,6 +674,35 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def plain_comparison(css, At_host, dev, k, c_bytes, n, S_mixed):
+    """The plain path beside the mixed one (outside the timed region): the
+    same selection with A streamed in FP32, its greedy-loop rate and HBM
+    rate, and both selections' reconstruction errors on the FP32 matrix,
+    each from the FP32 path's own recursion (Theorem 1), the mixed
+    selection replayed there as forced picks."""
+    A = At_host.to(dev).t()
+    a_bytes = A.shape[0] * A.shape[1] * 4
+    for _ in range(2):
+        css.select(A, k)
+    loop = []
+    for _ in range(3):
+        r = css.select(A, k, timing=True)
+        loop.append(r.timing_ms[1])
+    ms = statistics.mean(loop)
+    e_plain = float(r.trace[r.n_sel].item())
+    f = css.select(A, k, forced=S_mixed)
+    e_mixed = float(f.trace[f.n_sel].item())
+    del A
+    return {
+        "plain_f32": {"value": r.n_sel / (ms / 1e3), "unit": "iterations/s", "loop_ms": ms,
+                      "hbm_gbs": (a_bytes + c_bytes + 48 * n) * r.n_sel / (ms / 1e3) / 1e9},
+        "equal_error": {"mixed_bf16": e_mixed, "plain_f32": e_plain,
+                        "rel_diff": abs(e_mixed - e_plain) / e_plain,
+                        "evaluated": "||A - P_S A||_F^2 of each selection on the FP32 matrix by the "
+                                     "FP32 path's recursion (mixed selection forced)"},
+    }
 
 
 def e2e(css, A32, tdt, m, n, k, dev, args):

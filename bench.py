@@ -177,8 +177,10 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "m": c["m"], "n": c["n"], "k": c["k"],
-                   "stream_dtype": args.dtype},
+        "config": {"workload": WORKLOAD, "m": c["m"], "n": c["n"], "k": c["k"], "rank": c["rank"],
+                   "noise": c["noise"], "stream_dtype": args.dtype,
+                   "accumulate": "f64 throughout (the oracle; BF16 input rounded first)",
+                   "parallelism": "host cores"},
         "cpu_baseline": {"value": value, "unit": "iterations/s", "cores": cores, "kind": "oracle",
                          "sample": f"{iters_per_step} iterations of Algorithm 1 per step on the full "
                                    f"{c['m']}x{c['n']} matrix in FP64; initial scores "

@@ -583,6 +583,29 @@ class _Residual(torch.autograd.Function):
         return dA, None
 
 
+def residual_error(A: torch.Tensor, S) -> float:
+    """||A - P^(S) A||_F^2 for a fixed selected set S as an FP64 number, from
+    the residual R = A - Q (Q^T A) formed on the device (the forward half of
+    css_residual_backward, no gradient).  Unlike the selection's recursive
+    trace it keeps its accuracy when the error is a tiny fraction of
+    ||A||_F^2."""
+    m, n, lda = _colmajor(A)
+    dt = _DT[A.dtype]
+    lib = L.load()
+    sel = torch.as_tensor(list(S) if not torch.is_tensor(S) else S, dtype=torch.int32).to(A.device).contiguous()
+    loss = torch.empty(1, dtype=torch.float64, device=A.device)
+    o = L.default_opts()
+    k = int(sel.numel())
+    nbytes = lib.css_workspace_size(L.CSS_OP_BACKWARD, dt, m, n, 0, k, 0, C.byref(o))
+    if nbytes == 0:
+        raise ValueError("invalid sizes for css_residual_backward")
+    _keep, ws = _workspace(nbytes, A.device)
+    code = lib.css_residual_backward(_ptr(A), dt, m, n, lda, _ptr(sel), k, 1.0, C.c_void_p(0), 0,
+                                     _ptr(loss), _ptr(ws), nbytes, C.byref(o), _stream(None))
+    _check(code, "css_residual_backward(loss)")
+    return float(loss.item())
+
+
 def residual(A: torch.Tensor, S) -> torch.Tensor:
     """||A - P^(S) A||_F^2 (Eq. Projection) for a fixed selected set S, as an
     autograd function whose backward is the hand-written adjoint kernel."""

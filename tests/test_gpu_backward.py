@@ -87,6 +87,23 @@ def test_loss_only_and_grad_out_scaling(css):
     assert err <= 2e-6
 
 
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32, torch.bfloat16])
+def test_residual_error_resolves_tiny_errors(css, dtype):
+    """css.residual_error at an error of ~1e-8 of ||A||_F^2 (rank-k signal,
+    1e-4 noise, the signal's own k columns selected): the direct residual
+    keeps its accuracy where a recursion subtracting O(||A||^2) terms would
+    not."""
+    A_np = ci.lowrank_uv(200, 900, 12, 1e-4, 702)
+    A, vals = dev_matrix(A_np, dtype)
+    S = O.greedy_css(vals, 12).S
+    e_ref = O.reconstruction_error(vals, S)
+    # (BF16 rounding of the entries adds its own noise of ~2^-9 relative)
+    assert e_ref <= (1e-4 if dtype == torch.bfloat16 else 1e-7) * float(np.sum(vals * vals))
+    got = css.residual_error(A, S)
+    tol = 1e-10 if dtype == torch.float64 else 1e-5
+    assert abs(got - e_ref) <= tol * e_ref, (got, e_ref)
+
+
 def test_rank_deficient_selection_rejected(css):
     from paper_1312_6838_gb300._lib import CssError
     A_np = ci.lowrank_uv(30, 60, 5, 0.0, 701)

@@ -94,8 +94,8 @@ def test_signal_dominated_selection_full_size(css):
     # products, so the trace's error is absolute, a small multiple of 1e-7 of
     # the initial scores per step.  On this matrix the error itself falls to
     # 1.2e-4 of ||A||_F^2 by t = 256, the level that error reaches, so the
-    # late trace is checked against ||A||_F^2 (the FP64 path or css_embed give
-    # the error itself there).
+    # late trace is checked against ||A||_F^2 (css.residual_error gives the
+    # error itself there).
     for t in (1, 8, 64):
         direct = O.reconstruction_error(vals, S[:t], chunk=8192)
         assert abs(tr[t] - direct) <= 1e-4 * direct, (t, tr[t], direct)

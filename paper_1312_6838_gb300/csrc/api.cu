@@ -3,6 +3,7 @@
 // init_simt.cu, project.cu and backward.cu.
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 #include <mutex>
 #include <numeric>
 #include <vector>
@@ -974,6 +975,7 @@ struct BatchedPlanImpl {
 };
 constexpr uint64_t kPlanMagic = 0x43535342504c414eull;   // "CSSBPLAN"
 static_assert(sizeof(BatchedPlanImpl) <= sizeof(css_batched_plan), "css_batched_plan too small");
+static_assert(std::is_trivially_copyable<BatchedPlanImpl>::value, "the plan is copied as bytes");
 
 css_status batched_prepare(const css_problem* probs, int32_t count, css_dtype dtype, void* ws,
                            size_t ws_bytes, const css_opts& o, BatchedPlanImpl& P, cudaStream_t s) {
@@ -1078,14 +1080,14 @@ css_status css_select_batched_prepare(const css_problem* probs, int32_t count, c
   css_status cs = batched_prepare(probs, count, dtype, workspace, workspace_bytes, o, P,
                                   (cudaStream_t)stream);
   if (cs != CSS_OK) return cs;
-  std::memcpy(plan, &P, sizeof(P));
+  std::memcpy(static_cast<void*>(plan), static_cast<const void*>(&P), sizeof(P));
   return CSS_OK;
 }
 
 css_status css_select_batched_run(const css_batched_plan* plan, void* workspace, css_stream_t stream) {
   if (!plan) return CSS_ERR_INVALID_ARG;
   BatchedPlanImpl P;
-  std::memcpy(&P, plan, sizeof(P));
+  std::memcpy(static_cast<void*>(&P), static_cast<const void*>(plan), sizeof(P));
   if (P.magic != kPlanMagic || P.ws != workspace || !workspace) return CSS_ERR_INVALID_ARG;
   return batched_run(P, (cudaStream_t)stream, nullptr);
 }

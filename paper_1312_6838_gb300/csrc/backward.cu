@@ -819,7 +819,7 @@ BwLayout bw_layout(void* ws, size_t cap, int dt, int64_t m, int64_t n, int32_t k
 }
 
 template <typename TA>
-css_status run_backward(const TA* A, int dt, int m, int n, long long lda, const int* sel, int k,
+css_status run_backward(const TA* A, int m, int n, long long lda, const int* sel, int k,
                         double grad_out, TA* dA, long long ldda, double* loss, const BwLayout& L,
                         const css_opts& o, cudaStream_t s) {
   using TR = typename AccOf<TA>::type;
@@ -995,13 +995,13 @@ extern "C" css_status css_residual_backward(const void* A, css_dtype dtype, int6
   cudaStream_t s = (cudaStream_t)stream;
   switch (dtype) {
     case CSS_F64:
-      return run_backward<double>((const double*)A, dtype, (int)m, (int)n, lda, sel, k, grad_out,
+      return run_backward<double>((const double*)A, (int)m, (int)n, lda, sel, k, grad_out,
                                   (double*)dA, ldda, loss, L, o, s);
     case CSS_F32:
-      return run_backward<float>((const float*)A, dtype, (int)m, (int)n, lda, sel, k, grad_out,
+      return run_backward<float>((const float*)A, (int)m, (int)n, lda, sel, k, grad_out,
                                  (float*)dA, ldda, loss, L, o, s);
     default:
-      return run_backward<__nv_bfloat16>((const __nv_bfloat16*)A, dtype, (int)m, (int)n, lda, sel, k,
+      return run_backward<__nv_bfloat16>((const __nv_bfloat16*)A, (int)m, (int)n, lda, sel, k,
                                          grad_out, (__nv_bfloat16*)dA, ldda, loss, L, o, s);
   }
 }

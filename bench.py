@@ -556,8 +556,10 @@ def run_lowrank(args):
         "phases_ms": {"gram": phases[0], "eigendecomposition": phases[1], "products": phases[2]},
         "jacobi_sweeps": int(phases[3]),
         "embed_ms": embed_ms,
-        "fp64_tflops": {"gram": gram_tf,
-                        "products": v_flop / (phases[2] * 1e-3) / 1e12},
+        # algorithmic FLOP rates: the Gram matrix in FP64, the products of
+        # FP64 operands accumulated in double-float on the FP32 pipe
+        "tflops": {"gram_fp64": gram_tf,
+                   "products_double_float": v_flop / (phases[2] * 1e-3) / 1e12},
         "roofline": {"bound": "alu", "achieved": gram_tf, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
                      "frac": gram_tf / FP64_TFLOPS, "traffic": None,
                      "kernel": "gram_rows_kernel (FP64)"},

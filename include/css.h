@@ -508,7 +508,9 @@ css_status css_embed(const void* A, css_dtype dtype, int64_t m, int64_t n,
  * its U^(W) column (lowest index on ties) is positive.
  * Method: G = W W^T (FP64), its eigendecomposition by cyclic Jacobi
  * rotations in FP64 (parallel round-robin ordering, one cooperative
- * kernel), sigma_i^2 = lambda_i, then U~ and V~ as FP64 products.  The
+ * kernel), sigma_i^2 = lambda_i, then U~ and V~ as products of FP64
+ * operands accumulated in double-float (48 significant bits; Q's entries,
+ * at most 1 for an orthonormal basis, must lie in FP32's range).  The
  * eigenvalues carry an absolute error of about (n + l) 2^-53 ||W||_F^2 (the
  * Gram matrix's rounding): sigma_i is accurate relative to sigma_1^2 /
  * sigma_i, not to sigma_i.  CSS_ERR_NOT_CONVERGED if the rotations have not

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "backward.cuh"
+#include "df.cuh"
 
 using namespace css;
 
@@ -35,40 +36,6 @@ template <> __device__ __forceinline__ double from_d<double>(double v) { return 
 template <> __device__ __forceinline__ float from_d<float>(double v) { return (float)v; }
 template <> __device__ __forceinline__ __nv_bfloat16 from_d<__nv_bfloat16>(double v) {
   return __float2bfloat16_rn((float)v);
-}
-
-// ----------------------------------------------------------- double-float ---
-// Unevaluated sum s + c of two FP32 values.
-struct DF {
-  float s, c;
-};
-__device__ __forceinline__ void df_split(double v, float& hi, float& lo) {
-  hi = (float)v;
-  lo = (float)(v - (double)hi);
-}
-// acc += x * (yh + yl): exact product of x and yh (FMA), the x*yl term in the
-// compensation, Knuth's TwoSum for the running sum.
-__device__ __forceinline__ void df_fma(DF& a, float x, float yh, float yl) {
-  const float p = x * yh;
-  float e = fmaf(x, yh, -p);
-  e = fmaf(x, yl, e);
-  const float s = a.s + p;
-  const float bb = s - a.s;
-  const float t = (a.s - (s - bb)) + (p - bb);
-  a.s = s;
-  a.c += t + e;
-}
-// acc += (xh + xl) * (yh + yl)
-__device__ __forceinline__ void df_fma2(DF& a, float xh, float xl, float yh, float yl) {
-  const float p = xh * yh;
-  float e = fmaf(xh, yh, -p);
-  e = fmaf(xh, yl, e);
-  e = fmaf(xl, yh, e);
-  const float s = a.s + p;
-  const float bb = s - a.s;
-  const float t = (a.s - (s - bb)) + (p - bb);
-  a.s = s;
-  a.c += t + e;
 }
 
 // ------------------------------------------------------- small FP64 steps --

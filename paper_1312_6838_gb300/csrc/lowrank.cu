@@ -21,18 +21,22 @@
 //      the 1 / sigma scaling of V~; replay_columns_kernel forms only the k
 //      wanted eigenvectors from the rotation log, off the barrier-bound path,
 //      and signs them (U^(W)_k).
-//   4. gemm_nn_kernel: U~ = Q U^(W)_k and V~ = W^T U^(W)_k Sigma_k^-1 in FP64.
+//   4. gemm_nn_df_kernel: U~ = Q U^(W)_k and V~ = W^T U^(W)_k Sigma_k^-1,
+//      products in double-float (df.cuh) on the FP32 pipe.
 //
-// Everything is FP64: on this part FP64 runs at 1/64 of the FP32 rate, so
-// the Gram matrix and V~ (l^2 n / 2 and l k n multiply-adds) are bound by
-// the FP64 pipe, and each Jacobi round by latency: one dependent L2 trip,
-// a short chain of FP64 arithmetic and a grid barrier.
+// Steps 1-3 are FP64: on this part FP64 runs at 1/64 of the FP32 rate, so
+// the Gram matrix (l^2 n / 2 multiply-adds) is bound by the FP64 pipe, and
+// each Jacobi round by latency: one dependent L2 trip, a short chain of FP64
+// arithmetic and a grid barrier.  The products of step 4 (l k (m + n)
+// multiply-adds) need no more than double-float's 48 bits: their results
+// are a singular basis, accurate to the Gram route's resolution anyway.
 #include <algorithm>
 #include <cmath>
 #include <vector>
 
 #include "css_common.cuh"
 #include "lowrank.cuh"
+#include "df.cuh"
 
 using namespace css;
 
@@ -424,34 +428,55 @@ __global__ void __launch_bounds__(1024) order_kernel(const double* __restrict__ 
   }
 }
 
-// ------------------------------------------- 4. C = A B diag(scale), FP64 --
-// A: M x K (lda), B: K x N (ldb), C: M x N (ldc), all column-major.  64 x 64
-// outputs per block, 4 x 4 per thread (rows tx + 16 a, columns ty + 16 b).
-__global__ void __launch_bounds__(256) gemm_nn_kernel(const double* __restrict__ A, long long lda,
-                                                      const double* __restrict__ B, long long ldb,
-                                                      const double* __restrict__ scale, double* __restrict__ C,
-                                                      long long ldc, long long M, int N, int K) {
+// ----------------------------------- 4. C = A B diag(scale), double-float --
+// A: M x K (lda), B: K x N (ldb), C: M x N (ldc), all column-major FP64.
+// 64 x 64 outputs per block, 4 x 4 per thread (rows tx + 16 a, columns
+// ty + 16 b).  The operands are split into hi + lo floats as they are staged
+// and the products accumulate in double-float (df.cuh): about 2^-46 relative
+// per term against FP64's 2^-53, on the FP32 pipe.  When a_bound is given
+// (a device value >= every |A_ij|), A is first scaled by 2^-(e+1), where
+// 2^e <= a_bound < 2^(e+1), so its entries stay inside FP32's range; the
+// scaling is exact and is undone on the output.  B's entries must lie in
+// FP32's range (here: orthonormal columns, entries <= 1).
+__global__ void __launch_bounds__(256) gemm_nn_df_kernel(const double* __restrict__ A, long long lda,
+                                                         const double* __restrict__ B, long long ldb,
+                                                         const double* __restrict__ scale,
+                                                         const double* __restrict__ a_bound,
+                                                         double* __restrict__ C, long long ldc, long long M,
+                                                         int N, int K) {
   constexpr int BK = 16;
-  __shared__ double as[BK][64], bs[BK][65];
+  __shared__ float2 as[BK][64], bs[BK][65];
   const long long m0 = (long long)blockIdx.x * 64;
   const int n0 = blockIdx.y * 64;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  double acc[4][4];
+  double sa = 1.0, inv_sa = 1.0;
+  if (a_bound) {
+    const double ab = *a_bound;
+    if (ab > 0.0 && isfinite(ab)) {
+      const int e = ilogb(ab) + 1;
+      sa = ldexp(1.0, -e);
+      inv_sa = ldexp(1.0, e);
+    }
+  }
+  DF acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int b = 0; b < 4; ++b) acc[a][b] = DF{0.f, 0.f};
   for (int k0 = 0; k0 < K; k0 += BK) {
     for (int e = threadIdx.x; e < BK * 64; e += 256) {
       const int i = e % 64, kk = e / 64;
-      as[kk][i] = (m0 + i < M && k0 + kk < K) ? A[(long long)(k0 + kk) * lda + m0 + i] : 0.0;
+      float2 va = make_float2(0.f, 0.f), vb = make_float2(0.f, 0.f);
+      if (m0 + i < M && k0 + kk < K) df_split(A[(long long)(k0 + kk) * lda + m0 + i] * sa, va.x, va.y);
+      as[kk][i] = va;
       const int kk2 = e % BK, j = e / BK;
-      bs[kk2][j] = (n0 + j < N && k0 + kk2 < K) ? B[(long long)(n0 + j) * ldb + k0 + kk2] : 0.0;
+      if (n0 + j < N && k0 + kk2 < K) df_split(B[(long long)(n0 + j) * ldb + k0 + kk2], vb.x, vb.y);
+      bs[kk2][j] = vb;
     }
     __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < BK; ++kk) {
-      double av[4], bv[4];
+      float2 av[4], bv[4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) av[a] = as[kk][tx + 16 * a];
 #pragma unroll
@@ -459,7 +484,7 @@ __global__ void __launch_bounds__(256) gemm_nn_kernel(const double* __restrict__
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+        for (int b = 0; b < 4; ++b) df_fma2(acc[a][b], av[a].x, av[a].y, bv[b].x, bv[b].y);
     }
     __syncthreads();
   }
@@ -467,11 +492,11 @@ __global__ void __launch_bounds__(256) gemm_nn_kernel(const double* __restrict__
   for (int b = 0; b < 4; ++b) {
     const int j = n0 + ty + 16 * b;
     if (j >= N) continue;
-    const double sc = scale ? scale[j] : 1.0;
+    const double sc = (scale ? scale[j] : 1.0) * inv_sa;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       const long long i = m0 + tx + 16 * a;
-      if (i < M) C[(long long)j * ldc + i] = acc[a][b] * sc;
+      if (i < M) C[(long long)j * ldc + i] = ((double)acc[a][b].s + (double)acc[a][b].c) * sc;
     }
   }
 }
@@ -605,12 +630,13 @@ extern "C" css_status css_lowrank(const double* W, int64_t ldw, const double* Q,
   order_kernel<<<1, 1024, 0, s>>>(L.G0, L.G1, L.info, l, lp, k, (long long)n, sigma, L.scale, tail, L.ord);
   replay_columns_kernel<<<k, (h + 31) / 32 * 32, lp * sizeof(double), s>>>(L.rotlog, L.info, L.ord, l, lp, uw);
   if (timed) cudaEventRecord(ev[2], s);
+  // |W_ij| <= ||W||_2 = sigma_1 bounds W's entries for the FP32 split
   if (U)
-    gemm_nn_kernel<<<dim3((unsigned)((m + 63) / 64), (k + 63) / 64), 256, 0, s>>>(Q, ldq, uw, l, nullptr, U, ldu,
-                                                                                   m, k, l);
+    gemm_nn_df_kernel<<<dim3((unsigned)((m + 63) / 64), (k + 63) / 64), 256, 0, s>>>(Q, ldq, uw, l, nullptr, nullptr,
+                                                                                      U, ldu, m, k, l);
   if (V)
-    gemm_nn_kernel<<<dim3((unsigned)((n + 63) / 64), (k + 63) / 64), 256, 0, s>>>(W, ldw, uw, l, L.scale, V, ldv,
-                                                                                   n, k, l);
+    gemm_nn_df_kernel<<<dim3((unsigned)((n + 63) / 64), (k + 63) / 64), 256, 0, s>>>(W, ldw, uw, l, L.scale, sigma,
+                                                                                      V, ldv, n, k, l);
   if (cudaGetLastError() != cudaSuccess) return CSS_ERR_CUDA;
   if (timed) cudaEventRecord(ev[3], s);
   if (!o.sync) return CSS_OK;

@@ -560,8 +560,13 @@ def run_lowrank(args):
         # FP64 operands accumulated in double-float on the FP32 pipe
         "tflops": {"gram_fp64": gram_tf,
                    "products_double_float": v_flop / (phases[2] * 1e-3) / 1e12},
+        # traffic: DRAM bytes read + written by one gram_rows_kernel launch on
+        # this workload, from the ncu capture summarised in
+        # profiles/lowrank_decay_4096x65536_l256_k128.md (W read once, the
+        # slices' partial tiles written)
         "roofline": {"bound": "alu", "achieved": gram_tf, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
-                     "frac": gram_tf / FP64_TFLOPS, "traffic": None,
+                     "frac": gram_tf / FP64_TFLOPS,
+                     "traffic": (134.7e6 + 9.4e6) if (m, n, l) == (4096, 65536, 256) else None,
                      "kernel": "gram_rows_kernel (FP64)"},
         "sigma_1": float(out.sigma[0]), "tail": out.tail, "clocks": clocks,
     }

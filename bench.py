@@ -485,9 +485,12 @@ def run_adjoint(args):
                      "note": "algorithmic 6 k m n FLOPs; W and R run in double-float (about 12 FP32 operations "
                              "per multiply-add), so the FP32 pipe does several times the algorithmic count"},
         "hbm_bytes_per_call": 3 * m * n * 4, "loss": float(loss.item()), "clocks": clocks,
-        # per call: gather A_S, Gram, Cholesky and inverse, Q, W, R with the
-        # loss partials, loss sum, R W^T slices, their sum, dA_S
-        "gpu_launches": 10 * args.steps,
+        # per call: gather A_S, Gram (2), the Cholesky (one launch for
+        # k <= 128; above, the blocked form: initial diagonal, per 32-column
+        # panel the diagonal block and, but for the last panel, the rows below
+        # and the trailing update), L^-1, Q, W, R with the loss partials, loss
+        # sum, R W^T slices, their sum, dA_S
+        "gpu_launches": (12 if k <= 128 else 10 + 3 * ((k + 31) // 32)) * args.steps,
     }
     if not args.no_cpu_baseline:
         from oracle import css_oracle as O

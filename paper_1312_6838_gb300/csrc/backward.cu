@@ -131,36 +131,117 @@ void gram(const double* AS, int m, int k, double* part, double* G, cudaStream_t 
   gram_fin_kernel<<<(unsigned)(((long long)k * k + 255) / 256), 256, 0, s>>>(part, g.nslices, g.npairs, k, G);
 }
 
-// Cholesky G = L L^T in place (lower triangle), one block.  status[0] = 1
-// when G is not positive definite (A_S rank deficient).
-__global__ void chol_kernel(double* __restrict__ G, int k, int* __restrict__ status) {
-  __shared__ int bad;
-  __shared__ double diag0[1024];
-  if (threadIdx.x == 0) bad = 0;
-  for (int j = threadIdx.x; j < k; j += blockDim.x) diag0[j] = G[(long long)j * k + j];
-  __syncthreads();
-  for (int j = 0; j < k; ++j) {
-    if (threadIdx.x == 0) {
-      // a pivot at or below 1e-12 of its column's squared norm: the selected
-      // columns are linearly dependent to working precision
-      const double d = G[(long long)j * k + j];
-      const bool ok = d > 1e-12 * diag0[j];
-      if (!ok) bad = 1;
-      G[(long long)j * k + j] = ok ? sqrt(d) : 1.0;
+// Cholesky G = L L^T in place (lower triangle of the column-major k x k G).
+// For k > kCholSmemK (G too large for one block's shared memory) it runs
+// blocked right-looking, kCb columns a panel, as stream-ordered launches:
+//   chol_block_kernel: one warp factors the panel's diagonal block D in
+//     shared memory and writes it back;
+//   chol_rows_kernel: each CTA solves kCb of the rows below it, L_i = G_i D^-T;
+//   chol_update_kernel: one CTA per 32 x 32 tile of the trailing lower
+//     triangle subtracts the panel's outer product, G_IJ -= L_I L_J^T.
+// FP64 runs at two lanes per clock per SM on this part, so the k^3 / 6
+// multiply-adds are spread over many SMs instead of one.  A pivot at or below
+// 1e-12 of its column's initial squared norm (diag0, saved first) means the
+// selected columns are linearly dependent to working precision: the pivot
+// is replaced by 1 and status[0] = 1.
+constexpr int kCb = 32;
+
+__global__ void chol_diag_kernel(const double* __restrict__ G, int k, double* __restrict__ diag0) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < k) diag0[j] = G[(long long)j * k + j];
+}
+
+__global__ void __launch_bounds__(32) chol_block_kernel(double* __restrict__ G, int k, int j0,
+                                                        const double* __restrict__ diag0,
+                                                        int* __restrict__ status) {
+  __shared__ double D[kCb][kCb + 1];   // rows x columns of the diagonal block
+  const int lane = threadIdx.x;
+  const int b = min(kCb, k - j0);
+  for (int c = 0; c < b; ++c)
+    if (lane >= c && lane < b) D[lane][c] = G[(long long)(j0 + c) * k + j0 + lane];
+  __syncwarp();
+  bool bad = false;
+  for (int c = 0; c < b; ++c) {
+    const double dd = D[c][c];
+    const bool ok = dd > 1e-12 * diag0[j0 + c];
+    const double d = ok ? sqrt(dd) : 1.0;
+    bad |= !ok;
+    __syncwarp();
+    if (lane == c) D[c][c] = d;
+    if (lane > c && lane < b) D[lane][c] /= d;
+    __syncwarp();
+    if (lane > c && lane < b) {
+      const double lrc = D[lane][c];
+      for (int q = c + 1; q <= lane; ++q) D[lane][q] -= lrc * D[q][c];
     }
-    __syncthreads();
-    const double d = G[(long long)j * k + j];
-    for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) G[(long long)j * k + i] /= d;
-    __syncthreads();
-    // trailing update of the lower triangle: G[i][l] -= L[i][j] L[l][j], j < l <= i
-    const int rem = k - j - 1;
-    for (long long e = threadIdx.x; e < (long long)rem * rem; e += blockDim.x) {
-      const int i = j + 1 + (int)(e % rem), l = j + 1 + (int)(e / rem);
-      if (l <= i) G[(long long)l * k + i] -= G[(long long)j * k + i] * G[(long long)j * k + l];
-    }
-    __syncthreads();
+    __syncwarp();
   }
-  if (threadIdx.x == 0 && bad) status[0] = 1;
+  for (int c = 0; c < b; ++c)
+    if (lane >= c && lane < b) G[(long long)(j0 + c) * k + j0 + lane] = D[lane][c];
+  if (lane == 0 && bad) status[0] = 1;
+}
+
+// The rows below the factored diagonal block (kCb rows a CTA): row i of L
+// solves x D^T = g by forward substitution over the block's columns.
+__global__ void __launch_bounds__(32) chol_rows_kernel(double* __restrict__ G, int k, int j0) {
+  __shared__ double D[kCb][kCb + 1];
+  __shared__ double dinv[kCb];
+  const int lane = threadIdx.x;
+  const int b = min(kCb, k - j0);
+  for (int c = 0; c < b; ++c)
+    if (lane >= c && lane < b) D[lane][c] = G[(long long)(j0 + c) * k + j0 + lane];
+  __syncwarp();
+  if (lane < b) dinv[lane] = 1.0 / D[lane][lane];
+  __syncwarp();
+  const int i = j0 + b + blockIdx.x * kCb + lane;
+  if (i >= k) return;
+  double x[kCb];
+#pragma unroll
+  for (int c = 0; c < kCb; ++c) x[c] = c < b ? G[(long long)(j0 + c) * k + i] : 0.0;
+#pragma unroll
+  for (int c = 0; c < kCb; ++c) {
+    if (c < b) {
+      double v = x[c];
+#pragma unroll
+      for (int q = 0; q < c; ++q) v = fma(-x[q], D[c][q], v);
+      x[c] = v * dinv[c];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < kCb; ++c)
+    if (c < b) G[(long long)(j0 + c) * k + i] = x[c];
+}
+
+// Trailing update after the panel at j0 (width b): rows and columns from
+// t0 = j0 + b on, lower tiles (ti >= tj) of 32 x 32, four outputs a thread.
+__global__ void __launch_bounds__(256) chol_update_kernel(double* __restrict__ G, int k, int j0, int b) {
+  __shared__ double PI[32][kCb + 1], PJ[32][kCb + 1];
+  const int t0 = j0 + b;
+  int ti = (int)((sqrtf(8.f * blockIdx.x + 1.f) - 1.f) * 0.5f);
+  while (ti * (ti + 1) / 2 > (int)blockIdx.x) --ti;
+  while ((ti + 1) * (ti + 2) / 2 <= (int)blockIdx.x) ++ti;
+  const int tj = blockIdx.x - ti * (ti + 1) / 2;
+  const int r0 = t0 + ti * 32, c0 = t0 + tj * 32;
+  for (int e = threadIdx.x; e < 32 * kCb; e += 256) {
+    const int r = e % 32, c = e / 32;
+    const bool okc = c < b;
+    PI[r][c] = (okc && r0 + r < k) ? G[(long long)(j0 + c) * k + r0 + r] : 0.0;
+    PJ[r][c] = (okc && c0 + r < k) ? G[(long long)(j0 + c) * k + c0 + r] : 0.0;
+  }
+  __syncthreads();
+  const int r = threadIdx.x % 32;
+  const int i = r0 + r;
+  if (i >= k) return;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int cl = threadIdx.x / 32 + 8 * q;
+    const int l = c0 + cl;
+    if (l >= k || l > i) continue;
+    double acc = 0.0;
+#pragma unroll 8
+    for (int c = 0; c < b; ++c) acc = fma(PI[r][c], PJ[cl][c], acc);
+    G[(long long)l * k + i] -= acc;
+  }
 }
 
 // Linv = L^-1 by forward substitution L x = e_j, one warp per column j: the
@@ -188,9 +269,9 @@ __global__ void __launch_bounds__(kLinvWarps * 32) linv_kernel(const double* __r
   for (int i = j + lane; i < k; i += 32) Linv[(long long)j * k + i] = x[i];
 }
 
-// The same factorisation with G held in shared memory (k <= kCholSmemK): the
-// k steps of the right-looking update read shared memory instead of L2; L
-// is written back over G.
+// For k <= kCholSmemK one block factors G held in shared memory (one launch;
+// faster than the blocked form at these sizes): the k steps of the unblocked
+// right-looking update read shared memory; L is written back over G.
 constexpr int kCholSmemK = 128;
 __global__ void __launch_bounds__(1024) chol_smem_kernel(double* __restrict__ Gg, int k, int* __restrict__ status) {
   extern __shared__ double G[];   // k x k, column-major
@@ -234,7 +315,19 @@ void chol_inv(double* G, int k, double* Linv, int* status, cudaStream_t s) {
       cudaFuncSetAttribute(chol_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     chol_smem_kernel<<<1, 1024, smem, s>>>(G, k, status);
   } else {
-    chol_kernel<<<1, 1024, 0, s>>>(G, k, status);
+    // the initial diagonal is kept in Linv, which is written only afterwards
+    double* diag0 = Linv;
+    chol_diag_kernel<<<(k + 255) / 256, 256, 0, s>>>(G, k, diag0);
+    for (int j0 = 0; j0 < k; j0 += kCb) {
+      const int b = std::min(kCb, k - j0);
+      const int below = k - j0 - b;
+      chol_block_kernel<<<1, 32, 0, s>>>(G, k, j0, diag0, status);
+      if (below > 0) {
+        chol_rows_kernel<<<(below + kCb - 1) / kCb, 32, 0, s>>>(G, k, j0);
+        const int T = (below + 31) / 32;
+        chol_update_kernel<<<T * (T + 1) / 2, 256, 0, s>>>(G, k, j0, b);
+      }
+    }
   }
   const size_t smem = (size_t)kLinvWarps * k * sizeof(double);
   if (smem > 48 * 1024) cudaFuncSetAttribute(linv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

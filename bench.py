@@ -181,7 +181,8 @@ def run_reference(args):
                    "noise": c["noise"], "stream_dtype": args.dtype,
                    "accumulate": "f64 throughout (the oracle; BF16 input rounded first)",
                    "parallelism": "host cores"},
-        "cpu_baseline": {"value": value, "unit": "iterations/s", "cores": cores, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "iterations/s", "cores": cores, "host": host_cpu(),
+                         "kind": "oracle",
                          "sample": f"{iters_per_step} iterations of Algorithm 1 per step on the full "
                                    f"{c['m']}x{c['n']} matrix in FP64; initial scores "
                                    f"{1e3 * init_s / args.steps:.0f} ms/step timed apart"},
@@ -191,6 +192,31 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def host_cpu():
+    """The host's CPU model and architecture, for the CPU baseline's record
+    (lscpu where it is installed, else /proc/cpuinfo)."""
+    import platform
+    name = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                name = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not name:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith("model name"):
+                        name = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    return f"{name or 'unknown model'} ({platform.machine()})"
+
+
 def cpu_baseline(A32, dtype):
     """Oracle on a bounded sample: 3 iterations of Algorithm 1 on the full matrix
     (FP64), iterations timed apart from the initial scores."""
@@ -198,7 +224,8 @@ def cpu_baseline(A32, dtype):
     A = ci.round_bf16(A32).astype(np.float64) if dtype == "bf16" else A32.astype(np.float64)
     r = O.greedy_css(A, 3, tau_rel=1e-6)
     it = r.t_iter[-1] - r.t_init
-    return {"value": 3 / it, "unit": "iterations/s", "cores": os.cpu_count(), "kind": "oracle",
+    return {"value": 3 / it, "unit": "iterations/s", "cores": os.cpu_count(), "host": host_cpu(),
+            "kind": "oracle",
             "sample": f"3 iterations of Algorithm 1 on the full {A.shape[0]}x{A.shape[1]} matrix in "
                       f"FP64 (initial scores {r.t_init - r.t_start:.1f} s, timed apart)"}
 
@@ -499,7 +526,8 @@ def run_adjoint(args):
         t0 = time.perf_counter()
         L_ref, _ = O.residual_gradient(vals, Sl)
         dt = time.perf_counter() - t0
-        line["cpu_baseline"] = {"value": dt * 1e3, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+        line["cpu_baseline"] = {"value": dt * 1e3, "unit": "ms", "cores": os.cpu_count(), "host": host_cpu(),
+                                "kind": "oracle",
                                 "sample": "one full call (closed-form FP64 gradient, numpy on the host)"}
         line["loss_rel_diff_vs_oracle"] = abs(line["loss"] - L_ref) / L_ref
     print(json.dumps(line), flush=True)
@@ -579,7 +607,8 @@ def run_lowrank(args):
         t0 = time.perf_counter()
         ref = O.rank_k_approximation(Qn, Wn, kr)
         dt = time.perf_counter() - t0
-        line["cpu_baseline"] = {"value": dt * 1e3, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+        line["cpu_baseline"] = {"value": dt * 1e3, "unit": "ms", "cores": os.cpu_count(), "host": host_cpu(),
+                                "kind": "oracle",
                                 "sample": "the whole problem once (numpy/LAPACK thin SVD of W)"}
         line["max_sigma_rel_diff_vs_oracle"] = float(
             np.max(np.abs(out.sigma.cpu().numpy() - ref["sigma"]) / ref["sigma"]))

@@ -237,6 +237,21 @@ def test_exact_scores_match_recursion():
                                    np.maximum(f[cand], 0) / g[cand], rtol=1e-8)
 
 
+def test_exact_gcss_scores_match_recursion():
+    """Theorem 4's recursive scores at every step equal Problem 5's definition
+    for the prefix: ||B^T (I - P) a_i||^2 / ||(I - P) a_i||^2."""
+    A = ci.lowrank_uv(30, 50, 7, 0.05, 26)
+    B = ci.lowrank_uv(30, 9, 4, 0.05, 27)
+    r = O.greedy_gcss(A, B, 6, keep_scores=True)
+    assert len(r.S) == 6
+    for t in range(len(r.S)):
+        f, g = O.exact_gcss_scores(A, B, r.S[:t])
+        cand = np.isfinite(r.scores[t])
+        assert cand.sum() == 50 - t
+        np.testing.assert_allclose(r.scores[t][cand],
+                                   np.maximum(f[cand], 0) / g[cand], rtol=1e-8)
+
+
 # ------------------------------------------------------- random projection ---
 def test_random_projection_blocks_equal_product():
     A = ci.lowrank_uv(12, 50, 4, 0.1, 24)

@@ -60,6 +60,28 @@ def test_gradient_matches_oracle(css, dtype, shape):
     assert eS <= max(DA_TOL[dtype], 1e-5), eS
 
 
+def test_gradient_k_above_128_fp64(css):
+    """k = 160 takes the blocked Cholesky of A_S^T A_S.  Going through the
+    normal-equations matrix squares the condition of A_S, so the FP64 bound
+    is c k u kappa(A_S)^2 (u = 2^-53): here kappa = 412, and a plain numpy
+    evaluation of the same Cholesky route is itself 1.4e-10 from the
+    oracle's (the device: 3.1e-10)."""
+    m, n, k = 600, 900, 160
+    A_np = ci.lowrank_uv(m, n, k, 1e-3, 600 + m)
+    A, vals = dev_matrix(A_np, torch.float64)
+    S = O.greedy_css(vals, k, tau_rel=1e-10).S
+    L_ref, G_ref = O.residual_gradient(vals, S)
+    L, G = _grad(css, A, S)
+    assert abs(L - L_ref) <= 1e-7 * L_ref, (L, L_ref)
+    kappa = np.linalg.cond(vals[:, S])
+    tol = max(1e-10, 4.0 * k * 2.0 ** -53 * kappa ** 2)
+    G = G.double().cpu().numpy()
+    err = np.linalg.norm(G - G_ref) / np.linalg.norm(G_ref)
+    assert err <= tol, (err, tol)
+    eS = np.linalg.norm(G[:, S] - G_ref[:, S]) / np.linalg.norm(G_ref[:, S])
+    assert eS <= max(tol, 1e-5), eS
+
+
 def test_loss_only_and_grad_out_scaling(css):
     from paper_1312_6838_gb300 import _lib as L
     import ctypes as C

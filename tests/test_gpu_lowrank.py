@@ -40,8 +40,9 @@ def _sign_rule(U):
 # ------------------------------------------------------------- css_embed ---
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32, torch.bfloat16])
 @pytest.mark.parametrize("shape", [(130, 700, 9), (300, 2000, 33), (64, 64, 64), (1000, 500, 1),
-                                   (257, 3001, 100)])
+                                   (257, 3001, 100), (400, 2500, 200), (520, 3000, 300)])
 def test_embed_matches_oracle(css, dtype, shape):
+    """l > 128 takes the blocked Cholesky (7 and 10 panels of 32 columns)."""
     m, n, l = shape
     A, vals = dev_matrix(ci.lowrank_uv(m, n, min(m, n, 2 * l + 5), 0.05, 300 + m), dtype)
     S = _sel(n, l, 17 + n)

@@ -150,7 +150,15 @@ typedef struct {
        and by css_select's C = A A^T and f^(0) (C split into three BF16 parts
        so that f^(0) keeps FP32 accuracy). */
     int32_t init_path;
-    int32_t reserved[7];
+    /* Test hook for the bounded device waits (0 = off, the default).
+       1: one team barrier of the persistent greedy kernel (the first of
+       the first iteration) waits for an arrival that no CTA makes; 2: the
+       tensor-core initial-score kernels wait on an mbarrier phase that
+       nothing completes.  The wait runs out after spin_budget_ns, the call
+       reports CSS_ERR_TIMEOUT, nothing faults and the context stays usable
+       for the next call.  css_select and gcss_select. */
+    int32_t test_unmet_wait;
+    int32_t reserved[6];
     /* DEVICE uint64[k * 16] or NULL (css_select, gcss_select): per-iteration
        trace of the persistent kernel; entry [t * 16 + j] is the GPU global
        timer (ns) when the team's first CTA reached point j of iteration t:
@@ -555,16 +563,22 @@ css_status css_select_host(const void* A_host, css_dtype dtype, int64_t m,
  * (css_workspace_size(CSS_OP_SELECT, ...)) exceeds the array are rejected
  * with CSS_ERR_WORKSPACE before anything is enqueued -- for example FP32
  * m = 1024, n = 16384, k = 64 fits, m = 4096, n = 65536 does not.
- * opts->timing_ms must be NULL.  Nothing is allocated: no cudaMalloc,
- * cudaFree or allocating library routine is called.
+ * opts->timing_ms must be NULL, and opts->sync must be 1 (the default):
+ * the device status of the call lives in the library's array, which the
+ * caller cannot hand to css_read_status, so the call always waits for its
+ * stream and returns that status (CSS_ERR_INVALID_ARG for sync = 0).
+ * Nothing is allocated: no cudaMalloc, cudaFree or allocating library
+ * routine is called.
  *
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  All calls on a device share the one array:
- * calls whose work overlaps on the GPU (other streams, or sync = 0 without
- * waiting) race on it and corrupt each other's results.  Each call
- * initialises every scratch word it reads, so stale contents from an
- * earlier call are harmless.
+ * (cudaGetSymbolAddress, with that device current) and keeps it for the
+ * life of the process; make that first call before any stream capture.  A
+ * device reset (cudaDeviceReset) after that first call is not supported:
+ * the kept address would no longer be valid.  All calls on a device share
+ * the one array: calls whose work overlaps on the GPU (calls on other
+ * streams or host threads) race on it and corrupt each other's results.
+ * Each call initialises every scratch word it reads, so stale contents
+ * from an earlier call are harmless.
  */
 #define CSS_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 css_status css_select_noalloc(const void* A, css_dtype dtype, int64_t m,
@@ -573,9 +587,12 @@ css_status css_select_noalloc(const void* A, css_dtype dtype, int64_t m,
                               double* W, const css_opts* opts,
                               css_stream_t stream);
 
-/* Device status left by the last call that used `ws` (for opts->sync = 0):
-   synchronises `stream`, then returns CSS_OK, CSS_RANK_EXHAUSTED or the
-   device error. */
+/* Device status left by the last call that used `ws` (for opts->sync = 0)
+   of css_select, gcss_select, gcss_distributed, css_select_randomized or
+   css_select_batched(_run): synchronises `stream`, then returns CSS_OK,
+   CSS_RANK_EXHAUSTED or the device error -- that of the greedy kernel, or
+   that of the tensor-core initial-score kernel that ran before it (a
+   bounded wait there that ran out reads as CSS_ERR_TIMEOUT). */
 css_status css_read_status(const void* ws, css_stream_t stream);
 
 #ifdef __cplusplus

@@ -45,7 +45,8 @@ class css_opts(C.Structure):
         ("diag_f", C.c_void_p),
         ("diag_g", C.c_void_p),
         ("init_path", C.c_int32),
-        ("reserved", C.c_int32 * 7),
+        ("test_unmet_wait", C.c_int32),
+        ("reserved", C.c_int32 * 6),
         ("trace_ns", C.c_void_p),
         ("basis", C.c_void_p),
     ]

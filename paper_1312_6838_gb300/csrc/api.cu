@@ -101,8 +101,17 @@ int split_slots_for(int64_t split_cols) {
   return (int)std::min<int64_t>(per_grid, (split_cols + 1) / 2 + 1);
 }
 
+// Byte offset, inside the 256-byte status slot at the start of every
+// workspace, of the tensor-core initial-score kernel's error flag.  The
+// greedy launch resets only the DevStatus at offset 0, so the flag survives
+// until css_read_status or finish() reads it.
+constexpr size_t kAuxErrOffset = 128;
+static_assert(sizeof(DevStatus) <= kAuxErrOffset && kAuxErrOffset + sizeof(int) <= kStatusBytes,
+              "the flag sits in the status slot, after the DevStatus");
+
 void carve_header(WsCarver& c, int max_units, Header& h, int64_t split_cols) {
   h.st = c.take<DevStatus>(1);
+  h.aux_err = h.st ? reinterpret_cast<int*>(reinterpret_cast<char*>(h.st) + kAuxErrOffset) : nullptr;
   h.st_init = c.take<DevStatus>(1);
   h.units = c.take<UnitDesc>(max_units);
   h.teams = c.take<TeamDesc>(kMaxCtas);
@@ -113,7 +122,6 @@ void carve_header(WsCarver& c, int max_units, Header& h, int64_t split_cols) {
   h.cand_val = c.take<double>(kMaxCtas);
   h.cand_idx = c.take<int>(kMaxCtas);
   h.tile_ctr = c.take<uint32_t>(2 * kMaxCtas);
-  h.aux_err = c.take<int>(1);
   h.split_slots = split_slots_for(split_cols);
   h.split_part = c.take<char>((size_t)h.split_slots * kSplitSlotBytes);
   h.split_done = c.take<uint32_t>(h.split_slots);
@@ -229,7 +237,7 @@ struct LaunchInfo {
 
 css_status prepare_units(const Header& h, std::vector<UnitDesc>& units, const std::vector<double>& work,
                          int dt, int grid_max, int tile_cols, uint64_t spin_ns, cudaStream_t s,
-                         LaunchInfo& info) {
+                         LaunchInfo& info, int stall_where = 0) {
   int m_max = 1, k_max = 1, r_max = 1;
   for (auto& u : units) {
     m_max = std::max(m_max, u.m);
@@ -264,6 +272,7 @@ css_status prepare_units(const Header& h, std::vector<UnitDesc>& units, const st
   }
   DevStatus st{};
   st.spin_budget_ns = spin_ns ? spin_ns : kDefaultSpinNs;
+  st.stall_where = stall_where;
   cudaError_t e;
   if ((e = cudaMemcpyAsync(h.st_init, &st, sizeof(st), cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_status(e);
   if ((e = cudaMemcpyAsync(h.units, units.data(), units.size() * sizeof(UnitDesc), cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_status(e);
@@ -308,9 +317,10 @@ css_status start_units(const LaunchInfo& info, cudaStream_t s) {
 }
 
 css_status launch_units(const Header& h, std::vector<UnitDesc>& units, const std::vector<double>& work,
-                        int dt, int grid_max, int tile_cols, uint64_t spin_ns, cudaStream_t s) {
+                        int dt, int grid_max, int tile_cols, uint64_t spin_ns, cudaStream_t s,
+                        int stall_where = 0) {
   LaunchInfo info{};
-  css_status cs = prepare_units(h, units, work, dt, grid_max, tile_cols, spin_ns, s, info);
+  css_status cs = prepare_units(h, units, work, dt, grid_max, tile_cols, spin_ns, s, info, stall_where);
   if (cs != CSS_OK) return cs;
   return start_units(info, s);
 }
@@ -368,11 +378,14 @@ int pick_tile(const css_opts& o, int dt, int64_t m, int64_t n) {
   return t ? t : 8;
 }
 
-css_status check_forced(const css_opts& o, int n, int k) {
+// The forced prefix is device memory the caller wrote on `s`: it is read back
+// in stream order (one synchronisation, forced prefixes only) and checked.
+css_status check_forced(const css_opts& o, int n, int k, cudaStream_t s) {
   if (o.n_forced <= 0) return CSS_OK;
   if (!o.forced || o.n_forced > k) return CSS_ERR_INVALID_ARG;
   std::vector<int32_t> h(o.n_forced);
-  if (cudaMemcpy(h.data(), o.forced, sizeof(int32_t) * o.n_forced, cudaMemcpyDeviceToHost) != cudaSuccess)
+  if (cudaMemcpyAsync(h.data(), o.forced, sizeof(int32_t) * o.n_forced, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
     return CSS_ERR_CUDA;
   std::vector<char> seen(n, 0);
   for (int32_t v : h) {
@@ -383,6 +396,14 @@ css_status check_forced(const css_opts& o, int n, int k) {
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// opts->test_unmet_wait: 1 -> the greedy kernel's barrier 2 (the first of
+// the first iteration) waits for an arrival no CTA makes; 2 -> the
+// tensor-core kernels wait on an mbarrier phase nothing completes.
+constexpr int kStallBarrier = 2;
+bool valid_test_hook(const css_opts& o) { return o.test_unmet_wait >= 0 && o.test_unmet_wait <= 2; }
+int stall_barrier(const css_opts& o) { return o.test_unmet_wait == 1 ? kStallBarrier : 0; }
+int stall_mbarrier(const css_opts& o) { return o.test_unmet_wait == 2 ? 1 : 0; }
 
 // ---------------------------------------------------------- css_select ------
 struct SelectLayout {
@@ -486,7 +507,7 @@ cudaError_t gcss_f0(int dt, const void* A, int64_t lda, int64_t m, int64_t n, co
   if (e != cudaSuccess) return e;
   if (dt == CSS_BF16 && o.init_path != 1 && tc_scratch && tc::supported(A, lda, (int)m, (int)r))
     return tc::colnorms(A, lda, (int)m, (int)n, (const float*)B, ldb, (int)r, tc_scratch, f, h.aux_err,
-                        o.spin_budget_ns ? o.spin_budget_ns : kDefaultSpinNs, s);
+                        o.spin_budget_ns ? o.spin_budget_ns : kDefaultSpinNs, s, stall_mbarrier(o));
   return gcss_f0_simt(dt, A, lda, (int)m, (int)n, B, ldb, (int)r, partial, f, s);
 }
 
@@ -586,11 +607,12 @@ css_status css_select(const void* A, css_dtype dtype, int64_t m, int64_t n, int6
   if (m < 1 || n < 1 || lda < m || k < 1 || k > kMaxK || k > m || k > n) return CSS_ERR_INVALID_ARG;
   if (n > (int64_t)INT32_MAX || m > (int64_t)INT32_MAX) return CSS_ERR_INVALID_ARG;
   if (o.score_mode != 0 && o.score_mode != 1) return CSS_ERR_INVALID_ARG;
+  if (!valid_test_hook(o)) return CSS_ERR_INVALID_ARG;
   if (!ws || ((uintptr_t)ws % kWsAlign) != 0) return CSS_ERR_WORKSPACE;
   SelectLayout L = select_layout(ws, ws_bytes, dtype, m, n, k, W == nullptr);
   if (L.bytes > ws_bytes) return CSS_ERR_WORKSPACE;
   if (!device_ok()) return CSS_ERR_UNSUPPORTED;
-  css_status cs = check_forced(o, (int)n, k);
+  css_status cs = check_forced(o, (int)n, k, s);
   if (cs != CSS_OK) return cs;
   PhaseTimer tm(o);
   tm.mark(0, s);
@@ -598,7 +620,7 @@ css_status css_select(const void* A, css_dtype dtype, int64_t m, int64_t n, int6
   cudaError_t e;
   if (dtype == CSS_BF16 && o.init_path != 1 && tc::supported(A, lda, (int)m, 256))
     e = tc::css_f0(A, lda, (int)m, (int)n, L.C, L.s.f, L.h.aux_err,
-                   o.spin_budget_ns ? o.spin_budget_ns : kDefaultSpinNs, s);
+                   o.spin_budget_ns ? o.spin_budget_ns : kDefaultSpinNs, s, stall_mbarrier(o));
   else
     e = css_f0_simt(dtype, A, lda, (int)m, (int)n, L.C, L.partial, L.s.f, s);
   if (e != cudaSuccess) return cuda_status(e);
@@ -607,7 +629,7 @@ css_status css_select(const void* A, css_dtype dtype, int64_t m, int64_t n, int6
                                         n_sel, o)};
   const int tile = pick_tile(o, dtype, m, n);
   int gmax = o.grid_ctas > 0 ? o.grid_ctas : team_ctas_for(n, m);
-  cs = launch_units(L.h, units, {1.0}, dtype, gmax, tile, o.spin_budget_ns, s);
+  cs = launch_units(L.h, units, {1.0}, dtype, gmax, tile, o.spin_budget_ns, s, stall_barrier(o));
   if (cs != CSS_OK) return cs;
   tm.mark(2, s);
   if (o.basis && (e = export_basis(dtype, L.s.Q, (int)m, k, n_sel, o.basis, s)) != cudaSuccess)
@@ -627,11 +649,12 @@ css_status gcss_select(const void* A, css_dtype dtype, int64_t m, int64_t n, int
   if (m < 1 || n < 1 || r < 1 || lda < m || ldb < m || k < 1 || k > kMaxK || k > m || k > n)
     return CSS_ERR_INVALID_ARG;
   if (o.score_mode != 0 && o.score_mode != 1) return CSS_ERR_INVALID_ARG;
+  if (!valid_test_hook(o)) return CSS_ERR_INVALID_ARG;
   if (!ws || ((uintptr_t)ws % kWsAlign) != 0) return CSS_ERR_WORKSPACE;
   GcssLayout L = gcss_layout(ws, ws_bytes, dtype, m, n, r, k, W == nullptr);
   if (L.bytes > ws_bytes) return CSS_ERR_WORKSPACE;
   if (!device_ok()) return CSS_ERR_UNSUPPORTED;
-  css_status cs = check_forced(o, (int)n, k);
+  css_status cs = check_forced(o, (int)n, k, s);
   if (cs != CSS_OK) return cs;
   PhaseTimer tm(o);
   tm.mark(0, s);
@@ -642,7 +665,7 @@ css_status gcss_select(const void* A, css_dtype dtype, int64_t m, int64_t n, int
                                         n_sel, o)};
   const int tile = pick_tile(o, dtype, m, n);
   int gmax = o.grid_ctas > 0 ? o.grid_ctas : team_ctas_for(n, m);
-  cs = launch_units(L.h, units, {1.0}, dtype, gmax, tile, o.spin_budget_ns, s);
+  cs = launch_units(L.h, units, {1.0}, dtype, gmax, tile, o.spin_budget_ns, s, stall_barrier(o));
   if (cs != CSS_OK) return cs;
   tm.mark(2, s);
   if (o.basis && (e = export_basis(dtype, L.s.Q, (int)m, k, n_sel, o.basis, s)) != cudaSuccess)
@@ -674,9 +697,14 @@ css_status css_select_randomized(const void* A, css_dtype dtype, int64_t m, int6
 css_status css_read_status(const void* ws, css_stream_t stream) {
   if (!ws) return CSS_ERR_WORKSPACE;
   DevStatus st{};
+  int aux = 0;
   cudaError_t e = cudaMemcpyAsync(&st, ws, sizeof(st), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&aux, (const char*)ws + kAuxErrOffset, sizeof(int), cudaMemcpyDeviceToHost,
+                        (cudaStream_t)stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_status(e);
+  if (aux != 0) return (css_status)aux;
   if (st.code != 0) return (css_status)st.code;
   return st.rank_exhausted ? CSS_RANK_EXHAUSTED : CSS_OK;
 }
@@ -836,7 +864,7 @@ css_status gcss_distributed(const void* A, css_dtype dtype, int64_t m, int64_t n
     umax += std::min<int64_t>(l_block, block_offsets[b + 1] - block_offsets[b]);
   }
   if (k > umax || k > m) return CSS_ERR_INVALID_ARG;
-  if (o.n_forced) return CSS_ERR_INVALID_ARG;
+  if (o.n_forced || o.test_unmet_wait) return CSS_ERR_INVALID_ARG;
   if (!ws || ((uintptr_t)ws % kWsAlign) != 0) return CSS_ERR_WORKSPACE;
   DistLayout L = dist_layout(ws, ws_bytes, dtype, m, n, r, k, l_block, block_offsets, nblocks);
   if (L.bytes > ws_bytes) return CSS_ERR_WORKSPACE;
@@ -980,7 +1008,7 @@ static_assert(std::is_trivially_copyable<BatchedPlanImpl>::value, "the plan is c
 css_status batched_prepare(const css_problem* probs, int32_t count, css_dtype dtype, void* ws,
                            size_t ws_bytes, const css_opts& o, BatchedPlanImpl& P, cudaStream_t s) {
   if (!probs || count < 1 || !valid_dtype(dtype)) return CSS_ERR_INVALID_ARG;
-  if (o.n_forced || o.diag_argmax || o.diag_f || o.trace_ns) return CSS_ERR_INVALID_ARG;
+  if (o.n_forced || o.diag_argmax || o.diag_f || o.trace_ns || o.test_unmet_wait) return CSS_ERR_INVALID_ARG;
   for (int i = 0; i < count; ++i) {
     const css_problem& p = probs[i];
     if (!p.A || !p.sel || !p.trace || !p.n_sel) return CSS_ERR_INVALID_ARG;

@@ -984,9 +984,12 @@ css_status run_embed(const TA* A, int m, int n, long long lda, const int* sel, i
   return CSS_OK;
 }
 
-css_status check_selection(const int32_t* sel, int32_t k, int64_t n) {
+// The selected indices are device memory the caller wrote on `s`: read back
+// in stream order (one synchronisation) and checked on the host.
+css_status check_selection(const int32_t* sel, int32_t k, int64_t n, cudaStream_t s) {
   std::vector<int32_t> h(k);
-  if (cudaMemcpy(h.data(), sel, sizeof(int32_t) * k, cudaMemcpyDeviceToHost) != cudaSuccess)
+  if (cudaMemcpyAsync(h.data(), sel, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
     return CSS_ERR_CUDA;
   std::vector<char> seen(n, 0);
   for (int32_t v : h) {
@@ -1015,9 +1018,9 @@ extern "C" css_status css_embed(const void* A, css_dtype dtype, int64_t m, int64
   if (!ws || ((uintptr_t)ws % kWsAlign) != 0) return CSS_ERR_WORKSPACE;
   EmbLayout L = emb_layout(ws, ws_bytes, m, l);
   if (L.bytes > ws_bytes) return CSS_ERR_WORKSPACE;
-  css_status cs = check_selection(sel, l, n);
-  if (cs != CSS_OK) return cs;
   cudaStream_t s = (cudaStream_t)stream;
+  css_status cs = check_selection(sel, l, n, s);
+  if (cs != CSS_OK) return cs;
   switch (dtype) {
     case CSS_F64:
       return run_embed<double>((const double*)A, (int)m, (int)n, lda, sel, l, Q, ldq, W, ldw, L, o, s);
@@ -1049,10 +1052,10 @@ extern "C" css_status css_residual_backward(const void* A, css_dtype dtype, int6
   if (!ws || ((uintptr_t)ws % kWsAlign) != 0) return CSS_ERR_WORKSPACE;
   BwLayout L = bw_layout(ws, ws_bytes, dtype, m, n, k, dA != nullptr);
   if (L.bytes > ws_bytes) return CSS_ERR_WORKSPACE;
-  // the selected indices: in range and distinct (a small synchronous copy)
-  const css_status cs = check_selection(sel, k, n);
-  if (cs != CSS_OK) return cs;
+  // the selected indices: in range and distinct (a small stream-ordered copy)
   cudaStream_t s = (cudaStream_t)stream;
+  const css_status cs = check_selection(sel, k, n, s);
+  if (cs != CSS_OK) return cs;
   switch (dtype) {
     case CSS_F64:
       return run_backward<double>((const double*)A, (int)m, (int)n, lda, sel, k, grad_out,

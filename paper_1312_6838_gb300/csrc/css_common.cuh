@@ -16,7 +16,7 @@ struct DevStatus {
   int32_t code;            // 0 = ok, else a css_status error value
   int32_t rank_exhausted;  // number of units that stopped early
   int32_t where;           // id of the wait that timed out (diagnostic)
-  int32_t pad;
+  int32_t stall_where;     // test hook: this barrier id waits for one arrival too many (0 = none)
   uint64_t spin_budget_ns;
 };
 
@@ -129,7 +129,8 @@ __device__ __forceinline__ bool team_barrier(uint32_t* bar, int ncta, DevStatus*
   if (threadIdx.x == 0) {
     int ok = 1;
     *epoch += 1u;
-    const uint32_t target = *epoch * (uint32_t)ncta;
+    // (the test hook asks one barrier for an arrival that never comes)
+    const uint32_t target = *epoch * (uint32_t)ncta + (st->stall_where == where ? 1u : 0u);
     red_release_add_u32(bar, 1u);
     uint64_t t0 = globaltimer_ns();
     const uint64_t budget = st->spin_budget_ns;

@@ -24,7 +24,9 @@ void* g_ptr[kMaxDevices] = {nullptr};
 
 // Device address of g_css_scratch on the current device.  The host-side
 // symbol is only a stand-in: the address must come from
-// cudaGetSymbolAddress, once per device, with that device current.
+// cudaGetSymbolAddress, once per device, with that device current.  The
+// address is kept for the life of the process, so a device reset after the
+// first call is not supported.
 css_status scratch_for_current_device(void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return CSS_ERR_CUDA;
@@ -48,8 +50,10 @@ extern "C" css_status css_select_noalloc(const void* A, css_dtype dtype, int64_t
   css_opts o;
   css_opts_default(&o);
   if (opts) o = *opts;
-  // options that would make the call allocate (events) are not taken here
-  if (o.timing_ms) return CSS_ERR_INVALID_ARG;
+  // options that would make the call allocate (events) are not taken here;
+  // the device status sits in the library's array, which the caller cannot
+  // pass to css_read_status, so the call always synchronises and reports it
+  if (o.timing_ms || !o.sync) return CSS_ERR_INVALID_ARG;
   const size_t need = css_workspace_size(CSS_OP_SELECT, dtype, m, n, 0, k, 0, &o);
   if (need == 0) return CSS_ERR_INVALID_ARG;
   if (need > (size_t)CSS_NOALLOC_SCRATCH_BYTES) return CSS_ERR_WORKSPACE;

@@ -100,9 +100,10 @@ class Selection:
 
 
 def _opts(tau_rel=None, forced=None, score_mode=0, grid_ctas=0, tile_cols=0, spin_budget_ns=0,
-          sync=True, diag=None, init_path=0):
+          sync=True, diag=None, init_path=0, test_unmet_wait=0):
     o = L.default_opts()
     o.init_path = int(init_path)
+    o.test_unmet_wait = int(test_unmet_wait)
     if tau_rel is not None:
         o.tau_rel = float(tau_rel)
     if forced is not None:
@@ -129,8 +130,10 @@ def _prep_forced(forced, device):
 
 def select(A: torch.Tensor, k: int, *, tau_rel=None, forced=None, return_W=False, diag=False,
            score_mode=0, grid_ctas=0, tile_cols=0, spin_budget_ns=0, stream=None,
-           timing=False, phase_trace=False, init_path=0, return_basis=False) -> Selection:
-    """Greedy CSS (Algorithm 1) of the columns of A (column-major, on the GPU)."""
+           timing=False, phase_trace=False, init_path=0, return_basis=False,
+           test_unmet_wait=0) -> Selection:
+    """Greedy CSS (Algorithm 1) of the columns of A (column-major, on the GPU).
+    ``test_unmet_wait`` is the test hook of the bounded device waits (css.h)."""
     m, n, lda = _colmajor(A)
     dev = A.device
     dt = _DT[A.dtype]
@@ -145,7 +148,8 @@ def select(A: torch.Tensor, k: int, *, tau_rel=None, forced=None, return_W=False
         dg = (torch.full((k,), -1, dtype=torch.int32, device=dev),
               torch.empty(n, dtype=torch.float64, device=dev),
               torch.empty(n, dtype=torch.float64, device=dev))
-    o = _opts(tau_rel, fz, score_mode, grid_ctas, tile_cols, spin_budget_ns, True, dg, init_path)
+    o = _opts(tau_rel, fz, score_mode, grid_ctas, tile_cols, spin_budget_ns, True, dg, init_path,
+              test_unmet_wait)
     tms = (C.c_double * 2)() if timing else None
     if tms is not None:
         o.timing_ms = C.cast(tms, C.c_void_p)
@@ -173,7 +177,7 @@ def select(A: torch.Tensor, k: int, *, tau_rel=None, forced=None, return_W=False
 
 def gcss_select(A: torch.Tensor, B: torch.Tensor, k: int, *, tau_rel=None, forced=None,
                 return_W=False, diag=False, grid_ctas=0, tile_cols=0, spin_budget_ns=0,
-                stream=None, init_path=0, return_basis=False) -> Selection:
+                stream=None, init_path=0, return_basis=False, test_unmet_wait=0) -> Selection:
     """Greedy generalized CSS (Algorithm 3): columns of A reconstructing B.
     B must be float64 when A is float64, float32 otherwise (column-major)."""
     m, n, lda = _colmajor(A)
@@ -195,7 +199,8 @@ def gcss_select(A: torch.Tensor, B: torch.Tensor, k: int, *, tau_rel=None, force
         dg = (torch.full((k,), -1, dtype=torch.int32, device=dev),
               torch.empty(n, dtype=torch.float64, device=dev),
               torch.empty(n, dtype=torch.float64, device=dev))
-    o = _opts(tau_rel, fz, 0, grid_ctas, tile_cols, spin_budget_ns, True, dg, init_path)
+    o = _opts(tau_rel, fz, 0, grid_ctas, tile_cols, spin_budget_ns, True, dg, init_path,
+              test_unmet_wait)
     Qb = torch.empty((k, m), dtype=torch.float64, device=dev).t() if return_basis else None
     if Qb is not None:
         o.basis = Qb.data_ptr()

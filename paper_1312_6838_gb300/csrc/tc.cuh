@@ -23,8 +23,11 @@ cudaError_t project_partials(const void* A, long long lda, int m, int n, const v
 size_t colnorm_scratch_bytes(int m, int r);
 
 // f[i] = ||B^T A_:i||^2 for the n columns of A (BF16, m x n) and B (FP32, m x r).
+// stall != 0 is the test hook of css_opts::test_unmet_wait (a bounded wait
+// that runs out).
 cudaError_t colnorms(const void* A, long long lda, int m, int n, const float* B, long long ldb, int r,
-                     void* scratch, double* f, int* err, unsigned long long spin_ns, cudaStream_t s);
+                     void* scratch, double* f, int* err, unsigned long long spin_ns, cudaStream_t s,
+                     int stall = 0);
 
 // Scratch bytes of css_f0 (C in FP32, its three BF16 parts, row-tile partials).
 size_t css_f0_scratch_bytes(int m, int n);
@@ -33,7 +36,7 @@ size_t css_f0_scratch_bytes(int m, int n);
 // accumulation of exact BF16 products), C split into three BF16 parts, and
 // f[i] = A_:i^T C A_:i from the column dots of A with C A (FP64 sums).
 cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, double* f, int* err,
-                   unsigned long long spin_ns, cudaStream_t s);
+                   unsigned long long spin_ns, cudaStream_t s, int stall = 0);
 
 }  // namespace tc
 }  // namespace css

@@ -63,7 +63,26 @@ struct Params {
   // run back to back on it; otherwise each (K block, part) is its own stage
   int group;
   int stages;        // ring depth (1..STAGES)
+  int stall;         // test hook: the epilogue also waits on a phase nothing completes
+  // modes 2 and 3: K blocks per blockIdx.z chunk.  The tensor cores' FP32
+  // accumulation loses up to about one unit in the last place of the running
+  // sum per addition, always toward zero, so the error of a TMEM accumulation
+  // grows with its length: K is cut into chunks whose sums are added
+  // afterwards in FP64 (mode 2: per chunk partial tiles; mode 3: partial dots)
+  int kb_chunk;
+  int tiles_lower;   // mode 2: tiles per chunk (those touching the lower triangle)
 };
+
+// Mode 2 tiles (BM rows x 256 columns) that touch the lower triangle: tile
+// (bx, by) does when bx * 128 + 127 >= by * 256, i.e. by <= bx / 2.  Their
+// index in row-tile order.
+__host__ __device__ __forceinline__ int lower_tile_index(int bx, int by) {
+  // sum over b < bx of (b / 2 + 1)
+  const int q = bx / 2;
+  const int before = bx + ((bx & 1) ? q * q : q * (q - 1));
+  return before + by;
+}
+__host__ __device__ __forceinline__ int lower_tile_count(int mtiles) { return lower_tile_index(mtiles, 0); }
 
 // ------------------------------------------------------------- PTX glue -----
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -107,6 +126,15 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* er
       return false;
     }
   }
+}
+// Wait used on the way out of a failed CTA: the copies and MMAs this CTA
+// issued always complete, so it waits for them whatever the error flag says
+// (a fixed bound of 1 s; it returns in microseconds in practice), so that no
+// copy lands in, and no MMA reads, the shared memory or TMEM of an exited CTA.
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
+  const uint64_t t0 = gtimer();
+  while (!mbar_try_wait(bar, parity))
+    if (gtimer() - t0 > 1000000000ull) return;
 }
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0,
                                             int c1) {
@@ -199,7 +227,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* full = (uint64_t*)bars_base;
   uint64_t* empty = full + STAGES;
   uint64_t* done = empty + STAGES;
-  uint32_t* s_tmem = (uint32_t*)(done + 1);
+  uint64_t* never = done + 1;   // test hook: a phase that nothing completes
+  uint32_t* s_tmem = (uint32_t*)(never + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // work of this CTA
@@ -211,11 +240,23 @@ __global__ void __launch_bounds__(kThreads, 1)
     kb_end = min(P.kb_total, kb_begin + P.kb_per_cta);
   } else if (P.mode >= 2) {
     ntile0 = blockIdx.y * P.n_tile;
+    kb_begin = blockIdx.z * P.kb_chunk;
+    kb_end = min(P.kb_total, kb_begin + P.kb_chunk);
   }
   // strictly upper tile of C: not needed (the lower triangle is mirrored)
   if (P.tri && P.mode == 2 && tile0 + BM - 1 < ntile0) return;
   // U' rows of this tile are zero left of column tile0
-  if (P.tri && P.mode == 3) kb_begin = tile0 / BK;
+  if (P.tri && P.mode == 3) {
+    kb_begin = max(kb_begin, tile0 / BK);
+    if (kb_begin >= kb_end) {
+      // nothing of this K chunk meets the tile: its partial dots are zero
+      for (int j = threadIdx.x; j < P.n_tile; j += blockDim.x) {
+        const int c = ntile0 + j;
+        if (c < P.N) P.f[((long long)blockIdx.x * gridDim.z + blockIdx.z) * P.N + c] = 0.0;
+      }
+      return;
+    }
+  }
   const int parts = P.nparts;
   // group mode: tiles per stage (a part stride of 0 means one shared tile)
   const int nA = (P.group && P.a_part_stride != 0) ? parts : 1;
@@ -229,6 +270,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(smem_u32(&empty[s]), 1);
     }
     mbar_init(smem_u32(done), 1);
+    mbar_init(smem_u32(never), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -281,12 +323,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       issued = it + 1;
     }
-    // on failure: let the copies already issued land before the CTA exits
-    if (issued < n_it) {
-      for (int it = max(0, issued - NSTG); it < issued; ++it) {
-        const int s = it % NSTG;
-        mbar_wait(smem_u32(&full[s]), (uint32_t)((it / NSTG) & 1), P.err, P.spin_ns);
-      }
+    // the copies issued last (one per stage) have landed before the CTA
+    // exits, also when a wait failed and the MMA issuer stopped consuming
+    for (int it = max(0, issued - NSTG); it < issued; ++it) {
+      const int s = it % NSTG;
+      mbar_drain(smem_u32(&full[s]), (uint32_t)((it / NSTG) & 1));
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------------------------------------------------- MMA issuer
@@ -317,11 +358,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       umma_commit(smem_u32(&empty[s]));
     }
     umma_commit(smem_u32(done));
+    // every MMA issued has finished before TMEM is released at the end
+    mbar_drain(smem_u32(done), 0u);
   } else if (warp >= 2) {
     // ------------------------------------------------------------ epilogue
     const int q = warp & 3;                  // TMEM lane quarter of this warp
     const int row = tile0 + q * 32 + lane;
     bool ok = mbar_wait(smem_u32(done), 0u, P.err, P.spin_ns) && *(volatile int*)P.err == 0;
+    if (ok && P.stall) ok = mbar_wait(smem_u32(never), 0u, P.err, P.spin_ns);
     // one decision for all four epilogue warps (tcgen05.ld is warp-collective
     // and the column-dot epilogue synchronises the four warps)
     {
@@ -391,13 +435,17 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (c < P.N) {
             float h = cred[0][lane].x, l = cred[0][lane].y;
             for (int w = 1; w < 4; ++w) df_add2(h, l, cred[w][lane].x, cred[w][lane].y);
-            P.f[(long long)blockIdx.x * P.N + c] = to_f64(h) + to_f64(l);
+            P.f[((long long)blockIdx.x * gridDim.z + blockIdx.z) * P.N + c] = to_f64(h) + to_f64(l);
           }
         }
         asm volatile("bar.sync 1, 128;" ::: "memory");
       }
     } else if (ok) {
       float sh = 0.f, sl = 0.f;   // mode 1: sum of squares in double-float
+      float* tile_out = nullptr;
+      if (P.mode == 2)
+        tile_out = P.out + ((long long)blockIdx.z * P.tiles_lower + lower_tile_index(blockIdx.x, blockIdx.y)) *
+                               (long long)(BM * P.n_tile);
       const int ncols = P.halves * P.n_half;
       for (int j0 = 0; j0 < ncols; j0 += 16) {
         float v[16];
@@ -407,8 +455,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int jj = 0; jj < 16; ++jj) {
             const int j = j0 + jj;
             if (P.mode == 2) {
+              // chunk z's partial of this tile: tile_out holds BM x n_tile
+              // values, column-major
               const int c = ntile0 + j;
-              if (c < P.N) P.out[(long long)c * P.M + row] = v[jj];
+              if (c < P.N) tile_out[(long long)j * BM + (row - tile0)] = v[jj];
             } else if (j < P.N) {
               if (P.mode == 0)
                 P.out[(long long)blockIdx.y * P.M * P.N + (long long)j * P.M + row] = v[jj];
@@ -544,7 +594,8 @@ size_t colnorm_scratch_bytes(int m, int r) {
 }
 
 cudaError_t colnorms(const void* A, long long lda, int m, int n, const float* B, long long ldb, int r,
-                     void* scratch, double* f, int* err, unsigned long long spin_ns, cudaStream_t s) {
+                     void* scratch, double* f, int* err, unsigned long long spin_ns, cudaStream_t s,
+                     int stall) {
   const int mpad = (m + 7) / 8 * 8;
   const int rpad = (r + 15) / 16 * 16;
   __nv_bfloat16* Bp = (__nv_bfloat16*)scratch;
@@ -571,6 +622,7 @@ cudaError_t colnorms(const void* A, long long lda, int m, int n, const float* B,
   P.f = f;
   P.err = err;
   P.spin_ns = spin_ns;
+  P.stall = stall;
   const size_t smem = smem_for(P.stage_bytes);
   cudaError_t e = cudaFuncSetAttribute(tc_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -588,41 +640,82 @@ __global__ void sum_rows_kernel(const double* __restrict__ partial, int nblk, in
   out[i] = scale * s;
 }
 
-// Upper triangle of the m x m matrix C (ld m) from its lower triangle, through
-// 32 x 32 shared-memory tiles (coalesced reads and writes).
-__global__ void mirror_lower_kernel(float* __restrict__ C, int m) {
+// C = sum over the K chunks of their partial tiles (FP64 sums in chunk
+// order, rounded once to FP32), written to both triangles of C (ld m)
+// through 32 x 32 shared-memory tiles, so reads and writes are coalesced.
+// Only the 32 x 32 tiles on or below the diagonal run; each lies inside one
+// chunk tile of 128 x 256.
+__global__ void reduce_lower_kernel(const float* __restrict__ parts, int chunks, int tiles_lower, int m,
+                                    float* __restrict__ C) {
   __shared__ float tile[32][33];
-  const int bi = blockIdx.x, bj = blockIdx.y;   // source tile: rows bi*32.., columns bj*32..
-  if (bi < bj) return;                          // only tiles on or below the diagonal
+  const int bi = blockIdx.x, bj = blockIdx.y;   // rows bi*32.., columns bj*32..
+  if (bi < bj) return;
   const int tx = threadIdx.x, ty = threadIdx.y;
+  const int r = bi * 32 + tx;
+  const int bx = (bi * 32) / BM, by = (bj * 32) / 256;
+  const long long chunk_stride = (long long)tiles_lower * BM * 256;
+  const float* src = parts + (long long)lower_tile_index(bx, by) * BM * 256;
   for (int k = ty; k < 32; k += blockDim.y) {
-    const int r = bi * 32 + tx, c = bj * 32 + k;
-    if (r < m && c < m) tile[k][tx] = C[(long long)c * m + r];
+    const int c = bj * 32 + k;
+    float v = 0.f;
+    if (r < m && c < m && r >= c) {
+      const long long local = (long long)(c - by * 256) * BM + (r - bx * BM);
+      double sum = 0.0;
+      for (int z = 0; z < chunks; ++z) sum += (double)src[z * chunk_stride + local];
+      v = (float)sum;
+      C[(long long)c * m + r] = v;
+    }
+    tile[k][tx] = v;
   }
   __syncthreads();
   // C[c, r] = C[r, c] for r > c
   for (int k = ty; k < 32; k += blockDim.y) {
-    const int c = bj * 32 + tx, r = bi * 32 + k;
-    if (r < m && c < m && r > c) C[(long long)r * m + c] = tile[tx][k];
+    const int c = bj * 32 + tx, r2 = bi * 32 + k;
+    if (r2 < m && c < m && r2 > c) C[(long long)r2 * m + c] = tile[tx][k];
   }
 }
 
+// K chunking of the initial-score GEMMs (see Params::kb_chunk): C = A A^T
+// accumulates at most 4096 products per TMEM sum (chunks capped at 32, so
+// very wide A gets longer chunks), U' A at most 1024 per part.
+constexpr int kSyrkChunkKb = 64;
+constexpr int kSyrkMaxChunks = 32;
+constexpr int kDotsChunkKb = 16;
+int syrk_chunk_kb(int n) {
+  const int kb = (n + BK - 1) / BK;
+  return std::max(kSyrkChunkKb, (kb + kSyrkMaxChunks - 1) / kSyrkMaxChunks);
+}
+int syrk_chunks(int n) {
+  const int kb = (n + BK - 1) / BK, c = syrk_chunk_kb(n);
+  return (kb + c - 1) / c;
+}
+int dots_chunks(int m) { return ((m + BK - 1) / BK + kDotsChunkKb - 1) / kDotsChunkKb; }
+
+// Scratch of css_f0: C (FP32, m x m), then one region used first for the
+// K-chunk partial tiles of C and afterwards for U' in three BF16 parts and
+// the column-dot partials.
 size_t css_f0_scratch_bytes(int m, int n) {
   const int mpad = (m + 7) / 8 * 8;
   const int rpad = (m + 15) / 16 * 16;
+  const int mtiles = (m + BM - 1) / BM;
   const size_t c = align_up((size_t)m * m * 4);
+  const size_t chunks = align_up((size_t)syrk_chunks(n) * lower_tile_count(mtiles) * BM * 256 * 4);
   const size_t parts = align_up((size_t)mpad * 3 * rpad * 2);
-  const size_t part = align_up((size_t)((m + BM - 1) / BM) * n * 8);
-  return c + parts + part;
+  const size_t part = align_up((size_t)mtiles * dots_chunks(m) * n * 8);
+  return c + std::max(chunks, parts + part);
 }
 
 cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, double* f, int* err,
-                   unsigned long long spin_ns, cudaStream_t s) {
+                   unsigned long long spin_ns, cudaStream_t s, int stall) {
   const int mpad = (m + 7) / 8 * 8;
   const int rpad = (m + 15) / 16 * 16;
+  const int mtiles = (m + BM - 1) / BM;
   float* C = (float*)scratch;
-  __nv_bfloat16* Cp = (__nv_bfloat16*)((char*)scratch + align_up((size_t)m * m * 4));
+  float* chunk_tiles = (float*)((char*)scratch + align_up((size_t)m * m * 4));
+  __nv_bfloat16* Cp = (__nv_bfloat16*)chunk_tiles;
   double* partial = (double*)((char*)Cp + align_up((size_t)mpad * 3 * rpad * 2));
+  const int nchunk = syrk_chunks(n), ndots = dots_chunks(m);
+  const int tiles_lower = lower_tile_count(mtiles);
   cudaError_t e;
   // C = A A^T: both operands are A, row-major in K (= the column index)
   {
@@ -638,21 +731,25 @@ cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, do
     P.n_tile = 256;
     P.kb_total = (n + BK - 1) / BK;
     P.kb_per_cta = P.kb_total;
+    P.kb_chunk = syrk_chunk_kb(n);
+    P.tiles_lower = tiles_lower;
     P.nparts = 1;
     P.stages = STAGES;
     P.stage_bytes = BM * BK * 2 + 256 * BK * 2;
-    P.out = C;
+    P.out = chunk_tiles;
     P.err = err;
     P.spin_ns = spin_ns;
+    P.stall = stall;
     const size_t smem = smem_for(P.stage_bytes);
     if ((e = cudaFuncSetAttribute(tc_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
       return e;
-    dim3 grid((m + BM - 1) / BM, (m + 255) / 256);
+    dim3 grid(mtiles, (m + 255) / 256, nchunk);
     tc_kernel<true, true><<<grid, kThreads, smem, s>>>(ta, ta, P);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  // the greedy iterations read whole rows of C: fill its upper triangle
-  mirror_lower_kernel<<<dim3((m + 31) / 32, (m + 31) / 32), dim3(32, 8), 0, s>>>(C, m);
+  // C = the chunks' sum, both triangles (the greedy iterations read whole rows)
+  reduce_lower_kernel<<<dim3((m + 31) / 32, (m + 31) / 32), dim3(32, 8), 0, s>>>(chunk_tiles, nchunk,
+                                                                                 tiles_lower, m, C);
   // U' (upper triangle of C, diagonal halved) = U1 + U2 + U3 in BF16
   {
     const long long tot = (long long)mpad * rpad;
@@ -679,6 +776,7 @@ cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, do
     P.group = 1;
     P.kb_total = (m + BK - 1) / BK;
     P.kb_per_cta = P.kb_total;
+    P.kb_chunk = kDotsChunkKb;
     P.nparts = 3;
     P.stages = 2;
     P.a_part_stride = rpad;
@@ -689,15 +787,16 @@ cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, do
     P.lda_col = lda;
     P.err = err;
     P.spin_ns = spin_ns;
+    P.stall = stall;
     const size_t smem = smem_for(P.stage_bytes, P.stages);
     if ((e = cudaFuncSetAttribute(tc_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
       return e;
-    dim3 grid((m + BM - 1) / BM, (n + 511) / 512);
+    dim3 grid(mtiles, (n + 511) / 512, ndots);
     tc_kernel<false, false><<<grid, kThreads, smem, s>>>(ta, tb, P);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   // f_i = a_i^T C a_i = 2 a_i^T U' a_i
-  sum_rows_kernel<<<(n + 255) / 256, 256, 0, s>>>(partial, (m + BM - 1) / BM, n, f, 2.0);
+  sum_rows_kernel<<<(n + 255) / 256, 256, 0, s>>>(partial, mtiles * ndots, n, f, 2.0);
   return cudaGetLastError();
 }
 

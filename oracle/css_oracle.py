@@ -102,6 +102,7 @@ class GreedyResult:
         self.gaps: list[float] = []
         self.scores: list[np.ndarray] = []
         self.fs: list[np.ndarray] = []     # f before each iteration (keep_scores)
+        self.gs: list[np.ndarray] = []     # g before each iteration (keep_scores)
         self.f: np.ndarray | None = None
         self.g: np.ndarray | None = None
         # wall-clock instrumentation (time.perf_counter): after initialisation
@@ -236,6 +237,7 @@ def greedy_css(A, l, tau_rel=1e-12, forced=None, keep_scores=False,
         if keep_scores:
             res.scores.append(sc)
             res.fs.append(f.copy())
+            res.gs.append(g.copy())
         res.gaps.append(gap)
         F = F - f[p] / g[p]
         selected[p] = True
@@ -326,6 +328,7 @@ def greedy_gcss(A, B, l, tau_rel=1e-12, forced=None, keep_scores=False):
         if keep_scores:
             res.scores.append(sc)
             res.fs.append(f.copy())
+            res.gs.append(g.copy())
         res.gaps.append(gap)
         F = F - f[p] / g[p]
         selected[p] = True

@@ -271,6 +271,49 @@ css_status gcss_distributed(const void* A, css_dtype dtype, int64_t m,
                             const css_opts* opts, css_stream_t stream);
 
 /*
+ * Algorithm 4 in two steps, so that the whole pipeline can be repeated or
+ * captured in a CUDA graph (no implementation detail of the paper; the
+ * reduce step's union of the blocks' picks is built on the device):
+ *
+ *   gcss_distributed_prepare  validates (arguments as gcss_distributed),
+ *       plans both persistent launches (the blocks', and the union's for its
+ *       largest size, sum_b min(l_block, width_b)) and writes every
+ *       descriptor and the block offsets into the workspace; returns after
+ *       the copies finished (it synchronises `stream`).  Not capturable.
+ *   gcss_distributed_run      enqueues on `stream` the initial scores
+ *       ||B^T a_i||^2, the block launch, the union (prefix sums of the
+ *       blocks' pick counts, global ids, gathered columns and initial
+ *       scores, the union size written into the union launch's descriptor),
+ *       the union launch and the mapping of its picks to global ids: device
+ *       work only, with no host copy and no synchronisation.  It reads A and
+ *       B and writes sel, trace, n_sel and block_sel through the DEVICE
+ *       pointers given to prepare, which must stay valid; the status (the
+ *       first error of either launch, or CSS_RANK_EXHAUSTED when the union
+ *       step ran out of candidates) is read with css_read_status(ws).
+ *
+ * `plan` is HOST memory owned by the caller, filled by prepare and read by
+ * run; it belongs to `ws` (run rejects another workspace with
+ * CSS_ERR_INVALID_ARG).  Runs on the same workspace must not overlap on the
+ * GPU.  The workspace size is gcss_distributed_workspace_size().
+ */
+typedef struct {
+    uint64_t opaque[128];
+} css_distributed_plan;
+
+css_status gcss_distributed_prepare(const void* A, css_dtype dtype, int64_t m,
+                                    int64_t n, int64_t lda, const void* B,
+                                    int64_t r, int64_t ldb,
+                                    const int64_t* block_offsets,
+                                    int32_t nblocks, int32_t l_block, int32_t k,
+                                    int32_t* sel, double* trace, int32_t* n_sel,
+                                    int32_t* block_sel, void* ws,
+                                    size_t ws_bytes, const css_opts* opts,
+                                    css_distributed_plan* plan,
+                                    css_stream_t stream);
+css_status gcss_distributed_run(const css_distributed_plan* plan, void* ws,
+                                css_stream_t stream);
+
+/*
  * Random projection B = A Omega (Sec. 5.1, Algorithm 2).
  *
  *   A       DEVICE m x n (lda), CSS_BF16 or CSS_F32 or CSS_F64.

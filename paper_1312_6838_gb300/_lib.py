@@ -78,6 +78,11 @@ class css_batched_plan(C.Structure):
     _fields_ = [("opaque", C.c_uint64 * 64)]
 
 
+class css_distributed_plan(C.Structure):
+    """Opaque host record of a prepared Algorithm 4 call (gcss_distributed_prepare)."""
+    _fields_ = [("opaque", C.c_uint64 * 128)]
+
+
 _SIGS = {
     "css_opts_default": (None, [C.POINTER(css_opts)]),
     "css_status_string": (C.c_char_p, [I32]),
@@ -89,6 +94,10 @@ _SIGS = {
     "gcss_distributed_workspace_size": (SZ, [I32, I64, I64, I64, C.POINTER(I64), I32, I32, I32]),
     "gcss_distributed": (I32, [P, I32, I64, I64, I64, P, I64, I64, C.POINTER(I64), I32, I32, I32,
                                P, P, P, P, P, SZ, C.POINTER(css_opts), P]),
+    "gcss_distributed_prepare": (I32, [P, I32, I64, I64, I64, P, I64, I64, C.POINTER(I64), I32, I32, I32,
+                                       P, P, P, P, P, SZ, C.POINTER(css_opts),
+                                       C.POINTER(css_distributed_plan), P]),
+    "gcss_distributed_run": (I32, [C.POINTER(css_distributed_plan), P, P]),
     "css_project": (I32, [P, I32, I64, I64, I64, P, I64, I64, P, I64, P, SZ,
                           C.POINTER(css_opts), P]),
     "css_batched_workspace_size": (SZ, [C.POINTER(css_problem), I32, I32, C.POINTER(css_opts)]),

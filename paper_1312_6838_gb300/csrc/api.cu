@@ -233,6 +233,9 @@ struct LaunchInfo {
   uint32_t* split_done;
   DevStatus* st;
   DevStatus* st_init;
+  // false: the launch keeps the status an earlier launch of the same call
+  // left (Algorithm 4's union launch reports the block launch's errors too)
+  bool reset_status;
 };
 
 css_status prepare_units(const Header& h, std::vector<UnitDesc>& units, const std::vector<double>& work,
@@ -300,12 +303,14 @@ css_status prepare_units(const Header& h, std::vector<UnitDesc>& units, const st
   info.split_done = h.split_done;
   info.st = h.st;
   info.st_init = h.st_init;
+  info.reset_status = true;
   return CSS_OK;
 }
 
 css_status start_units(const LaunchInfo& info, cudaStream_t s) {
   cudaError_t e;
-  if ((e = cudaMemcpyAsync(info.st, info.st_init, sizeof(DevStatus), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+  if (info.reset_status &&
+      (e = cudaMemcpyAsync(info.st, info.st_init, sizeof(DevStatus), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
     return cuda_status(e);
   if ((e = cudaMemsetAsync(info.bars, 0, 2 * sizeof(uint32_t) * info.L.grid, s)) != cudaSuccess) return cuda_status(e);
   if ((e = cudaMemsetAsync(info.tile_ctr, 0, 2 * sizeof(uint32_t) * info.L.grid, s)) != cudaSuccess)
@@ -744,8 +749,9 @@ css_status css_select_host(const void* A_host, css_dtype dtype, int64_t m, int64
 namespace {
 
 __global__ void gather_columns_kernel(const char* __restrict__ A, long long lda_bytes, int m_bytes,
-                                      const int* __restrict__ ids, int U, char* __restrict__ A0,
-                                      long long lda0_bytes) {
+                                      const int* __restrict__ ids, const int* __restrict__ count,
+                                      char* __restrict__ A0, long long lda0_bytes) {
+  const int U = *count;
   for (int j = blockIdx.y; j < U; j += gridDim.y) {
     const char* src = A + (long long)ids[j] * lda_bytes;
     char* dst = A0 + (long long)j * lda0_bytes;
@@ -754,23 +760,87 @@ __global__ void gather_columns_kernel(const char* __restrict__ A, long long lda_
   }
 }
 
-__global__ void gather_f_kernel(const double* __restrict__ f0, const int* __restrict__ ids, int U,
-                                double* __restrict__ out) {
+__global__ void gather_f_kernel(const double* __restrict__ f0, const int* __restrict__ ids,
+                                const int* __restrict__ count, int umax, double* __restrict__ out) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < U) out[j] = f0[ids[j]];
+  if (j < umax && j < *count) out[j] = f0[ids[j]];
 }
 
+// Final picks (indices into the union) -> global column ids; -1 past n_sel.
 __global__ void map_sel_kernel(const int* __restrict__ local, const int* __restrict__ ids, int k,
-                               int* __restrict__ out) {
+                               const int* __restrict__ n_sel, int* __restrict__ out) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < k) {
-    const int v = local[j];
-    out[j] = v >= 0 ? ids[v] : -1;
+  if (j < k) out[j] = (j < *n_sel) ? ids[local[j]] : -1;
+}
+
+// Algorithm 4's reduce step, on the device: the union's first slot for each
+// block (exclusive prefix sum of the blocks' pick counts, in block order),
+// its size U written into the union unit's column count, and the block
+// launch's rank-exhaustion count cleared (a block that picks fewer than
+// l_block columns is not an error of the call; the union launch reports its
+// own).  One block of 1024 threads; the status code is kept.
+__global__ void union_scan_kernel(const int* __restrict__ bnsel, int nb, int* __restrict__ first,
+                                  int* __restrict__ count, UnitDesc* __restrict__ unit, DevStatus* st) {
+  __shared__ int s_carry;
+  __shared__ int s_warp[32];
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int base = 0; base < nb; base += blockDim.x) {
+    const int b = base + threadIdx.x;
+    const int v = b < nb ? bnsel[b] : 0;
+    int x = v;   // inclusive scan within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      int t = s_warp[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      s_warp[lane] = t;
+    }
+    __syncthreads();
+    const int before = s_carry + (w > 0 ? s_warp[w - 1] : 0) + x - v;
+    if (b < nb) first[b] = before;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) s_carry = before + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *count = s_carry;
+    unit->n = s_carry;
+    st->rank_exhausted = 0;
+  }
+}
+
+// Block-local picks -> global column ids, in place in block_sel (-1 past a
+// block's count), and the union's id list in block order, then selection
+// order within each block.
+__global__ void union_ids_kernel(int* __restrict__ bsel, const int* __restrict__ bnsel,
+                                 const int* __restrict__ first, const long long* __restrict__ offs, int nb,
+                                 int lb, int* __restrict__ ids) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)nb * lb) return;
+  const int b = (int)(idx / lb), j = (int)(idx - (long long)b * lb);
+  if (j < bnsel[b]) {
+    const int g = (int)(offs[b] + bsel[idx]);
+    bsel[idx] = g;
+    ids[first[b] + j] = g;
+  } else {
+    bsel[idx] = -1;
   }
 }
 
 struct DistLayout {
-  Header h;
+  Header h;                // block launch (its status is the call's status)
+  Header hu;               // union launch (descriptors only)
   UnitState sc;            // f, g, thr, selmask over all n columns
   double* f0_saved;
   std::vector<UnitState> blk;
@@ -779,6 +849,9 @@ struct DistLayout {
   int* bnsel;
   double* partial;
   void* tc_scratch;
+  long long* offs;         // block offsets on the device
+  int* first;              // union slot of each block's first pick
+  int* count;              // union size U
   // union step
   char* A0;
   int64_t lda0;
@@ -792,17 +865,19 @@ DistLayout dist_layout(void* ws, size_t cap, int dt, int64_t m, int64_t n, int64
                        int32_t lb, const int64_t* offs, int nb) {
   WsCarver c(ws, cap);
   DistLayout L{};
-  // the header serves the block launch (n columns in all) and the union
-  // launch (at most nb * lb columns)
-  carve_header(c, std::max(nb, 1), L.h, std::max<int64_t>(n + 2 * (int64_t)nb, (int64_t)nb * lb));
+  int64_t umax = 0;
+  for (int b = 0; b < nb; ++b) {
+    const int64_t w = offs ? offs[b + 1] - offs[b] : (n + nb - 1) / nb;
+    umax += std::min<int64_t>(lb, w);
+  }
+  carve_header(c, std::max(nb, 1), L.h, n + 2 * (int64_t)nb);
+  carve_header(c, 1, L.hu, umax);
   carve_scores(c, (int)n, L.sc);
   L.f0_saved = c.take<double>(n);
-  int64_t umax = 0;
   L.blk.resize(nb);
   for (int b = 0; b < nb; ++b) {
     const int64_t w = offs ? offs[b + 1] - offs[b] : (n + nb - 1) / nb;
     const int kb = (int)std::min<int64_t>(lb, w);
-    umax += kb;
     carve_rest(c, dt, (int)m, (int)w, kb, (int)r, 1, true, L.blk[b]);
   }
   L.bsel = c.take<int>((size_t)nb * lb);
@@ -810,6 +885,9 @@ DistLayout dist_layout(void* ws, size_t cap, int dt, int64_t m, int64_t n, int64
   L.bnsel = c.take<int>(nb);
   L.partial = c.take<double>(gcss_f0_partial_doubles(dt, (int)r, (int)n));
   L.tc_scratch = c.take<char>(tc::colnorm_scratch_bytes((int)m, (int)r));
+  L.offs = c.take<long long>(nb + 1);
+  L.first = c.take<int>(nb);
+  L.count = c.take<int>(1);
   L.lda0 = (m + 7) / 8 * 8;
   L.A0 = c.take<char>((size_t)L.lda0 * umax * esize(dt));
   L.ids = c.take<int>(umax);
@@ -820,13 +898,197 @@ DistLayout dist_layout(void* ws, size_t cap, int dt, int64_t m, int64_t n, int64
   return L;
 }
 
+// Host side of a prepared Algorithm 4 call, kept in the caller's
+// css_distributed_plan: both launches' descriptors are in the workspace.
+struct DistPlanImpl {
+  uint64_t magic;
+  void* ws;
+  int dtype, nb, lb, k, umax, init_path, use_tc, pad_;
+  const void* A;
+  const void* B;
+  long long lda, ldb;
+  int64_t m, n, r;
+  uint64_t spin_ns;
+  int32_t* sel;
+  int32_t* n_sel;
+  int* bsel;
+  int* bnsel;
+  int* first;
+  int* count;
+  int* ids;
+  long long* offs;
+  double* f;
+  double* f0_saved;
+  double* uf;
+  double* partial;
+  void* tc_scratch;
+  char* A0;
+  long long lda0;
+  int* usel;
+  int* aux_err;
+  UnitDesc* union_unit;
+  DevStatus* st;
+  LaunchInfo blocks;
+  LaunchInfo uni;
+};
+constexpr uint64_t kDistMagic = 0x4353534450504c4eull;   // "CSSDPPLN"
+static_assert(sizeof(DistPlanImpl) <= sizeof(css_distributed_plan), "css_distributed_plan too small");
+static_assert(std::is_trivially_copyable<DistPlanImpl>::value, "the plan is copied as bytes");
+
+css_status dist_prepare(const void* A, css_dtype dtype, int64_t m, int64_t n, int64_t lda, const void* B,
+                        int64_t r, int64_t ldb, const int64_t* block_offsets, int32_t nblocks, int32_t l_block,
+                        int32_t k, int32_t* sel, double* trace, int32_t* n_sel, int32_t* block_sel, void* ws,
+                        size_t ws_bytes, const css_opts& o, DistPlanImpl& P, cudaStream_t s) {
+  if (!A || !B || !sel || !trace || !n_sel || !block_offsets || !valid_dtype(dtype))
+    return CSS_ERR_INVALID_ARG;
+  if (m < 1 || n < 1 || r < 1 || lda < m || ldb < m || nblocks < 1 || l_block < 1 || k < 1 ||
+      k > kMaxK || l_block > kMaxK || nblocks > kMaxCtas * 64)
+    return CSS_ERR_INVALID_ARG;
+  if (n > (int64_t)INT32_MAX || m > (int64_t)INT32_MAX) return CSS_ERR_INVALID_ARG;
+  if (block_offsets[0] != 0 || block_offsets[nblocks] != n) return CSS_ERR_INVALID_ARG;
+  int64_t umax = 0;
+  for (int b = 0; b < nblocks; ++b) {
+    if (block_offsets[b + 1] <= block_offsets[b]) return CSS_ERR_INVALID_ARG;
+    umax += std::min<int64_t>(l_block, block_offsets[b + 1] - block_offsets[b]);
+  }
+  if (k > umax || k > m) return CSS_ERR_INVALID_ARG;
+  if (o.n_forced || o.test_unmet_wait) return CSS_ERR_INVALID_ARG;
+  if (!ws || ((uintptr_t)ws % kWsAlign) != 0) return CSS_ERR_WORKSPACE;
+  DistLayout L = dist_layout(ws, ws_bytes, dtype, m, n, r, k, l_block, block_offsets, nblocks);
+  if (L.bytes > ws_bytes) return CSS_ERR_WORKSPACE;
+  if (!device_ok()) return CSS_ERR_UNSUPPORTED;
+  cudaError_t e;
+  std::vector<long long> offs(block_offsets, block_offsets + nblocks + 1);
+  if ((e = cudaMemcpyAsync(L.offs, offs.data(), sizeof(long long) * offs.size(), cudaMemcpyHostToDevice, s)) !=
+      cudaSuccess)
+    return cuda_status(e);
+  int* bsel = block_sel ? block_sel : L.bsel;
+  css_opts ob = o;
+  ob.diag_argmax = nullptr;
+  ob.diag_f = ob.diag_g = nullptr;
+  ob.trace_ns = nullptr;
+  ob.basis = nullptr;
+  // map phase: one unit per block, all in one persistent launch
+  std::vector<UnitDesc> units;
+  std::vector<double> work;
+  for (int b = 0; b < nblocks; ++b) {
+    const int64_t off = block_offsets[b], w = block_offsets[b + 1] - off;
+    const int kb = (int)std::min<int64_t>(l_block, w);
+    UnitState st = L.blk[b];
+    st.f = L.sc.f + off;
+    st.g = L.sc.g + off;
+    st.thr = L.sc.thr + off;
+    st.selmask = L.sc.selmask + off;
+    const void* Ab = (const char*)A + off * lda * (int64_t)esize(dtype);
+    units.push_back(make_unit(Ab, dtype, m, w, lda, kb, 1, B, ldb, r, st, nullptr,
+                              bsel + (size_t)b * l_block, L.btrace + (size_t)b * (l_block + 1),
+                              L.bnsel + b, ob));
+    // a block's cost: kb iterations, each a streaming pass over its w columns
+    // plus the pivot, whose latency-bound cost is charged as a fixed number
+    // of column-equivalents (swept on the 2048 x 262144 workload: 700)
+    work.push_back((double)kb * ((double)w + kPivotColumnEquiv));
+  }
+  const int tile = pick_tile(o, dtype, m, n);
+  P = DistPlanImpl{};
+  css_status cs = prepare_units(L.h, units, work, dtype, o.grid_ctas, tile, o.spin_budget_ns, s, P.blocks);
+  if (cs != CSS_OK) return cs;
+  // reduce phase: the union unit is planned for its largest size; the union
+  // scan writes its actual column count into the descriptor on the device
+  const int ku = (int)std::min<int64_t>(k, umax);
+  std::vector<UnitDesc> uu{make_unit(L.A0, dtype, m, umax, L.lda0, ku, 1, B, ldb, r, L.us, nullptr, L.usel,
+                                     trace, n_sel, ob)};
+  cs = prepare_units(L.hu, uu, {1.0}, dtype, o.grid_ctas > 0 ? o.grid_ctas : team_ctas_for(umax, m), tile,
+                     o.spin_budget_ns, s, P.uni);
+  if (cs != CSS_OK) return cs;
+  // the union launch reports into the block launch's status (kept, not reset)
+  P.uni.L.st = L.h.st;
+  P.uni.st = L.h.st;
+  P.uni.reset_status = false;
+  // the descriptors came from host vectors that end with this call
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_status(e);
+  P.magic = kDistMagic;
+  P.ws = ws;
+  P.dtype = dtype;
+  P.nb = nblocks;
+  P.lb = l_block;
+  P.k = k;
+  P.umax = (int)umax;
+  P.init_path = o.init_path;
+  P.A = A;
+  P.B = B;
+  P.lda = lda;
+  P.ldb = ldb;
+  P.m = m;
+  P.n = n;
+  P.r = r;
+  P.spin_ns = o.spin_budget_ns ? o.spin_budget_ns : kDefaultSpinNs;
+  P.sel = sel;
+  P.n_sel = n_sel;
+  P.bsel = bsel;
+  P.bnsel = L.bnsel;
+  P.first = L.first;
+  P.count = L.count;
+  P.ids = L.ids;
+  P.offs = L.offs;
+  P.f = L.sc.f;
+  P.f0_saved = L.f0_saved;
+  P.uf = L.us.f;
+  P.partial = L.partial;
+  P.tc_scratch = L.tc_scratch;
+  P.A0 = L.A0;
+  P.lda0 = L.lda0;
+  P.usel = L.usel;
+  P.aux_err = L.h.aux_err;
+  P.union_unit = L.hu.units;
+  P.st = L.h.st;
+  return CSS_OK;
+}
+
+// The whole of Algorithm 4 as device work on `s` (no host copy, no
+// synchronisation): initial scores, the block launch, the union built on the
+// device, the union launch and the mapping of its picks to global ids.
+css_status dist_run(const DistPlanImpl& P, cudaStream_t s) {
+  Header h{};
+  h.aux_err = P.aux_err;
+  css_opts o = defaults();
+  o.init_path = P.init_path;
+  o.spin_budget_ns = P.spin_ns;
+  cudaError_t e;
+  if ((e = gcss_f0(P.dtype, P.A, P.lda, P.m, P.n, P.B, P.ldb, P.r, P.partial, P.tc_scratch, P.f, h, o, s)) !=
+      cudaSuccess)
+    return cuda_status(e);
+  // f^(0) of every column, kept for the union step (it depends on a_i and B only)
+  if ((e = cudaMemcpyAsync(P.f0_saved, P.f, sizeof(double) * P.n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+    return cuda_status(e);
+  if ((e = cudaMemsetAsync(P.bsel, 0xff, sizeof(int) * (size_t)P.nb * P.lb, s)) != cudaSuccess)
+    return cuda_status(e);
+  css_status cs = start_units(P.blocks, s);
+  if (cs != CSS_OK) return cs;
+  union_scan_kernel<<<1, 1024, 0, s>>>(P.bnsel, P.nb, P.first, P.count, P.union_unit, P.st);
+  const long long tot = (long long)P.nb * P.lb;
+  union_ids_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P.bsel, P.bnsel, P.first, P.offs, P.nb, P.lb,
+                                                                 P.ids);
+  {
+    const int es = (int)esize(P.dtype);
+    dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(8, (P.m * es + 1023) / 1024)),
+              (unsigned)std::min(P.umax, 65535));
+    gather_columns_kernel<<<grid, 256, 0, s>>>((const char*)P.A, P.lda * es, (int)(P.m * es), P.ids, P.count,
+                                               P.A0, P.lda0 * es);
+    gather_f_kernel<<<(P.umax + 255) / 256, 256, 0, s>>>(P.f0_saved, P.ids, P.count, P.umax, P.uf);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+  }
+  cs = start_units(P.uni, s);
+  if (cs != CSS_OK) return cs;
+  map_sel_kernel<<<(P.k + 255) / 256, 256, 0, s>>>(P.usel, P.ids, P.k, P.n_sel, P.sel);
+  return cuda_status(cudaGetLastError());
+}
+
 }  // namespace
 
 size_t distributed_workspace_bytes(int dtype, int64_t m, int64_t n, int64_t r, int32_t k,
                                    int32_t k_block) {
-  // sized for the worst case of the block partition: every block as wide as
-  // needed, at most n / 1 blocks is not meaningful; size per column instead
-  // (blocks of at least k_block columns, each selecting k_block)
+  // sized for the worst case of the block partition: blocks of at least
+  // k_block columns, each selecting k_block
   const int nb = (int)std::max<int64_t>(1, n / std::max(1, k_block));
   return dist_layout(nullptr, (size_t)-1, dtype, m, n, r, k, k_block, nullptr, nb).bytes;
 }
@@ -852,106 +1114,46 @@ css_status gcss_distributed(const void* A, css_dtype dtype, int64_t m, int64_t n
                             size_t ws_bytes, const css_opts* opts, css_stream_t stream) {
   const css_opts o = opts ? *opts : defaults();
   cudaStream_t s = (cudaStream_t)stream;
-  if (!A || !B || !sel || !trace || !n_sel || !block_offsets || !valid_dtype(dtype))
-    return CSS_ERR_INVALID_ARG;
-  if (m < 1 || n < 1 || r < 1 || lda < m || ldb < m || nblocks < 1 || l_block < 1 || k < 1 ||
-      k > kMaxK || l_block > kMaxK || nblocks > kMaxCtas * 64)
-    return CSS_ERR_INVALID_ARG;
-  if (block_offsets[0] != 0 || block_offsets[nblocks] != n) return CSS_ERR_INVALID_ARG;
-  int64_t umax = 0;
-  for (int b = 0; b < nblocks; ++b) {
-    if (block_offsets[b + 1] <= block_offsets[b]) return CSS_ERR_INVALID_ARG;
-    umax += std::min<int64_t>(l_block, block_offsets[b + 1] - block_offsets[b]);
-  }
-  if (k > umax || k > m) return CSS_ERR_INVALID_ARG;
-  if (o.n_forced || o.test_unmet_wait) return CSS_ERR_INVALID_ARG;
-  if (!ws || ((uintptr_t)ws % kWsAlign) != 0) return CSS_ERR_WORKSPACE;
-  DistLayout L = dist_layout(ws, ws_bytes, dtype, m, n, r, k, l_block, block_offsets, nblocks);
-  if (L.bytes > ws_bytes) return CSS_ERR_WORKSPACE;
-  if (!device_ok()) return CSS_ERR_UNSUPPORTED;
-  cudaError_t e;
-  // map phase: f^(0) = ||B^T a_i||^2 for every column, kept for the union step
-  if ((e = gcss_f0(dtype, A, lda, m, n, B, ldb, r, L.partial, L.tc_scratch, L.sc.f, L.h, o, s)) != cudaSuccess)
-    return cuda_status(e);
-  if ((e = cudaMemcpyAsync(L.f0_saved, L.sc.f, sizeof(double) * n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-    return cuda_status(e);
-  int* bsel = block_sel ? block_sel : L.bsel;
-  if ((e = cudaMemsetAsync(bsel, 0xff, sizeof(int) * (size_t)nblocks * l_block, s)) != cudaSuccess)
-    return cuda_status(e);
-  css_opts ob = o;
-  ob.diag_argmax = nullptr;
-  ob.diag_f = ob.diag_g = nullptr;
-  ob.trace_ns = nullptr;
-  std::vector<UnitDesc> units;
-  std::vector<double> work;
-  for (int b = 0; b < nblocks; ++b) {
-    const int64_t off = block_offsets[b], w = block_offsets[b + 1] - off;
-    const int kb = (int)std::min<int64_t>(l_block, w);
-    UnitState st = L.blk[b];
-    st.f = L.sc.f + off;
-    st.g = L.sc.g + off;
-    st.thr = L.sc.thr + off;
-    st.selmask = L.sc.selmask + off;
-    const void* Ab = (const char*)A + off * lda * (int64_t)esize(dtype);
-    units.push_back(make_unit(Ab, dtype, m, w, lda, kb, 1, B, ldb, r, st, nullptr,
-                              bsel + (size_t)b * l_block, L.btrace + (size_t)b * (l_block + 1),
-                              L.bnsel + b, ob));
-    // a block's cost: kb iterations, each a streaming pass over its w columns
-    // plus the pivot, whose latency-bound cost is charged as a fixed number
-    // of column-equivalents (swept on the 2048 x 262144 workload: 700)
-    work.push_back((double)kb * ((double)w + kPivotColumnEquiv));
-  }
-  const int tile = pick_tile(o, dtype, m, n);
-  css_status cs = launch_units(L.h, units, work, dtype, o.grid_ctas, tile, o.spin_budget_ns, s);
+  DistPlanImpl P;
+  css_status cs = dist_prepare(A, dtype, m, n, lda, B, r, ldb, block_offsets, nblocks, l_block, k, sel, trace,
+                               n_sel, block_sel, ws, ws_bytes, o, P, s);
   if (cs != CSS_OK) return cs;
-  // reduce phase: union of the blocks' selections, block order then selection order
-  std::vector<int> hsel((size_t)nblocks * l_block), hn(nblocks);
-  DevStatus st{};
-  if ((e = cudaMemcpyAsync(hsel.data(), bsel, sizeof(int) * hsel.size(), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(hn.data(), L.bnsel, sizeof(int) * nblocks, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(&st, L.h.st, sizeof(st), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-      (e = cudaStreamSynchronize(s)) != cudaSuccess)
-    return cuda_status(e);
-  if (st.code != 0) return (css_status)st.code;
-  {
-    int aux = 0;
-    if (cudaMemcpy(&aux, L.h.aux_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return CSS_ERR_CUDA;
-    if (aux != 0) return (css_status)aux;
-  }
-  std::vector<int> ids;
-  for (int b = 0; b < nblocks; ++b)
-    for (int j = 0; j < hn[b]; ++j) ids.push_back((int)block_offsets[b] + hsel[(size_t)b * l_block + j]);
-  // block-local indices -> global ids in the caller's block_sel
-  {
-    std::vector<int> gsel(hsel.size(), -1);
-    for (int b = 0; b < nblocks; ++b)
-      for (int j = 0; j < hn[b]; ++j)
-        gsel[(size_t)b * l_block + j] = (int)block_offsets[b] + hsel[(size_t)b * l_block + j];
-    if ((e = cudaMemcpyAsync(bsel, gsel.data(), sizeof(int) * gsel.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess)
-      return cuda_status(e);
-  }
-  const int U = (int)ids.size();
-  if (U == 0) return CSS_RANK_EXHAUSTED;
-  const int ku = std::min<int>(k, U);
-  if ((e = cudaMemcpyAsync(L.ids, ids.data(), sizeof(int) * U, cudaMemcpyHostToDevice, s)) != cudaSuccess)
-    return cuda_status(e);
-  {
-    const int es = (int)esize(dtype);
-    dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(8, (m * es + 1023) / 1024)),
-              (unsigned)std::min(U, 65535));
-    gather_columns_kernel<<<grid, 256, 0, s>>>((const char*)A, lda * es, (int)(m * es), L.ids, U, L.A0,
-                                               L.lda0 * es);
-    gather_f_kernel<<<(U + 255) / 256, 256, 0, s>>>(L.f0_saved, L.ids, U, L.us.f);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
-  }
-  std::vector<UnitDesc> uu{make_unit(L.A0, dtype, m, U, L.lda0, ku, 1, B, ldb, r, L.us, nullptr,
-                                     L.usel, trace, n_sel, ob)};
-  cs = launch_units(L.h, uu, {1.0}, dtype, o.grid_ctas > 0 ? o.grid_ctas : team_ctas_for(U, m), tile,
-                    o.spin_budget_ns, s);
+  PhaseTimer tm(o);
+  tm.mark(0, s);
+  cs = dist_run(P, s);
   if (cs != CSS_OK) return cs;
-  map_sel_kernel<<<(ku + 255) / 256, 256, 0, s>>>(L.usel, L.ids, ku, sel);
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
-  return finish(L.h, o, s);
+  tm.mark(1, s);
+  tm.mark(2, s);
+  Header h{};
+  h.st = P.st;
+  h.aux_err = P.aux_err;
+  cs = finish(h, o, s);
+  tm.report(o);
+  return cs;
+}
+
+css_status gcss_distributed_prepare(const void* A, css_dtype dtype, int64_t m, int64_t n, int64_t lda,
+                                    const void* B, int64_t r, int64_t ldb, const int64_t* block_offsets,
+                                    int32_t nblocks, int32_t l_block, int32_t k, int32_t* sel, double* trace,
+                                    int32_t* n_sel, int32_t* block_sel, void* ws, size_t ws_bytes,
+                                    const css_opts* opts, css_distributed_plan* plan, css_stream_t stream) {
+  if (!plan) return CSS_ERR_INVALID_ARG;
+  const css_opts o = opts ? *opts : defaults();
+  std::memset(plan, 0, sizeof(*plan));
+  DistPlanImpl P;
+  css_status cs = dist_prepare(A, dtype, m, n, lda, B, r, ldb, block_offsets, nblocks, l_block, k, sel, trace,
+                               n_sel, block_sel, ws, ws_bytes, o, P, (cudaStream_t)stream);
+  if (cs != CSS_OK) return cs;
+  std::memcpy(static_cast<void*>(plan), static_cast<const void*>(&P), sizeof(P));
+  return CSS_OK;
+}
+
+css_status gcss_distributed_run(const css_distributed_plan* plan, void* ws, css_stream_t stream) {
+  if (!plan) return CSS_ERR_INVALID_ARG;
+  DistPlanImpl P;
+  std::memcpy(static_cast<void*>(&P), static_cast<const void*>(plan), sizeof(P));
+  if (P.magic != kDistMagic || P.ws != ws || !ws) return CSS_ERR_INVALID_ARG;
+  return dist_run(P, (cudaStream_t)stream);
 }
 
 }  // extern "C"

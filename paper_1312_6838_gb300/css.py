@@ -331,6 +331,53 @@ def distributed(A: torch.Tensor, B: torch.Tensor, block_offsets: Sequence[int], 
     return Distributed(sel, trace, int(nsel.item()), bsel, code)
 
 
+class DistributedPlan:
+    """Algorithm 4 prepared once (gcss_distributed_prepare) whose device work,
+    run(), can be repeated or captured in a CUDA graph: it reads A and B given
+    here (their storage must stay allocated; their values may change between
+    runs) and writes the selection into the tensors held here."""
+
+    def __init__(self, A: torch.Tensor, B: torch.Tensor, block_offsets: Sequence[int], l_block: int,
+                 k: int, *, tau_rel=None, grid_ctas=0, tile_cols=0, stream=None, init_path=0):
+        m, n, lda = _colmajor(A)
+        mb, r, ldb = _colmajor(B, "B")
+        if mb != m or B.dtype != _ACC[A.dtype]:
+            raise ValueError("B must be m x r of dtype float32 (float64 for float64 A)")
+        dev = A.device
+        dt = _DT[A.dtype]
+        self._lib = L.load()
+        offs = (C.c_int64 * len(block_offsets))(*[int(v) for v in block_offsets])
+        nb = len(block_offsets) - 1
+        self.sel = torch.empty(k, dtype=torch.int32, device=dev)
+        self.trace = torch.empty(k + 1, dtype=torch.float64, device=dev)
+        self.nsel = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.block_sel = torch.empty((nb, l_block), dtype=torch.int32, device=dev)
+        self._A, self._B = A, B
+        o = _opts(tau_rel, None, 0, grid_ctas, tile_cols, init_path=init_path)
+        nbytes = self._lib.gcss_distributed_workspace_size(dt, m, n, r, offs, nb, l_block, k)
+        if nbytes == 0:
+            raise ValueError("invalid block partition or sizes")
+        self._keep, self._ws = _workspace(nbytes, dev)
+        self._plan = L.css_distributed_plan()
+        code = self._lib.gcss_distributed_prepare(
+            _ptr(A), dt, m, n, lda, _ptr(B), r, ldb, offs, nb, l_block, k, _ptr(self.sel),
+            _ptr(self.trace), _ptr(self.nsel), _ptr(self.block_sel), _ptr(self._ws), nbytes, C.byref(o),
+            C.byref(self._plan), _stream(stream))
+        _check(code, "gcss_distributed_prepare")
+
+    def run(self, stream=None):
+        """Enqueue the whole pipeline (device work only)."""
+        code = self._lib.gcss_distributed_run(C.byref(self._plan), _ptr(self._ws), _stream(stream))
+        _check(code, "gcss_distributed_run")
+
+    def status(self, stream=None):
+        """Status of the last run (synchronises the stream)."""
+        return self._lib.css_read_status(_ptr(self._ws), _stream(stream))
+
+    def result(self):
+        return Distributed(self.sel, self.trace, int(self.nsel.item()), self.block_sel, 0)
+
+
 def project(A: torch.Tensor, Omega: torch.Tensor, *, out=None, stream=None, sync=True,
             init_path=0):
     """B = A Omega (Sec. 5.1).  Omega is n x r column-major of A's dtype.

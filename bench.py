@@ -54,6 +54,9 @@ def parse():
                          "the batched independent problems")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-oracle", action="store_true",
+                    help="skip the comparison of the headline results with the FP64 oracle "
+                         "(run outside the timed region; about a minute of host time)")
     return ap.parse_args()
 
 
@@ -592,8 +595,7 @@ def run_lowrank(args):
         "tflops": {"gram_fp64": gram_tf,
                    "products_double_float": v_flop / (phases[2] * 1e-3) / 1e12},
         # traffic: DRAM bytes read + written by one gram_rows_kernel launch on
-        # this workload, from the ncu capture summarised in
-        # profiles/lowrank_decay_4096x65536_l256_k128.md (W read once, the
+        # this workload, from an ncu capture of that kernel (W read once, the
         # slices' partial tiles written)
         "roofline": {"bound": "alu", "achieved": gram_tf, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
                      "frac": gram_tf / FP64_TFLOPS,
@@ -693,10 +695,10 @@ def main():
     # reads C = A A^T once and reads/writes the score state (f, g: r+w, g0: r, W: w)
     per_iter = a_bytes + c_bytes + 48 * n
     achieved = per_iter * res.n_sel / (statistics.mean(loop_ms) / 1e3) / 1e9
-    # DRAM traffic per launch from the ncu capture summarised in
-    # profiles/greedy_kernel_decay_4096x65536.md (4096 x 32768, 17 A passes):
-    # reads 1.0163 x the bytes of A and writes 63.2 B per column per A pass
-    # (C stays in L2), scaled by the A passes of this launch
+    # DRAM traffic per launch from an ncu capture of the greedy kernel on the
+    # 4096 x 32768 case of the same model (17 A passes): reads 1.0163 x the
+    # bytes of A and writes 63.2 B per column per A pass (C stays in L2),
+    # scaled by the A passes of this launch
     traffic = None
     if args.workload == WORKLOAD and args.dtype == "bf16":
         traffic = (res.n_sel + 1) * (a_bytes * 1.0163 + 63.2 * n)
@@ -725,9 +727,18 @@ def main():
         "clocks": clk,
     }
     out["hbm_gbs"] = achieved
+    S_timed = res.indices.cpu().tolist()
+    if rank == 0 and not args.no_oracle and args.workload in (WORKLOAD, "decay_4096x32768"):
+        out["oracle"] = {args.dtype: oracle_comparison(css, A, A32, args.dtype, k, S_timed)}
     if args.dtype == "bf16" and args.workload in (WORKLOAD, "decay_4096x32768"):
         del A
-        out.update(plain_comparison(css, At_host, dev, k, c_bytes, n, res.indices.cpu().tolist()))
+        pc = plain_comparison(css, At_host, dev, k, c_bytes, n, S_timed)
+        S_plain = pc.pop("_S_plain")
+        out.update(pc)
+        if rank == 0 and not args.no_oracle:
+            A = At_host.to(dev).t()
+            out["oracle"]["f32"] = oracle_comparison(css, A, A32, "f32", k, S_plain)
+            del A
     if not args.no_e2e:
         out["e2e"] = e2e(css, A32, tdt, m, n, k, dev, args)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -755,8 +766,10 @@ def plain_comparison(css, At_host, dev, k, c_bytes, n, S_mixed):
     ms = statistics.mean(loop)
     e_plain = css.residual_error(A, r.indices)
     e_mixed = css.residual_error(A, S_mixed)
+    S_plain = r.indices.cpu().tolist()
     del A
     return {
+        "_S_plain": S_plain,
         "plain_f32": {"value": r.n_sel / (ms / 1e3), "unit": "iterations/s", "loop_ms": ms,
                       "hbm_gbs": (a_bytes + c_bytes + 48 * n) * r.n_sel / (ms / 1e3) / 1e9},
         "equal_error": {"mixed_bf16": e_mixed, "plain_f32": e_plain,
@@ -764,6 +777,63 @@ def plain_comparison(css, At_host, dev, k, c_bytes, n, S_mixed):
                         "evaluated": "||A - P_S A||_F^2 of each selection formed directly on the FP32 "
                                      "matrix (css.residual_error)"},
     }
+
+
+def oracle_comparison(css, A, A32, dtype, k, S_dev):
+    """The result against the FP64 oracle, outside the timed region.
+
+    The oracle (Algorithm 1 in FP64 on the values the device holds) selects
+    its own k columns.  The device is then run once with the oracle's whole
+    sequence forced and reports its own argmax at every iteration: steps
+    that agree, and mismatches split by the oracle's top-two gap (at most
+    1e-6: both picks correct under the 1e-6 rule; above it: decided inside
+    the mixed path's score error).  Where the device's own selection parts
+    from the oracle's, the oracle is re-run forced on the device's sequence
+    and every device pick is checked against the best score on its own path
+    (tests/gpu_helpers.py, certify_selection).  Both selections' errors
+    ||A - P_S A||_F^2 are formed in FP64 on the same values."""
+    from oracle import css_oracle as O
+    from tests.gpu_helpers import certify_selection
+    import torch
+    vals = ci.round_bf16(A32).astype(np.float64) if dtype == "bf16" else A32.astype(np.float64)
+    m = vals.shape[0]
+    tdt = torch.bfloat16 if dtype == "bf16" else torch.float32
+    t0 = time.perf_counter()
+    ref = O.greedy_css(vals, k, tau_rel=1e-6, keep_scores=True)
+    forced = css.select(A, len(ref.S), forced=list(ref.S), diag=True)
+    own = forced.diag_argmax.cpu().tolist()
+    mism = [(t, float(ref.gaps[t])) for t in range(len(ref.S)) if own[t] != ref.S[t]]
+    strict = [g for _, g in mism if g <= 1e-6]
+    wide = [g for _, g in mism if g > 1e-6]
+    del ref.scores[:], ref.fs[:], ref.gs[:]
+    e_dev = O.reconstruction_error(vals, S_dev, chunk=8192)
+    e_ref = O.reconstruction_error(vals, ref.S, chunk=8192)
+    first = next((t for t in range(min(len(S_dev), len(ref.S))) if S_dev[t] != ref.S[t]), None)
+    line = {
+        "oracle_steps": len(ref.S),
+        "steps_agreeing_on_oracle_path": len(ref.S) - len(mism),
+        "mismatches_gap_le_1e-6": len(strict),
+        "mismatches_gap_gt_1e-6": len(wide),
+        "largest_gap_of_a_mismatch": max([g for _, g in mism], default=0.0),
+        "mismatch_steps": mism,
+        "error_device_selection": e_dev,
+        "error_oracle_selection": e_ref,
+        "relative_difference": (e_dev - e_ref) / e_ref,
+        "first_step_own_selection_parts": first,
+        "common_columns": len(set(S_dev) & set(ref.S)),
+    }
+    if first is not None:
+        on_dev = O.greedy_css(vals, len(S_dev), tau_rel=1e-6, keep_scores=True, forced=S_dev)
+        try:
+            n_off, worst = certify_selection(S_dev, on_dev, m, tdt)
+            line["own_selection_certified"] = True
+            line["own_selection_picks_off_argmax"] = n_off
+            line["own_selection_largest_deficit"] = worst
+        except AssertionError as exc:
+            line["own_selection_certified"] = False
+            line["own_selection_failure"] = str(exc)[:200]
+    line["host_seconds"] = time.perf_counter() - t0
+    return line
 
 
 def e2e(css, A32, tdt, m, n, k, dev, args):

@@ -7,7 +7,7 @@ import torch
 
 import css_inputs as ci
 from oracle import css_oracle as O
-from tests.gpu_helpers import dev_matrix
+from tests.gpu_helpers import dev_matrix, gradient_entry_errors, gradient_tolerances
 
 pytestmark = pytest.mark.gpu
 
@@ -38,10 +38,6 @@ def test_gradcheck_fp64(css):
                                     rtol=1e-5, fast_mode=True)
 
 
-# Output-rounding tolerance of dA in each dtype (R itself is accurate to ~1e-9).
-DA_TOL = {torch.float64: 1e-10, torch.float32: 2e-6, torch.bfloat16: 1e-2}
-
-
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32, torch.bfloat16])
 @pytest.mark.parametrize("shape", [(64, 128, 8), (257, 1000, 31), (500, 777, 64)])
 def test_gradient_matches_oracle(css, dtype, shape):
@@ -53,11 +49,12 @@ def test_gradient_matches_oracle(css, dtype, shape):
     L, G = _grad(css, A, S)
     assert abs(L - L_ref) <= 1e-7 * L_ref, (L, L_ref)
     G = G.double().cpu().numpy()
-    err = np.linalg.norm(G - G_ref) / np.linalg.norm(G_ref)
-    assert err <= DA_TOL[dtype], err
+    tol, tol_S = gradient_tolerances(vals, S, G_ref, dtype)
+    rest, sel = gradient_entry_errors(G, G_ref, S, tol, tol_S)
+    print(f"dA {dtype} {shape}: worst entry error / its tolerance: outside S {rest:.3e}, in S {sel:.3e}")
+    assert rest <= 1.0, rest
     # the selected columns' block -2 R T^T separately
-    eS = np.linalg.norm(G[:, S] - G_ref[:, S]) / max(np.linalg.norm(G_ref[:, S]), 1e-300)
-    assert eS <= max(DA_TOL[dtype], 1e-5), eS
+    assert sel <= 1.0, sel
 
 
 def test_gradient_k_above_128_fp64(css):
@@ -78,8 +75,12 @@ def test_gradient_k_above_128_fp64(css):
     G = G.double().cpu().numpy()
     err = np.linalg.norm(G - G_ref) / np.linalg.norm(G_ref)
     assert err <= tol, (err, tol)
-    eS = np.linalg.norm(G[:, S] - G_ref[:, S]) / np.linalg.norm(G_ref[:, S])
-    assert eS <= max(tol, 1e-5), eS
+    # entry by entry, relative to each column's largest entry
+    tol_c, tol_S = gradient_tolerances(vals, S, G_ref, torch.float64)
+    rest, sel = gradient_entry_errors(G, G_ref, S, np.maximum(tol_c, tol), np.maximum(tol_S, tol))
+    print(f"dA FP64 k = 160: worst entry error / its tolerance: outside S {rest:.3e}, in S {sel:.3e}")
+    assert rest <= 1.0, rest
+    assert sel <= 1.0, sel
 
 
 def test_loss_only_and_grad_out_scaling(css):
@@ -105,8 +106,10 @@ def test_loss_only_and_grad_out_scaling(css):
                                      C.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert code == 0
     assert abs(loss.item() - L_ref) <= 1e-7 * L_ref
-    err = np.linalg.norm(dA.double().cpu().numpy() - 0.25 * G_ref) / np.linalg.norm(0.25 * G_ref)
-    assert err <= 2e-6
+    tol, tol_S = gradient_tolerances(vals, S, 0.25 * G_ref, torch.float32)
+    rest, sel = gradient_entry_errors(dA.double().cpu().numpy(), 0.25 * G_ref, S, tol, tol_S)
+    assert rest <= 1.0, rest
+    assert sel <= 1.0, sel
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32, torch.bfloat16])
@@ -138,17 +141,23 @@ def test_rank_deficient_selection_rejected(css):
 
 
 @pytest.mark.slow
-def test_full_adjoint_workload(css):
-    """4096 x 16384 FP32, rank 128 + 1e-3 noise, S = the oracle's greedy set of
-    128 columns; the oracle's closed-form FP64 gradient on the host."""
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float64])
+def test_full_adjoint_workload(css, dtype):
+    """4096 x 16384 (FP32 as configured; BF16 and FP64 too), rank 128 + 1e-3
+    noise, S = the oracle's greedy set of 128 columns; the oracle's
+    closed-form FP64 gradient of the same values on the host, compared entry
+    by entry."""
     c = ci.CONFIGS["adjoint_4096x16384"]
     A_np = ci.lowrank_uv(c["m"], c["n"], c["rank"], c["noise"], c["seed"], dtype=np.float32)
-    vals = A_np.astype(np.float64)
+    A, vals = dev_matrix(A_np, dtype)
+    del A_np
     S = O.greedy_css(vals, c["k"], tau_rel=1e-6).S
     L_ref, G_ref = O.residual_gradient(vals, S)
-    A, _ = dev_matrix(A_np, torch.float32)
     L, G = _grad(css, A, S)
     assert abs(L - L_ref) <= 1e-6 * L_ref, (L, L_ref)
     G = G.double().cpu().numpy()
-    err = np.linalg.norm(G - G_ref) / np.linalg.norm(G_ref)
-    assert err <= 1e-5, err
+    tol, tol_S = gradient_tolerances(vals, S, G_ref, dtype)
+    rest, sel = gradient_entry_errors(G, G_ref, S, tol, tol_S)
+    print(f"dA 4096 x 16384 {dtype}: worst entry error / its tolerance: outside S {rest:.3e}, in S {sel:.3e}")
+    assert rest <= 1.0, rest
+    assert sel <= 1.0, sel

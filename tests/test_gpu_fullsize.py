@@ -2,10 +2,11 @@
 (default options), against the FP64 oracle on the same values:
 
 * the headline selection, 4096 x 65536 (1/i spectrum of rank 256 + 1e-3
-  noise), k = 256, streamed in BF16 and in FP32: step-by-step index parity
-  with teacher-forced replay where the oracle's top-two gap is below the
-  path's tolerance, the final error of the device's own selection, and
-  Theorem 1's recursive trace against the direct error at sampled steps;
+  noise), k = 256, streamed in BF16 and in FP32: the device's argmax at
+  every iteration of the oracle's path (teacher-forced), mismatches counted
+  by the oracle's gap and explained by the device's measured score errors,
+  the final error of the device's own selection within 1e-4 of the
+  oracle's, and Theorem 1's recursive trace against the direct error;
 * a signal-dominated matrix of the same shape (U V + 0.01 N, rank 256);
 * the distributed pipeline (Algorithm 4), 2048 x 262144 BF16, 64 log-normal
   blocks, l_block = 100, k = 100, on the oracle's own target B;
@@ -19,7 +20,8 @@ import torch
 
 import css_inputs as ci
 from oracle import css_oracle as O
-from tests.gpu_helpers import GAP_TOL, dev_matrix, first_mismatch, score_error_bound, teacher_forced_parity
+from tests.gpu_helpers import (GAP_TOL, certify_selection, dev_matrix, first_mismatch, oracle_path_parity,
+                               pair_error_bound)
 
 pytestmark = pytest.mark.gpu
 
@@ -33,8 +35,18 @@ def css():
     return mod
 
 
+def _forced_runner(css, A):
+    return lambda prefix, k, diag: css.select(A, k, forced=prefix if prefix else None, diag=diag)
+
+
 @pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float32])
 def test_headline_selection_full_size(css, dtype):
+    """Every iteration on the oracle's path: the device's own argmax against
+    the oracle's pick (oracle_path_parity counts the steps that agree, the
+    mismatches at gaps up to 1e-6 and those above it, and checks the
+    device's measured score errors against the derived bound at sampled
+    steps); then the final error of the device's own selection within the
+    the benchmark spec's 1e-4 of the oracle's."""
     c = ci.CONFIGS["decay_4096x65536"]
     m, n, k = c["m"], c["n"], c["k"]
     A32 = ci.lowrank_decaying(m, n, c["rank"], c["noise"], c["seed"], dtype=np.float32)
@@ -42,9 +54,10 @@ def test_headline_selection_full_size(css, dtype):
     del A32
     ref = O.greedy_css(vals, k, tau_rel=1e-6, keep_scores=True)
     assert len(ref.S) == k
-    restarts = teacher_forced_parity(
-        lambda forced: css.select(A, k, forced=forced if forced else None).indices.cpu().tolist(),
-        ref, m=m, dtype=dtype, max_rounds=k)
+    stats = oracle_path_parity(_forced_runner(css, A), ref, m, dtype, 1e-6,
+                               sample_steps=(1, 16, 128, 255))
+    print(f"headline {dtype}: {stats.as_dict()}")
+    assert stats.agree + stats.strict + stats.widened == k
     res = css.select(A, k)
     S = res.indices.cpu().tolist()
     tr = res.trace.cpu().numpy()
@@ -54,10 +67,9 @@ def test_headline_selection_full_size(css, dtype):
     # final error of the device's own selection against the oracle's
     e_gpu = O.reconstruction_error(vals, S, chunk=8192)
     e_ref = O.reconstruction_error(vals, ref.S, chunk=8192)
-    if restarts == 0:
-        assert abs(e_gpu - e_ref) <= 1e-4 * e_ref
-    else:
-        assert e_gpu <= e_ref * 1.01
+    print(f"headline {dtype}: final error device {e_gpu!r}, oracle {e_ref!r}, "
+          f"relative difference {(e_gpu - e_ref) / e_ref:.3e}")
+    assert abs(e_gpu - e_ref) <= 1e-4 * e_ref
     # Theorem 1's recursion against the direct error of the same prefix
     for t in (1, 2, 4, 16, 64, 256):
         direct = O.reconstruction_error(vals, S[:t], chunk=8192)
@@ -67,29 +79,31 @@ def test_headline_selection_full_size(css, dtype):
 def test_signal_dominated_selection_full_size(css):
     """The U V + 0.01 N model of the small FP64 configuration at the headline
     shape (4096 x 65536, rank 256, k = 256, BF16 stream): the signal is far
-    above the noise, so most top-two gaps are wide; step-by-step index parity
-    (teacher-forced where the gap is within the path's tolerance), the final
-    error, and Theorem 1's trace against the direct error."""
+    above the noise, so most top-two gaps are wide.  Every iteration on the
+    oracle's path as for the headline, the final error, and Theorem 1's trace
+    against the direct error."""
     m, n, k = 4096, 65536, 256
     A32 = ci.lowrank_uv(m, n, 256, 0.01, 7, dtype=np.float32)
     A, vals = dev_matrix(A32, torch.bfloat16)
     del A32
     ref = O.greedy_css(vals, k, tau_rel=1e-6, keep_scores=True)
     assert len(ref.S) == k
-    restarts = teacher_forced_parity(
-        lambda forced: css.select(A, k, forced=forced if forced else None).indices.cpu().tolist(),
-        ref, m=m, dtype=torch.bfloat16, max_rounds=k)
+    stats = oracle_path_parity(_forced_runner(css, A), ref, m, torch.bfloat16, 1e-6,
+                               sample_steps=(1, 64, 192, 255))
+    print(f"signal-dominated: {stats.as_dict()}")
     res = css.select(A, k)
     S = res.indices.cpu().tolist()
     tr = res.trace.cpu().numpy()
     e_gpu = O.reconstruction_error(vals, S, chunk=8192)
     e_ref = O.reconstruction_error(vals, ref.S, chunk=8192)
-    # the last picks of a rank-256 signal are ill-conditioned, so after a
-    # near-tie the two valid paths end at errors up to about a percent apart
-    if restarts == 0:
+    print(f"signal-dominated: final error device {e_gpu!r}, oracle {e_ref!r}, "
+          f"relative difference {(e_gpu - e_ref) / e_ref:.3e}")
+    if S == list(ref.S):
         assert abs(e_gpu - e_ref) <= 1e-4 * e_ref, (e_gpu, e_ref)
     else:
-        assert e_gpu <= e_ref * 1.01, (restarts, e_gpu, e_ref)
+        # parted at a near-tie: the device's own selection is not worse than
+        # the oracle's by more than the north star's 1e-4
+        assert e_gpu <= e_ref * (1 + 1e-4), (e_gpu, e_ref)
     # Theorem 1's recursion: the mixed path's scores come from FP32 dot
     # products, so the trace's error is absolute, a small multiple of 1e-7 of
     # the initial scores per step.  On this matrix the error itself falls to
@@ -123,22 +137,36 @@ def test_distributed_pipeline_full_size(css):
     # oracle's, both evaluated in FP64 on the same B
     e_gpu = O.reconstruction_error(vals, S, B64)
     e_ref = O.reconstruction_error(vals, final, B64)
-    if S == list(final):
-        assert abs(e_gpu - e_ref) <= 1e-4 * e_ref, (e_gpu, e_ref)
-    else:
-        assert e_gpu <= e_ref * 1.01, (e_gpu, e_ref)
-    # every block's selection: where the device's and the oracle's picks part
-    # (near-ties under the mixed path's score error), the block's GCSS error
-    # of the device's picks is as good to 1 percent
+    print(f"distributed: final GCSS error device {e_gpu!r}, oracle {e_ref!r}, "
+          f"relative difference {(e_gpu - e_ref) / e_ref:.3e}")
+    # every block's selection: identical to the oracle's, or (where the two
+    # part at a near-tie under the mixed path's score error) a greedy GCSS
+    # selection within the rule on its own path (initial scores ||B^T a_i||^2
+    # are dot products of length m)
     bsel = got.block_sel.cpu().numpy()
+    union = []
+    parted = 0
     for b, ids in enumerate(per_block):
         dev = [int(v) for v in bsel[b] if v >= 0]
         assert len(dev) == len(ids), b
+        union += dev
         if dev != ids:
+            parted += 1
             lo, hi = offs[b], offs[b + 1]
-            e_d = O.reconstruction_error(vals[:, lo:hi], [j - lo for j in dev], B64)
-            e_o = O.reconstruction_error(vals[:, lo:hi], [j - lo for j in ids], B64)
-            assert e_d <= e_o * 1.01, (b, e_d, e_o)
+            local = [j - lo for j in dev]
+            ref_b = O.greedy_gcss(vals[:, lo:hi], B64, len(local), tau_rel=1e-6, keep_scores=True,
+                                  forced=local)
+            certify_selection(local, ref_b, m, torch.bfloat16)
+    # the union step on the device's own union (block order, then selection
+    # order): the final picks are greedy GCSS picks within the rule
+    pos = {j: i for i, j in enumerate(union)}
+    local = [pos[j] for j in S]
+    ref_u = O.greedy_gcss(vals[:, union], B64, len(local), tau_rel=1e-6, keep_scores=True, forced=local)
+    n_off, worst = certify_selection(local, ref_u, m, torch.bfloat16)
+    print(f"distributed: {parted} of {len(per_block)} blocks parted from the oracle's picks; "
+          f"union step: {n_off} picks off the oracle's argmax, largest deficit {worst:.3e}")
+    if S == list(final):
+        assert abs(e_gpu - e_ref) <= 1e-4 * e_ref, (e_gpu, e_ref)
 
 
 def test_batched_workload_full_size(css):
@@ -166,11 +194,14 @@ def test_batched_workload_full_size(css):
         # there the oracle's gap must be within the FP32 path's score error
         t = first_mismatch(S, list(ref.S))
         if t is not None:
-            tol = max(GAP_TOL, score_error_bound(ref, t, m, torch.float32))
+            tol = max(GAP_TOL, pair_error_bound(ref, t, m, torch.float32))
             assert ref.gaps[t] <= tol, (i, t, ref.gaps[t], tol)
         e_gpu = O.reconstruction_error(vals, S)
         e_ref = O.reconstruction_error(vals, ref.S)
         if t is None:
             assert abs(e_gpu - e_ref) <= 1e-4 * e_ref, (i, e_gpu, e_ref)
         else:
-            assert e_gpu <= e_ref * 1.01, (i, e_gpu, e_ref)
+            # parted at a near-tie: the device's own picks are greedy picks
+            # within the rule on its own path
+            ref_dev = O.greedy_css(vals, len(S), tau_rel=1e-6, keep_scores=True, forced=S)
+            certify_selection(S, ref_dev, m, torch.float32)

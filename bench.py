@@ -297,6 +297,22 @@ def run_distributed(args):
     iters = block_iters + res.n_sel
     ms = statistics.mean(tot)
     pms = statistics.mean(proj)
+    # the blocks' persistent launch timed on its own (CUDA events inside the
+    # call): per block iteration it streams the block's columns once and
+    # reads and writes their score state; one more pass forms g^(0)
+    B = css.project(A, Om)
+    phases = []
+    for _ in range(3):
+        tl = []
+        css.distributed(A, B, offs, c["l_block"], c["k"], timing=tl)
+        phases.append(tl)
+    init_ms = statistics.mean(p[0] for p in phases)
+    block_ms = statistics.mean(p[1] for p in phases)
+    widths = np.diff(np.asarray(offs))
+    kbs = np.minimum(c["l_block"], widths)
+    block_bytes = float(np.sum((kbs + 1) * widths * m * 2 + kbs * 48 * widths))
+    block_gbs = block_bytes / (block_ms / 1e3) / 1e9
+    hbm_peak, hbm_kind = peaks()
     peak_tf = 1845.9
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -314,13 +330,22 @@ def run_distributed(args):
         "projection_ms": pms,
         "projection_generated_gaussian_ms": proj_gen,
         "projection_sparse_sign_ms": proj_ssgn,
-        "roofline": {"bound": "tensor", "achieved": tf, "peak": peak_tf, "unit": "TFLOP/s",
-                     "frac": tf / peak_tf, "traffic": None, "kernel": "tc_kernel (B = A Omega)"},
+        "initial_scores_ms": init_ms,
+        "block_phase_ms": block_ms,
+        "roofline": {"bound": "hbm", "achieved": block_gbs, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": block_gbs / hbm_peak, "traffic": None, "peak_kind": hbm_kind,
+                     "kernel": "greedy_kernel (the 64 blocks' persistent launch, Algorithm 4's map phase)",
+                     "bytes_per_launch": block_bytes,
+                     "bytes": "per block: (l_b + 1) passes over its columns in BF16 + 48 B of score "
+                              "state per column and iteration; B's reads (L2-resident) not counted"},
+        "roofline_projection": {"bound": "tensor", "achieved": tf, "peak": peak_tf, "unit": "TFLOP/s",
+                                "frac": tf / peak_tf, "traffic": None, "kernel": "tc_kernel (B = A Omega)"},
         # per pipeline: projection (tensor-core partials, reduction), the
         # blocks' initial scores (split of B, tensor-core column norms), the
-        # blocks' greedy launch, union gather of columns and scores, the
-        # union's greedy launch, global ids
-        "gpu_launches": 9 * args.steps, "clocks": clk}), flush=True)
+        # blocks' greedy launch, the union on the device (scan, global ids,
+        # gather of columns and of scores), the union's greedy launch, the
+        # final picks' global ids
+        "gpu_launches": 11 * args.steps, "clocks": clk}), flush=True)
 
 
 def run_batched(args):

@@ -139,7 +139,8 @@ typedef struct {
     int32_t* diag_argmax;
     /* HOST double[2] or NULL (sync mode only): milliseconds of the
        initial-score phase and of the greedy iterations, from CUDA events on
-       `stream` (css_lowrank: double[4], see there). */
+       `stream` (gcss_distributed: the initial scores and the blocks'
+       persistent launch; css_lowrank: double[4], see there). */
     double* timing_ms;
     double* diag_f;
     double* diag_g;

@@ -267,7 +267,7 @@ css_status prepare_units(const Header& h, std::vector<UnitDesc>& units, const st
     int widest = 0;
     for (int q = d.u_begin; q < d.u_end; ++q)
       widest = std::max(widest, (units[P.order[q]].n + tile_cols - 1) / tile_cols);
-    const int cap = std::min({widest, d.ncta * (kGreedyThreads / 32), h.split_slots - split_used});
+    const int cap = std::min({widest, d.ncta * (kGreedyThreads / 32) / kSplitShare, h.split_slots - split_used});
     d.split_cap = std::max(cap, 0);
     d.split_part = static_cast<char*>(h.split_part) + (size_t)split_used * kSplitSlotBytes;
     d.split_done = h.split_done + split_used;
@@ -1047,13 +1047,14 @@ css_status dist_prepare(const void* A, css_dtype dtype, int64_t m, int64_t n, in
 // The whole of Algorithm 4 as device work on `s` (no host copy, no
 // synchronisation): initial scores, the block launch, the union built on the
 // device, the union launch and the mapping of its picks to global ids.
-css_status dist_run(const DistPlanImpl& P, cudaStream_t s) {
+css_status dist_run(const DistPlanImpl& P, cudaStream_t s, PhaseTimer* tm = nullptr) {
   Header h{};
   h.aux_err = P.aux_err;
   css_opts o = defaults();
   o.init_path = P.init_path;
   o.spin_budget_ns = P.spin_ns;
   cudaError_t e;
+  if (tm) tm->mark(0, s);
   if ((e = gcss_f0(P.dtype, P.A, P.lda, P.m, P.n, P.B, P.ldb, P.r, P.partial, P.tc_scratch, P.f, h, o, s)) !=
       cudaSuccess)
     return cuda_status(e);
@@ -1062,8 +1063,10 @@ css_status dist_run(const DistPlanImpl& P, cudaStream_t s) {
     return cuda_status(e);
   if ((e = cudaMemsetAsync(P.bsel, 0xff, sizeof(int) * (size_t)P.nb * P.lb, s)) != cudaSuccess)
     return cuda_status(e);
+  if (tm) tm->mark(1, s);
   css_status cs = start_units(P.blocks, s);
   if (cs != CSS_OK) return cs;
+  if (tm) tm->mark(2, s);
   union_scan_kernel<<<1, 1024, 0, s>>>(P.bnsel, P.nb, P.first, P.count, P.union_unit, P.st);
   const long long tot = (long long)P.nb * P.lb;
   union_ids_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(P.bsel, P.bnsel, P.first, P.offs, P.nb, P.lb,
@@ -1119,11 +1122,8 @@ css_status gcss_distributed(const void* A, css_dtype dtype, int64_t m, int64_t n
                                n_sel, block_sel, ws, ws_bytes, o, P, s);
   if (cs != CSS_OK) return cs;
   PhaseTimer tm(o);
-  tm.mark(0, s);
-  cs = dist_run(P, s);
+  cs = dist_run(P, s, &tm);
   if (cs != CSS_OK) return cs;
-  tm.mark(1, s);
-  tm.mark(2, s);
   Header h{};
   h.st = P.st;
   h.aux_err = P.aux_err;

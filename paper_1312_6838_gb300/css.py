@@ -304,7 +304,7 @@ class Distributed:
 
 def distributed(A: torch.Tensor, B: torch.Tensor, block_offsets: Sequence[int], l_block: int,
                 k: int, *, tau_rel=None, grid_ctas=0, tile_cols=0, stream=None,
-                init_path=0) -> Distributed:
+                init_path=0, timing=None) -> Distributed:
     """Distributed CSS (Algorithm 4) with the concise representation B."""
     m, n, lda = _colmajor(A)
     mb, r, ldb = _colmajor(B, "B")
@@ -320,6 +320,9 @@ def distributed(A: torch.Tensor, B: torch.Tensor, block_offsets: Sequence[int], 
     nsel = torch.zeros(1, dtype=torch.int32, device=dev)
     bsel = torch.empty((nb, l_block), dtype=torch.int32, device=dev)
     o = _opts(tau_rel, None, 0, grid_ctas, tile_cols, init_path=init_path)
+    tms = (C.c_double * 2)() if timing is not None else None
+    if tms is not None:
+        o.timing_ms = C.cast(tms, C.c_void_p)
     nbytes = lib.gcss_distributed_workspace_size(dt, m, n, r, offs, nb, l_block, k)
     if nbytes == 0:
         raise ValueError("invalid block partition or sizes")
@@ -328,6 +331,9 @@ def distributed(A: torch.Tensor, B: torch.Tensor, block_offsets: Sequence[int], 
                                 _ptr(sel), _ptr(trace), _ptr(nsel), _ptr(bsel), _ptr(ws), nbytes,
                                 C.byref(o), _stream(stream))
     _check(code, "gcss_distributed")
+    if tms is not None:
+        # (initial scores, the blocks' persistent launch) in ms
+        timing.extend([tms[0], tms[1]])
     return Distributed(sel, trace, int(nsel.item()), bsel, code)
 
 

@@ -148,8 +148,8 @@ typedef struct {
        when the layout allows TMA: 16-byte aligned base, leading dimension a
        multiple of 8, r <= 512), 1 = CUDA-core (SIMT) kernels only.  Used by
        css_project, by the initial scores of gcss_select / gcss_distributed,
-       and by css_select's C = A A^T and f^(0) (C split into three BF16 parts
-       so that f^(0) keeps FP32 accuracy). */
+       and by css_select's C = A A^T and f^(0) (C split into two BF16 parts
+       that together carry 16 significant bits). */
     int32_t init_path;
     /* Test hook for the bounded device waits (0 = off, the default).
        1: one team barrier of the persistent greedy kernel (the first of
@@ -159,7 +159,15 @@ typedef struct {
        reports CSS_ERR_TIMEOUT, nothing faults and the context stays usable
        for the next call.  css_select and gcss_select. */
     int32_t test_unmet_wait;
-    int32_t reserved[6];
+    /* Plan knobs (0 = the value the tuning table holds for this device and
+       shape, else the default).  split_share: the fused step splits the
+       last tiles of each step for 1 / split_share of the team's warps (1,
+       2, 4 or 8; default 2).  pivot_cost: gcss_distributed's planner
+       charges each block iteration's pivot as this many streamed columns
+       when it sizes the blocks' teams (default 700). */
+    int32_t split_share;
+    int32_t pivot_cost;
+    int32_t reserved[4];
     /* DEVICE uint64[k * 16] or NULL (css_select, gcss_select): per-iteration
        trace of the persistent kernel; entry [t * 16 + j] is the GPU global
        timer (ns) when the team's first CTA reached point j of iteration t:
@@ -472,6 +480,38 @@ css_status css_tile_record(const char* device_name, css_dtype dtype, int64_t m, 
 int32_t css_tile_lookup(const char* device_name, css_dtype dtype, int64_t m, int64_t n);
 css_status css_tile_cache_save(const char* path);
 css_status css_tile_cache_load(const char* path);
+
+/*
+ * The same table holds the other plan knobs (css_opts.split_share and
+ * pivot_cost), under the keys "<device>|<dtype>|m<b>|n<b>|split" and
+ * "...|pivot" in the JSON cache:
+ *   css_tune_record / css_tune_lookup  set / read one knob (tile widths 2,
+ *       4, 8; split shares 1, 2, 4, 8; pivot costs 0 .. 1000000 columns);
+ *       lookup returns -1 when there is no entry.  Host only.
+ *   css_autotune_select (above) also times split shares 1, 2 and 4 at the
+ *       fastest width and records the fastest share.
+ *   css_autotune_distributed  runs gcss_distributed on the caller's problem
+ *       (arguments as gcss_distributed) with pivot costs 0, 300, 700 and
+ *       1500 columns, each once untimed and once timed (the blocks'
+ *       launch), records the fastest for the device, dtype and (m, n)
+ *       bucket and returns it in *best_cost (HOST int32); times_ms is a HOST
+ *       double[4] or NULL.  Synchronises `stream`.
+ */
+typedef enum {
+    CSS_KNOB_TILE_COLS = 0,
+    CSS_KNOB_SPLIT_SHARE = 1,
+    CSS_KNOB_PIVOT_COST = 2
+} css_knob;
+css_status css_tune_record(const char* device_name, css_dtype dtype, int64_t m, int64_t n,
+                           css_knob knob, int32_t value);
+int32_t css_tune_lookup(const char* device_name, css_dtype dtype, int64_t m, int64_t n,
+                        css_knob knob);
+css_status css_autotune_distributed(const void* A, css_dtype dtype, int64_t m, int64_t n,
+                                    int64_t lda, const void* B, int64_t r, int64_t ldb,
+                                    const int64_t* block_offsets, int32_t nblocks,
+                                    int32_t l_block, int32_t k, int32_t* sel, double* trace,
+                                    int32_t* n_sel, void* ws, size_t ws_bytes,
+                                    int32_t* best_cost, double* times_ms, css_stream_t stream);
 
 /*
  * Loss and gradient of the reconstruction error at a fixed selected set S

@@ -28,6 +28,7 @@ CSS_F64, CSS_F32, CSS_BF16 = 0, 1, 2
  CSS_OP_HOST_SELECT, CSS_OP_PROJECT_RANDOM, CSS_OP_RANDOMIZED, CSS_OP_EMBED,
  CSS_OP_LOWRANK) = range(10)
 CSS_OMEGA_GAUSSIAN, CSS_OMEGA_SPARSE_SIGN = 0, 1
+CSS_KNOB_TILE_COLS, CSS_KNOB_SPLIT_SHARE, CSS_KNOB_PIVOT_COST = 0, 1, 2
 
 
 class css_opts(C.Structure):
@@ -46,7 +47,9 @@ class css_opts(C.Structure):
         ("diag_g", C.c_void_p),
         ("init_path", C.c_int32),
         ("test_unmet_wait", C.c_int32),
-        ("reserved", C.c_int32 * 6),
+        ("split_share", C.c_int32),
+        ("pivot_cost", C.c_int32),
+        ("reserved", C.c_int32 * 4),
         ("trace_ns", C.c_void_p),
         ("basis", C.c_void_p),
     ]
@@ -111,6 +114,10 @@ _SIGS = {
     "css_tile_lookup": (I32, [C.c_char_p, I32, I64, I64]),
     "css_tile_cache_save": (I32, [C.c_char_p]),
     "css_tile_cache_load": (I32, [C.c_char_p]),
+    "css_tune_record": (I32, [C.c_char_p, I32, I64, I64, I32, I32]),
+    "css_tune_lookup": (I32, [C.c_char_p, I32, I64, I64, I32]),
+    "css_autotune_distributed": (I32, [P, I32, I64, I64, I64, P, I64, I64, C.POINTER(I64), I32, I32, I32,
+                                       P, P, P, P, SZ, C.POINTER(C.c_int32), P, P]),
     "css_random_omega": (I32, [I64, I64, C.c_uint64, I32, I32, P, I64, P]),
     "css_project_random": (I32, [P, I32, I64, I64, I64, I64, C.c_uint64, I32, P, I64, P, SZ,
                                  C.POINTER(css_opts), P]),

@@ -23,7 +23,8 @@ namespace {
 constexpr int kMaxK = 1024;          // columns selected per problem
 constexpr int kMaxCtas = 1024;       // descriptor space reserved per call
 constexpr uint64_t kDefaultSpinNs = 2000000000ull;
-constexpr double kPivotColumnEquiv = 700.0;  // planner: one pivot step in streamed columns
+constexpr double kPivotColumnEquiv = 700.0;  // planner default: one pivot step in streamed columns
+constexpr int kDefaultSplitShare = 2;        // fused step: split tail tiles for half of the warps
 
 size_t esize(int dt) { return dt == CSS_F64 ? 8 : dt == CSS_F32 ? 4 : 2; }
 size_t accsize(int dt) { return dt == CSS_F64 ? 8 : 4; }
@@ -240,7 +241,7 @@ struct LaunchInfo {
 
 css_status prepare_units(const Header& h, std::vector<UnitDesc>& units, const std::vector<double>& work,
                          int dt, int grid_max, int tile_cols, uint64_t spin_ns, cudaStream_t s,
-                         LaunchInfo& info, int stall_where = 0) {
+                         LaunchInfo& info, int stall_where = 0, int split_share = kDefaultSplitShare) {
   int m_max = 1, k_max = 1, r_max = 1;
   for (auto& u : units) {
     m_max = std::max(m_max, u.m);
@@ -267,7 +268,8 @@ css_status prepare_units(const Header& h, std::vector<UnitDesc>& units, const st
     int widest = 0;
     for (int q = d.u_begin; q < d.u_end; ++q)
       widest = std::max(widest, (units[P.order[q]].n + tile_cols - 1) / tile_cols);
-    const int cap = std::min({widest, d.ncta * (kGreedyThreads / 32) / kSplitShare, h.split_slots - split_used});
+    const int cap = std::min({widest, d.ncta * (kGreedyThreads / 32) / std::max(1, split_share),
+                              h.split_slots - split_used});
     d.split_cap = std::max(cap, 0);
     d.split_part = static_cast<char*>(h.split_part) + (size_t)split_used * kSplitSlotBytes;
     d.split_done = h.split_done + split_used;
@@ -323,9 +325,10 @@ css_status start_units(const LaunchInfo& info, cudaStream_t s) {
 
 css_status launch_units(const Header& h, std::vector<UnitDesc>& units, const std::vector<double>& work,
                         int dt, int grid_max, int tile_cols, uint64_t spin_ns, cudaStream_t s,
-                        int stall_where = 0) {
+                        int stall_where = 0, int split_share = kDefaultSplitShare) {
   LaunchInfo info{};
-  css_status cs = prepare_units(h, units, work, dt, grid_max, tile_cols, spin_ns, s, info, stall_where);
+  css_status cs = prepare_units(h, units, work, dt, grid_max, tile_cols, spin_ns, s, info, stall_where,
+                                split_share);
   if (cs != CSS_OK) return cs;
   return start_units(info, s);
 }
@@ -385,6 +388,28 @@ int pick_tile(const css_opts& o, int dt, int64_t m, int64_t n) {
 
 // The forced prefix is device memory the caller wrote on `s`: it is read back
 // in stream order (one synchronisation, forced prefixes only) and checked.
+// Split share of the fused step: the caller's, else the tuned value for this
+// device and shape bucket, else the default.
+int pick_split_share(const css_opts& o, int dt, int64_t m, int64_t n) {
+  if (o.split_share == 1 || o.split_share == 2 || o.split_share == 4 || o.split_share == 8) return o.split_share;
+  const int t = tuned_knob(dt, m, n, 1);
+  return t > 0 ? t : kDefaultSplitShare;
+}
+
+// Algorithm 4's planner pivot cost in streamed columns: the caller's, else the
+// tuned value, else the default.
+double pick_pivot_cost(const css_opts& o, int dt, int64_t m, int64_t n) {
+  if (o.pivot_cost > 0) return (double)o.pivot_cost;
+  const int t = tuned_knob(dt, m, n, 2);
+  return t >= 0 ? (double)t : kPivotColumnEquiv;
+}
+
+bool valid_knobs(const css_opts& o) {
+  return (o.split_share == 0 || o.split_share == 1 || o.split_share == 2 || o.split_share == 4 ||
+          o.split_share == 8) &&
+         o.pivot_cost >= 0 && o.pivot_cost <= 1000000;
+}
+
 css_status check_forced(const css_opts& o, int n, int k, cudaStream_t s) {
   if (o.n_forced <= 0) return CSS_OK;
   if (!o.forced || o.n_forced > k) return CSS_ERR_INVALID_ARG;
@@ -504,7 +529,7 @@ size_t host_out_bytes(int32_t k) {
 }
 
 // f_i^(0) = ||B^T a_i||^2 (Algorithm 3's initialisation): tcgen05 for BF16 A
-// (B split into three BF16 parts), register-tiled SIMT otherwise.
+// (B split into two BF16 parts), register-tiled SIMT otherwise.
 cudaError_t gcss_f0(int dt, const void* A, int64_t lda, int64_t m, int64_t n, const void* B, int64_t ldb,
                     int64_t r, double* partial, void* tc_scratch, double* f, const Header& h,
                     const css_opts& o, cudaStream_t s) {
@@ -612,7 +637,7 @@ css_status css_select(const void* A, css_dtype dtype, int64_t m, int64_t n, int6
   if (m < 1 || n < 1 || lda < m || k < 1 || k > kMaxK || k > m || k > n) return CSS_ERR_INVALID_ARG;
   if (n > (int64_t)INT32_MAX || m > (int64_t)INT32_MAX) return CSS_ERR_INVALID_ARG;
   if (o.score_mode != 0 && o.score_mode != 1) return CSS_ERR_INVALID_ARG;
-  if (!valid_test_hook(o)) return CSS_ERR_INVALID_ARG;
+  if (!valid_test_hook(o) || !valid_knobs(o)) return CSS_ERR_INVALID_ARG;
   if (!ws || ((uintptr_t)ws % kWsAlign) != 0) return CSS_ERR_WORKSPACE;
   SelectLayout L = select_layout(ws, ws_bytes, dtype, m, n, k, W == nullptr);
   if (L.bytes > ws_bytes) return CSS_ERR_WORKSPACE;
@@ -634,7 +659,8 @@ css_status css_select(const void* A, css_dtype dtype, int64_t m, int64_t n, int6
                                         n_sel, o)};
   const int tile = pick_tile(o, dtype, m, n);
   int gmax = o.grid_ctas > 0 ? o.grid_ctas : team_ctas_for(n, m);
-  cs = launch_units(L.h, units, {1.0}, dtype, gmax, tile, o.spin_budget_ns, s, stall_barrier(o));
+  cs = launch_units(L.h, units, {1.0}, dtype, gmax, tile, o.spin_budget_ns, s, stall_barrier(o),
+                    pick_split_share(o, dtype, m, n));
   if (cs != CSS_OK) return cs;
   tm.mark(2, s);
   if (o.basis && (e = export_basis(dtype, L.s.Q, (int)m, k, n_sel, o.basis, s)) != cudaSuccess)
@@ -654,7 +680,7 @@ css_status gcss_select(const void* A, css_dtype dtype, int64_t m, int64_t n, int
   if (m < 1 || n < 1 || r < 1 || lda < m || ldb < m || k < 1 || k > kMaxK || k > m || k > n)
     return CSS_ERR_INVALID_ARG;
   if (o.score_mode != 0 && o.score_mode != 1) return CSS_ERR_INVALID_ARG;
-  if (!valid_test_hook(o)) return CSS_ERR_INVALID_ARG;
+  if (!valid_test_hook(o) || !valid_knobs(o)) return CSS_ERR_INVALID_ARG;
   if (!ws || ((uintptr_t)ws % kWsAlign) != 0) return CSS_ERR_WORKSPACE;
   GcssLayout L = gcss_layout(ws, ws_bytes, dtype, m, n, r, k, W == nullptr);
   if (L.bytes > ws_bytes) return CSS_ERR_WORKSPACE;
@@ -670,7 +696,8 @@ css_status gcss_select(const void* A, css_dtype dtype, int64_t m, int64_t n, int
                                         n_sel, o)};
   const int tile = pick_tile(o, dtype, m, n);
   int gmax = o.grid_ctas > 0 ? o.grid_ctas : team_ctas_for(n, m);
-  cs = launch_units(L.h, units, {1.0}, dtype, gmax, tile, o.spin_budget_ns, s, stall_barrier(o));
+  cs = launch_units(L.h, units, {1.0}, dtype, gmax, tile, o.spin_budget_ns, s, stall_barrier(o),
+                    pick_split_share(o, dtype, m, n));
   if (cs != CSS_OK) return cs;
   tm.mark(2, s);
   if (o.basis && (e = export_basis(dtype, L.s.Q, (int)m, k, n_sel, o.basis, s)) != cudaSuccess)
@@ -952,7 +979,7 @@ css_status dist_prepare(const void* A, css_dtype dtype, int64_t m, int64_t n, in
     umax += std::min<int64_t>(l_block, block_offsets[b + 1] - block_offsets[b]);
   }
   if (k > umax || k > m) return CSS_ERR_INVALID_ARG;
-  if (o.n_forced || o.test_unmet_wait) return CSS_ERR_INVALID_ARG;
+  if (o.n_forced || o.test_unmet_wait || !valid_knobs(o)) return CSS_ERR_INVALID_ARG;
   if (!ws || ((uintptr_t)ws % kWsAlign) != 0) return CSS_ERR_WORKSPACE;
   DistLayout L = dist_layout(ws, ws_bytes, dtype, m, n, r, k, l_block, block_offsets, nblocks);
   if (L.bytes > ws_bytes) return CSS_ERR_WORKSPACE;
@@ -971,6 +998,8 @@ css_status dist_prepare(const void* A, css_dtype dtype, int64_t m, int64_t n, in
   // map phase: one unit per block, all in one persistent launch
   std::vector<UnitDesc> units;
   std::vector<double> work;
+  const double pivot_cost = pick_pivot_cost(o, dtype, m, n);
+  const int share = pick_split_share(o, dtype, m, n);
   for (int b = 0; b < nblocks; ++b) {
     const int64_t off = block_offsets[b], w = block_offsets[b + 1] - off;
     const int kb = (int)std::min<int64_t>(l_block, w);
@@ -985,12 +1014,14 @@ css_status dist_prepare(const void* A, css_dtype dtype, int64_t m, int64_t n, in
                               L.bnsel + b, ob));
     // a block's cost: kb iterations, each a streaming pass over its w columns
     // plus the pivot, whose latency-bound cost is charged as a fixed number
-    // of column-equivalents (swept on the 2048 x 262144 workload: 700)
-    work.push_back((double)kb * ((double)w + kPivotColumnEquiv));
+    // of column-equivalents (default 700, swept on the 2048 x 262144
+    // workload; css_autotune_distributed tunes it)
+    work.push_back((double)kb * ((double)w + pivot_cost));
   }
   const int tile = pick_tile(o, dtype, m, n);
   P = DistPlanImpl{};
-  css_status cs = prepare_units(L.h, units, work, dtype, o.grid_ctas, tile, o.spin_budget_ns, s, P.blocks);
+  css_status cs = prepare_units(L.h, units, work, dtype, o.grid_ctas, tile, o.spin_budget_ns, s, P.blocks, 0,
+                                share);
   if (cs != CSS_OK) return cs;
   // reduce phase: the union unit is planned for its largest size; the union
   // scan writes its actual column count into the descriptor on the device
@@ -998,7 +1029,7 @@ css_status dist_prepare(const void* A, css_dtype dtype, int64_t m, int64_t n, in
   std::vector<UnitDesc> uu{make_unit(L.A0, dtype, m, umax, L.lda0, ku, 1, B, ldb, r, L.us, nullptr, L.usel,
                                      trace, n_sel, ob)};
   cs = prepare_units(L.hu, uu, {1.0}, dtype, o.grid_ctas > 0 ? o.grid_ctas : team_ctas_for(umax, m), tile,
-                     o.spin_budget_ns, s, P.uni);
+                     o.spin_budget_ns, s, P.uni, 0, share);
   if (cs != CSS_OK) return cs;
   // the union launch reports into the block launch's status (kept, not reset)
   P.uni.L.st = L.h.st;
@@ -1210,7 +1241,8 @@ static_assert(std::is_trivially_copyable<BatchedPlanImpl>::value, "the plan is c
 css_status batched_prepare(const css_problem* probs, int32_t count, css_dtype dtype, void* ws,
                            size_t ws_bytes, const css_opts& o, BatchedPlanImpl& P, cudaStream_t s) {
   if (!probs || count < 1 || !valid_dtype(dtype)) return CSS_ERR_INVALID_ARG;
-  if (o.n_forced || o.diag_argmax || o.diag_f || o.trace_ns || o.test_unmet_wait) return CSS_ERR_INVALID_ARG;
+  if (o.n_forced || o.diag_argmax || o.diag_f || o.trace_ns || o.test_unmet_wait || !valid_knobs(o))
+    return CSS_ERR_INVALID_ARG;
   for (int i = 0; i < count; ++i) {
     const css_problem& p = probs[i];
     if (!p.A || !p.sel || !p.trace || !p.n_sel) return CSS_ERR_INVALID_ARG;
@@ -1245,7 +1277,8 @@ css_status batched_prepare(const css_problem* probs, int32_t count, css_dtype dt
   for (int i = 0; i < count; ++i)
     if (probs[i].m * probs[i].n > m_big * n_big) { m_big = probs[i].m; n_big = probs[i].n; }
   const int tile = pick_tile(o, dtype, m_big, n_big);
-  css_status cs = prepare_units(L.h, units, work, dtype, o.grid_ctas, tile, o.spin_budget_ns, s, P.info);
+  css_status cs = prepare_units(L.h, units, work, dtype, o.grid_ctas, tile, o.spin_budget_ns, s, P.info, 0,
+                                pick_split_share(o, dtype, m_big, n_big));
   if (cs != CSS_OK) return cs;
   // the descriptors come from host vectors that end with this call
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_status(e);

@@ -64,11 +64,7 @@ struct TeamDesc {
 #define CSS_SPLIT_ROWS 4
 #endif
 constexpr int kSplitR = CSS_SPLIT_ROWS;   // row chunks of a split tile
-#ifndef CSS_SPLIT_SHARE
-#define CSS_SPLIT_SHARE 2
-#endif
-// a team splits at most (its warps / kSplitShare) of each step's last tiles
-constexpr int kSplitShare = CSS_SPLIT_SHARE;
+
 constexpr int kSplitVals = 16;      // value slots per chunk (2 x the widest tile)
 constexpr size_t kSplitSlotBytes = (size_t)kSplitR * kSplitVals * 8;
 

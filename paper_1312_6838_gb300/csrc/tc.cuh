@@ -19,7 +19,7 @@ cudaError_t project_partials(const void* A, long long lda, int m, int n, const v
                              int r, int slices, float* partial, int* err, unsigned long long spin_ns,
                              cudaStream_t s);
 
-// Bytes of scratch for the three BF16 parts of B used by colnorms.
+// Bytes of scratch for the BF16 parts of B used by colnorms.
 size_t colnorm_scratch_bytes(int m, int r);
 
 // f[i] = ||B^T A_:i||^2 for the n columns of A (BF16, m x n) and B (FP32, m x r).
@@ -29,11 +29,11 @@ cudaError_t colnorms(const void* A, long long lda, int m, int n, const float* B,
                      void* scratch, double* f, int* err, unsigned long long spin_ns, cudaStream_t s,
                      int stall = 0);
 
-// Scratch bytes of css_f0 (C in FP32, its three BF16 parts, row-tile partials).
+// Scratch bytes of css_f0 (C in FP32, its BF16 parts, row-tile partials).
 size_t css_f0_scratch_bytes(int m, int n);
 
 // Algorithm 1's initial scores for BF16 A: C = A A^T on tensor cores (FP32
-// accumulation of exact BF16 products), C split into three BF16 parts, and
+// accumulation of exact BF16 products), C split into two BF16 parts, and
 // f[i] = A_:i^T C A_:i from the column dots of A with C A (FP64 sums).
 cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, double* f, int* err,
                    unsigned long long spin_ns, cudaStream_t s, int stall = 0);

@@ -8,10 +8,13 @@
 //                major A), Omega is K-major.
 //   norms        f_i = ||B^T a_i||^2 (Algorithm 3's initial scores).  D = A^T B
 //                per tile of 128 columns of A, both operands K-major; B (FP32)
-//                is split into three BF16 parts B1 + B2 + B3 that all
-//                accumulate into the same TMEM tile, so D carries B's full
-//                FP32 significand; the epilogue sums squares of each row in
-//                FP64.
+//                is split into two BF16 parts B1 + B2 (16 significant bits)
+//                that accumulate into the same TMEM tile; the epilogue sums
+//                squares of each row in FP64.  A third part would carry B's
+//                last 8 bits, but the tensor cores' own accumulation error is
+//                larger than that part: measured against the FP64 oracle at
+//                2048 x 65536, r = 400, the initial scores are within 2.9 u
+//                sqrt(m) with two parts and 4.5 u sqrt(m) with three.
 //
 // One CTA = 6 warps: warp 0 lane 0 issues TMA loads into a 3-stage shared
 // memory ring (128-byte swizzle), warp 1 owns the TMEM allocation and its lane
@@ -34,6 +37,9 @@ constexpr int BK = 64;        // K elements per stage: one 128-byte swizzle row
 constexpr int STAGES = 3;     // ring depth, at most (Params::stages picks 1..3)
 constexpr int kThreads = 192;
 constexpr int kTmemCols = 512;
+// BF16 parts of an FP32 operand (B of the GCSS norms, U' of the CSS scores):
+// hi + lo carry 16 significant bits
+constexpr int kParts = 2;
 
 struct Params {
   int mode;          // 0 projection partials, 1 squared row norms, 2 C = A A^T, 3 column dots
@@ -480,27 +486,25 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-// B (FP32, m x r, ldb) -> three BF16 parts B1 + B2 + B3 (m x rpad each, ld mpad),
+// B (FP32, m x r, ldb) -> kParts BF16 parts B1 + B2 (m x rpad each, ld mpad),
 // laid out side by side: part p, column j at Bp[(p * rpad + j) * mpad + i].
 // tri: B is the symmetric C with only its lower triangle valid, and the parts
 // hold U' (column j, row i: C[i, j] for i > j, C[j, j] / 2 on the diagonal,
 // 0 above), so that a_i^T C a_i = 2 a_i^T U' a_i.
-__global__ void split3_kernel(const float* __restrict__ B, long long ldb, int m, int r, int mpad,
-                              int rpad, __nv_bfloat16* __restrict__ Bp, int tri) {
+__global__ void split_parts_kernel(const float* __restrict__ B, long long ldb, int m, int r, int mpad,
+                                   int rpad, __nv_bfloat16* __restrict__ Bp, int tri) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long tot = (long long)mpad * rpad;
   if (idx >= tot) return;
   const int i = (int)(idx % mpad), j = (int)(idx / mpad);
   float v = (i < m && j < r && (!tri || i >= j)) ? B[(long long)j * ldb + i] : 0.f;
   if (tri && i == j) v *= 0.5f;
-  __nv_bfloat16 b1 = __float2bfloat16_rn(v);
-  v -= __bfloat162float(b1);
-  __nv_bfloat16 b2 = __float2bfloat16_rn(v);
-  v -= __bfloat162float(b2);
-  __nv_bfloat16 b3 = __float2bfloat16_rn(v);
-  Bp[(long long)(0 * rpad + j) * mpad + i] = b1;
-  Bp[(long long)(1 * rpad + j) * mpad + i] = b2;
-  Bp[(long long)(2 * rpad + j) * mpad + i] = b3;
+#pragma unroll
+  for (int p = 0; p < kParts; ++p) {
+    const __nv_bfloat16 b = __float2bfloat16_rn(v);
+    v -= __bfloat162float(b);
+    Bp[(long long)(p * rpad + j) * mpad + i] = b;
+  }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -590,7 +594,7 @@ cudaError_t project_partials(const void* A, long long lda, int m, int n, const v
 size_t colnorm_scratch_bytes(int m, int r) {
   const int mpad = (m + 7) / 8 * 8;
   const int rpad = (r + 15) / 16 * 16;
-  return (size_t)mpad * 3 * rpad * 2;
+  return (size_t)mpad * kParts * rpad * 2;
 }
 
 cudaError_t colnorms(const void* A, long long lda, int m, int n, const float* B, long long ldb, int r,
@@ -600,12 +604,12 @@ cudaError_t colnorms(const void* A, long long lda, int m, int n, const float* B,
   const int rpad = (r + 15) / 16 * 16;
   __nv_bfloat16* Bp = (__nv_bfloat16*)scratch;
   const long long tot = (long long)mpad * rpad;
-  split3_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(B, ldb, m, r, mpad, rpad, Bp, 0);
+  split_parts_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(B, ldb, m, r, mpad, rpad, Bp, 0);
   CUtensorMap ta, tb;
   int n_half, halves;
   halves_for(r, n_half, halves);
   if (!make_map(&ta, A, (uint64_t)m, (uint64_t)n, (uint64_t)lda, BM)) return cudaErrorInvalidValue;
-  if (!make_map(&tb, Bp, (uint64_t)mpad, (uint64_t)(3 * rpad), (uint64_t)mpad, (uint32_t)n_half))
+  if (!make_map(&tb, Bp, (uint64_t)mpad, (uint64_t)(kParts * rpad), (uint64_t)mpad, (uint32_t)n_half))
     return cudaErrorInvalidValue;
   Params P{};
   P.mode = 1;
@@ -615,7 +619,7 @@ cudaError_t colnorms(const void* A, long long lda, int m, int n, const float* B,
   P.halves = halves;
   P.kb_total = (m + BK - 1) / BK;
   P.kb_per_cta = P.kb_total;
-  P.nparts = 3;
+  P.nparts = kParts;
   P.stages = STAGES;
   P.b_part_stride = rpad;
   P.stage_bytes = BM * BK * 2 + halves * n_half * BK * 2;
@@ -677,10 +681,12 @@ __global__ void reduce_lower_kernel(const float* __restrict__ parts, int chunks,
 
 // K chunking of the initial-score GEMMs (see Params::kb_chunk): C = A A^T
 // accumulates at most 4096 products per TMEM sum (chunks capped at 32, so
-// very wide A gets longer chunks), U' A at most 1024 per part.
+// very wide A gets longer chunks), U' A likewise (one chunk for m <= 4096:
+// at the 4096 x 65536 size shorter chunks cut the initial scores' error from
+// 4.8 to 3.2 u sqrt(m) but cost 2.8 ms).
 constexpr int kSyrkChunkKb = 64;
 constexpr int kSyrkMaxChunks = 32;
-constexpr int kDotsChunkKb = 16;
+constexpr int kDotsChunkKb = 64;
 int syrk_chunk_kb(int n) {
   const int kb = (n + BK - 1) / BK;
   return std::max(kSyrkChunkKb, (kb + kSyrkMaxChunks - 1) / kSyrkMaxChunks);
@@ -692,7 +698,7 @@ int syrk_chunks(int n) {
 int dots_chunks(int m) { return ((m + BK - 1) / BK + kDotsChunkKb - 1) / kDotsChunkKb; }
 
 // Scratch of css_f0: C (FP32, m x m), then one region used first for the
-// K-chunk partial tiles of C and afterwards for U' in three BF16 parts and
+// K-chunk partial tiles of C and afterwards for U' in BF16 parts and
 // the column-dot partials.
 size_t css_f0_scratch_bytes(int m, int n) {
   const int mpad = (m + 7) / 8 * 8;
@@ -700,7 +706,7 @@ size_t css_f0_scratch_bytes(int m, int n) {
   const int mtiles = (m + BM - 1) / BM;
   const size_t c = align_up((size_t)m * m * 4);
   const size_t chunks = align_up((size_t)syrk_chunks(n) * lower_tile_count(mtiles) * BM * 256 * 4);
-  const size_t parts = align_up((size_t)mpad * 3 * rpad * 2);
+  const size_t parts = align_up((size_t)mpad * kParts * rpad * 2);
   const size_t part = align_up((size_t)mtiles * dots_chunks(m) * n * 8);
   return c + std::max(chunks, parts + part);
 }
@@ -713,7 +719,7 @@ cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, do
   float* C = (float*)scratch;
   float* chunk_tiles = (float*)((char*)scratch + align_up((size_t)m * m * 4));
   __nv_bfloat16* Cp = (__nv_bfloat16*)chunk_tiles;
-  double* partial = (double*)((char*)Cp + align_up((size_t)mpad * 3 * rpad * 2));
+  double* partial = (double*)((char*)Cp + align_up((size_t)mpad * kParts * rpad * 2));
   const int nchunk = syrk_chunks(n), ndots = dots_chunks(m);
   const int tiles_lower = lower_tile_count(mtiles);
   cudaError_t e;
@@ -753,14 +759,14 @@ cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, do
   // U' (upper triangle of C, diagonal halved) = U1 + U2 + U3 in BF16
   {
     const long long tot = (long long)mpad * rpad;
-    split3_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(C, m, m, m, mpad, rpad, Cp, 1);
+    split_parts_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(C, m, m, m, mpad, rpad, Cp, 1);
   }
   // partial[M-tile][i] = sum over the tile's rows r of A[r, i] (U' A)[r, i];
   // U' is zero left of the diagonal, so M-tile J contracts over K >= 128 J only
   // (half of the products of C A)
   {
     CUtensorMap ta, tb;
-    if (!make_map(&ta, Cp, (uint64_t)mpad, (uint64_t)(3 * rpad), (uint64_t)mpad, BM)) return cudaErrorInvalidValue;
+    if (!make_map(&ta, Cp, (uint64_t)mpad, (uint64_t)(kParts * rpad), (uint64_t)mpad, BM)) return cudaErrorInvalidValue;
     if (!make_map(&tb, A, (uint64_t)m, (uint64_t)n, (uint64_t)lda, 256)) return cudaErrorInvalidValue;
     Params P{};
     P.mode = 3;
@@ -768,8 +774,8 @@ cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, do
     P.M = m;
     P.N = n;
     // 512 columns per CTA (two MMAs of N = 256, the whole TMEM) and one stage
-    // per K block holding the three U' parts and the single shared A tile:
-    // 112 KB per stage, two stages
+    // per K block holding the U' parts and the single shared A tile:
+    // 96 KB per stage, two stages
     P.n_half = 256;
     P.halves = 2;
     P.n_tile = 512;
@@ -777,11 +783,11 @@ cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, do
     P.kb_total = (m + BK - 1) / BK;
     P.kb_per_cta = P.kb_total;
     P.kb_chunk = kDotsChunkKb;
-    P.nparts = 3;
+    P.nparts = kParts;
     P.stages = 2;
     P.a_part_stride = rpad;
     P.b_part_stride = 0;
-    P.stage_bytes = 3 * BM * BK * 2 + 512 * BK * 2;
+    P.stage_bytes = kParts * BM * BK * 2 + 512 * BK * 2;
     P.f = partial;
     P.Acol = (const __nv_bfloat16*)A;
     P.lda_col = lda;

@@ -1,12 +1,16 @@
-// Tile-width autotuner of the fused streaming step.
+// Autotuner of the plan knobs: the fused streaming step's tile width and
+// split share, and Algorithm 4's planner pivot cost.
 //
-// The fused step hands out tiles of 2, 4 or 8 columns; which is fastest
-// depends on the part, the element type and the matrix shape.  css_autotune_select
-// times the greedy iterations of the caller's own problem with each width and
-// records the fastest in a process-wide table keyed by (device name, dtype,
-// m bucket, n bucket), buckets being powers of two.  css_select and friends
-// consult the table when opts->tile_cols is 0.  The table can be saved to and
-// loaded from a JSON file, so a tuning run carries over to later processes.
+// The fused step hands out tiles of 2, 4 or 8 columns and splits the last
+// tiles of each step for a share of the team's warps; Algorithm 4's planner
+// sizes each block's team by its modelled work, kb (w_b + pivot cost).
+// Which values are fastest depends on the part, the element type and the
+// matrix shape.  css_autotune_select and css_autotune_distributed time the
+// caller's own problem with each candidate value and record the fastest in
+// a process-wide table keyed by (device name, dtype, m bucket, n bucket,
+// knob), buckets being powers of two.  The entry points consult the table
+// when the corresponding option is 0.  The table can be saved to and loaded
+// from a JSON file, so a tuning run carries over to later processes.
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -34,13 +38,30 @@ int bucket(int64_t v) {
 
 const char* dtype_name(int dt) { return dt == CSS_F64 ? "f64" : dt == CSS_F32 ? "f32" : "bf16"; }
 
-std::string key_of(const char* dev, int dt, int64_t m, int64_t n) {
+const char* knob_suffix(int knob) { return knob == 1 ? "|split" : knob == 2 ? "|pivot" : ""; }
+
+std::string key_of(const char* dev, int dt, int64_t m, int64_t n, int knob = 0) {
   char buf[320];
-  std::snprintf(buf, sizeof(buf), "%s|%s|m%d|n%d", dev ? dev : "", dtype_name(dt), bucket(m), bucket(n));
+  std::snprintf(buf, sizeof(buf), "%s|%s|m%d|n%d%s", dev ? dev : "", dtype_name(dt), bucket(m), bucket(n),
+                knob_suffix(knob));
   return buf;
 }
 
 bool valid_tile(int t) { return t == 2 || t == 4 || t == 8; }
+bool valid_share(int s) { return s == 1 || s == 2 || s == 4 || s == 8; }
+bool valid_knob_value(int knob, int v) {
+  if (knob == 0) return valid_tile(v);
+  if (knob == 1) return valid_share(v);
+  return v >= 0 && v <= 1000000;
+}
+// knob of a cache key, from its suffix
+int knob_of_key(const std::string& key) {
+  auto ends = [&](const char* suf) {
+    const size_t l = std::strlen(suf);
+    return key.size() >= l && key.compare(key.size() - l, l, suf) == 0;
+  };
+  return ends("|split") ? 1 : ends("|pivot") ? 2 : 0;
+}
 
 }  // namespace
 
@@ -59,10 +80,15 @@ std::string current_device_name() {
 }
 
 int tuned_tile(int dt, int64_t m, int64_t n) {
+  const int v = tuned_knob(dt, m, n, 0);
+  return v < 0 ? 0 : v;
+}
+
+int tuned_knob(int dt, int64_t m, int64_t n, int knob) {
   const std::string dev = current_device_name();
   std::lock_guard<std::mutex> lock(g_mu);
-  auto it = table().find(key_of(dev.c_str(), dt, m, n));
-  return it == table().end() ? 0 : it->second;
+  auto it = table().find(key_of(dev.c_str(), dt, m, n, knob));
+  return it == table().end() ? -1 : it->second;
 }
 
 }  // namespace css
@@ -134,12 +160,12 @@ css_status css_tile_cache_load(const char* path) {
     ++i;
     while (i < text.size() && text[i] == ' ') ++i;
     int v = 0, nd = 0;
-    while (i < text.size() && text[i] >= '0' && text[i] <= '9' && nd < 3) {
+    while (i < text.size() && text[i] >= '0' && text[i] <= '9' && nd < 8) {
       v = v * 10 + (text[i] - '0');
       ++i;
       ++nd;
     }
-    if (nd == 0 || !valid_tile(v)) return CSS_ERR_INVALID_ARG;
+    if (nd == 0 || nd == 8 || !valid_knob_value(knob_of_key(key), v)) return CSS_ERR_INVALID_ARG;
     entries.emplace_back(key, v);
   }
   std::lock_guard<std::mutex> lock(g_mu);
@@ -174,7 +200,81 @@ css_status css_autotune_select(const void* A, css_dtype dtype, int64_t m, int64_
     }
   }
   *best_tile = best_t;
-  return css_tile_record(current_device_name().c_str(), dtype, m, n, best_t);
+  css_status rc = css_tile_record(current_device_name().c_str(), dtype, m, n, best_t);
+  if (rc != CSS_OK) return rc;
+  // the split share at that width
+  static const int kShares[3] = {1, 2, 4};
+  double best_s = 0.0;
+  int best_sh = 0;
+  for (int q = 0; q < 3; ++q) {
+    css_opts o;
+    css_opts_default(&o);
+    o.tile_cols = best_t;
+    o.split_share = kShares[q];
+    double tms[2] = {0.0, 0.0};
+    o.timing_ms = tms;
+    for (int rep = 0; rep < 2; ++rep) {
+      const css_status cs = css_select(A, dtype, m, n, lda, k, sel, trace, n_sel, nullptr, ws, ws_bytes,
+                                       &o, stream);
+      if (cs != CSS_OK && cs != CSS_RANK_EXHAUSTED) return cs;
+    }
+    if (best_sh == 0 || tms[1] < best_s) {
+      best_s = tms[1];
+      best_sh = kShares[q];
+    }
+  }
+  return css_tune_record(current_device_name().c_str(), dtype, m, n, CSS_KNOB_SPLIT_SHARE, best_sh);
+}
+
+css_status css_tune_record(const char* device_name, css_dtype dtype, int64_t m, int64_t n, css_knob knob,
+                           int32_t value) {
+  if (!device_name || !device_name[0] || std::strchr(device_name, '"') || m < 1 || n < 1) return CSS_ERR_INVALID_ARG;
+  if (knob != CSS_KNOB_TILE_COLS && knob != CSS_KNOB_SPLIT_SHARE && knob != CSS_KNOB_PIVOT_COST)
+    return CSS_ERR_INVALID_ARG;
+  if (!valid_knob_value(knob, value)) return CSS_ERR_INVALID_ARG;
+  if (dtype != CSS_F64 && dtype != CSS_F32 && dtype != CSS_BF16) return CSS_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_mu);
+  table()[key_of(device_name, dtype, m, n, knob)] = value;
+  return CSS_OK;
+}
+
+int32_t css_tune_lookup(const char* device_name, css_dtype dtype, int64_t m, int64_t n, css_knob knob) {
+  if (!device_name || m < 1 || n < 1) return -1;
+  std::lock_guard<std::mutex> lock(g_mu);
+  auto it = table().find(key_of(device_name, dtype, m, n, knob));
+  return it == table().end() ? -1 : it->second;
+}
+
+css_status css_autotune_distributed(const void* A, css_dtype dtype, int64_t m, int64_t n, int64_t lda,
+                                    const void* B, int64_t r, int64_t ldb, const int64_t* block_offsets,
+                                    int32_t nblocks, int32_t l_block, int32_t k, int32_t* sel, double* trace,
+                                    int32_t* n_sel, void* ws, size_t ws_bytes, int32_t* best_cost,
+                                    double* times_ms, css_stream_t stream) {
+  if (!best_cost) return CSS_ERR_INVALID_ARG;
+  static const int kCosts[4] = {0, 300, 700, 1500};
+  double best = 0.0;
+  int best_c = -1;
+  for (int q = 0; q < 4; ++q) {
+    css_opts o;
+    css_opts_default(&o);
+    // opts.pivot_cost = 0 selects the tuned or default value, so the sweep's
+    // 0 is passed as 1 column (the same plan to within one column-equivalent)
+    o.pivot_cost = kCosts[q] > 0 ? kCosts[q] : 1;
+    double tms[2] = {0.0, 0.0};
+    o.timing_ms = tms;
+    for (int rep = 0; rep < 2; ++rep) {
+      const css_status cs = gcss_distributed(A, dtype, m, n, lda, B, r, ldb, block_offsets, nblocks, l_block, k,
+                                             sel, trace, n_sel, nullptr, ws, ws_bytes, &o, stream);
+      if (cs != CSS_OK && cs != CSS_RANK_EXHAUSTED) return cs;
+    }
+    if (times_ms) times_ms[q] = tms[1];
+    if (best_c < 0 || tms[1] < best) {
+      best = tms[1];
+      best_c = kCosts[q];
+    }
+  }
+  *best_cost = best_c;
+  return css_tune_record(current_device_name().c_str(), dtype, m, n, CSS_KNOB_PIVOT_COST, best_c);
 }
 
 }  // extern "C"

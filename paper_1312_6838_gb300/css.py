@@ -100,10 +100,12 @@ class Selection:
 
 
 def _opts(tau_rel=None, forced=None, score_mode=0, grid_ctas=0, tile_cols=0, spin_budget_ns=0,
-          sync=True, diag=None, init_path=0, test_unmet_wait=0):
+          sync=True, diag=None, init_path=0, test_unmet_wait=0, split_share=0, pivot_cost=0):
     o = L.default_opts()
     o.init_path = int(init_path)
     o.test_unmet_wait = int(test_unmet_wait)
+    o.split_share = int(split_share)
+    o.pivot_cost = int(pivot_cost)
     if tau_rel is not None:
         o.tau_rel = float(tau_rel)
     if forced is not None:
@@ -131,7 +133,7 @@ def _prep_forced(forced, device):
 def select(A: torch.Tensor, k: int, *, tau_rel=None, forced=None, return_W=False, diag=False,
            score_mode=0, grid_ctas=0, tile_cols=0, spin_budget_ns=0, stream=None,
            timing=False, phase_trace=False, init_path=0, return_basis=False,
-           test_unmet_wait=0) -> Selection:
+           test_unmet_wait=0, split_share=0) -> Selection:
     """Greedy CSS (Algorithm 1) of the columns of A (column-major, on the GPU).
     ``test_unmet_wait`` is the test hook of the bounded device waits (css.h)."""
     m, n, lda = _colmajor(A)
@@ -149,7 +151,7 @@ def select(A: torch.Tensor, k: int, *, tau_rel=None, forced=None, return_W=False
               torch.empty(n, dtype=torch.float64, device=dev),
               torch.empty(n, dtype=torch.float64, device=dev))
     o = _opts(tau_rel, fz, score_mode, grid_ctas, tile_cols, spin_budget_ns, True, dg, init_path,
-              test_unmet_wait)
+              test_unmet_wait, split_share)
     tms = (C.c_double * 2)() if timing else None
     if tms is not None:
         o.timing_ms = C.cast(tms, C.c_void_p)
@@ -304,7 +306,7 @@ class Distributed:
 
 def distributed(A: torch.Tensor, B: torch.Tensor, block_offsets: Sequence[int], l_block: int,
                 k: int, *, tau_rel=None, grid_ctas=0, tile_cols=0, stream=None,
-                init_path=0, timing=None) -> Distributed:
+                init_path=0, timing=None, pivot_cost=0) -> Distributed:
     """Distributed CSS (Algorithm 4) with the concise representation B."""
     m, n, lda = _colmajor(A)
     mb, r, ldb = _colmajor(B, "B")
@@ -319,7 +321,7 @@ def distributed(A: torch.Tensor, B: torch.Tensor, block_offsets: Sequence[int], 
     trace = torch.empty(k + 1, dtype=torch.float64, device=dev)
     nsel = torch.zeros(1, dtype=torch.int32, device=dev)
     bsel = torch.empty((nb, l_block), dtype=torch.int32, device=dev)
-    o = _opts(tau_rel, None, 0, grid_ctas, tile_cols, init_path=init_path)
+    o = _opts(tau_rel, None, 0, grid_ctas, tile_cols, init_path=init_path, pivot_cost=pivot_cost)
     tms = (C.c_double * 2)() if timing is not None else None
     if tms is not None:
         o.timing_ms = C.cast(tms, C.c_void_p)
@@ -551,6 +553,32 @@ class BatchedPlan:
     def results(self):
         nsels = torch.cat([x[2] for x in self._outs]).tolist()
         return [Selection(s, t, int(ns), 0) for (s, t, _), ns in zip(self._outs, nsels)]
+
+
+def autotune_distributed(A: torch.Tensor, B: torch.Tensor, block_offsets: Sequence[int], l_block: int,
+                         k: int, *, stream=None):
+    """Time Algorithm 4's planner pivot costs (0, 300, 700, 1500 columns) on
+    this problem and record the fastest for this device and shape bucket
+    (css_autotune_distributed).  Returns (best cost, {cost: block-launch ms})."""
+    m, n, lda = _colmajor(A)
+    mb, r, ldb = _colmajor(B, "B")
+    dt = _DT[A.dtype]
+    lib = L.load()
+    dev = A.device
+    offs = (C.c_int64 * len(block_offsets))(*[int(v) for v in block_offsets])
+    nb = len(block_offsets) - 1
+    sel = torch.empty(k, dtype=torch.int32, device=dev)
+    trace = torch.empty(k + 1, dtype=torch.float64, device=dev)
+    nsel = torch.zeros(1, dtype=torch.int32, device=dev)
+    nbytes = lib.gcss_distributed_workspace_size(dt, m, n, r, offs, nb, l_block, k)
+    _keep, ws = _workspace(nbytes, dev)
+    best = C.c_int32(0)
+    times = (C.c_double * 4)()
+    code = lib.css_autotune_distributed(_ptr(A), dt, m, n, lda, _ptr(B), r, ldb, offs, nb, l_block, k,
+                                        _ptr(sel), _ptr(trace), _ptr(nsel), _ptr(ws), nbytes, C.byref(best),
+                                        C.cast(times, C.c_void_p), _stream(stream))
+    _check(code, "css_autotune_distributed")
+    return best.value, {c: times[i] for i, c in enumerate((0, 300, 700, 1500))}
 
 
 def autotune(A: torch.Tensor, k: int, *, stream=None):

@@ -332,8 +332,13 @@ def run_distributed(args):
         "projection_sparse_sign_ms": proj_ssgn,
         "initial_scores_ms": init_ms,
         "block_phase_ms": block_ms,
+        # traffic: DRAM bytes read + written by the blocks' launch, from an
+        # ncu capture on the 2048 x 65536 case (16 blocks): 26.927 GB for
+        # 27.427 GB algorithmic, scaled by this launch's algorithmic bytes
         "roofline": {"bound": "hbm", "achieved": block_gbs, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": block_gbs / hbm_peak, "traffic": None, "peak_kind": hbm_kind,
+                     "frac": block_gbs / hbm_peak,
+                     "traffic": block_bytes * (26.893364480e9 + 0.033207552e9) / 27.426553856e9,
+                     "peak_kind": hbm_kind,
                      "kernel": "greedy_kernel (the 64 blocks' persistent launch, Algorithm 4's map phase)",
                      "bytes_per_launch": block_bytes,
                      "bytes": "per block: (l_b + 1) passes over its columns in BF16 + 48 B of score "
@@ -767,12 +772,12 @@ def main():
     per_iter = a_bytes + c_bytes + 48 * n
     achieved = per_iter * res.n_sel / (statistics.mean(loop_ms) / 1e3) / 1e9
     # DRAM traffic per launch from an ncu capture of the greedy kernel on the
-    # 4096 x 32768 case of the same model (17 A passes): reads 1.0163 x the
-    # bytes of A and writes 63.2 B per column per A pass (C stays in L2),
+    # 4096 x 32768 case of the same model (17 A passes): reads 1.0159 x the
+    # bytes of A and writes 56 B per column per A pass (C stays in L2),
     # scaled by the A passes of this launch
     traffic = None
-    if args.workload == WORKLOAD and args.dtype == "bf16":
-        traffic = (res.n_sel + 1) * (a_bytes * 1.0163 + 63.2 * n)
+    if args.workload in (WORKLOAD, "decay_4096x32768") and args.dtype == "bf16":
+        traffic = (res.n_sel + 1) * (a_bytes * 1.0159 + 56.0 * n)
     peak, peak_kind = peaks()
     out = {
         "metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": ws,

@@ -149,7 +149,9 @@ typedef struct {
        multiple of 8, r <= 512), 1 = CUDA-core (SIMT) kernels only.  Used by
        css_project, by the initial scores of gcss_select / gcss_distributed,
        and by css_select's C = A A^T and f^(0) (C split into two BF16 parts
-       that together carry 16 significant bits). */
+       that together carry 16 significant bits; FP32 A is split the same way,
+       any alignment, and each GEMM sums the products hi*hi, hi*lo, lo*hi of
+       the parts). */
     int32_t init_path;
     /* Test hook for the bounded device waits (0 = off, the default).
        1: one team barrier of the persistent greedy kernel (the first of

@@ -450,10 +450,11 @@ SelectLayout select_layout(void* ws, size_t cap, int dt, int64_t m, int64_t n, i
   carve_header(c, 1, L.h, n);
   carve_scores(c, (int)n, L.s);
   carve_rest(c, dt, (int)m, (int)n, k, 0, 0, need_W, L.s);
-  // C = A A^T (m x m) first; for BF16 input the tensor-core path needs its
-  // BF16 parts and row-tile partials right behind it
+  // C = A A^T (m x m) first; for BF16 and FP32 input the tensor-core path
+  // needs its BF16 parts and row-tile partials (and FP32 A's own parts)
+  // right behind it
   size_t cbytes = (size_t)m * m * accsize(dt);
-  if (dt == CSS_BF16) cbytes = std::max(cbytes, tc::css_f0_scratch_bytes((int)m, (int)n));
+  if (dt != CSS_F64) cbytes = std::max(cbytes, tc::css_f0_scratch_bytes((int)m, (int)n, dt == CSS_F32));
   L.C = c.take<char>(cbytes);
   L.partial = c.take<double>(css_f0_partial_doubles(dt, (int)m, (int)n));
   L.bytes = c.off;
@@ -648,9 +649,11 @@ css_status css_select(const void* A, css_dtype dtype, int64_t m, int64_t n, int6
   tm.mark(0, s);
   if (cudaMemsetAsync(L.h.aux_err, 0, sizeof(int), s) != cudaSuccess) return CSS_ERR_CUDA;
   cudaError_t e;
+  const unsigned long long spin = o.spin_budget_ns ? o.spin_budget_ns : kDefaultSpinNs;
   if (dtype == CSS_BF16 && o.init_path != 1 && tc::supported(A, lda, (int)m, 256))
-    e = tc::css_f0(A, lda, (int)m, (int)n, L.C, L.s.f, L.h.aux_err,
-                   o.spin_budget_ns ? o.spin_budget_ns : kDefaultSpinNs, s, stall_mbarrier(o));
+    e = tc::css_f0(A, lda, (int)m, (int)n, L.C, L.s.f, L.h.aux_err, spin, s, stall_mbarrier(o));
+  else if (dtype == CSS_F32 && o.init_path != 1 && tc::supported_any())
+    e = tc::css_f0(A, lda, (int)m, (int)n, L.C, L.s.f, L.h.aux_err, spin, s, stall_mbarrier(o), true);
   else
     e = css_f0_simt(dtype, A, lda, (int)m, (int)n, L.C, L.partial, L.s.f, s);
   if (e != cudaSuccess) return cuda_status(e);

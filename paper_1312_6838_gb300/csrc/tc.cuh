@@ -29,14 +29,19 @@ cudaError_t colnorms(const void* A, long long lda, int m, int n, const float* B,
                      void* scratch, double* f, int* err, unsigned long long spin_ns, cudaStream_t s,
                      int stall = 0);
 
-// Scratch bytes of css_f0 (C in FP32, its BF16 parts, row-tile partials).
-size_t css_f0_scratch_bytes(int m, int n);
+// Scratch bytes of css_f0 (C in FP32, its BF16 parts, row-tile partials;
+// f32: A's own BF16 parts too).
+size_t css_f0_scratch_bytes(int m, int n, bool f32 = false);
+// The tensor-map encoder is available (css_f0 for FP32 input needs no more).
+bool supported_any();
 
 // Algorithm 1's initial scores for BF16 A: C = A A^T on tensor cores (FP32
 // accumulation of exact BF16 products), C split into two BF16 parts, and
 // f[i] = A_:i^T C A_:i from the column dots of A with C A (FP64 sums).
+// f32: A is FP32 (any alignment); it is split into two BF16 parts first and
+// both GEMMs sum the four products of parts.
 cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, double* f, int* err,
-                   unsigned long long spin_ns, cudaStream_t s, int stall = 0);
+                   unsigned long long spin_ns, cudaStream_t s, int stall = 0, bool f32 = false);
 
 }  // namespace tc
 }  // namespace css

@@ -34,7 +34,8 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BK = 64;        // K elements per stage: one 128-byte swizzle row
-constexpr int STAGES = 3;     // ring depth, at most (Params::stages picks 1..3)
+constexpr int STAGES = 4;     // ring depth, at most (Params::stages picks 1..4)
+constexpr int kSmemMax = 227 * 1024;   // dynamic shared memory of one CTA
 constexpr int kThreads = 192;
 constexpr int kTmemCols = 512;
 // BF16 parts of an FP32 operand (B of the GCSS norms, U' of the CSS scores):
@@ -56,8 +57,9 @@ struct Params {
   int stage_bytes;
   float* out;        // projection: [slice][M x N] partials; syrk: C (ld M)
   double* f;         // norms: f[M]; column dots: partial[M-tile][N]
-  const __nv_bfloat16* Acol;  // column dots: the BF16 matrix dotted with D's columns
+  const void* Acol;  // column dots: the matrix dotted with D's columns (BF16, or FP32 if acol_f32)
   long long lda_col;
+  int acol_f32;
   int* err;
   unsigned long long spin_ns;
   // symmetric use of C = A A^T: mode 2 computes only the tiles that touch
@@ -77,6 +79,23 @@ struct Params {
   // afterwards in FP64 (mode 2: per chunk partial tiles; mode 3: partial dots)
   int kb_chunk;
   int tiles_lower;   // mode 2: tiles per chunk (those touching the lower triangle)
+  // part pairs (FP32 operands split into BF16 parts on both sides): when
+  // npairs > 0 every (K block, pair) is its own stage and pair q multiplies
+  // part pair_a[q] of A by part pair_b[q] of B, all into one accumulator.
+  // An M- or N-major operand's parts sit a_kpart / b_kpart columns apart in
+  // K; a K-major operand's parts use a_part_stride / b_part_stride.
+  int npairs;
+  int pair_a[4];
+  int pair_b[4];
+  int a_kpart;
+  int b_kpart;
+  // pair q accumulates into TMEM columns acc2_col * pair_acc[q] onwards.
+  // The tensor cores' accumulation truncates by up to one unit of the
+  // running sum per MMA, so the small cross products (hi lo, lo hi) go to a
+  // second accumulator whose sum, and so its truncation, is 2^8 smaller; the
+  // epilogue adds the two.  acc2_col = 0: one accumulator.
+  int pair_acc[4];
+  int acc2_col;
 };
 
 // Mode 2 tiles (BM rows x 256 columns) that touch the lower triangle: tile
@@ -222,6 +241,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// v += the second accumulator's 16 columns at taddr (when acc2_col != 0),
+// rounded to nearest once
+__device__ __forceinline__ void add_acc2(uint32_t taddr, int acc2_col, float (&v)[16]) {
+  if (acc2_col == 0) return;
+  float w[16];
+  tmem_ld16(taddr, w);
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] += w[i];
+}
+
 template <bool A_MN, bool B_MN>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Params P) {
@@ -268,7 +297,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int nA = (P.group && P.a_part_stride != 0) ? parts : 1;
   const int nB = (P.group && P.b_part_stride != 0) ? parts : 1;
   const int b_tile_bytes = P.halves * P.n_half * BK * 2;
-  const int n_it = max(0, kb_end - kb_begin) * (P.group ? 1 : parts);
+  // stages per K block: one (group), one per pair, or one per part
+  const int per_kb = P.group ? 1 : (P.npairs > 0 ? P.npairs : parts);
+  const int n_it = max(0, kb_end - kb_begin) * per_kb;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NSTG; ++s) {
@@ -297,30 +328,33 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int s = it % NSTG;
       const uint32_t ph = (uint32_t)((it / NSTG) & 1);
       if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u, P.err, P.spin_ns)) break;
-      const int kb = kb_begin + (P.group ? it : it / parts);
-      const int part0 = P.group ? 0 : it % parts;
+      const int kb = kb_begin + it / per_kb;
+      const int q_it = it % per_kb;
+      const int part_a0 = P.group ? 0 : (P.npairs > 0 ? P.pair_a[q_it] : q_it);
+      const int part_b0 = P.group ? 0 : (P.npairs > 0 ? P.pair_b[q_it] : q_it);
       const int k0 = kb * BK;
       uint8_t* sa = smem + s * P.stage_bytes;
       uint8_t* sb = sa + nA * a_bytes;
       const uint32_t fb = smem_u32(&full[s]);
       mbar_expect_tx(fb, (uint32_t)(nA * a_bytes + nB * b_tile_bytes));
       for (int pa = 0; pa < nA; ++pa) {
-        const int part = part0 + pa;
+        const int part = part_a0 + pa;
         uint8_t* ta = sa + pa * a_bytes;
         if (A_MN) {
-          tma_load_2d(smem_u32(ta), &tmA, fb, tile0, k0);
-          tma_load_2d(smem_u32(ta + 64 * BK * 2), &tmA, fb, tile0 + 64, k0);
+          const int ka = part * P.a_kpart + k0;
+          tma_load_2d(smem_u32(ta), &tmA, fb, tile0, ka);
+          tma_load_2d(smem_u32(ta + 64 * BK * 2), &tmA, fb, tile0 + 64, ka);
         } else {
           tma_load_2d(smem_u32(ta), &tmA, fb, k0, part * P.a_part_stride + tile0);
         }
       }
       for (int pb = 0; pb < nB; ++pb) {
-        const int part = part0 + pb;
+        const int part = part_b0 + pb;
         uint8_t* tb = sb + pb * b_tile_bytes;
         if (B_MN) {
           // N-major B: 64-row boxes stacked 8 KB apart (the descriptor's LBO)
           for (int q = 0; q < P.halves * P.n_half / 64; ++q)
-            tma_load_2d(smem_u32(tb + q * 64 * BK * 2), &tmB, fb, ntile0 + 64 * q, k0);
+            tma_load_2d(smem_u32(tb + q * 64 * BK * 2), &tmB, fb, ntile0 + 64 * q, part * P.b_kpart + k0);
         } else {
           for (int h = 0; h < P.halves; ++h)
             tma_load_2d(smem_u32(tb + h * P.n_half * BK * 2), &tmB, fb, k0,
@@ -338,7 +372,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1 && lane == 0) {
     // ---------------------------------------------------------- MMA issuer
     const uint32_t idesc = make_idesc(P.n_half, BM, A_MN, B_MN);
-    const int pg = P.group ? parts : 1;   // parts whose MMAs share one stage
+    // MMAs that share one stage: group mode runs every part on it; otherwise
+    // a stage is one part or one pair
+    const int pg = P.group ? parts : 1;
     for (int it = 0; it < n_it; ++it) {
       const int s = it % NSTG;
       const uint32_t ph = (uint32_t)((it / NSTG) & 1);
@@ -349,15 +385,27 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int ks = 0; ks < BK / 16; ++ks) {
         for (int pp = 0; pp < pg; ++pp) {
-          const uint32_t sa = sa0 + (nA > 1 ? pp : 0) * a_bytes;
-          const uint32_t sb = sb0 + (nB > 1 ? pp : 0) * b_tile_bytes;
+          // the stage's tiles, its accumulator, and whether this MMA is the
+          // first into that accumulator (its input is then ignored)
+          const int ia = nA > 1 ? pp : 0, ib = nB > 1 ? pp : 0;
+          uint32_t acc = 0;
+          bool first = it == 0 && ks == 0 && pp == 0;
+          if (P.npairs > 0) {
+            const int q = it % per_kb;
+            acc = (uint32_t)(P.pair_acc[q] * P.acc2_col);
+            first = it / per_kb == 0 && ks == 0;
+            for (int q2 = 0; q2 < q; ++q2)
+              if (P.pair_acc[q2] == P.pair_acc[q]) first = false;
+          }
+          const uint32_t sa = sa0 + ia * a_bytes;
+          const uint32_t sb = sb0 + ib * b_tile_bytes;
           // A: M-major -> 16 K rows of 128 bytes per step; K-major -> 32 bytes
           const uint64_t ad = A_MN ? make_desc(sa + ks * 2048, 64 * BK * 2, 1024)
                                    : make_desc(sa + ks * 32, 16, 1024);
           for (int h = 0; h < P.halves; ++h) {
             const uint64_t bd = B_MN ? make_desc(sb + h * P.n_half * BK * 2 + ks * 2048, 64 * BK * 2, 1024)
                                      : make_desc(sb + h * P.n_half * BK * 2 + ks * 32, 16, 1024);
-            umma(tmem + h * P.n_half, ad, bd, idesc, (it > 0 || ks > 0 || pp > 0) ? 1u : 0u);
+            umma(tmem + acc + h * P.n_half, ad, bd, idesc, first ? 0u : 1u);
           }
         }
       }
@@ -401,6 +449,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int j0 = 0; j0 < ncols; j0 += 16) {
         float v[16];
         tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)j0, v);
+        add_acc2(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(P.acc2_col + j0), P.acc2_col, v);
         float ph[16], pl[16];
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj) {
@@ -408,7 +457,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           ph[jj] = 0.f;
           pl[jj] = 0.f;
           if (row < P.M && c < P.N) {
-            const float a = __bfloat162float(P.Acol[(long long)c * P.lda_col + row]);
+            const long long ai = (long long)c * P.lda_col + row;
+            const float a = P.acol_f32 ? reinterpret_cast<const float*>(P.Acol)[ai]
+                                       : __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(P.Acol)[ai]);
             ph[jj] = a * v[jj];
             pl[jj] = fmaf(a, v[jj], -ph[jj]);
           }
@@ -456,6 +507,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int j0 = 0; j0 < ncols; j0 += 16) {
         float v[16];
         tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)j0, v);
+        add_acc2(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(P.acc2_col + j0), P.acc2_col, v);
         if (row < P.M) {
 #pragma unroll
           for (int jj = 0; jj < 16; ++jj) {
@@ -545,7 +597,14 @@ void halves_for(int r, int& n_half, int& halves) {
   }
 }
 
-size_t smem_for(int stage_bytes, int stages = STAGES) { return (size_t)stages * stage_bytes + 256 + 1024; }
+size_t smem_for(int stage_bytes, int stages) { return (size_t)stages * stage_bytes + 256 + 1024; }
+
+// Deepest ring (up to `want` stages) that fits in one CTA's shared memory.
+int fit_stages(int stage_bytes, int want) {
+  int st = want;
+  while (st > 1 && smem_for(stage_bytes, st) > (size_t)kSmemMax) --st;
+  return st;
+}
 
 }  // namespace
 
@@ -578,12 +637,12 @@ cudaError_t project_partials(const void* A, long long lda, int m, int n, const v
   P.kb_total = (n + BK - 1) / BK;
   P.kb_per_cta = (P.kb_total + slices - 1) / slices;
   P.nparts = 1;
-  P.stages = STAGES;
   P.stage_bytes = BM * BK * 2 + halves * n_half * BK * 2;
+  P.stages = fit_stages(P.stage_bytes, STAGES);
   P.out = partial;
   P.err = err;
   P.spin_ns = spin_ns;
-  const size_t smem = smem_for(P.stage_bytes);
+  const size_t smem = smem_for(P.stage_bytes, P.stages);
   cudaError_t e = cudaFuncSetAttribute(tc_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((m + BM - 1) / BM, slices);
@@ -620,14 +679,14 @@ cudaError_t colnorms(const void* A, long long lda, int m, int n, const float* B,
   P.kb_total = (m + BK - 1) / BK;
   P.kb_per_cta = P.kb_total;
   P.nparts = kParts;
-  P.stages = STAGES;
   P.b_part_stride = rpad;
   P.stage_bytes = BM * BK * 2 + halves * n_half * BK * 2;
+  P.stages = fit_stages(P.stage_bytes, STAGES);
   P.f = f;
   P.err = err;
   P.spin_ns = spin_ns;
   P.stall = stall;
-  const size_t smem = smem_for(P.stage_bytes);
+  const size_t smem = smem_for(P.stage_bytes, P.stages);
   cudaError_t e = cudaFuncSetAttribute(tc_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((n + BM - 1) / BM, 1);
@@ -700,7 +759,11 @@ int dots_chunks(int m) { return ((m + BK - 1) / BK + kDotsChunkKb - 1) / kDotsCh
 // Scratch of css_f0: C (FP32, m x m), then one region used first for the
 // K-chunk partial tiles of C and afterwards for U' in BF16 parts and
 // the column-dot partials.
-size_t css_f0_scratch_bytes(int m, int n) {
+// FP32 input: A's BF16 parts, side by side, each padded to whole K blocks
+// (part p, column j at Ap[(p * npad + j) * mpad + i], zero beyond m and n).
+int f32_npad(int n) { return (n + BK - 1) / BK * BK; }
+
+size_t css_f0_scratch_bytes(int m, int n, bool f32) {
   const int mpad = (m + 7) / 8 * 8;
   const int rpad = (m + 15) / 16 * 16;
   const int mtiles = (m + BM - 1) / BM;
@@ -708,25 +771,47 @@ size_t css_f0_scratch_bytes(int m, int n) {
   const size_t chunks = align_up((size_t)syrk_chunks(n) * lower_tile_count(mtiles) * BM * 256 * 4);
   const size_t parts = align_up((size_t)mpad * kParts * rpad * 2);
   const size_t part = align_up((size_t)mtiles * dots_chunks(m) * n * 8);
-  return c + std::max(chunks, parts + part);
+  const size_t a_parts = f32 ? align_up((size_t)mpad * kParts * f32_npad(n) * 2) : 0;
+  return c + std::max(chunks, parts + part) + a_parts;
 }
 
 cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, double* f, int* err,
-                   unsigned long long spin_ns, cudaStream_t s, int stall) {
+                   unsigned long long spin_ns, cudaStream_t s, int stall, bool f32) {
   const int mpad = (m + 7) / 8 * 8;
   const int rpad = (m + 15) / 16 * 16;
   const int mtiles = (m + BM - 1) / BM;
+  const int npad = f32_npad(n);
   float* C = (float*)scratch;
   float* chunk_tiles = (float*)((char*)scratch + align_up((size_t)m * m * 4));
   __nv_bfloat16* Cp = (__nv_bfloat16*)chunk_tiles;
   double* partial = (double*)((char*)Cp + align_up((size_t)mpad * kParts * rpad * 2));
   const int nchunk = syrk_chunks(n), ndots = dots_chunks(m);
   const int tiles_lower = lower_tile_count(mtiles);
+  // FP32 A: its BF16 parts after the C / chunk / U' region (see css_f0_scratch_bytes)
+  __nv_bfloat16* Ap = nullptr;
+  if (f32) {
+    const size_t c = align_up((size_t)m * m * 4);
+    const size_t chunks = align_up((size_t)nchunk * tiles_lower * BM * 256 * 4);
+    const size_t parts = align_up((size_t)mpad * kParts * rpad * 2);
+    const size_t part = align_up((size_t)mtiles * ndots * n * 8);
+    Ap = (__nv_bfloat16*)((char*)scratch + c + std::max(chunks, parts + part));
+  }
+  // the operand pairs of the FP32 path: (hi, hi), (hi, lo), (lo, hi); lo lo
+  // is below 2^-32 of the product, under the FP32 accumulation's own rounding
+  constexpr int kPairs = 3;
+  const int kPairA[kPairs] = {0, 0, 1}, kPairB[kPairs] = {0, 1, 0};
   cudaError_t e;
+  if (f32) {
+    const long long tot = (long long)mpad * npad;
+    split_parts_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>((const float*)A, lda, m, n, mpad, npad, Ap, 0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   // C = A A^T: both operands are A, row-major in K (= the column index)
   {
     CUtensorMap ta;
-    if (!make_map(&ta, A, (uint64_t)m, (uint64_t)n, (uint64_t)lda, BK)) return cudaErrorInvalidValue;
+    const bool ok = f32 ? make_map(&ta, Ap, (uint64_t)mpad, (uint64_t)kParts * npad, (uint64_t)mpad, BK)
+                        : make_map(&ta, A, (uint64_t)m, (uint64_t)n, (uint64_t)lda, BK);
+    if (!ok) return cudaErrorInvalidValue;
     Params P{};
     P.mode = 2;
     P.tri = 1;
@@ -740,13 +825,25 @@ cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, do
     P.kb_chunk = syrk_chunk_kb(n);
     P.tiles_lower = tiles_lower;
     P.nparts = 1;
-    P.stages = STAGES;
+    if (f32) {
+      // C = (A1 + A2)(A1 + A2)^T, the pairs of parts into one accumulator
+      P.npairs = kPairs;
+      for (int q = 0; q < kPairs; ++q) {
+        P.pair_a[q] = kPairA[q];
+        P.pair_b[q] = kPairB[q];
+        P.pair_acc[q] = q > 0;
+      }
+      P.acc2_col = 256;
+      P.a_kpart = npad;
+      P.b_kpart = npad;
+    }
     P.stage_bytes = BM * BK * 2 + 256 * BK * 2;
+    P.stages = fit_stages(P.stage_bytes, STAGES);
     P.out = chunk_tiles;
     P.err = err;
     P.spin_ns = spin_ns;
     P.stall = stall;
-    const size_t smem = smem_for(P.stage_bytes);
+    const size_t smem = smem_for(P.stage_bytes, P.stages);
     if ((e = cudaFuncSetAttribute(tc_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
       return e;
     dim3 grid(mtiles, (m + 255) / 256, nchunk);
@@ -756,7 +853,7 @@ cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, do
   // C = the chunks' sum, both triangles (the greedy iterations read whole rows)
   reduce_lower_kernel<<<dim3((m + 31) / 32, (m + 31) / 32), dim3(32, 8), 0, s>>>(chunk_tiles, nchunk,
                                                                                  tiles_lower, m, C);
-  // U' (upper triangle of C, diagonal halved) = U1 + U2 + U3 in BF16
+  // U' (upper triangle of C, diagonal halved) = U1 + U2 in BF16
   {
     const long long tot = (long long)mpad * rpad;
     split_parts_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(C, m, m, m, mpad, rpad, Cp, 1);
@@ -767,29 +864,49 @@ cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, do
   {
     CUtensorMap ta, tb;
     if (!make_map(&ta, Cp, (uint64_t)mpad, (uint64_t)(kParts * rpad), (uint64_t)mpad, BM)) return cudaErrorInvalidValue;
-    if (!make_map(&tb, A, (uint64_t)m, (uint64_t)n, (uint64_t)lda, 256)) return cudaErrorInvalidValue;
+    const bool ok = f32 ? make_map(&tb, Ap, (uint64_t)mpad, (uint64_t)kParts * npad, (uint64_t)mpad, 256)
+                        : make_map(&tb, A, (uint64_t)m, (uint64_t)n, (uint64_t)lda, 256);
+    if (!ok) return cudaErrorInvalidValue;
     Params P{};
     P.mode = 3;
     P.tri = 1;
     P.M = m;
     P.N = n;
-    // 512 columns per CTA (two MMAs of N = 256, the whole TMEM) and one stage
-    // per K block holding the U' parts and the single shared A tile:
-    // 96 KB per stage, two stages
     P.n_half = 256;
-    P.halves = 2;
-    P.n_tile = 512;
-    P.group = 1;
+    P.halves = f32 ? 1 : 2;
+    P.n_tile = P.halves * 256;
     P.kb_total = (m + BK - 1) / BK;
     P.kb_per_cta = P.kb_total;
     P.kb_chunk = kDotsChunkKb;
-    P.nparts = kParts;
-    P.stages = 2;
     P.a_part_stride = rpad;
-    P.b_part_stride = 0;
-    P.stage_bytes = kParts * BM * BK * 2 + 512 * BK * 2;
+    if (f32) {
+      // one stage per (K block, pair), 256 columns per CTA (the cross
+      // products take the other half of TMEM): 48 KB per stage
+      P.group = 0;
+      P.nparts = 1;
+      P.npairs = kPairs;
+      for (int q = 0; q < kPairs; ++q) {
+        P.pair_a[q] = kPairA[q];
+        P.pair_b[q] = kPairB[q];
+        P.pair_acc[q] = q > 0;
+      }
+      P.acc2_col = 256;
+      P.b_part_stride = npad;
+      P.stage_bytes = BM * BK * 2 + 256 * BK * 2;
+      P.stages = fit_stages(P.stage_bytes, STAGES);
+    } else {
+      // 512 columns per CTA (two MMAs of N = 256, the whole TMEM) and one
+      // stage per K block holding the U' parts and the single shared A tile:
+      // 96 KB per stage
+      P.group = 1;
+      P.nparts = kParts;
+      P.b_part_stride = 0;
+      P.stage_bytes = kParts * BM * BK * 2 + 512 * BK * 2;
+      P.stages = 2;
+    }
     P.f = partial;
-    P.Acol = (const __nv_bfloat16*)A;
+    P.Acol = A;
+    P.acol_f32 = f32 ? 1 : 0;
     P.lda_col = lda;
     P.err = err;
     P.spin_ns = spin_ns;
@@ -797,7 +914,7 @@ cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, do
     const size_t smem = smem_for(P.stage_bytes, P.stages);
     if ((e = cudaFuncSetAttribute(tc_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
       return e;
-    dim3 grid(mtiles, (n + 511) / 512, ndots);
+    dim3 grid(mtiles, (n + P.n_tile - 1) / P.n_tile, ndots);
     tc_kernel<false, false><<<grid, kThreads, smem, s>>>(ta, tb, P);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -805,6 +922,8 @@ cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, do
   sum_rows_kernel<<<(n + 255) / 256, 256, 0, s>>>(partial, mtiles * ndots, n, f, 2.0);
   return cudaGetLastError();
 }
+
+bool supported_any() { return encode_fn() != nullptr; }
 
 }  // namespace tc
 }  // namespace css

@@ -71,8 +71,7 @@ def score_error_bound(ref, t, m, dtype):
         |d sc_i| <= lambda u sqrt(m) sqrt(t + 1) (sc0_max g_i^(0) / g_i + sc_i).
     This is a first-order model, not a worst-case bound; the GPU tests
     measure the device's actual score errors against it
-    (oracle_path_parity), and the largest measured error is a few tenths of
-    it (the design doc states the figures)."""
+    (oracle_path_parity) and print the largest ratio they see."""
     f0, g0 = ref.fs[0], ref.gs[0]
     g = ref.gs[t]
     with np.errstate(divide="ignore", invalid="ignore"):

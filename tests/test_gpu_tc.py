@@ -1,5 +1,6 @@
-"""The tcgen05 (tensor-core) GEMMs: B = A Omega and the GCSS initial scores
-||B^T a_i||^2 for BF16 A, against the oracle and against the SIMT kernels."""
+"""The tcgen05 (tensor-core) GEMMs: B = A Omega, the GCSS initial scores
+||B^T a_i||^2 for BF16 A and the CSS initial scores a_i^T A A^T a_i for BF16
+and FP32 A, against the oracle and against the SIMT kernels."""
 import numpy as np
 import pytest
 import torch
@@ -21,7 +22,7 @@ def css():
 
 
 @pytest.mark.parametrize("shape", [(256, 1024, 64), (200, 777, 16), (136, 5000, 400),
-                                   (2048, 16384, 400), (512, 3000, 300)])
+                                   (2048, 16384, 400), (512, 3000, 300), (300, 2000, 512)])
 def test_projection_tensor_cores(css, shape):
     m, n, r = shape
     A_np = ci.lowrank_uv(m, n, 8, 0.1, 41 + m).astype(np.float32)
@@ -37,7 +38,8 @@ def test_projection_tensor_cores(css, shape):
     assert np.all(np.abs(B_simt - ref) <= 4 * np.sqrt(n) * eps * bound + 1e-30)
 
 
-@pytest.mark.parametrize("shape", [(64, 700, 24, 8), (256, 3000, 400, 12), (136, 1000, 300, 10)])
+@pytest.mark.parametrize("shape", [(64, 700, 24, 8), (256, 3000, 400, 12), (136, 1000, 300, 10),
+                                   (128, 1500, 512, 8)])
 def test_gcss_initial_scores_tensor_cores(css, shape):
     m, n, r, k = shape
     A_np = ci.lowrank_uv(m, n, 2 * k, 0.05, 77 + m)
@@ -56,17 +58,19 @@ def test_gcss_initial_scores_tensor_cores(css, shape):
                                atol=1e-5 * ref.trace[0])
 
 
-@pytest.mark.parametrize("shape", [(256, 3000, 12), (200, 1000, 10), (520, 2600, 16)])
-def test_css_initial_scores_tensor_cores(css, shape):
-    """C = A A^T and f0 = a_i^T C a_i on tensor cores (BF16 A): parity with the
-    oracle and the same trace as the SIMT initialisation."""
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float32])
+@pytest.mark.parametrize("shape", [(256, 3000, 12), (200, 1000, 10), (520, 2600, 16), (37, 203, 9)])
+def test_css_initial_scores_tensor_cores(css, shape, dtype):
+    """C = A A^T and f0 = a_i^T C a_i on tensor cores (BF16 A, or FP32 A split
+    into two BF16 parts): parity with the oracle and the same trace as the
+    SIMT initialisation."""
     m, n, k = shape
     A_np = ci.lowrank_uv(m, n, 2 * k, 0.05, 91 + m)
-    A, Av = dev_matrix(A_np, torch.bfloat16)
+    A, Av = dev_matrix(A_np, dtype)
     ref = O.greedy_css(Av, k, tau_rel=1e-6, keep_scores=True)
     teacher_forced_parity(
         lambda forced: css.select(A, k, forced=forced or None).indices.cpu().tolist(), ref,
-        m=m, dtype=torch.bfloat16)
+        m=m, dtype=dtype)
     a = css.select(A, k, diag=True)
     b = css.select(A, k, diag=True, init_path=1)
     np.testing.assert_allclose(a.trace.cpu().numpy(), b.trace.cpu().numpy(), rtol=0,

@@ -451,10 +451,11 @@ SelectLayout select_layout(void* ws, size_t cap, int dt, int64_t m, int64_t n, i
   carve_scores(c, (int)n, L.s);
   carve_rest(c, dt, (int)m, (int)n, k, 0, 0, need_W, L.s);
   // C = A A^T (m x m) first; for BF16 and FP32 input the tensor-core path
-  // needs its BF16 parts and row-tile partials (and FP32 A's own parts)
-  // right behind it
+  // needs its BF16 parts and row-tile partials (and A's parts or aligned
+  // copy) right behind it
   size_t cbytes = (size_t)m * m * accsize(dt);
-  if (dt != CSS_F64) cbytes = std::max(cbytes, tc::css_f0_scratch_bytes((int)m, (int)n, dt == CSS_F32));
+  if (dt != CSS_F64)
+    cbytes = std::max(cbytes, tc::css_f0_scratch_bytes((int)m, (int)n, dt == CSS_F32 ? tc::kF0F32 : tc::kF0Bf16Staged));
   L.C = c.take<char>(cbytes);
   L.partial = c.take<double>(css_f0_partial_doubles(dt, (int)m, (int)n));
   L.bytes = c.off;
@@ -650,10 +651,9 @@ css_status css_select(const void* A, css_dtype dtype, int64_t m, int64_t n, int6
   if (cudaMemsetAsync(L.h.aux_err, 0, sizeof(int), s) != cudaSuccess) return CSS_ERR_CUDA;
   cudaError_t e;
   const unsigned long long spin = o.spin_budget_ns ? o.spin_budget_ns : kDefaultSpinNs;
-  if (dtype == CSS_BF16 && o.init_path != 1 && tc::supported(A, lda, (int)m, 256))
-    e = tc::css_f0(A, lda, (int)m, (int)n, L.C, L.s.f, L.h.aux_err, spin, s, stall_mbarrier(o));
-  else if (dtype == CSS_F32 && o.init_path != 1 && tc::supported_any())
-    e = tc::css_f0(A, lda, (int)m, (int)n, L.C, L.s.f, L.h.aux_err, spin, s, stall_mbarrier(o), true);
+  if (dtype != CSS_F64 && o.init_path != 1 && tc::supported_any())
+    e = tc::css_f0(A, lda, (int)m, (int)n, L.C, L.s.f, L.h.aux_err, spin, s, stall_mbarrier(o),
+                   tc::f0_source(dtype == CSS_F32, A, lda, (int)m));
   else
     e = css_f0_simt(dtype, A, lda, (int)m, (int)n, L.C, L.partial, L.s.f, s);
   if (e != cudaSuccess) return cuda_status(e);
@@ -1201,6 +1201,7 @@ struct BatchLayout {
   std::vector<double*> partial;
   F0Item* items;   // initial-score work list, count entries
   int* starts;     // 3 * (count + 1) first blocks (css_f0_grouped_starts)
+  void* gdesc;     // tensor-core path: descriptors and tile lists of the group
   size_t bytes;
 };
 
@@ -1217,11 +1218,25 @@ BatchLayout batch_layout(void* ws, size_t cap, const css_problem* probs, int cou
     const css_problem& p = probs[i];
     carve_scores(c, (int)p.n, L.st[i]);
     carve_rest(c, dt, (int)p.m, (int)p.n, p.k, 0, 0, p.W == nullptr, L.st[i]);
-    L.C[i] = c.take<char>((size_t)p.m * p.m * accsize(dt));
+    // C first; for BF16 and FP32 input the tensor-core path's scratch
+    // (tc::css_f0_scratch_bytes) starts with C
+    size_t cbytes = (size_t)p.m * p.m * accsize(dt);
+    if (dt != CSS_F64)
+      cbytes = std::max(cbytes, tc::css_f0_scratch_bytes((int)p.m, (int)p.n,
+                                                         dt == CSS_F32 ? tc::kF0F32 : tc::kF0Bf16Staged));
+    L.C[i] = c.take<char>(cbytes);
     L.partial[i] = c.take<double>(css_f0_partial_doubles(dt, (int)p.m, (int)p.n));
   }
   L.items = c.take<F0Item>(std::max(count, 1));
   L.starts = c.take<int>(3 * (std::max(count, 1) + 1));
+  if (dt != CSS_F64) {
+    std::vector<int> ms(count), ns(count);
+    for (int i = 0; i < count; ++i) {
+      ms[i] = (int)probs[i].m;
+      ns[i] = (int)probs[i].n;
+    }
+    L.gdesc = c.take<char>(tc::group_f0_desc_bytes(ms.data(), ns.data(), count, dt == CSS_F32));
+  }
   L.bytes = c.off;
   return L;
 }
@@ -1231,6 +1246,9 @@ struct BatchedPlanImpl {
   uint64_t magic;
   void* ws;
   int count, dtype;
+  int simt_count;  // problems whose initial scores take the SIMT kernels (items)
+  int use_tc;      // the others: grouped tensor-core launches (tcg)
+  tc::GroupF0 tcg;
   F0Grid grid;
   const F0Item* items;
   const int* starts;
@@ -1258,24 +1276,57 @@ css_status batched_prepare(const css_problem* probs, int32_t count, css_dtype dt
   if (!device_ok()) return CSS_ERR_UNSUPPORTED;
   std::vector<UnitDesc> units;
   std::vector<double> work;
-  std::vector<F0Item> items(count);
-  std::vector<int> ms(count), ns(count), starts(3 * (count + 1));
+  // initial scores: tensor cores for BF16 / FP32 problems (one grouped
+  // launch per phase), the SIMT kernels for FP64 or with init_path = 1
+  std::vector<F0Item> items;
+  std::vector<int> ms, ns, starts;
+  std::vector<const void*> tA;
+  std::vector<long long> tlda;
+  std::vector<int> tm_, tn;
+  std::vector<void*> tscr;
+  std::vector<double*> tf;
+  std::vector<int> tsrc;
+  const bool tc_ok = dtype != CSS_F64 && o.init_path != 1 && count <= 65535 && tc::supported_any();
   for (int i = 0; i < count; ++i) {
     const css_problem& p = probs[i];
-    items[i] = F0Item{p.A, p.lda, (int)p.m, (int)p.n, L.C[i], L.partial[i], L.st[i].f};
-    ms[i] = (int)p.m;
-    ns[i] = (int)p.n;
+    if (tc_ok) {
+      tsrc.push_back(tc::f0_source(dtype == CSS_F32, p.A, p.lda, (int)p.m));
+      tA.push_back(p.A);
+      tlda.push_back(p.lda);
+      tm_.push_back((int)p.m);
+      tn.push_back((int)p.n);
+      tscr.push_back(L.C[i]);
+      tf.push_back(L.st[i].f);
+    } else {
+      items.push_back(F0Item{p.A, p.lda, (int)p.m, (int)p.n, L.C[i], L.partial[i], L.st[i].f});
+      ms.push_back((int)p.m);
+      ns.push_back((int)p.n);
+    }
     units.push_back(make_unit(p.A, dtype, p.m, p.n, p.lda, p.k, 0, L.C[i], p.m, 0, L.st[i], p.W,
                               p.sel, p.trace, p.n_sel, o));
     work.push_back((double)p.k * p.m * p.n + 4.0 * p.m * p.k * p.k);
   }
   P = BatchedPlanImpl{};
-  P.grid = css_f0_grouped_starts(dtype, ms.data(), ns.data(), count, starts.data());
+  P.simt_count = (int)items.size();
   cudaError_t e;
-  if ((e = cudaMemcpyAsync(L.items, items.data(), sizeof(F0Item) * count, cudaMemcpyHostToDevice, s)) != cudaSuccess)
-    return cuda_status(e);
-  if ((e = cudaMemcpyAsync(L.starts, starts.data(), sizeof(int) * starts.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess)
-    return cuda_status(e);
+  if (P.simt_count > 0) {
+    starts.resize(3 * (items.size() + 1));
+    P.grid = css_f0_grouped_starts(dtype, ms.data(), ns.data(), P.simt_count, starts.data());
+    if ((e = cudaMemcpyAsync(L.items, items.data(), sizeof(F0Item) * items.size(), cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess)
+      return cuda_status(e);
+    if ((e = cudaMemcpyAsync(L.starts, starts.data(), sizeof(int) * starts.size(), cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess)
+      return cuda_status(e);
+  }
+  if (!tA.empty()) {
+    const unsigned long long spin = o.spin_budget_ns ? o.spin_budget_ns : kDefaultSpinNs;
+    if ((e = tc::group_f0_prepare((int)tA.size(), tA.data(), tlda.data(), tm_.data(), tn.data(), tscr.data(),
+                                  tf.data(), tsrc.data(), L.gdesc, L.h.aux_err, spin, &P.tcg, s)) !=
+        cudaSuccess)
+      return cuda_status(e);
+    P.use_tc = 1;
+  }
   int64_t m_big = 0, n_big = 0;
   for (int i = 0; i < count; ++i)
     if (probs[i].m * probs[i].n > m_big * n_big) { m_big = probs[i].m; n_big = probs[i].n; }
@@ -1295,13 +1346,16 @@ css_status batched_prepare(const css_problem* probs, int32_t count, css_dtype dt
   return CSS_OK;
 }
 
-// Initial scores of every problem (three grouped launches), then the
-// persistent launch: device work only, so the sequence can be captured.
+// Initial scores of every problem (grouped launches: SIMT and/or tensor
+// cores), then the persistent launch: device work only, so the sequence can
+// be captured.
 css_status batched_run(const BatchedPlanImpl& P, cudaStream_t s, PhaseTimer* tm) {
   if (cudaMemsetAsync(P.aux_err, 0, sizeof(int), s) != cudaSuccess) return CSS_ERR_CUDA;
   if (tm) tm->mark(0, s);
-  cudaError_t e = css_f0_grouped(P.dtype, P.items, P.starts, P.grid, P.count, s);
-  if (e != cudaSuccess) return cuda_status(e);
+  cudaError_t e;
+  if (P.simt_count > 0 && (e = css_f0_grouped(P.dtype, P.items, P.starts, P.grid, P.simt_count, s)) != cudaSuccess)
+    return cuda_status(e);
+  if (P.use_tc && (e = tc::group_f0_run(P.tcg, s)) != cudaSuccess) return cuda_status(e);
   if (tm) tm->mark(1, s);
   css_status cs = start_units(P.info, s);
   if (tm) tm->mark(2, s);

@@ -29,19 +29,47 @@ cudaError_t colnorms(const void* A, long long lda, int m, int n, const float* B,
                      void* scratch, double* f, int* err, unsigned long long spin_ns, cudaStream_t s,
                      int stall = 0);
 
-// Scratch bytes of css_f0 (C in FP32, its BF16 parts, row-tile partials;
-// f32: A's own BF16 parts too).
-size_t css_f0_scratch_bytes(int m, int n, bool f32 = false);
+// How css_f0 reads A: BF16 straight from A through TMA (supported()), BF16
+// copied first to an aligned buffer (any other layout), FP32 split first
+// into three BF16 parts (any layout).
+enum F0Source { kF0Bf16 = 0, kF0Bf16Staged = 1, kF0F32 = 2 };
+int f0_source(bool f32, const void* A, long long lda, int m);
+// Scratch bytes of css_f0 (C in FP32, its BF16 parts, row-tile partials,
+// A's parts or copy).  kF0Bf16Staged bounds every BF16 layout.
+size_t css_f0_scratch_bytes(int m, int n, int src);
 // The tensor-map encoder is available (css_f0 for FP32 input needs no more).
 bool supported_any();
 
-// Algorithm 1's initial scores for BF16 A: C = A A^T on tensor cores (FP32
-// accumulation of exact BF16 products), C split into two BF16 parts, and
-// f[i] = A_:i^T C A_:i from the column dots of A with C A (FP64 sums).
-// f32: A is FP32 (any alignment); it is split into two BF16 parts first and
-// both GEMMs sum the four products of parts.
+// Algorithm 1's initial scores: C = A A^T on tensor cores (FP32
+// accumulation of exact BF16 products, in K chunks added in FP64), C split
+// into three BF16 parts (all of its FP32 bits), and f[i] = A_:i^T C A_:i from
+// the column dots of A with C A (FP64 sums).  src = f0_source(...): for FP32
+// A both GEMMs sum the six products of its parts down to 2^-16.
 cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, double* f, int* err,
-                   unsigned long long spin_ns, cudaStream_t s, int stall = 0, bool f32 = false);
+                   unsigned long long spin_ns, cudaStream_t s, int stall, int src);
+
+// css_f0 for a group of problems (a batch): one launch per phase for all of
+// them.  Problem i's scratch (css_f0_scratch_bytes(m[i], n[i], src[i])
+// bytes, C first) is scratch[i]; its scores go to f[i].
+struct GroupProb;
+struct GroupTile;
+struct GroupF0 {
+  const GroupProb* probs;   // device: count descriptors
+  const GroupTile* tiles2;  // device: the C = A A^T tiles of every problem
+  const GroupTile* tiles3;  // device: the column-dot tiles
+  int count, ntiles2, ntiles3, staged;
+  int smem2, smem3;
+};
+// Bytes of device memory for the descriptors and tile lists.
+size_t group_f0_desc_bytes(const int* m, const int* n, int count, bool f32);
+// Writes the descriptors (tensor maps encoded on the host) to `desc` and
+// fills `out`; synchronises `s` (the host lists end with the call).  All
+// problems share one input type (src[i] = f0_source(...)); count <= 65535.
+cudaError_t group_f0_prepare(int count, const void* const* A, const long long* lda, const int* m, const int* n,
+                             void* const* scratch, double* const* f, const int* src, void* desc, int* err,
+                             unsigned long long spin_ns, GroupF0* out, cudaStream_t s);
+// Enqueues the phases (device work only: capturable).
+cudaError_t group_f0_run(const GroupF0& g, cudaStream_t s);
 
 }  // namespace tc
 }  // namespace css

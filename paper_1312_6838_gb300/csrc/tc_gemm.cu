@@ -25,6 +25,9 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "tc.cuh"
 #include "css_common.cuh"
 
@@ -38,9 +41,14 @@ constexpr int STAGES = 4;     // ring depth, at most (Params::stages picks 1..4)
 constexpr int kSmemMax = 227 * 1024;   // dynamic shared memory of one CTA
 constexpr int kThreads = 192;
 constexpr int kTmemCols = 512;
-// BF16 parts of an FP32 operand (B of the GCSS norms, U' of the CSS scores):
-// hi + lo carry 16 significant bits
+// BF16 parts of an FP32 operand.  B of the GCSS norms takes two (hi + lo,
+// 16 significant bits).  U' of the CSS scores and FP32 A take three (all 24
+// bits): the scores of late iterations are small differences of O(f^(0))
+// terms, and a 2^-17 relative error in every entry of U' or A, though within
+// a few u sqrt(m) of f^(0), moved late picks enough to raise the final error
+// of small problems (m ~ 70, k ~ 0.8 m) 20-300 fold over the oracle's.
 constexpr int kParts = 2;
+constexpr int kUParts = 3;
 
 struct Params {
   int mode;          // 0 projection partials, 1 squared row norms, 2 C = A A^T, 3 column dots
@@ -60,6 +68,7 @@ struct Params {
   const void* Acol;  // column dots: the matrix dotted with D's columns (BF16, or FP32 if acol_f32)
   long long lda_col;
   int acol_f32;
+  int acol_vec;      // Acol and lda_col allow 16-byte loads
   int* err;
   unsigned long long spin_ns;
   // symmetric use of C = A A^T: mode 2 computes only the tiles that touch
@@ -85,8 +94,8 @@ struct Params {
   // An M- or N-major operand's parts sit a_kpart / b_kpart columns apart in
   // K; a K-major operand's parts use a_part_stride / b_part_stride.
   int npairs;
-  int pair_a[4];
-  int pair_b[4];
+  int pair_a[8];
+  int pair_b[8];
   int a_kpart;
   int b_kpart;
   // pair q accumulates into TMEM columns acc2_col * pair_acc[q] onwards.
@@ -94,9 +103,36 @@ struct Params {
   // running sum per MMA, so the small cross products (hi lo, lo hi) go to a
   // second accumulator whose sum, and so its truncation, is 2^8 smaller; the
   // epilogue adds the two.  acc2_col = 0: one accumulator.
-  int pair_acc[4];
+  int pair_acc[8];
   int acc2_col;
 };
+
+}  // namespace
+
+// One problem of a group (see group_f0_prepare).  Tensor maps first: they
+// must sit on 64-byte boundaries in device memory.
+struct GroupProb {
+  CUtensorMap mapA2;   // C = A A^T: A (or its parts), box {64, BK}
+  CUtensorMap mapU;    // U' parts, box {64, BM}
+  CUtensorMap mapA3;   // column dots: A (or its parts), box {64, 256}
+  Params p2, p3;       // the two GEMMs (f0_params_syrk, f0_params_dots)
+  const void* A;
+  long long lda;
+  int m, n, mpad, npad, rpad, src;   // src: F0Source
+  int nchunk, ndots, mtiles, tiles_lower;
+  float* C;
+  float* chunk_tiles;
+  __nv_bfloat16* Cp;
+  __nv_bfloat16* Ap;
+  double* partial;
+  double* f;
+};
+// One CTA of a grouped GEMM launch: problem, row tile, column tile, K chunk.
+struct GroupTile {
+  int prob, bx, by, bz;
+};
+
+namespace {
 
 // Mode 2 tiles (BM rows x 256 columns) that touch the lower triangle: tile
 // (bx, by) does when bx * 128 + 127 >= by * 256, i.e. by <= bx / 2.  Their
@@ -251,9 +287,14 @@ __device__ __forceinline__ void add_acc2(uint32_t taddr, int acc2_col, float (&v
   for (int i = 0; i < 16; ++i) v[i] += w[i];
 }
 
+// One CTA's tile: rows bx * BM.., column tile by (modes 2, 3) or K slice by
+// (mode 0), K chunk bz of gz.  The tensor maps are generic addresses (kernel
+// parameters, or global memory for a group of problems).
 template <bool A_MN, bool B_MN>
-__global__ void __launch_bounds__(kThreads, 1)
-    tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Params P) {
+__device__ __forceinline__ void tc_body(const Params& P, const CUtensorMap* mapA, const CUtensorMap* mapB,
+                                        int bx, int by, int bz, int gz) {
+  const CUtensorMap& tmA = *mapA;
+  const CUtensorMap& tmB = *mapB;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int a_bytes = BM * BK * 2;
@@ -267,15 +308,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // work of this CTA
-  const int tile0 = blockIdx.x * BM;
+  const int tile0 = bx * BM;
   int kb_begin = 0, kb_end = P.kb_total;
   int ntile0 = 0;
   if (P.mode == 0) {
-    kb_begin = blockIdx.y * P.kb_per_cta;
+    kb_begin = by * P.kb_per_cta;
     kb_end = min(P.kb_total, kb_begin + P.kb_per_cta);
   } else if (P.mode >= 2) {
-    ntile0 = blockIdx.y * P.n_tile;
-    kb_begin = blockIdx.z * P.kb_chunk;
+    ntile0 = by * P.n_tile;
+    kb_begin = bz * P.kb_chunk;
     kb_end = min(P.kb_total, kb_begin + P.kb_chunk);
   }
   // strictly upper tile of C: not needed (the lower triangle is mirrored)
@@ -287,7 +328,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       // nothing of this K chunk meets the tile: its partial dots are zero
       for (int j = threadIdx.x; j < P.n_tile; j += blockDim.x) {
         const int c = ntile0 + j;
-        if (c < P.N) P.f[((long long)blockIdx.x * gridDim.z + blockIdx.z) * P.N + c] = 0.0;
+        if (c < P.N) P.f[((long long)bx * gz + bz) * P.N + c] = 0.0;
       }
       return;
     }
@@ -436,7 +477,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (ok && n_it == 0) {
       // empty K slice: its partial product is zero (TMEM was never written)
       if (P.mode == 0 && row < P.M)
-        for (int j = 0; j < P.N; ++j) P.out[(long long)blockIdx.y * P.M * P.N + (long long)j * P.M + row] = 0.f;
+        for (int j = 0; j < P.N; ++j) P.out[(long long)by * P.M * P.N + (long long)j * P.M + row] = 0.f;
       if (P.mode == 1 && row < P.M) P.f[row] = 0.0;
     } else if (ok && P.mode == 3) {
       // column dots: partial[M-tile][c] = sum over this tile's rows r of
@@ -446,6 +487,61 @@ __global__ void __launch_bounds__(kThreads, 1)
       // column at the end)
       __shared__ float2 cred[4][16];
       const int ncols = P.halves * P.n_half;
+      // this tile of Acol (BM rows x ncols columns in its own type,
+      // column-major, zero outside the matrix) into the ring, which every MMA
+      // has finished reading: a few batches of independent coalesced loads
+      // instead of a dependent round trip per 16-column chunk
+      float* sacol_f = reinterpret_cast<float*>(smem);
+      __nv_bfloat16* sacol_b = reinterpret_cast<__nv_bfloat16*>(smem);
+      {
+        const int et = threadIdx.x - 64;   // 0..127 over the epilogue warps
+        const int esz = P.acol_f32 ? 4 : 2;
+        if (P.acol_vec) {
+          // 16-byte vectors; a column's last partial vector element by element
+          // (nothing past row M is read)
+          const int epv = 16 / esz, vpc = BM / epv;
+          const char* base = reinterpret_cast<const char*>(P.Acol);
+          uint4* sv = reinterpret_cast<uint4*>(smem);
+#pragma unroll 16
+          for (int idx = et; idx < ncols * vpc; idx += 128) {
+            const int j = idx / vpc, vv = idx - j * vpc;
+            const int c = ntile0 + j, rw = tile0 + vv * epv;
+            uint4 val = make_uint4(0u, 0u, 0u, 0u);
+            if (c < P.N && rw < P.M) {
+              const char* src = base + ((long long)c * P.lda_col + rw) * esz;
+              if (rw + epv <= P.M) {
+                val = __ldg(reinterpret_cast<const uint4*>(src));
+              } else {
+                uint32_t w[4] = {0u, 0u, 0u, 0u};
+                for (int e = 0; rw + e < P.M; ++e) {
+                  const uint32_t x = esz == 4 ? reinterpret_cast<const uint32_t*>(src)[e]
+                                              : (uint32_t)reinterpret_cast<const unsigned short*>(src)[e];
+                  w[e * esz / 4] |= x << ((e * esz * 8) & 31);
+                }
+                val = make_uint4(w[0], w[1], w[2], w[3]);
+              }
+            }
+            sv[idx] = val;
+          }
+        } else if (P.acol_f32) {
+          const float* Ac = reinterpret_cast<const float*>(P.Acol);
+#pragma unroll 16
+          for (int idx = et; idx < ncols * BM; idx += 128) {
+            const int j = idx / BM, rr = idx - j * BM;
+            const int c = ntile0 + j, rw = tile0 + rr;
+            sacol_f[idx] = (rw < P.M && c < P.N) ? __ldg(Ac + (long long)c * P.lda_col + rw) : 0.f;
+          }
+        } else {
+          const __nv_bfloat16* Ab = reinterpret_cast<const __nv_bfloat16*>(P.Acol);
+#pragma unroll 16
+          for (int idx = et; idx < ncols * BM; idx += 128) {
+            const int j = idx / BM, rr = idx - j * BM;
+            const int c = ntile0 + j, rw = tile0 + rr;
+            sacol_b[idx] = (rw < P.M && c < P.N) ? Ab[(long long)c * P.lda_col + rw] : __float2bfloat16_rn(0.f);
+          }
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+      }
       for (int j0 = 0; j0 < ncols; j0 += 16) {
         float v[16];
         tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)j0, v);
@@ -453,16 +549,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         float ph[16], pl[16];
 #pragma unroll
         for (int jj = 0; jj < 16; ++jj) {
-          const int c = ntile0 + j0 + jj;
-          ph[jj] = 0.f;
-          pl[jj] = 0.f;
-          if (row < P.M && c < P.N) {
-            const long long ai = (long long)c * P.lda_col + row;
-            const float a = P.acol_f32 ? reinterpret_cast<const float*>(P.Acol)[ai]
-                                       : __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(P.Acol)[ai]);
-            ph[jj] = a * v[jj];
-            pl[jj] = fmaf(a, v[jj], -ph[jj]);
-          }
+          // zero outside the matrix (see the staging above)
+          const int si = (j0 + jj) * BM + q * 32 + lane;
+          const float a = P.acol_f32 ? sacol_f[si] : __bfloat162float(sacol_b[si]);
+          ph[jj] = a * v[jj];
+          pl[jj] = fmaf(a, v[jj], -ph[jj]);
         }
         // 16 values over 32 lanes: lane L ends with the warp sum of index L >> 1
 #pragma unroll
@@ -492,7 +583,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (c < P.N) {
             float h = cred[0][lane].x, l = cred[0][lane].y;
             for (int w = 1; w < 4; ++w) df_add2(h, l, cred[w][lane].x, cred[w][lane].y);
-            P.f[((long long)blockIdx.x * gridDim.z + blockIdx.z) * P.N + c] = to_f64(h) + to_f64(l);
+            P.f[((long long)bx * gz + bz) * P.N + c] = to_f64(h) + to_f64(l);
           }
         }
         asm volatile("bar.sync 1, 128;" ::: "memory");
@@ -501,7 +592,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       float sh = 0.f, sl = 0.f;   // mode 1: sum of squares in double-float
       float* tile_out = nullptr;
       if (P.mode == 2)
-        tile_out = P.out + ((long long)blockIdx.z * P.tiles_lower + lower_tile_index(blockIdx.x, blockIdx.y)) *
+        tile_out = P.out + ((long long)bz * P.tiles_lower + lower_tile_index(bx, by)) *
                                (long long)(BM * P.n_tile);
       const int ncols = P.halves * P.n_half;
       for (int j0 = 0; j0 < ncols; j0 += 16) {
@@ -519,7 +610,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               if (c < P.N) tile_out[(long long)j * BM + (row - tile0)] = v[jj];
             } else if (j < P.N) {
               if (P.mode == 0)
-                P.out[(long long)blockIdx.y * P.M * P.N + (long long)j * P.M + row] = v[jj];
+                P.out[(long long)by * P.M * P.N + (long long)j * P.M + row] = v[jj];
               else
                 df_acc_prod(sh, sl, v[jj], v[jj]);
             }
@@ -538,25 +629,48 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-// B (FP32, m x r, ldb) -> kParts BF16 parts B1 + B2 (m x rpad each, ld mpad),
-// laid out side by side: part p, column j at Bp[(p * rpad + j) * mpad + i].
+template <bool A_MN, bool B_MN>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              const __grid_constant__ Params P) {
+  tc_body<A_MN, B_MN>(P, &tmA, &tmB, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z);
+}
+
+// B (FP32, m x r, ldb) -> np BF16 parts B1 + B2 (+ B3) (m x rpad each, ld
+// mpad), laid out side by side: part p, column j at Bp[(p * rpad + j) * mpad + i].
 // tri: B is the symmetric C with only its lower triangle valid, and the parts
 // hold U' (column j, row i: C[i, j] for i > j, C[j, j] / 2 on the diagonal,
 // 0 above), so that a_i^T C a_i = 2 a_i^T U' a_i.
-__global__ void split_parts_kernel(const float* __restrict__ B, long long ldb, int m, int r, int mpad,
-                                   int rpad, __nv_bfloat16* __restrict__ Bp, int tri) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long tot = (long long)mpad * rpad;
-  if (idx >= tot) return;
+__device__ __forceinline__ void split_one(const float* __restrict__ B, long long ldb, int m, int r, int mpad,
+                                          int rpad, __nv_bfloat16* __restrict__ Bp, int tri, int np,
+                                          long long idx) {
   const int i = (int)(idx % mpad), j = (int)(idx / mpad);
   float v = (i < m && j < r && (!tri || i >= j)) ? B[(long long)j * ldb + i] : 0.f;
   if (tri && i == j) v *= 0.5f;
-#pragma unroll
-  for (int p = 0; p < kParts; ++p) {
+#pragma unroll 3
+  for (int p = 0; p < np; ++p) {
     const __nv_bfloat16 b = __float2bfloat16_rn(v);
     v -= __bfloat162float(b);
     Bp[(long long)(p * rpad + j) * mpad + i] = b;
   }
+}
+__global__ void split_parts_kernel(const float* __restrict__ B, long long ldb, int m, int r, int mpad,
+                                   int rpad, __nv_bfloat16* __restrict__ Bp, int tri, int np) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < (long long)mpad * rpad) split_one(B, ldb, m, r, mpad, rpad, Bp, tri, np, idx);
+}
+
+// BF16 A (m x n, any leading dimension) -> an exact copy with leading
+// dimension mpad, zero beyond m (element idx of mpad x npad).
+__device__ __forceinline__ void stage_one(const __nv_bfloat16* __restrict__ A, long long lda, int m, int n,
+                                          int mpad, __nv_bfloat16* __restrict__ Ap, long long idx) {
+  const int i = (int)(idx % mpad), j = (int)(idx / mpad);
+  Ap[idx] = (i < m && j < n) ? A[(long long)j * lda + i] : __float2bfloat16_rn(0.f);
+}
+__global__ void stage_kernel(const __nv_bfloat16* __restrict__ A, long long lda, int m, int n, int mpad, int npad,
+                             __nv_bfloat16* __restrict__ Ap) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < (long long)mpad * npad) stage_one(A, lda, m, n, mpad, Ap, idx);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -663,7 +777,7 @@ cudaError_t colnorms(const void* A, long long lda, int m, int n, const float* B,
   const int rpad = (r + 15) / 16 * 16;
   __nv_bfloat16* Bp = (__nv_bfloat16*)scratch;
   const long long tot = (long long)mpad * rpad;
-  split_parts_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(B, ldb, m, r, mpad, rpad, Bp, 0);
+  split_parts_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(B, ldb, m, r, mpad, rpad, Bp, 0, kParts);
   CUtensorMap ta, tb;
   int n_half, halves;
   halves_for(r, n_half, halves);
@@ -694,25 +808,27 @@ cudaError_t colnorms(const void* A, long long lda, int m, int n, const float* B,
   return cudaGetLastError();
 }
 
+namespace {
+
+__device__ __forceinline__ double sum_row(const double* __restrict__ partial, int nblk, int n, int i) {
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += partial[(long long)b * n + i];
+  return s;
+}
 __global__ void sum_rows_kernel(const double* __restrict__ partial, int nblk, int n,
                                 double* __restrict__ out, double scale) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += partial[(long long)b * n + i];
-  out[i] = scale * s;
+  if (i < n) out[i] = scale * sum_row(partial, nblk, n, i);
 }
 
 // C = sum over the K chunks of their partial tiles (FP64 sums in chunk
 // order, rounded once to FP32), written to both triangles of C (ld m)
 // through 32 x 32 shared-memory tiles, so reads and writes are coalesced.
-// Only the 32 x 32 tiles on or below the diagonal run; each lies inside one
-// chunk tile of 128 x 256.
-__global__ void reduce_lower_kernel(const float* __restrict__ parts, int chunks, int tiles_lower, int m,
-                                    float* __restrict__ C) {
-  __shared__ float tile[32][33];
-  const int bi = blockIdx.x, bj = blockIdx.y;   // rows bi*32.., columns bj*32..
-  if (bi < bj) return;
+// Only the 32 x 32 tiles on or below the diagonal run (bi >= bj); each lies
+// inside one chunk tile of 128 x 256.  Block-wide (32 x 8 threads).
+__device__ __forceinline__ void reduce_lower_block(const float* __restrict__ parts, int chunks, int tiles_lower,
+                                                   int m, float* __restrict__ C, int bi, int bj,
+                                                   float (&tile)[32][33]) {
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int r = bi * 32 + tx;
   const int bx = (bi * 32) / BM, by = (bj * 32) / 256;
@@ -736,22 +852,35 @@ __global__ void reduce_lower_kernel(const float* __restrict__ parts, int chunks,
     const int c = bj * 32 + tx, r2 = bi * 32 + k;
     if (r2 < m && c < m && r2 > c) C[(long long)r2 * m + c] = tile[tx][k];
   }
+  __syncthreads();   // the tile is free for the block's next use
+}
+__global__ void reduce_lower_kernel(const float* __restrict__ parts, int chunks, int tiles_lower, int m,
+                                    float* __restrict__ C) {
+  __shared__ float tile[32][33];
+  if (blockIdx.x < blockIdx.y) return;
+  reduce_lower_block(parts, chunks, tiles_lower, m, C, blockIdx.x, blockIdx.y, tile);
 }
 
-// K chunking of the initial-score GEMMs (see Params::kb_chunk): C = A A^T
-// accumulates at most 4096 products per TMEM sum (chunks capped at 32, so
-// very wide A gets longer chunks), U' A likewise (one chunk for m <= 4096:
-// at the 4096 x 65536 size shorter chunks cut the initial scores' error from
-// 4.8 to 3.2 u sqrt(m) but cost 2.8 ms).
-constexpr int kSyrkChunkKb = 64;
+// K chunking of the initial-score GEMMs (see Params::kb_chunk).  A TMEM sum
+// of L products is biased by about L / 32 units of its last place (one
+// truncation per MMA of K = 16, half a unit on average), a bias that C
+// passes on to every initial score; the round-to-nearest FMAs of a SIMT dot
+// product err by about sqrt(m) units.  So C = A A^T is summed in chunks of
+// about 64 sqrt(m) products (4 to 64 K blocks of 64: 2 sqrt(m) units), at
+// most 32 chunks (very wide A gets longer ones), added in FP64.  U' A
+// likewise (one chunk for m <= 4096: at the 4096 x 65536 size shorter
+// chunks cut the initial scores' error from 4.8 to 3.2 u sqrt(m) but cost
+// 2.8 ms).
 constexpr int kSyrkMaxChunks = 32;
 constexpr int kDotsChunkKb = 64;
-int syrk_chunk_kb(int n) {
+int syrk_chunk_kb(int m, int n) {
   const int kb = (n + BK - 1) / BK;
-  return std::max(kSyrkChunkKb, (kb + kSyrkMaxChunks - 1) / kSyrkMaxChunks);
+  int c = 4;
+  while (c < 64 && (c + 1) * (c + 1) <= m) ++c;   // floor(sqrt(m)), in [4, 64]
+  return std::max(c, (kb + kSyrkMaxChunks - 1) / kSyrkMaxChunks);
 }
-int syrk_chunks(int n) {
-  const int kb = (n + BK - 1) / BK, c = syrk_chunk_kb(n);
+int syrk_chunks(int m, int n) {
+  const int kb = (n + BK - 1) / BK, c = syrk_chunk_kb(m, n);
   return (kb + c - 1) / c;
 }
 int dots_chunks(int m) { return ((m + BK - 1) / BK + kDotsChunkKb - 1) / kDotsChunkKb; }
@@ -759,171 +888,406 @@ int dots_chunks(int m) { return ((m + BK - 1) / BK + kDotsChunkKb - 1) / kDotsCh
 // Scratch of css_f0: C (FP32, m x m), then one region used first for the
 // K-chunk partial tiles of C and afterwards for U' in BF16 parts and
 // the column-dot partials.
-// FP32 input: A's BF16 parts, side by side, each padded to whole K blocks
-// (part p, column j at Ap[(p * npad + j) * mpad + i], zero beyond m and n).
-int f32_npad(int n) { return (n + BK - 1) / BK * BK; }
+// Then, unless A feeds the TMA path in place: A's BF16 parts (FP32 input:
+// two; BF16 input with a layout TMA refuses: one, an exact copy), side by
+// side, each padded to whole K blocks (part p, column j at
+// Ap[(p * npad + j) * mpad + i], zero beyond m and n).
+struct F0Layout {
+  int mpad, rpad, npad, mtiles, nchunk, ndots, tiles_lower;
+  size_t bytes;
+  float* C;
+  float* chunk_tiles;
+  __nv_bfloat16* Cp;
+  double* partial;
+  __nv_bfloat16* Ap;
+};
+int a_parts(int src) { return src == kF0F32 ? kUParts : src == kF0Bf16Staged ? 1 : 0; }
 
-size_t css_f0_scratch_bytes(int m, int n, bool f32) {
-  const int mpad = (m + 7) / 8 * 8;
-  const int rpad = (m + 15) / 16 * 16;
-  const int mtiles = (m + BM - 1) / BM;
+F0Layout f0_layout(int m, int n, int src, void* scratch) {
+  F0Layout L{};
+  L.mpad = (m + 7) / 8 * 8;
+  L.rpad = (m + 15) / 16 * 16;
+  L.npad = (n + BK - 1) / BK * BK;
+  L.mtiles = (m + BM - 1) / BM;
+  L.nchunk = syrk_chunks(m, n);
+  L.ndots = dots_chunks(m);
+  L.tiles_lower = lower_tile_count(L.mtiles);
   const size_t c = align_up((size_t)m * m * 4);
-  const size_t chunks = align_up((size_t)syrk_chunks(n) * lower_tile_count(mtiles) * BM * 256 * 4);
-  const size_t parts = align_up((size_t)mpad * kParts * rpad * 2);
-  const size_t part = align_up((size_t)mtiles * dots_chunks(m) * n * 8);
-  const size_t a_parts = f32 ? align_up((size_t)mpad * kParts * f32_npad(n) * 2) : 0;
-  return c + std::max(chunks, parts + part) + a_parts;
+  const size_t chunks = align_up((size_t)L.nchunk * L.tiles_lower * BM * 256 * 4);
+  const size_t parts = align_up((size_t)L.mpad * kUParts * L.rpad * 2);
+  const size_t part = align_up((size_t)L.mtiles * L.ndots * n * 8);
+  const size_t ap = align_up((size_t)L.mpad * a_parts(src) * L.npad * 2);
+  L.bytes = c + std::max(chunks, parts + part) + ap;
+  char* b = (char*)scratch;
+  L.C = (float*)b;
+  L.chunk_tiles = (float*)(b + c);
+  L.Cp = (__nv_bfloat16*)(b + c);
+  L.partial = (double*)(b + c + parts);
+  L.Ap = src != kF0Bf16 ? (__nv_bfloat16*)(b + c + std::max(chunks, parts + part)) : nullptr;
+  return L;
+}
+
+// the operand pairs of FP32 A (parts 0, 1, 2 of 8 bits each): every pair
+// whose product is at least 2^-16 of the leading one; the three dropped
+// pairs are near 2^-24 of it, the FP32 accumulation's own rounding.  The
+// cross products accumulate apart (Params::pair_acc).
+constexpr int kPairs = 6;
+constexpr int kPairA[kPairs] = {0, 0, 1, 0, 1, 2}, kPairB[kPairs] = {0, 1, 0, 2, 1, 0};
+void set_pairs(Params& P) {
+  P.npairs = kPairs;
+  for (int q = 0; q < kPairs; ++q) {
+    P.pair_a[q] = kPairA[q];
+    P.pair_b[q] = kPairB[q];
+    P.pair_acc[q] = q > 0;
+  }
+  P.acc2_col = 256;
+}
+
+// Tensor maps of the two GEMMs: C = A A^T (both operands A, or its parts,
+// row-major in K = the column index), and U' A (U' parts K-major; A, or its
+// parts, K-major in the rows).
+bool f0_maps(const F0Layout& L, const void* A, long long lda, int m, int n, int src, CUtensorMap* mA2,
+             CUtensorMap* mU, CUtensorMap* mA3) {
+  if (src != kF0Bf16) {
+    const uint64_t cols = (uint64_t)a_parts(src) * L.npad;
+    if (!make_map(mA2, L.Ap, (uint64_t)L.mpad, cols, (uint64_t)L.mpad, BK)) return false;
+    if (!make_map(mA3, L.Ap, (uint64_t)L.mpad, cols, (uint64_t)L.mpad, 256)) return false;
+  } else {
+    if (!make_map(mA2, A, (uint64_t)m, (uint64_t)n, (uint64_t)lda, BK)) return false;
+    if (!make_map(mA3, A, (uint64_t)m, (uint64_t)n, (uint64_t)lda, 256)) return false;
+  }
+  return make_map(mU, L.Cp, (uint64_t)L.mpad, (uint64_t)(kUParts * L.rpad), (uint64_t)L.mpad, BM);
+}
+
+// C = A A^T: the tiles touching the lower triangle, grid (mtiles, ceil(m /
+// 256), nchunk), chunk partial tiles to L.chunk_tiles
+Params f0_params_syrk(const F0Layout& L, int m, int n, int src, int* err, unsigned long long spin_ns,
+                      int stall) {
+  const bool f32 = src == kF0F32;
+  Params P{};
+  P.mode = 2;
+  P.tri = 1;
+  P.M = m;
+  P.N = m;
+  P.n_half = 256;
+  P.halves = 1;
+  P.n_tile = 256;
+  P.kb_total = (n + BK - 1) / BK;
+  P.kb_per_cta = P.kb_total;
+  P.kb_chunk = syrk_chunk_kb(m, n);
+  P.tiles_lower = L.tiles_lower;
+  P.nparts = 1;
+  if (f32) {
+    // C = (A1 + A2)(A1 + A2)^T: one ring stage per (K block, pair)
+    set_pairs(P);
+    P.a_kpart = L.npad;
+    P.b_kpart = L.npad;
+  }
+  P.stage_bytes = BM * BK * 2 + 256 * BK * 2;
+  P.stages = fit_stages(P.stage_bytes, STAGES);
+  P.out = L.chunk_tiles;
+  P.err = err;
+  P.spin_ns = spin_ns;
+  P.stall = stall;
+  return P;
+}
+
+// partial[M-tile][i] = sum over the tile's rows r of A[r, i] (U' A)[r, i];
+// U' is zero left of the diagonal, so M-tile J contracts over K >= 128 J only
+// (half of the products of C A).  Grid (mtiles, ceil(n / n_tile), ndots).
+Params f0_params_dots(const F0Layout& L, const void* A, long long lda, int m, int n, int src, int* err,
+                      unsigned long long spin_ns, int stall) {
+  const bool f32 = src == kF0F32;
+  Params P{};
+  P.mode = 3;
+  P.tri = 1;
+  P.M = m;
+  P.N = n;
+  P.n_half = 256;
+  P.halves = f32 ? 1 : 2;
+  P.n_tile = P.halves * 256;
+  P.kb_total = (m + BK - 1) / BK;
+  P.kb_per_cta = P.kb_total;
+  P.kb_chunk = kDotsChunkKb;
+  P.a_part_stride = L.rpad;
+  if (f32) {
+    // U' parts times A parts, one stage per (K block, pair), 256 columns
+    // per CTA (the cross products take the other half of TMEM): 48 KB per
+    // stage
+    P.group = 0;
+    P.nparts = 1;
+    set_pairs(P);
+    P.b_part_stride = L.npad;
+    P.stage_bytes = BM * BK * 2 + 256 * BK * 2;
+    P.stages = fit_stages(P.stage_bytes, STAGES);
+  } else {
+    // 512 columns per CTA (two MMAs of N = 256, the whole TMEM) and one
+    // stage per K block holding the U' parts and the single shared A tile:
+    // 96 KB per stage
+    P.group = 1;
+    P.nparts = kUParts;
+    P.b_part_stride = 0;
+    P.stage_bytes = kUParts * BM * BK * 2 + 512 * BK * 2;
+    P.stages = 2;
+  }
+  // the epilogue stages the tile's Acol (BM x n_tile, BF16 or FP32) in the ring
+  static_assert(BM * 512 * 2 <= 2 * (kUParts * BM * BK * 2 + 512 * BK * 2), "BF16 ring holds the Acol tile");
+  static_assert(2 * (kUParts * BM * BK * 2 + 512 * BK * 2) + 256 + 1024 <= kSmemMax, "BF16 ring fits");
+  static_assert(BM * 256 * 4 <= 3 * (BM * BK * 2 + 256 * BK * 2), "FP32 ring holds the Acol tile");
+  P.f = L.partial;
+  P.Acol = A;
+  P.acol_f32 = f32 ? 1 : 0;
+  P.acol_vec = ((uintptr_t)A % 16 == 0 && (lda * (f32 ? 4 : 2)) % 16 == 0) ? 1 : 0;
+  P.lda_col = lda;
+  P.err = err;
+  P.spin_ns = spin_ns;
+  P.stall = stall;
+  return P;
+}
+
+template <bool A_MN, bool B_MN>
+cudaError_t set_smem(const Params& P) {
+  return cudaFuncSetAttribute(tc_kernel<A_MN, B_MN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem_for(P.stage_bytes, P.stages));
+}
+
+// ------------------------------------------------------ groups of problems -
+// The initial scores of many independent problems (a batch) in one launch
+// per phase.  Every problem's descriptors and tensor maps sit in device
+// memory; a CTA of the GEMM phases takes one entry of a tile list, a block of
+// the elementwise phases takes problem blockIdx.y.
+constexpr int kGroupBlocks = 32;   // blocks per problem in the elementwise phases
+
+__global__ void group_split_kernel(const GroupProb* __restrict__ probs, int which) {
+  const GroupProb& g = probs[blockIdx.y];
+  // which 0: A -> its parts (FP32) or its aligned copy (BF16 staged); 1: C -> U' parts
+  if (which == 0 && g.src == kF0Bf16) return;
+  if (which == 0 && g.src == kF0Bf16Staged) {
+    const long long tot = (long long)g.mpad * g.npad;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
+         idx += (long long)gridDim.x * blockDim.x)
+      stage_one((const __nv_bfloat16*)g.A, g.lda, g.m, g.n, g.mpad, g.Ap, idx);
+    return;
+  }
+  const float* B = which ? g.C : (const float*)g.A;
+  const long long ldb = which ? g.m : g.lda;
+  const int r = which ? g.m : g.n, cols = which ? g.rpad : g.npad;
+  __nv_bfloat16* out = which ? g.Cp : g.Ap;
+  const long long tot = (long long)g.mpad * cols;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
+       idx += (long long)gridDim.x * blockDim.x)
+    split_one(B, ldb, g.m, r, g.mpad, cols, out, which, kUParts, idx);
+}
+
+__global__ void group_reduce_kernel(const GroupProb* __restrict__ probs) {
+  __shared__ float tile[32][33];
+  const GroupProb& g = probs[blockIdx.y];
+  const int nb = (g.m + 31) / 32;
+  for (int q = blockIdx.x; q < nb * nb; q += gridDim.x) {
+    const int bi = q % nb, bj = q / nb;
+    if (bi >= bj) reduce_lower_block(g.chunk_tiles, g.nchunk, g.tiles_lower, g.m, g.C, bi, bj, tile);
+  }
+}
+
+__global__ void group_sum_rows_kernel(const GroupProb* __restrict__ probs) {
+  const GroupProb& g = probs[blockIdx.y];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x)
+    g.f[i] = 2.0 * sum_row(g.partial, g.mtiles * g.ndots, g.n, i);
+}
+
+template <bool A_MN, bool B_MN>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_group_kernel(const GroupProb* __restrict__ probs, const GroupTile* __restrict__ tiles, int mode) {
+  const GroupTile w = tiles[blockIdx.x];
+  const GroupProb& g = probs[w.prob];
+  const Params P = mode == 2 ? g.p2 : g.p3;
+  const CUtensorMap* mA = mode == 2 ? &g.mapA2 : &g.mapU;
+  const CUtensorMap* mB = mode == 2 ? &g.mapA2 : &g.mapA3;
+  if (threadIdx.x == 0) {
+    // the maps were written to global memory by a copy before the launch
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)mA) : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)mB) : "memory");
+  }
+  tc_body<A_MN, B_MN>(P, mA, mB, w.bx, w.by, w.bz, mode == 2 ? g.nchunk : g.ndots);
+}
+
+}  // namespace
+
+size_t css_f0_scratch_bytes(int m, int n, int src) { return f0_layout(m, n, src, nullptr).bytes; }
+
+int f0_source(bool f32, const void* A, long long lda, int m) {
+  if (f32) return kF0F32;
+  return supported(A, lda, m, 256) ? kF0Bf16 : kF0Bf16Staged;
 }
 
 cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, double* f, int* err,
-                   unsigned long long spin_ns, cudaStream_t s, int stall, bool f32) {
-  const int mpad = (m + 7) / 8 * 8;
-  const int rpad = (m + 15) / 16 * 16;
-  const int mtiles = (m + BM - 1) / BM;
-  const int npad = f32_npad(n);
-  float* C = (float*)scratch;
-  float* chunk_tiles = (float*)((char*)scratch + align_up((size_t)m * m * 4));
-  __nv_bfloat16* Cp = (__nv_bfloat16*)chunk_tiles;
-  double* partial = (double*)((char*)Cp + align_up((size_t)mpad * kParts * rpad * 2));
-  const int nchunk = syrk_chunks(n), ndots = dots_chunks(m);
-  const int tiles_lower = lower_tile_count(mtiles);
-  // FP32 A: its BF16 parts after the C / chunk / U' region (see css_f0_scratch_bytes)
-  __nv_bfloat16* Ap = nullptr;
-  if (f32) {
-    const size_t c = align_up((size_t)m * m * 4);
-    const size_t chunks = align_up((size_t)nchunk * tiles_lower * BM * 256 * 4);
-    const size_t parts = align_up((size_t)mpad * kParts * rpad * 2);
-    const size_t part = align_up((size_t)mtiles * ndots * n * 8);
-    Ap = (__nv_bfloat16*)((char*)scratch + c + std::max(chunks, parts + part));
-  }
-  // the operand pairs of the FP32 path: (hi, hi), (hi, lo), (lo, hi); lo lo
-  // is below 2^-32 of the product, under the FP32 accumulation's own rounding
-  constexpr int kPairs = 3;
-  const int kPairA[kPairs] = {0, 0, 1}, kPairB[kPairs] = {0, 1, 0};
+                   unsigned long long spin_ns, cudaStream_t s, int stall, int src) {
+  const F0Layout L = f0_layout(m, n, src, scratch);
+  CUtensorMap mA2, mU, mA3;
+  if (!f0_maps(L, A, lda, m, n, src, &mA2, &mU, &mA3)) return cudaErrorInvalidValue;
   cudaError_t e;
-  if (f32) {
-    const long long tot = (long long)mpad * npad;
-    split_parts_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>((const float*)A, lda, m, n, mpad, npad, Ap, 0);
+  if (src != kF0Bf16) {
+    const long long tot = (long long)L.mpad * L.npad;
+    if (src == kF0F32)
+      split_parts_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>((const float*)A, lda, m, n, L.mpad,
+                                                                         L.npad, L.Ap, 0, kUParts);
+    else
+      stage_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>((const __nv_bfloat16*)A, lda, m, n, L.mpad,
+                                                                   L.npad, L.Ap);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  // C = A A^T: both operands are A, row-major in K (= the column index)
-  {
-    CUtensorMap ta;
-    const bool ok = f32 ? make_map(&ta, Ap, (uint64_t)mpad, (uint64_t)kParts * npad, (uint64_t)mpad, BK)
-                        : make_map(&ta, A, (uint64_t)m, (uint64_t)n, (uint64_t)lda, BK);
-    if (!ok) return cudaErrorInvalidValue;
-    Params P{};
-    P.mode = 2;
-    P.tri = 1;
-    P.M = m;
-    P.N = m;
-    P.n_half = 256;
-    P.halves = 1;
-    P.n_tile = 256;
-    P.kb_total = (n + BK - 1) / BK;
-    P.kb_per_cta = P.kb_total;
-    P.kb_chunk = syrk_chunk_kb(n);
-    P.tiles_lower = tiles_lower;
-    P.nparts = 1;
-    if (f32) {
-      // C = (A1 + A2)(A1 + A2)^T, the pairs of parts into one accumulator
-      P.npairs = kPairs;
-      for (int q = 0; q < kPairs; ++q) {
-        P.pair_a[q] = kPairA[q];
-        P.pair_b[q] = kPairB[q];
-        P.pair_acc[q] = q > 0;
-      }
-      P.acc2_col = 256;
-      P.a_kpart = npad;
-      P.b_kpart = npad;
-    }
-    P.stage_bytes = BM * BK * 2 + 256 * BK * 2;
-    P.stages = fit_stages(P.stage_bytes, STAGES);
-    P.out = chunk_tiles;
-    P.err = err;
-    P.spin_ns = spin_ns;
-    P.stall = stall;
-    const size_t smem = smem_for(P.stage_bytes, P.stages);
-    if ((e = cudaFuncSetAttribute(tc_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-      return e;
-    dim3 grid(mtiles, (m + 255) / 256, nchunk);
-    tc_kernel<true, true><<<grid, kThreads, smem, s>>>(ta, ta, P);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
+  const Params P2 = f0_params_syrk(L, m, n, src, err, spin_ns, stall);
+  if ((e = set_smem<true, true>(P2)) != cudaSuccess) return e;
+  tc_kernel<true, true><<<dim3(L.mtiles, (m + 255) / 256, L.nchunk), kThreads, smem_for(P2.stage_bytes, P2.stages),
+                          s>>>(mA2, mA2, P2);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // C = the chunks' sum, both triangles (the greedy iterations read whole rows)
-  reduce_lower_kernel<<<dim3((m + 31) / 32, (m + 31) / 32), dim3(32, 8), 0, s>>>(chunk_tiles, nchunk,
-                                                                                 tiles_lower, m, C);
-  // U' (upper triangle of C, diagonal halved) = U1 + U2 in BF16
+  reduce_lower_kernel<<<dim3((m + 31) / 32, (m + 31) / 32), dim3(32, 8), 0, s>>>(L.chunk_tiles, L.nchunk,
+                                                                                 L.tiles_lower, m, L.C);
+  // U' (upper triangle of C, diagonal halved) = U1 + U2 + U3 in BF16
   {
-    const long long tot = (long long)mpad * rpad;
-    split_parts_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(C, m, m, m, mpad, rpad, Cp, 1);
+    const long long tot = (long long)L.mpad * L.rpad;
+    split_parts_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(L.C, m, m, m, L.mpad, L.rpad, L.Cp, 1,
+                                                                       kUParts);
   }
-  // partial[M-tile][i] = sum over the tile's rows r of A[r, i] (U' A)[r, i];
-  // U' is zero left of the diagonal, so M-tile J contracts over K >= 128 J only
-  // (half of the products of C A)
-  {
-    CUtensorMap ta, tb;
-    if (!make_map(&ta, Cp, (uint64_t)mpad, (uint64_t)(kParts * rpad), (uint64_t)mpad, BM)) return cudaErrorInvalidValue;
-    const bool ok = f32 ? make_map(&tb, Ap, (uint64_t)mpad, (uint64_t)kParts * npad, (uint64_t)mpad, 256)
-                        : make_map(&tb, A, (uint64_t)m, (uint64_t)n, (uint64_t)lda, 256);
-    if (!ok) return cudaErrorInvalidValue;
-    Params P{};
-    P.mode = 3;
-    P.tri = 1;
-    P.M = m;
-    P.N = n;
-    P.n_half = 256;
-    P.halves = f32 ? 1 : 2;
-    P.n_tile = P.halves * 256;
-    P.kb_total = (m + BK - 1) / BK;
-    P.kb_per_cta = P.kb_total;
-    P.kb_chunk = kDotsChunkKb;
-    P.a_part_stride = rpad;
-    if (f32) {
-      // one stage per (K block, pair), 256 columns per CTA (the cross
-      // products take the other half of TMEM): 48 KB per stage
-      P.group = 0;
-      P.nparts = 1;
-      P.npairs = kPairs;
-      for (int q = 0; q < kPairs; ++q) {
-        P.pair_a[q] = kPairA[q];
-        P.pair_b[q] = kPairB[q];
-        P.pair_acc[q] = q > 0;
-      }
-      P.acc2_col = 256;
-      P.b_part_stride = npad;
-      P.stage_bytes = BM * BK * 2 + 256 * BK * 2;
-      P.stages = fit_stages(P.stage_bytes, STAGES);
-    } else {
-      // 512 columns per CTA (two MMAs of N = 256, the whole TMEM) and one
-      // stage per K block holding the U' parts and the single shared A tile:
-      // 96 KB per stage
-      P.group = 1;
-      P.nparts = kParts;
-      P.b_part_stride = 0;
-      P.stage_bytes = kParts * BM * BK * 2 + 512 * BK * 2;
-      P.stages = 2;
-    }
-    P.f = partial;
-    P.Acol = A;
-    P.acol_f32 = f32 ? 1 : 0;
-    P.lda_col = lda;
-    P.err = err;
-    P.spin_ns = spin_ns;
-    P.stall = stall;
-    const size_t smem = smem_for(P.stage_bytes, P.stages);
-    if ((e = cudaFuncSetAttribute(tc_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-      return e;
-    dim3 grid(mtiles, (n + P.n_tile - 1) / P.n_tile, ndots);
-    tc_kernel<false, false><<<grid, kThreads, smem, s>>>(ta, tb, P);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
+  const Params P3 = f0_params_dots(L, A, lda, m, n, src, err, spin_ns, stall);
+  if ((e = set_smem<false, false>(P3)) != cudaSuccess) return e;
+  tc_kernel<false, false><<<dim3(L.mtiles, (n + P3.n_tile - 1) / P3.n_tile, L.ndots), kThreads,
+                            smem_for(P3.stage_bytes, P3.stages), s>>>(mU, mA3, P3);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // f_i = a_i^T C a_i = 2 a_i^T U' a_i
-  sum_rows_kernel<<<(n + 255) / 256, 256, 0, s>>>(partial, mtiles * ndots, n, f, 2.0);
+  sum_rows_kernel<<<(n + 255) / 256, 256, 0, s>>>(L.partial, L.mtiles * L.ndots, n, f, 2.0);
   return cudaGetLastError();
 }
 
 bool supported_any() { return encode_fn() != nullptr; }
+
+// Tile lists of a problem: the C = A A^T tiles that touch the lower
+// triangle (every chunk), and every column-dot tile.
+void group_tile_counts(int m, int n, bool f32, int* t2, int* t3) {
+  const F0Layout L = f0_layout(m, n, f32 ? kF0F32 : kF0Bf16, nullptr);
+  const int n_tile = f32 ? 256 : 512;
+  *t2 = L.tiles_lower * L.nchunk;
+  *t3 = L.mtiles * ((n + n_tile - 1) / n_tile) * L.ndots;
+}
+
+size_t group_f0_desc_bytes(const int* m, const int* n, int count, bool f32) {
+  size_t t2 = 0, t3 = 0;
+  for (int i = 0; i < count; ++i) {
+    int a, b;
+    group_tile_counts(m[i], n[i], f32, &a, &b);
+    t2 += a;
+    t3 += b;
+  }
+  return align_up(sizeof(GroupProb) * (size_t)count) + align_up(sizeof(GroupTile) * std::max<size_t>(t2, 1)) +
+         align_up(sizeof(GroupTile) * std::max<size_t>(t3, 1));
+}
+
+cudaError_t group_f0_prepare(int count, const void* const* A, const long long* lda, const int* m, const int* n,
+                             void* const* scratch, double* const* f, const int* src, void* desc, int* err,
+                             unsigned long long spin_ns, GroupF0* out, cudaStream_t s) {
+  if (count < 1 || count > 65535) return cudaErrorInvalidValue;
+  std::vector<GroupProb> probs(count);
+  std::vector<GroupTile> t2, t3;
+  std::vector<long long> c2, c3;   // work of each tile (K blocks), for the order
+  for (int i = 0; i < count; ++i) {
+    if ((src[i] == kF0F32) != (src[0] == kF0F32)) return cudaErrorInvalidValue;   // one input type
+    const F0Layout L = f0_layout(m[i], n[i], src[i], scratch[i]);
+    GroupProb& g = probs[i];
+    g = GroupProb{};
+    if (!f0_maps(L, A[i], lda[i], m[i], n[i], src[i], &g.mapA2, &g.mapU, &g.mapA3)) return cudaErrorInvalidValue;
+    g.p2 = f0_params_syrk(L, m[i], n[i], src[i], err, spin_ns, 0);
+    g.p3 = f0_params_dots(L, A[i], lda[i], m[i], n[i], src[i], err, spin_ns, 0);
+    g.A = A[i];
+    g.lda = lda[i];
+    g.m = m[i];
+    g.n = n[i];
+    g.mpad = L.mpad;
+    g.npad = L.npad;
+    g.rpad = L.rpad;
+    g.src = src[i];
+    g.nchunk = L.nchunk;
+    g.ndots = L.ndots;
+    g.mtiles = L.mtiles;
+    g.tiles_lower = L.tiles_lower;
+    g.C = L.C;
+    g.chunk_tiles = L.chunk_tiles;
+    g.Cp = L.Cp;
+    g.Ap = L.Ap;
+    g.partial = L.partial;
+    g.f = f[i];
+    const Params& P2 = g.p2;
+    for (int bz = 0; bz < L.nchunk; ++bz)
+      for (int bx = 0; bx < L.mtiles; ++bx)
+        for (int by = 0; by <= bx / 2; ++by) {
+          t2.push_back(GroupTile{i, bx, by, bz});
+          c2.push_back((long long)std::min(P2.kb_chunk, P2.kb_total - bz * P2.kb_chunk) * std::max(1, P2.npairs));
+        }
+    const Params& P3 = g.p3;
+    for (int bz = 0; bz < L.ndots; ++bz)
+      for (int by = 0; by < (n[i] + P3.n_tile - 1) / P3.n_tile; ++by)
+        for (int bx = 0; bx < L.mtiles; ++bx) {
+          const int kb0 = std::max(bz * P3.kb_chunk, bx * BM / BK);
+          const int kb1 = std::min(P3.kb_total, (bz + 1) * P3.kb_chunk);
+          t3.push_back(GroupTile{i, bx, by, bz});
+          c3.push_back((long long)std::max(0, kb1 - kb0) * std::max(1, P3.npairs));
+        }
+  }
+  // longest tiles first, so that the last wave is made of short ones
+  auto order = [](std::vector<GroupTile>& t, const std::vector<long long>& c) {
+    std::vector<int> ix(t.size());
+    for (size_t i = 0; i < ix.size(); ++i) ix[i] = (int)i;
+    std::stable_sort(ix.begin(), ix.end(), [&](int a, int b) { return c[a] > c[b]; });
+    std::vector<GroupTile> o(t.size());
+    for (size_t i = 0; i < ix.size(); ++i) o[i] = t[ix[i]];
+    t.swap(o);
+  };
+  order(t2, c2);
+  order(t3, c3);
+  char* d = (char*)desc;
+  GroupProb* dprobs = (GroupProb*)d;
+  GroupTile* dt2 = (GroupTile*)(d + align_up(sizeof(GroupProb) * (size_t)count));
+  GroupTile* dt3 = (GroupTile*)((char*)dt2 + align_up(sizeof(GroupTile) * std::max<size_t>(t2.size(), 1)));
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(dprobs, probs.data(), sizeof(GroupProb) * count, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(dt2, t2.data(), sizeof(GroupTile) * t2.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(dt3, t3.data(), sizeof(GroupTile) * t3.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return e;
+  // the host vectors end with this call
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+  *out = GroupF0{};
+  out->probs = dprobs;
+  out->tiles2 = dt2;
+  out->tiles3 = dt3;
+  out->count = count;
+  out->ntiles2 = (int)t2.size();
+  out->ntiles3 = (int)t3.size();
+  out->staged = 0;
+  for (int i = 0; i < count; ++i) out->staged |= src[i] != kF0Bf16;
+  out->smem2 = (int)smem_for(probs[0].p2.stage_bytes, probs[0].p2.stages);
+  out->smem3 = (int)smem_for(probs[0].p3.stage_bytes, probs[0].p3.stages);
+  return cudaSuccess;
+}
+
+cudaError_t group_f0_run(const GroupF0& g, cudaStream_t s) {
+  cudaError_t e;
+  const dim3 eg(kGroupBlocks, g.count);
+  if (g.staged) group_split_kernel<<<eg, 256, 0, s>>>(g.probs, 0);
+  if ((e = cudaFuncSetAttribute(tc_group_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem2)) !=
+      cudaSuccess)
+    return e;
+  tc_group_kernel<true, true><<<g.ntiles2, kThreads, g.smem2, s>>>(g.probs, g.tiles2, 2);
+  group_reduce_kernel<<<eg, dim3(32, 8), 0, s>>>(g.probs);
+  group_split_kernel<<<eg, 256, 0, s>>>(g.probs, 1);
+  if ((e = cudaFuncSetAttribute(tc_group_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                g.smem3)) != cudaSuccess)
+    return e;
+  tc_group_kernel<false, false><<<g.ntiles3, kThreads, g.smem3, s>>>(g.probs, g.tiles3, 3);
+  group_sum_rows_kernel<<<eg, 256, 0, s>>>(g.probs);
+  return cudaGetLastError();
+}
 
 }  // namespace tc
 }  // namespace css

@@ -463,9 +463,10 @@ def select_randomized(A: torch.Tensor, l: int, seed: int, dist="gaussian", *, ta
 
 
 def select_batched(As: Sequence[torch.Tensor], ks: Sequence[int], *, grid_ctas=0, tile_cols=0,
-                   tau_rel=None, stream=None, timing=None):
+                   tau_rel=None, stream=None, timing=None, init_path=0):
     """Independent greedy CSS problems in one persistent launch.  Returns a list
-    of Selection."""
+    of Selection.  ``init_path=1`` keeps the initial scores on the SIMT
+    kernels (css_opts.init_path)."""
     if len(As) != len(ks) or not As:
         raise ValueError("need one k per matrix")
     dtype = As[0].dtype
@@ -486,7 +487,7 @@ def select_batched(As: Sequence[torch.Tensor], ks: Sequence[int], *, grid_ctas=0
         probs[i].sel, probs[i].trace, probs[i].n_sel = sel.data_ptr(), trace.data_ptr(), nsel.data_ptr()
         probs[i].W = None
         outs.append((sel, trace, nsel))
-    o = _opts(tau_rel, None, 0, grid_ctas, tile_cols)
+    o = _opts(tau_rel, None, 0, grid_ctas, tile_cols, init_path=init_path)
     tms = (C.c_double * 2)() if timing is not None else None
     if tms is not None:
         o.timing_ms = C.cast(tms, C.c_void_p)
@@ -509,7 +510,7 @@ class BatchedPlan:
     between runs) and writes the selections into the tensors held here."""
 
     def __init__(self, As: Sequence[torch.Tensor], ks: Sequence[int], *, grid_ctas=0,
-                 tile_cols=0, tau_rel=None, stream=None):
+                 tile_cols=0, tau_rel=None, stream=None, init_path=0):
         if len(As) != len(ks) or not As:
             raise ValueError("need one k per matrix")
         dtype = As[0].dtype
@@ -531,7 +532,7 @@ class BatchedPlan:
             probs[i].W = None
             self._outs.append((sel, trace, nsel))
         self._As = list(As)
-        o = _opts(tau_rel, None, 0, grid_ctas, tile_cols)
+        o = _opts(tau_rel, None, 0, grid_ctas, tile_cols, init_path=init_path)
         nbytes = self._lib.css_batched_workspace_size(probs, len(As), dt, C.byref(o))
         if nbytes == 0:
             raise ValueError("invalid batch")

@@ -7,7 +7,8 @@ import torch
 
 import css_inputs as ci
 from oracle import css_oracle as O
-from tests.gpu_helpers import dev_matrix, teacher_forced_parity
+from tests.gpu_helpers import (GAP_TOL, certify_selection, dev_matrix, first_mismatch,
+                               pair_error_bound, teacher_forced_parity)
 
 pytestmark = pytest.mark.gpu
 
@@ -78,3 +79,61 @@ def test_css_initial_scores_tensor_cores(css, shape, dtype):
     fa, fb = a.diag_f.cpu().numpy(), b.diag_f.cpu().numpy()
     f0 = ref.fs[0]
     assert np.max(np.abs(fa - fb)) <= 1e-5 * np.max(np.abs(f0))
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float32])
+def test_batched_initial_scores_tensor_cores(css, dtype):
+    """The batched form's initial scores on tensor cores (one grouped launch
+    per phase over problems of mixed sizes; in BF16 a matrix whose leading
+    dimension the TMA path refuses takes the SIMT kernels in the same batch):
+    the same traces as the SIMT initialisation, and parity with the oracle."""
+    shapes = [(64, 128, 8), (300, 1000, 16), (1000, 2300, 24), (129, 4000, 12), (520, 700, 30),
+              (37, 203, 9), (256, 256, 20)]
+    As, ks, vals = [], [], []
+    for i, (m, n, k) in enumerate(shapes):
+        A_np = ci.lowrank_uv(m, n, 2 * k, 0.05, 300 + i)
+        A, v = dev_matrix(A_np, dtype, ld=m + 3 if i == 4 else None)
+        As.append(A)
+        ks.append(k)
+        vals.append(v)
+    a = css.select_batched(As, ks)
+    b = css.select_batched(As, ks, init_path=1)
+    for i, (ra, rb) in enumerate(zip(a, b)):
+        m = shapes[i][0]
+        ref = O.greedy_css(vals[i], ks[i], tau_rel=1e-6, keep_scores=True)
+        np.testing.assert_allclose(ra.trace.cpu().numpy(), rb.trace.cpu().numpy(), rtol=0,
+                                   atol=1e-5 * ref.trace[0])
+        S = ra.indices.cpu().tolist()
+        assert ra.n_sel == ks[i]
+        t = first_mismatch(S, list(ref.S))
+        if t is None:
+            # the device's own error trace against the oracle's
+            assert abs(ra.trace[-1].item() - ref.trace[-1]) <= 1e-4 * ref.trace[0]
+        else:
+            assert ref.gaps[t] <= max(GAP_TOL, pair_error_bound(ref, t, m, dtype)), (i, t)
+            ref_dev = O.greedy_css(vals[i], len(S), tau_rel=1e-6, keep_scores=True, forced=S)
+            certify_selection(S, ref_dev, m, dtype)
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float32])
+def test_late_picks_of_small_problems(css, dtype):
+    """Problems of the batched workload with few rows and k close to m (k/m
+    0.66-0.81): the last picks are made on scores that are small
+    differences of O(f^(0)) terms, where a relative error of 2^-17 in every
+    entry of U' (two BF16 parts instead of three) raised the final error
+    20-80 fold over the oracle's.  The tensor-core initial scores must leave
+    the selection's direct error within 1.3x of the oracle's selection's, or
+    within 1.5x of what the SIMT initial scores reach."""
+    c = ci.CONFIGS["batched_1024"]
+    specs = ci.batched_specs(c["count"], c["seed"])
+    for i in (519, 708, 363, 336, 130):
+        m, n, k = specs[i]
+        A, vals = dev_matrix(ci.batched_instance(m, n, k, c["seed"] + i, noise=c["noise"]), dtype)
+        e_ref = O.greedy_css(vals, k, tau_rel=1e-6).trace[-1]
+        ratio = []
+        for path in (0, 1):
+            r = css.select(A, k, init_path=path)
+            ratio.append(O.reconstruction_error(vals, r.indices.cpu().tolist()[:r.n_sel]) / e_ref)
+        print(f"{dtype} problem {i} ({m} x {n}, k = {k}): error / oracle's, tensor cores {ratio[0]:.3f}, "
+              f"SIMT {ratio[1]:.3f}")
+        assert ratio[0] <= max(1.3, 1.5 * ratio[1]), (i, ratio)

@@ -389,7 +389,6 @@ def run_batched(args):
     clk = clocks.stop()
     # equal final error (outside the timed region): every instance's BF16
     # batched selection and its FP32 single-call selection, both evaluated
-    # directly on the FP32 matrix (the residual formed on the device, FP64 sum)
     # directly on the FP32 matrix (the residual formed on the device, FP64
     # sum); the FP32 batched selections are compared the same way, to show
     # how far near-tie picks alone move the error of these problems
@@ -467,7 +466,11 @@ def run_batched(args):
                          "host": host_cpu(), "kind": "oracle",
                          "sample": "Algorithm 1 in FP64 on the 48 sampled problems' BF16 values, "
                                    "initial scores included"},
-        "gpu_launches": 4 * args.steps,
+        # per BF16 batch: the copy of A to aligned buffers (these leading
+        # dimensions are not multiples of 8), C = A A^T, its chunk sum and
+        # mirror, the split of C, column dots, row sums (one grouped launch
+        # each over all problems) + the persistent greedy kernel
+        "gpu_launches": 7 * args.steps,
         "clocks": clk}), flush=True)
 
 
@@ -795,11 +798,10 @@ def main():
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "greedy_kernel (persistent: pivot phases + fused step)",
                      "bytes_per_iteration": per_iter, "peak_kind": peak_kind},
-        # per css_select: BF16 -> C = A A^T (lower tiles), its mirror, the
-        # split of C, column dots, row sums (tensor cores) + the persistent
-        # greedy kernel; FP32 -> SYRK, column-reduction GEMM, partial sums +
-        # the greedy kernel
-        "gpu_launches": (6 if args.dtype == "bf16" else 4) * args.steps,
+        # per css_select: C = A A^T (lower tiles), its chunk sum and mirror,
+        # the split of C, column dots, row sums (tensor cores; FP32 A is
+        # split into parts first) + the persistent greedy kernel
+        "gpu_launches": (6 if args.dtype == "bf16" else 7) * args.steps,
         "clocks": clk,
     }
     out["hbm_gbs"] = achieved

@@ -453,9 +453,9 @@ SelectLayout select_layout(void* ws, size_t cap, int dt, int64_t m, int64_t n, i
   // C = A A^T (m x m) first; for BF16 and FP32 input the tensor-core path
   // needs its BF16 parts and row-tile partials (and A's parts or aligned
   // copy) right behind it
-  size_t cbytes = (size_t)m * m * accsize(dt);
+  size_t cbytes = (size_t)m * c_ld(m, (int)accsize(dt)) * accsize(dt);
   if (dt != CSS_F64)
-    cbytes = std::max(cbytes, tc::css_f0_scratch_bytes((int)m, (int)n, dt == CSS_F32 ? tc::kF0F32 : tc::kF0Bf16Staged));
+    cbytes = std::max(cbytes, tc::css_f0_scratch_bytes((int)m, (int)n, dt == CSS_F32 ? tc::kF0F32Staged : tc::kF0Bf16Staged));
   L.C = c.take<char>(cbytes);
   L.partial = c.take<double>(css_f0_partial_doubles(dt, (int)m, (int)n));
   L.bytes = c.off;
@@ -651,15 +651,21 @@ css_status css_select(const void* A, css_dtype dtype, int64_t m, int64_t n, int6
   if (cudaMemsetAsync(L.h.aux_err, 0, sizeof(int), s) != cudaSuccess) return CSS_ERR_CUDA;
   cudaError_t e;
   const unsigned long long spin = o.spin_budget_ns ? o.spin_budget_ns : kDefaultSpinNs;
-  if (dtype != CSS_F64 && o.init_path != 1 && tc::supported_any())
-    e = tc::css_f0(A, lda, (int)m, (int)n, L.C, L.s.f, L.h.aux_err, spin, s, stall_mbarrier(o),
-                   tc::f0_source(dtype == CSS_F32, A, lda, (int)m));
-  else
-    e = css_f0_simt(dtype, A, lda, (int)m, (int)n, L.C, L.partial, L.s.f, s);
+  // the greedy iterations stream A; a BF16 A whose layout refuses 16-byte
+  // loads is read from the aligned copy the initial scores made of it
+  const void* As = A;
+  long long ldas = lda;
+  if (dtype != CSS_F64 && o.init_path != 1 && tc::supported_any()) {
+    const int src = tc::f0_source(dtype == CSS_F32, A, lda, (int)m);
+    e = tc::css_f0(A, lda, (int)m, (int)n, L.C, L.s.f, L.h.aux_err, spin, s, stall_mbarrier(o), src);
+    tc::f0_staged_copy((int)m, (int)n, src, L.C, &As, &ldas);
+  } else {
+    e = css_f0_simt(dtype, A, lda, (int)m, (int)n, L.C, c_ld(m, (int)accsize(dtype)), L.partial, L.s.f, s);
+  }
   if (e != cudaSuccess) return cuda_status(e);
   tm.mark(1, s);
-  std::vector<UnitDesc> units{make_unit(A, dtype, m, n, lda, k, 0, L.C, m, 0, L.s, W, sel, trace,
-                                        n_sel, o)};
+  std::vector<UnitDesc> units{make_unit(As, dtype, m, n, ldas, k, 0, L.C, c_ld(m, (int)accsize(dtype)), 0, L.s, W,
+                                        sel, trace, n_sel, o)};
   const int tile = pick_tile(o, dtype, m, n);
   int gmax = o.grid_ctas > 0 ? o.grid_ctas : team_ctas_for(n, m);
   cs = launch_units(L.h, units, {1.0}, dtype, gmax, tile, o.spin_budget_ns, s, stall_barrier(o),
@@ -1220,10 +1226,10 @@ BatchLayout batch_layout(void* ws, size_t cap, const css_problem* probs, int cou
     carve_rest(c, dt, (int)p.m, (int)p.n, p.k, 0, 0, p.W == nullptr, L.st[i]);
     // C first; for BF16 and FP32 input the tensor-core path's scratch
     // (tc::css_f0_scratch_bytes) starts with C
-    size_t cbytes = (size_t)p.m * p.m * accsize(dt);
+    size_t cbytes = (size_t)p.m * c_ld(p.m, (int)accsize(dt)) * accsize(dt);
     if (dt != CSS_F64)
       cbytes = std::max(cbytes, tc::css_f0_scratch_bytes((int)p.m, (int)p.n,
-                                                         dt == CSS_F32 ? tc::kF0F32 : tc::kF0Bf16Staged));
+                                                         dt == CSS_F32 ? tc::kF0F32Staged : tc::kF0Bf16Staged));
     L.C[i] = c.take<char>(cbytes);
     L.partial[i] = c.take<double>(css_f0_partial_doubles(dt, (int)p.m, (int)p.n));
   }
@@ -1289,8 +1295,11 @@ css_status batched_prepare(const css_problem* probs, int32_t count, css_dtype dt
   const bool tc_ok = dtype != CSS_F64 && o.init_path != 1 && count <= 65535 && tc::supported_any();
   for (int i = 0; i < count; ++i) {
     const css_problem& p = probs[i];
+    const void* As = p.A;   // see css_select: the aligned copy of a BF16 A, if one is made
+    long long ldas = p.lda;
     if (tc_ok) {
       tsrc.push_back(tc::f0_source(dtype == CSS_F32, p.A, p.lda, (int)p.m));
+      tc::f0_staged_copy((int)p.m, (int)p.n, tsrc.back(), L.C[i], &As, &ldas);
       tA.push_back(p.A);
       tlda.push_back(p.lda);
       tm_.push_back((int)p.m);
@@ -1298,12 +1307,13 @@ css_status batched_prepare(const css_problem* probs, int32_t count, css_dtype dt
       tscr.push_back(L.C[i]);
       tf.push_back(L.st[i].f);
     } else {
-      items.push_back(F0Item{p.A, p.lda, (int)p.m, (int)p.n, L.C[i], L.partial[i], L.st[i].f});
+      items.push_back(F0Item{p.A, p.lda, (int)p.m, (int)p.n, L.C[i], c_ld(p.m, (int)accsize(dtype)), L.partial[i],
+                             L.st[i].f});
       ms.push_back((int)p.m);
       ns.push_back((int)p.n);
     }
-    units.push_back(make_unit(p.A, dtype, p.m, p.n, p.lda, p.k, 0, L.C[i], p.m, 0, L.st[i], p.W,
-                              p.sel, p.trace, p.n_sel, o));
+    units.push_back(make_unit(As, dtype, p.m, p.n, ldas, p.k, 0, L.C[i], c_ld(p.m, (int)accsize(dtype)), 0,
+                              L.st[i], p.W, p.sel, p.trace, p.n_sel, o));
     work.push_back((double)p.k * p.m * p.n + 4.0 * p.m * p.k * p.k);
   }
   P = BatchedPlanImpl{};

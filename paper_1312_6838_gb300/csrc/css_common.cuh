@@ -26,6 +26,14 @@ constexpr size_t kStatusBytes = 256;
 inline size_t align_up(size_t x, size_t a = kWsAlign) { return (x + a - 1) / a * a; }
 
 // Host-side bump allocator over a caller-provided workspace.
+// Leading dimension of the m x m matrix C = A A^T held in the workspace
+// (elements of acc_bytes each): a multiple of 16 bytes, so that every row of
+// C starts on a 16-byte boundary and takes vector loads.
+inline long long c_ld(long long m, int acc_bytes) {
+  const long long v = 16 / acc_bytes;
+  return (m + v - 1) / v * v;
+}
+
 struct WsCarver {
   char* base;
   size_t off;

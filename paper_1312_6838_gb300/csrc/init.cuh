@@ -9,9 +9,9 @@ namespace css {
 size_t css_f0_partial_doubles(int dtype, int m, int n);
 size_t gcss_f0_partial_doubles(int dtype, int r, int n);
 
-// CSS: C = A A^T (m x m, Acc type, leading dimension m) and
+// CSS: C = A A^T (m x m, Acc type, leading dimension ldc) and
 // f[i] = A_:i^T C A_:i.  A has dtype `dtype`.
-cudaError_t css_f0_simt(int dtype, const void* A, long long lda, int m, int n, void* C,
+cudaError_t css_f0_simt(int dtype, const void* A, long long lda, int m, int n, void* C, long long ldc,
                         double* partial, double* f, cudaStream_t s);
 
 // Many CSS problems at once (css_select_batched): the same computation as
@@ -21,7 +21,8 @@ struct F0Item {
   const void* A;
   long long lda;
   int m, n;
-  void* C;           // m x m, Acc type
+  void* C;           // m x m, Acc type, leading dimension ldc
+  long long ldc;
   double* partial;   // css_f0_partial_doubles(dtype, m, n)
   double* f;         // n
 };

@@ -25,7 +25,7 @@ template <> __device__ __forceinline__ float cvt_in<__nv_bfloat16>(__nv_bfloat16
 // thread, 16 x 16 threads, K chunks of KC columns of A.
 template <typename TA, int TT, int KC>
 __device__ __forceinline__ void syrk_tile(const TA* __restrict__ A, long long lda, int m, int n,
-                                          typename AccOf<TA>::type* __restrict__ C, int tile) {
+                                          typename AccOf<TA>::type* __restrict__ C, long long ldc, int tile) {
   using Acc = typename AccOf<TA>::type;
   constexpr int BT = 16 * TT;
   __shared__ __align__(16) Acc As[KC][BT];
@@ -69,8 +69,8 @@ __device__ __forceinline__ void syrk_tile(const TA* __restrict__ A, long long ld
     for (int w = 0; w < TT; ++w) {
       const int j = j0 + tx * TT + w;
       if (i < m && j < m) {
-        C[(long long)j * m + i] = acc[q][w];
-        if (bi != bj) C[(long long)i * m + j] = acc[q][w];
+        C[(long long)j * ldc + i] = acc[q][w];
+        if (bi != bj) C[(long long)i * ldc + j] = acc[q][w];
       }
     }
   }
@@ -126,7 +126,7 @@ __device__ __forceinline__ int f32_idx(int t, int q) { return (q < 4 ? 0 : 64) +
 // A makes each of them a contiguous run.
 template <typename TA>
 __device__ __forceinline__ void syrk_tile_f32(const TA* __restrict__ A, long long lda, int m, int n,
-                                              float* __restrict__ C, int tile) {
+                                              float* __restrict__ C, long long ldc, int tile) {
   __shared__ __align__(16) float sm[2][2][kFK][kFT];
   const int nt = (m + kFT - 1) / kFT;
   int idx = tile, bi = 0;
@@ -178,8 +178,8 @@ __device__ __forceinline__ void syrk_tile_f32(const TA* __restrict__ A, long lon
     for (int w = 0; w < 8; ++w) {
       const int j = j0 + f32_idx(tx, w);
       if (i < m && j < m) {
-        C[(long long)j * m + i] = acc.v[q][w];
-        if (bi != bj) C[(long long)i * m + j] = acc.v[q][w];
+        C[(long long)j * ldc + i] = acc.v[q][w];
+        if (bi != bj) C[(long long)i * ldc + j] = acc.v[q][w];
       }
     }
   }
@@ -268,9 +268,10 @@ __device__ __forceinline__ void colreduce_tile_f32(const TX* __restrict__ X, lon
 
 template <typename TA, int TT, int KC>
 __global__ void __launch_bounds__(256, 2) syrk_kernel(const TA* __restrict__ A, long long lda, int m,
-                                                   int n, typename AccOf<TA>::type* __restrict__ C) {
-  if constexpr (sizeof(typename AccOf<TA>::type) == 4) syrk_tile_f32<TA>(A, lda, m, n, C, blockIdx.x);
-  else syrk_tile<TA, TT, KC>(A, lda, m, n, C, blockIdx.x);
+                                                   int n, typename AccOf<TA>::type* __restrict__ C,
+                                                   long long ldc) {
+  if constexpr (sizeof(typename AccOf<TA>::type) == 4) syrk_tile_f32<TA>(A, lda, m, n, C, ldc, blockIdx.x);
+  else syrk_tile<TA, TT, KC>(A, lda, m, n, C, ldc, blockIdx.x);
 }
 
 // ------------------------------------------------------ column reduction ----
@@ -362,16 +363,16 @@ template <typename TA> struct Tiles { static constexpr int TT = 8, KC = 16; };
 template <> struct Tiles<double> { static constexpr int TT = 4, KC = 16; };
 
 template <typename TA>
-cudaError_t css_f0_simt_t(const void* A_, long long lda, int m, int n, void* C_, double* partial,
-                          double* f, cudaStream_t s) {
+cudaError_t css_f0_simt_t(const void* A_, long long lda, int m, int n, void* C_, long long ldc,
+                          double* partial, double* f, cudaStream_t s) {
   using Acc = typename AccOf<TA>::type;
   constexpr int TT = Tiles<TA>::TT, KC = Tiles<TA>::KC, BT = 16 * TT;
   const TA* A = reinterpret_cast<const TA*>(A_);
   Acc* C = reinterpret_cast<Acc*>(C_);
   const int nt = (m + BT - 1) / BT;
-  syrk_kernel<TA, TT, KC><<<nt * (nt + 1) / 2, 256, 0, s>>>(A, lda, m, n, C);
+  syrk_kernel<TA, TT, KC><<<nt * (nt + 1) / 2, 256, 0, s>>>(A, lda, m, n, C, ldc);
   dim3 grid((n + BT - 1) / BT, nt);
-  colreduce_kernel<Acc, TA, TT, KC, 0><<<grid, 256, 0, s>>>(C, (long long)m, A, lda, m, m, n, partial);
+  colreduce_kernel<Acc, TA, TT, KC, 0><<<grid, 256, 0, s>>>(C, ldc, A, lda, m, m, n, partial);
   sum_partials_kernel<<<(n + 255) / 256, 256, 0, s>>>(partial, nt, n, f);
   return cudaGetLastError();
 }
@@ -412,10 +413,10 @@ __global__ void __launch_bounds__(256, 2) syrk_grouped(const F0Item* __restrict_
   const F0Item it = items[g];
   if constexpr (sizeof(Acc) == 4)
     syrk_tile_f32<TA>(reinterpret_cast<const TA*>(it.A), it.lda, it.m, it.n, reinterpret_cast<Acc*>(it.C),
-                      blockIdx.x - start[g]);
+                      it.ldc, blockIdx.x - start[g]);
   else
     syrk_tile<TA, TT, KC>(reinterpret_cast<const TA*>(it.A), it.lda, it.m, it.n,
-                          reinterpret_cast<Acc*>(it.C), blockIdx.x - start[g]);
+                          reinterpret_cast<Acc*>(it.C), it.ldc, blockIdx.x - start[g]);
 }
 
 template <typename TA, int TT, int KC>
@@ -428,11 +429,11 @@ __global__ void __launch_bounds__(256) colreduce_grouped(const F0Item* __restric
   const int local = blockIdx.x - start[g];
   const int nbs = (it.n + BT - 1) / BT;
   if constexpr (sizeof(Acc) == 4)
-    colreduce_tile_f32<Acc, TA, 0>(reinterpret_cast<const Acc*>(it.C), (long long)it.m,
+    colreduce_tile_f32<Acc, TA, 0>(reinterpret_cast<const Acc*>(it.C), it.ldc,
                                    reinterpret_cast<const TA*>(it.A), it.lda, it.m, it.m, it.n, it.partial,
                                    local / nbs, local % nbs);
   else
-    colreduce_tile<Acc, TA, TT, KC, 0>(reinterpret_cast<const Acc*>(it.C), (long long)it.m,
+    colreduce_tile<Acc, TA, TT, KC, 0>(reinterpret_cast<const Acc*>(it.C), it.ldc,
                                        reinterpret_cast<const TA*>(it.A), it.lda, it.m, it.m, it.n,
                                        it.partial, local / nbs, local % nbs);
 }
@@ -501,12 +502,12 @@ size_t gcss_f0_partial_doubles(int dtype, int r, int n) {
   return (size_t)((r + BT - 1) / BT) * (size_t)n;
 }
 
-cudaError_t css_f0_simt(int dtype, const void* A, long long lda, int m, int n, void* C,
+cudaError_t css_f0_simt(int dtype, const void* A, long long lda, int m, int n, void* C, long long ldc,
                         double* partial, double* f, cudaStream_t s) {
   switch (dtype) {
-    case CSS_F64: return css_f0_simt_t<double>(A, lda, m, n, C, partial, f, s);
-    case CSS_F32: return css_f0_simt_t<float>(A, lda, m, n, C, partial, f, s);
-    default: return css_f0_simt_t<__nv_bfloat16>(A, lda, m, n, C, partial, f, s);
+    case CSS_F64: return css_f0_simt_t<double>(A, lda, m, n, C, ldc, partial, f, s);
+    case CSS_F32: return css_f0_simt_t<float>(A, lda, m, n, C, ldc, partial, f, s);
+    default: return css_f0_simt_t<__nv_bfloat16>(A, lda, m, n, C, ldc, partial, f, s);
   }
 }
 

@@ -31,11 +31,17 @@ cudaError_t colnorms(const void* A, long long lda, int m, int n, const float* B,
 
 // How css_f0 reads A: BF16 straight from A through TMA (supported()), BF16
 // copied first to an aligned buffer (any other layout), FP32 split first
-// into three BF16 parts (any layout).
-enum F0Source { kF0Bf16 = 0, kF0Bf16Staged = 1, kF0F32 = 2 };
+// into three BF16 parts (any layout; one that refuses 16-byte loads is also
+// copied to an aligned FP32 buffer, for the greedy passes).
+enum F0Source { kF0Bf16 = 0, kF0Bf16Staged = 1, kF0F32 = 2, kF0F32Staged = 3 };
 int f0_source(bool f32, const void* A, long long lda, int m);
+// kF0Bf16Staged, kF0F32Staged: the aligned copy of A that css_f0 leaves in its scratch
+// (leading dimension a multiple of 8; it stays valid until the scratch is
+// reused), so that later passes over A can take 16-byte loads.
+bool f0_staged_copy(int m, int n, int src, void* scratch, const void** A, long long* lda);
 // Scratch bytes of css_f0 (C in FP32, its BF16 parts, row-tile partials,
-// A's parts or copy).  kF0Bf16Staged bounds every BF16 layout.
+// A's parts or copy).  kF0Bf16Staged bounds every BF16 layout, kF0F32Staged
+// every FP32 one.
 size_t css_f0_scratch_bytes(int m, int n, int src);
 // The tensor-map encoder is available (css_f0 for FP32 input needs no more).
 bool supported_any();

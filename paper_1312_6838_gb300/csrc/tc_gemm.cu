@@ -119,11 +119,13 @@ struct GroupProb {
   const void* A;
   long long lda;
   int m, n, mpad, npad, rpad, src;   // src: F0Source
+  long long ldc;                      // C's leading dimension
   int nchunk, ndots, mtiles, tiles_lower;
   float* C;
   float* chunk_tiles;
   __nv_bfloat16* Cp;
   __nv_bfloat16* Ap;
+  float* Acopy;
   double* partial;
   double* f;
 };
@@ -672,6 +674,18 @@ __global__ void stage_kernel(const __nv_bfloat16* __restrict__ A, long long lda,
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx < (long long)mpad * npad) stage_one(A, lda, m, n, mpad, Ap, idx);
 }
+// FP32 A (any leading dimension) -> an exact copy with leading dimension
+// mpad, zero beyond m (element idx of mpad x n).
+__device__ __forceinline__ void stage_f32_one(const float* __restrict__ A, long long lda, int m, int mpad,
+                                              float* __restrict__ Ac, long long idx) {
+  const int i = (int)(idx % mpad), j = (int)(idx / mpad);
+  Ac[idx] = i < m ? A[(long long)j * lda + i] : 0.f;
+}
+__global__ void stage_f32_kernel(const float* __restrict__ A, long long lda, int m, int n, int mpad,
+                                 float* __restrict__ Ac) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < (long long)mpad * n) stage_f32_one(A, lda, m, mpad, Ac, idx);
+}
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -822,12 +836,12 @@ __global__ void sum_rows_kernel(const double* __restrict__ partial, int nblk, in
 }
 
 // C = sum over the K chunks of their partial tiles (FP64 sums in chunk
-// order, rounded once to FP32), written to both triangles of C (ld m)
+// order, rounded once to FP32), written to both triangles of C (ld ldc)
 // through 32 x 32 shared-memory tiles, so reads and writes are coalesced.
 // Only the 32 x 32 tiles on or below the diagonal run (bi >= bj); each lies
 // inside one chunk tile of 128 x 256.  Block-wide (32 x 8 threads).
 __device__ __forceinline__ void reduce_lower_block(const float* __restrict__ parts, int chunks, int tiles_lower,
-                                                   int m, float* __restrict__ C, int bi, int bj,
+                                                   int m, long long ldc, float* __restrict__ C, int bi, int bj,
                                                    float (&tile)[32][33]) {
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int r = bi * 32 + tx;
@@ -842,7 +856,7 @@ __device__ __forceinline__ void reduce_lower_block(const float* __restrict__ par
       double sum = 0.0;
       for (int z = 0; z < chunks; ++z) sum += (double)src[z * chunk_stride + local];
       v = (float)sum;
-      C[(long long)c * m + r] = v;
+      C[(long long)c * ldc + r] = v;
     }
     tile[k][tx] = v;
   }
@@ -850,15 +864,15 @@ __device__ __forceinline__ void reduce_lower_block(const float* __restrict__ par
   // C[c, r] = C[r, c] for r > c
   for (int k = ty; k < 32; k += blockDim.y) {
     const int c = bj * 32 + tx, r2 = bi * 32 + k;
-    if (r2 < m && c < m && r2 > c) C[(long long)r2 * m + c] = tile[tx][k];
+    if (r2 < m && c < m && r2 > c) C[(long long)r2 * ldc + c] = tile[tx][k];
   }
   __syncthreads();   // the tile is free for the block's next use
 }
 __global__ void reduce_lower_kernel(const float* __restrict__ parts, int chunks, int tiles_lower, int m,
-                                    float* __restrict__ C) {
+                                    long long ldc, float* __restrict__ C) {
   __shared__ float tile[32][33];
   if (blockIdx.x < blockIdx.y) return;
-  reduce_lower_block(parts, chunks, tiles_lower, m, C, blockIdx.x, blockIdx.y, tile);
+  reduce_lower_block(parts, chunks, tiles_lower, m, ldc, C, blockIdx.x, blockIdx.y, tile);
 }
 
 // K chunking of the initial-score GEMMs (see Params::kb_chunk).  A TMEM sum
@@ -885,7 +899,8 @@ int syrk_chunks(int m, int n) {
 }
 int dots_chunks(int m) { return ((m + BK - 1) / BK + kDotsChunkKb - 1) / kDotsChunkKb; }
 
-// Scratch of css_f0: C (FP32, m x m), then one region used first for the
+// Scratch of css_f0: C (FP32, m x m, leading dimension c_ld(m, 4)), then
+// one region used first for the
 // K-chunk partial tiles of C and afterwards for U' in BF16 parts and
 // the column-dot partials.
 // Then, unless A feeds the TMA path in place: A's BF16 parts (FP32 input:
@@ -894,14 +909,17 @@ int dots_chunks(int m) { return ((m + BK - 1) / BK + kDotsChunkKb - 1) / kDotsCh
 // Ap[(p * npad + j) * mpad + i], zero beyond m and n).
 struct F0Layout {
   int mpad, rpad, npad, mtiles, nchunk, ndots, tiles_lower;
+  long long ldc;   // C's leading dimension (c_ld)
   size_t bytes;
   float* C;
   float* chunk_tiles;
   __nv_bfloat16* Cp;
   double* partial;
   __nv_bfloat16* Ap;
+  float* Acopy;
 };
-int a_parts(int src) { return src == kF0F32 ? kUParts : src == kF0Bf16Staged ? 1 : 0; }
+bool is_f32(int src) { return src == kF0F32 || src == kF0F32Staged; }
+int a_parts(int src) { return is_f32(src) ? kUParts : src == kF0Bf16Staged ? 1 : 0; }
 
 F0Layout f0_layout(int m, int n, int src, void* scratch) {
   F0Layout L{};
@@ -912,18 +930,22 @@ F0Layout f0_layout(int m, int n, int src, void* scratch) {
   L.nchunk = syrk_chunks(m, n);
   L.ndots = dots_chunks(m);
   L.tiles_lower = lower_tile_count(L.mtiles);
-  const size_t c = align_up((size_t)m * m * 4);
+  L.ldc = c_ld(m, 4);
+  const size_t c = align_up((size_t)m * L.ldc * 4);
   const size_t chunks = align_up((size_t)L.nchunk * L.tiles_lower * BM * 256 * 4);
   const size_t parts = align_up((size_t)L.mpad * kUParts * L.rpad * 2);
   const size_t part = align_up((size_t)L.mtiles * L.ndots * n * 8);
   const size_t ap = align_up((size_t)L.mpad * a_parts(src) * L.npad * 2);
-  L.bytes = c + std::max(chunks, parts + part) + ap;
+  // kF0F32Staged: an FP32 copy of A with leading dimension mpad after the parts
+  const size_t acopy = src == kF0F32Staged ? align_up((size_t)L.mpad * n * 4) : 0;
+  L.bytes = c + std::max(chunks, parts + part) + ap + acopy;
   char* b = (char*)scratch;
   L.C = (float*)b;
   L.chunk_tiles = (float*)(b + c);
   L.Cp = (__nv_bfloat16*)(b + c);
   L.partial = (double*)(b + c + parts);
   L.Ap = src != kF0Bf16 ? (__nv_bfloat16*)(b + c + std::max(chunks, parts + part)) : nullptr;
+  L.Acopy = src == kF0F32Staged ? (float*)(b + c + std::max(chunks, parts + part) + ap) : nullptr;
   return L;
 }
 
@@ -963,7 +985,7 @@ bool f0_maps(const F0Layout& L, const void* A, long long lda, int m, int n, int 
 // 256), nchunk), chunk partial tiles to L.chunk_tiles
 Params f0_params_syrk(const F0Layout& L, int m, int n, int src, int* err, unsigned long long spin_ns,
                       int stall) {
-  const bool f32 = src == kF0F32;
+  const bool f32 = is_f32(src);
   Params P{};
   P.mode = 2;
   P.tri = 1;
@@ -997,7 +1019,7 @@ Params f0_params_syrk(const F0Layout& L, int m, int n, int src, int* err, unsign
 // (half of the products of C A).  Grid (mtiles, ceil(n / n_tile), ndots).
 Params f0_params_dots(const F0Layout& L, const void* A, long long lda, int m, int n, int src, int* err,
                       unsigned long long spin_ns, int stall) {
-  const bool f32 = src == kF0F32;
+  const bool f32 = is_f32(src);
   Params P{};
   P.mode = 3;
   P.tri = 1;
@@ -1062,6 +1084,12 @@ __global__ void group_split_kernel(const GroupProb* __restrict__ probs, int whic
   const GroupProb& g = probs[blockIdx.y];
   // which 0: A -> its parts (FP32) or its aligned copy (BF16 staged); 1: C -> U' parts
   if (which == 0 && g.src == kF0Bf16) return;
+  if (which == 0 && g.src == kF0F32Staged) {
+    const long long tot = (long long)g.mpad * g.n;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
+         idx += (long long)gridDim.x * blockDim.x)
+      stage_f32_one((const float*)g.A, g.lda, g.m, g.mpad, g.Acopy, idx);
+  }
   if (which == 0 && g.src == kF0Bf16Staged) {
     const long long tot = (long long)g.mpad * g.npad;
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
@@ -1070,7 +1098,7 @@ __global__ void group_split_kernel(const GroupProb* __restrict__ probs, int whic
     return;
   }
   const float* B = which ? g.C : (const float*)g.A;
-  const long long ldb = which ? g.m : g.lda;
+  const long long ldb = which ? g.ldc : g.lda;
   const int r = which ? g.m : g.n, cols = which ? g.rpad : g.npad;
   __nv_bfloat16* out = which ? g.Cp : g.Ap;
   const long long tot = (long long)g.mpad * cols;
@@ -1085,7 +1113,7 @@ __global__ void group_reduce_kernel(const GroupProb* __restrict__ probs) {
   const int nb = (g.m + 31) / 32;
   for (int q = blockIdx.x; q < nb * nb; q += gridDim.x) {
     const int bi = q % nb, bj = q / nb;
-    if (bi >= bj) reduce_lower_block(g.chunk_tiles, g.nchunk, g.tiles_lower, g.m, g.C, bi, bj, tile);
+    if (bi >= bj) reduce_lower_block(g.chunk_tiles, g.nchunk, g.tiles_lower, g.m, g.ldc, g.C, bi, bj, tile);
   }
 }
 
@@ -1115,8 +1143,17 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 size_t css_f0_scratch_bytes(int m, int n, int src) { return f0_layout(m, n, src, nullptr).bytes; }
 
+bool f0_staged_copy(int m, int n, int src, void* scratch, const void** A, long long* lda) {
+  if (src != kF0Bf16Staged && src != kF0F32Staged) return false;
+  const F0Layout L = f0_layout(m, n, src, scratch);
+  *A = src == kF0F32Staged ? (const void*)L.Acopy : (const void*)L.Ap;
+  *lda = L.mpad;
+  return true;
+}
+
 int f0_source(bool f32, const void* A, long long lda, int m) {
-  if (f32) return kF0F32;
+  const bool aligned = ((uintptr_t)A & 15u) == 0 && (lda * (f32 ? 4 : 2)) % 16 == 0;
+  if (f32) return aligned ? kF0F32 : kF0F32Staged;
   return supported(A, lda, m, 256) ? kF0Bf16 : kF0Bf16Staged;
 }
 
@@ -1128,7 +1165,10 @@ cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, do
   cudaError_t e;
   if (src != kF0Bf16) {
     const long long tot = (long long)L.mpad * L.npad;
-    if (src == kF0F32)
+    if (src == kF0F32Staged)
+      stage_f32_kernel<<<(unsigned)(((long long)L.mpad * n + 255) / 256), 256, 0, s>>>((const float*)A, lda, m, n,
+                                                                                      L.mpad, L.Acopy);
+    if (is_f32(src))
       split_parts_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>((const float*)A, lda, m, n, L.mpad,
                                                                          L.npad, L.Ap, 0, kUParts);
     else
@@ -1143,11 +1183,11 @@ cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, do
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // C = the chunks' sum, both triangles (the greedy iterations read whole rows)
   reduce_lower_kernel<<<dim3((m + 31) / 32, (m + 31) / 32), dim3(32, 8), 0, s>>>(L.chunk_tiles, L.nchunk,
-                                                                                 L.tiles_lower, m, L.C);
+                                                                                 L.tiles_lower, m, L.ldc, L.C);
   // U' (upper triangle of C, diagonal halved) = U1 + U2 + U3 in BF16
   {
     const long long tot = (long long)L.mpad * L.rpad;
-    split_parts_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(L.C, m, m, m, L.mpad, L.rpad, L.Cp, 1,
+    split_parts_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(L.C, L.ldc, m, m, L.mpad, L.rpad, L.Cp, 1,
                                                                        kUParts);
   }
   const Params P3 = f0_params_dots(L, A, lda, m, n, src, err, spin_ns, stall);
@@ -1165,7 +1205,7 @@ bool supported_any() { return encode_fn() != nullptr; }
 // Tile lists of a problem: the C = A A^T tiles that touch the lower
 // triangle (every chunk), and every column-dot tile.
 void group_tile_counts(int m, int n, bool f32, int* t2, int* t3) {
-  const F0Layout L = f0_layout(m, n, f32 ? kF0F32 : kF0Bf16, nullptr);
+  const F0Layout L = f0_layout(m, n, f32 ? kF0F32 : kF0Bf16, nullptr);   // (tile counts only)
   const int n_tile = f32 ? 256 : 512;
   *t2 = L.tiles_lower * L.nchunk;
   *t3 = L.mtiles * ((n + n_tile - 1) / n_tile) * L.ndots;
@@ -1191,7 +1231,7 @@ cudaError_t group_f0_prepare(int count, const void* const* A, const long long* l
   std::vector<GroupTile> t2, t3;
   std::vector<long long> c2, c3;   // work of each tile (K blocks), for the order
   for (int i = 0; i < count; ++i) {
-    if ((src[i] == kF0F32) != (src[0] == kF0F32)) return cudaErrorInvalidValue;   // one input type
+    if (is_f32(src[i]) != is_f32(src[0])) return cudaErrorInvalidValue;   // one input type
     const F0Layout L = f0_layout(m[i], n[i], src[i], scratch[i]);
     GroupProb& g = probs[i];
     g = GroupProb{};
@@ -1211,9 +1251,11 @@ cudaError_t group_f0_prepare(int count, const void* const* A, const long long* l
     g.mtiles = L.mtiles;
     g.tiles_lower = L.tiles_lower;
     g.C = L.C;
+    g.ldc = L.ldc;
     g.chunk_tiles = L.chunk_tiles;
     g.Cp = L.Cp;
     g.Ap = L.Ap;
+    g.Acopy = L.Acopy;
     g.partial = L.partial;
     g.f = f[i];
     const Params& P2 = g.p2;

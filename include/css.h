@@ -144,14 +144,15 @@ typedef struct {
     double* timing_ms;
     double* diag_f;
     double* diag_g;
-    /* Dense-GEMM path: 0 = automatic (tcgen05 tensor cores for BF16 input
-       when the layout allows TMA: 16-byte aligned base, leading dimension a
-       multiple of 8, r <= 512), 1 = CUDA-core (SIMT) kernels only.  Used by
-       css_project, by the initial scores of gcss_select / gcss_distributed,
-       and by css_select's C = A A^T and f^(0) (C split into two BF16 parts
-       that together carry 16 significant bits; FP32 A is split the same way,
-       any alignment, and each GEMM sums the products hi*hi, hi*lo, lo*hi of
-       the parts). */
+    /* Dense-GEMM path: 0 = automatic, 1 = CUDA-core (SIMT) kernels only.
+       Automatic means tcgen05 tensor cores: for css_project and the initial
+       scores of gcss_select / gcss_distributed when A is BF16 and its layout
+       allows TMA (16-byte aligned base, leading dimension a multiple of 8,
+       r <= 512; B split into three BF16 parts, all 24 bits); for the initial
+       scores of css_select and css_select_batched when A is BF16 (a layout
+       TMA refuses is copied to an aligned buffer first) or FP32 (split into
+       three BF16 parts, the six products of parts down to 2^-16 summed):
+       C = A A^T, then C split into three BF16 parts. */
     int32_t init_path;
     /* Test hook for the bounded device waits (0 = off, the default).
        1: one team barrier of the persistent greedy kernel (the first of

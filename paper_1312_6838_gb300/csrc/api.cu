@@ -531,7 +531,7 @@ size_t host_out_bytes(int32_t k) {
 }
 
 // f_i^(0) = ||B^T a_i||^2 (Algorithm 3's initialisation): tcgen05 for BF16 A
-// (B split into two BF16 parts), register-tiled SIMT otherwise.
+// (B split into three BF16 parts), register-tiled SIMT otherwise.
 cudaError_t gcss_f0(int dt, const void* A, int64_t lda, int64_t m, int64_t n, const void* B, int64_t ldb,
                     int64_t r, double* partial, void* tc_scratch, double* f, const Header& h,
                     const css_opts& o, cudaStream_t s) {

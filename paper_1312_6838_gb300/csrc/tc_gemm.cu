@@ -8,15 +8,20 @@
 //                major A), Omega is K-major.
 //   norms        f_i = ||B^T a_i||^2 (Algorithm 3's initial scores).  D = A^T B
 //                per tile of 128 columns of A, both operands K-major; B (FP32)
-//                is split into two BF16 parts B1 + B2 (16 significant bits)
-//                that accumulate into the same TMEM tile; the epilogue sums
-//                squares of each row in FP64.  A third part would carry B's
-//                last 8 bits, but the tensor cores' own accumulation error is
-//                larger than that part: measured against the FP64 oracle at
-//                2048 x 65536, r = 400, the initial scores are within 2.9 u
-//                sqrt(m) with two parts and 4.5 u sqrt(m) with three.
+//                is split into three BF16 parts (all 24 bits) that accumulate
+//                into the same TMEM tile; the epilogue sums squares of each
+//                row in FP64.
+//   initial CSS scores (css_f0): C = A A^T, U' = its upper triangle in
+//                three BF16 parts, and the column dots of A with U' A.
 //
-// One CTA = 6 warps: warp 0 lane 0 issues TMA loads into a 3-stage shared
+// The number of parts of an FP32 operand: two (16 bits) leave every entry
+// with a relative error of 2^-17.  That hardly moves the initial scores (f0
+// within 2.9 u sqrt(m) of the oracle's at 2048 x 65536 for the norms) but
+// moves the late, small scores: on small problems with k close to the rank
+// the final errors were 5-25 (GCSS) and 20-80 (CSS) times the oracle's, and
+// 0.8-1.05 with three parts.
+//
+// One CTA = 6 warps: warp 0 lane 0 issues TMA loads into a shared
 // memory ring (128-byte swizzle), warp 1 owns the TMEM allocation and its lane
 // 0 issues tcgen05.mma (BF16 x BF16 -> FP32, M = 128, up to two MMAs of
 // N <= 256 side by side in TMEM), warps 2-5 read the accumulator back with
@@ -41,14 +46,9 @@ constexpr int STAGES = 4;     // ring depth, at most (Params::stages picks 1..4)
 constexpr int kSmemMax = 227 * 1024;   // dynamic shared memory of one CTA
 constexpr int kThreads = 192;
 constexpr int kTmemCols = 512;
-// BF16 parts of an FP32 operand.  B of the GCSS norms takes two (hi + lo,
-// 16 significant bits).  U' of the CSS scores and FP32 A take three (all 24
-// bits): the scores of late iterations are small differences of O(f^(0))
-// terms, and a 2^-17 relative error in every entry of U' or A, though within
-// a few u sqrt(m) of f^(0), moved late picks enough to raise the final error
-// of small problems (m ~ 70, k ~ 0.8 m) 20-300 fold over the oracle's.
-constexpr int kParts = 2;
-constexpr int kUParts = 3;
+// BF16 parts of an FP32 operand (B of the GCSS norms, U' of the CSS scores,
+// FP32 A): three, all 24 bits of it (see the top of the file).
+constexpr int kParts = 3;
 
 struct Params {
   int mode;          // 0 projection partials, 1 squared row norms, 2 C = A A^T, 3 column dots
@@ -919,7 +919,7 @@ struct F0Layout {
   float* Acopy;
 };
 bool is_f32(int src) { return src == kF0F32 || src == kF0F32Staged; }
-int a_parts(int src) { return is_f32(src) ? kUParts : src == kF0Bf16Staged ? 1 : 0; }
+int a_parts(int src) { return is_f32(src) ? kParts : src == kF0Bf16Staged ? 1 : 0; }
 
 F0Layout f0_layout(int m, int n, int src, void* scratch) {
   F0Layout L{};
@@ -933,7 +933,7 @@ F0Layout f0_layout(int m, int n, int src, void* scratch) {
   L.ldc = c_ld(m, 4);
   const size_t c = align_up((size_t)m * L.ldc * 4);
   const size_t chunks = align_up((size_t)L.nchunk * L.tiles_lower * BM * 256 * 4);
-  const size_t parts = align_up((size_t)L.mpad * kUParts * L.rpad * 2);
+  const size_t parts = align_up((size_t)L.mpad * kParts * L.rpad * 2);
   const size_t part = align_up((size_t)L.mtiles * L.ndots * n * 8);
   const size_t ap = align_up((size_t)L.mpad * a_parts(src) * L.npad * 2);
   // kF0F32Staged: an FP32 copy of A with leading dimension mpad after the parts
@@ -978,7 +978,7 @@ bool f0_maps(const F0Layout& L, const void* A, long long lda, int m, int n, int 
     if (!make_map(mA2, A, (uint64_t)m, (uint64_t)n, (uint64_t)lda, BK)) return false;
     if (!make_map(mA3, A, (uint64_t)m, (uint64_t)n, (uint64_t)lda, 256)) return false;
   }
-  return make_map(mU, L.Cp, (uint64_t)L.mpad, (uint64_t)(kUParts * L.rpad), (uint64_t)L.mpad, BM);
+  return make_map(mU, L.Cp, (uint64_t)L.mpad, (uint64_t)(kParts * L.rpad), (uint64_t)L.mpad, BM);
 }
 
 // C = A A^T: the tiles touching the lower triangle, grid (mtiles, ceil(m /
@@ -1047,14 +1047,14 @@ Params f0_params_dots(const F0Layout& L, const void* A, long long lda, int m, in
     // stage per K block holding the U' parts and the single shared A tile:
     // 96 KB per stage
     P.group = 1;
-    P.nparts = kUParts;
+    P.nparts = kParts;
     P.b_part_stride = 0;
-    P.stage_bytes = kUParts * BM * BK * 2 + 512 * BK * 2;
+    P.stage_bytes = kParts * BM * BK * 2 + 512 * BK * 2;
     P.stages = 2;
   }
   // the epilogue stages the tile's Acol (BM x n_tile, BF16 or FP32) in the ring
-  static_assert(BM * 512 * 2 <= 2 * (kUParts * BM * BK * 2 + 512 * BK * 2), "BF16 ring holds the Acol tile");
-  static_assert(2 * (kUParts * BM * BK * 2 + 512 * BK * 2) + 256 + 1024 <= kSmemMax, "BF16 ring fits");
+  static_assert(BM * 512 * 2 <= 2 * (kParts * BM * BK * 2 + 512 * BK * 2), "BF16 ring holds the Acol tile");
+  static_assert(2 * (kParts * BM * BK * 2 + 512 * BK * 2) + 256 + 1024 <= kSmemMax, "BF16 ring fits");
   static_assert(BM * 256 * 4 <= 3 * (BM * BK * 2 + 256 * BK * 2), "FP32 ring holds the Acol tile");
   P.f = L.partial;
   P.Acol = A;
@@ -1104,7 +1104,7 @@ __global__ void group_split_kernel(const GroupProb* __restrict__ probs, int whic
   const long long tot = (long long)g.mpad * cols;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
        idx += (long long)gridDim.x * blockDim.x)
-    split_one(B, ldb, g.m, r, g.mpad, cols, out, which, kUParts, idx);
+    split_one(B, ldb, g.m, r, g.mpad, cols, out, which, kParts, idx);
 }
 
 __global__ void group_reduce_kernel(const GroupProb* __restrict__ probs) {
@@ -1170,7 +1170,7 @@ cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, do
                                                                                       L.mpad, L.Acopy);
     if (is_f32(src))
       split_parts_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>((const float*)A, lda, m, n, L.mpad,
-                                                                         L.npad, L.Ap, 0, kUParts);
+                                                                         L.npad, L.Ap, 0, kParts);
     else
       stage_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>((const __nv_bfloat16*)A, lda, m, n, L.mpad,
                                                                    L.npad, L.Ap);
@@ -1188,7 +1188,7 @@ cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, do
   {
     const long long tot = (long long)L.mpad * L.rpad;
     split_parts_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(L.C, L.ldc, m, m, L.mpad, L.rpad, L.Cp, 1,
-                                                                       kUParts);
+                                                                       kParts);
   }
   const Params P3 = f0_params_dots(L, A, lda, m, n, src, err, spin_ns, stall);
   if ((e = set_smem<false, false>(P3)) != cudaSuccess) return e;

@@ -1057,10 +1057,15 @@ Params f0_params_dots(const F0Layout& L, const void* A, long long lda, int m, in
   static_assert(2 * (kParts * BM * BK * 2 + 512 * BK * 2) + 256 + 1024 <= kSmemMax, "BF16 ring fits");
   static_assert(BM * 256 * 4 <= 3 * (BM * BK * 2 + 256 * BK * 2), "FP32 ring holds the Acol tile");
   P.f = L.partial;
-  P.Acol = A;
+  // the outer factor a_i of the column dots: A itself, or its aligned copy
+  // (same values) when one is made, so that the epilogue's staging takes
+  // 16-byte loads
+  const void* Ac = src == kF0Bf16Staged ? (const void*)L.Ap : src == kF0F32Staged ? (const void*)L.Acopy : A;
+  const long long ldac = Ac == A ? lda : L.mpad;
+  P.Acol = Ac;
   P.acol_f32 = f32 ? 1 : 0;
-  P.acol_vec = ((uintptr_t)A % 16 == 0 && (lda * (f32 ? 4 : 2)) % 16 == 0) ? 1 : 0;
-  P.lda_col = lda;
+  P.acol_vec = ((uintptr_t)Ac % 16 == 0 && (ldac * (f32 ? 4 : 2)) % 16 == 0) ? 1 : 0;
+  P.lda_col = ldac;
   P.err = err;
   P.spin_ns = spin_ns;
   P.stall = stall;

@@ -483,9 +483,27 @@ __device__ void fused_step(const Ctx<typename AccOf<TA>::type>& x, const UnitDes
   int unit = 0;
   if (x.lane == 0) unit = (int)atomicAdd(ctr, 1u);
   unit = __shfl_sync(0xffffffffu, unit, 0);
+  // short columns (at most 2 KB): a tile's loads are one or two dependent
+  // memory round trips, so the warp asks L2 for the columns of its next unit
+  // as soon as it draws it (one bulk prefetch per column).  Measured on the
+  // batched workload (one CTA per problem, every SM streaming): the greedy
+  // launch 4-7 % shorter; with 4 KB columns (the distributed blocks, 2048
+  // rows) it was 5 % longer, so those are left alone
+  const bool pf_next = u.vec_ok && (size_t)m * sizeof(TA) <= 2048 && (size_t)m * sizeof(TA) >= 16;
   while (unit < nunits) {
     int next = 0;
     if (x.lane == 0) next = (int)atomicAdd(ctr, 1u);
+    if (pf_next) {
+      const int nx = __shfl_sync(0xffffffffu, next, 0);
+      if (nx < nunits && x.lane < CW) {
+        const int nt = nx < nbulk ? nx : nbulk + (nx - nbulk) / kSplitR;
+        const int col = nt * CW + x.lane;
+        if (col < n)
+          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(A + (long long)col * u.lda),
+                       "r"((unsigned)((size_t)m * sizeof(TA)) & ~15u)
+                       : "memory");
+      }
+    }
     int tile = unit, sidx = -1, chunk = 0, r_lo = 0, r_hi = m;
     if (unit >= nbulk) {
       sidx = (unit - nbulk) / kSplitR;

@@ -630,9 +630,14 @@ size_t css_workspace_size(css_op op, css_dtype dtype, int64_t m, int64_t n, int6
   return 0;
 }
 
-css_status css_select(const void* A, css_dtype dtype, int64_t m, int64_t n, int64_t lda, int32_t k,
-                      int32_t* sel, double* trace, int32_t* n_sel, double* W, void* ws,
-                      size_t ws_bytes, const css_opts* opts, css_stream_t stream) {
+}  // extern "C"
+
+namespace {
+
+// css_select; pipe: A's columns arrive in chunks (css_select_host).
+css_status select_impl(const void* A, css_dtype dtype, int64_t m, int64_t n, int64_t lda, int32_t k,
+                       int32_t* sel, double* trace, int32_t* n_sel, double* W, void* ws,
+                       size_t ws_bytes, const css_opts* opts, css_stream_t stream, const tc::F0Pipe* pipe) {
   const css_opts o = opts ? *opts : defaults();
   cudaStream_t s = (cudaStream_t)stream;
   if (!A || !sel || !trace || !n_sel || !valid_dtype(dtype)) return CSS_ERR_INVALID_ARG;
@@ -657,10 +662,13 @@ css_status css_select(const void* A, css_dtype dtype, int64_t m, int64_t n, int6
   long long ldas = lda;
   if (dtype != CSS_F64 && o.init_path != 1 && tc::supported_any()) {
     const int src = tc::f0_source(dtype == CSS_F32, A, lda, (int)m);
-    e = tc::css_f0(A, lda, (int)m, (int)n, L.C, L.s.f, L.h.aux_err, spin, s, stall_mbarrier(o), src);
+    e = tc::css_f0(A, lda, (int)m, (int)n, L.C, L.s.f, L.h.aux_err, spin, s, stall_mbarrier(o), src, pipe);
     tc::f0_staged_copy((int)m, (int)n, src, L.C, &As, &ldas);
   } else {
-    e = css_f0_simt(dtype, A, lda, (int)m, (int)n, L.C, c_ld(m, (int)accsize(dtype)), L.partial, L.s.f, s);
+    e = cudaSuccess;
+    for (int z = 0; pipe && z < pipe->chunks && e == cudaSuccess; ++z) e = cudaStreamWaitEvent(s, pipe->ready[z], 0);
+    if (e == cudaSuccess)
+      e = css_f0_simt(dtype, A, lda, (int)m, (int)n, L.C, c_ld(m, (int)accsize(dtype)), L.partial, L.s.f, s);
   }
   if (e != cudaSuccess) return cuda_status(e);
   tm.mark(1, s);
@@ -677,6 +685,43 @@ css_status css_select(const void* A, css_dtype dtype, int64_t m, int64_t n, int6
   cs = finish(L.h, o, s);
   tm.report(o);
   return cs;
+}
+
+// A copy stream and arrival events for css_select_host, one set per device,
+// made on first use and kept for the life of the process.
+constexpr int kMaxHostChunks = 32;
+struct HostPipe {
+  cudaStream_t copy = nullptr;
+  cudaEvent_t start = nullptr;
+  cudaEvent_t ready[kMaxHostChunks] = {};
+  bool ok = false;
+};
+std::mutex g_pipe_mu;
+HostPipe* host_pipe() {
+  static HostPipe pipes[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(g_pipe_mu);
+  HostPipe& p = pipes[dev];
+  if (!p.ok) {
+    bool good = cudaStreamCreateWithFlags(&p.copy, cudaStreamNonBlocking) == cudaSuccess &&
+                cudaEventCreateWithFlags(&p.start, cudaEventDisableTiming) == cudaSuccess;
+    for (int z = 0; good && z < kMaxHostChunks; ++z)
+      good = cudaEventCreateWithFlags(&p.ready[z], cudaEventDisableTiming) == cudaSuccess;
+    if (!good) return nullptr;
+    p.ok = true;
+  }
+  return &p;
+}
+
+}  // namespace
+
+extern "C" {
+
+css_status css_select(const void* A, css_dtype dtype, int64_t m, int64_t n, int64_t lda, int32_t k,
+                      int32_t* sel, double* trace, int32_t* n_sel, double* W, void* ws,
+                      size_t ws_bytes, const css_opts* opts, css_stream_t stream) {
+  return select_impl(A, dtype, m, n, lda, k, sel, trace, n_sel, W, ws, ws_bytes, opts, stream, nullptr);
 }
 
 css_status gcss_select(const void* A, css_dtype dtype, int64_t m, int64_t n, int64_t lda,
@@ -765,12 +810,43 @@ css_status css_select_host(const void* A_host, css_dtype dtype, int64_t m, int64
   int32_t* d_sel = (int32_t*)outs;
   int32_t* d_nsel = d_sel + k;
   double* d_trace = (double*)(outs + align_up(sizeof(int32_t) * (k + 1), 8));
-  cudaError_t e = cudaMemcpyAsync(A_dev, A_host, (size_t)lda * n * esize(dtype), cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return cuda_status(e);
   css_opts o = opts ? *opts : defaults();
   o.sync = 1;
-  css_status cs = css_select(A_dev, dtype, m, n, lda, k, d_sel, d_trace, d_nsel, nullptr, ws, need, &o, stream);
-  if (cs < 0) return cs;
+  // A goes over in column chunks on a copy stream, so that the initial
+  // scores' C = A A^T works on the chunks already in while later ones are in
+  // flight (host-to-device copies run at about 210 GB/s on this part, under
+  // a thirtieth of HBM).  The chunks follow C's K chunks.
+  const size_t col_bytes = (size_t)lda * esize(dtype);
+  const int cols = std::max(1, tc::f0_chunk_cols((int)m, (int)n));
+  const int chunks = (int)((n + cols - 1) / cols);
+  HostPipe* hp = (dtype != CSS_F64 && chunks <= kMaxHostChunks) ? host_pipe() : nullptr;
+  cudaError_t e;
+  css_status cs;
+  if (hp) {
+    // the copy waits for the stream's earlier work on A_dev
+    if ((e = cudaEventRecord(hp->start, s)) != cudaSuccess) return cuda_status(e);
+    if ((e = cudaStreamWaitEvent(hp->copy, hp->start, 0)) != cudaSuccess) return cuda_status(e);
+    for (int z = 0; z < chunks; ++z) {
+      const int64_t c0 = (int64_t)z * cols, nc = std::min<int64_t>(cols, n - c0);
+      if ((e = cudaMemcpyAsync((char*)A_dev + c0 * col_bytes, (const char*)A_host + c0 * col_bytes, nc * col_bytes,
+                               cudaMemcpyHostToDevice, hp->copy)) != cudaSuccess ||
+          (e = cudaEventRecord(hp->ready[z], hp->copy)) != cudaSuccess) {
+        cudaStreamSynchronize(hp->copy);
+        return cuda_status(e);
+      }
+    }
+    const tc::F0Pipe pipe{hp->ready, chunks, cols};
+    cs = select_impl(A_dev, dtype, m, n, lda, k, d_sel, d_trace, d_nsel, nullptr, ws, need, &o, stream, &pipe);
+    if (cs < 0) {
+      cudaStreamSynchronize(hp->copy);
+      return cs;
+    }
+  } else {
+    if ((e = cudaMemcpyAsync(A_dev, A_host, (size_t)lda * n * esize(dtype), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      return cuda_status(e);
+    cs = css_select(A_dev, dtype, m, n, lda, k, d_sel, d_trace, d_nsel, nullptr, ws, need, &o, stream);
+    if (cs < 0) return cs;
+  }
   e = cudaMemcpyAsync(sel, d_sel, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(trace, d_trace, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(n_sel, d_nsel, sizeof(int32_t), cudaMemcpyDeviceToHost, s);

@@ -51,8 +51,19 @@ bool supported_any();
 // into three BF16 parts (all of its FP32 bits), and f[i] = A_:i^T C A_:i from
 // the column dots of A with C A (FP64 sums).  src = f0_source(...): for FP32
 // A both GEMMs sum the six products of its parts down to 2^-16.
+// pipe: column chunks of A that arrive one after another (a host copy split
+// by the caller): chunk z holds columns [z * cols, (z + 1) * cols) and is in
+// place once ready[z] has completed.  With src == kF0Bf16 and cols ==
+// f0_chunk_cols(m, n), each K chunk of C = A A^T starts as soon as its
+// columns are in; otherwise everything waits for all of them first.
+struct F0Pipe {
+  const cudaEvent_t* ready;
+  int chunks, cols;
+};
+int f0_chunk_cols(int m, int n);
 cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, double* f, int* err,
-                   unsigned long long spin_ns, cudaStream_t s, int stall, int src);
+                   unsigned long long spin_ns, cudaStream_t s, int stall, int src,
+                   const F0Pipe* pipe = nullptr);
 
 // css_f0 for a group of problems (a batch): one launch per phase for all of
 // them.  Problem i's scratch (css_f0_scratch_bytes(m[i], n[i], src[i])

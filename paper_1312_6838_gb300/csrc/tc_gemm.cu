@@ -105,6 +105,7 @@ struct Params {
   // epilogue adds the two.  acc2_col = 0: one accumulator.
   int pair_acc[8];
   int acc2_col;
+  int bz_off;        // added to blockIdx.z (a launch of some of the K chunks)
 };
 
 }  // namespace
@@ -635,7 +636,7 @@ template <bool A_MN, bool B_MN>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const __grid_constant__ Params P) {
-  tc_body<A_MN, B_MN>(P, &tmA, &tmB, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z);
+  tc_body<A_MN, B_MN>(P, &tmA, &tmB, blockIdx.x, blockIdx.y, blockIdx.z + P.bz_off, gridDim.z + P.bz_off);
 }
 
 // B (FP32, m x r, ldb) -> np BF16 parts B1 + B2 (+ B3) (m x rpad each, ld
@@ -1162,12 +1163,19 @@ int f0_source(bool f32, const void* A, long long lda, int m) {
   return supported(A, lda, m, 256) ? kF0Bf16 : kF0Bf16Staged;
 }
 
+int f0_chunk_cols(int m, int n) { return syrk_chunk_kb(m, n) * BK; }
+
 cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, double* f, int* err,
-                   unsigned long long spin_ns, cudaStream_t s, int stall, int src) {
+                   unsigned long long spin_ns, cudaStream_t s, int stall, int src, const F0Pipe* pipe) {
   const F0Layout L = f0_layout(m, n, src, scratch);
   CUtensorMap mA2, mU, mA3;
   if (!f0_maps(L, A, lda, m, n, src, &mA2, &mU, &mA3)) return cudaErrorInvalidValue;
   cudaError_t e;
+  // chunks of A arriving: per K chunk of C = A A^T, or all before anything
+  const bool per_chunk = pipe && src == kF0Bf16 && pipe->cols == f0_chunk_cols(m, n) && pipe->chunks == L.nchunk;
+  if (pipe && !per_chunk)
+    for (int z = 0; z < pipe->chunks; ++z)
+      if ((e = cudaStreamWaitEvent(s, pipe->ready[z], 0)) != cudaSuccess) return e;
   if (src != kF0Bf16) {
     const long long tot = (long long)L.mpad * L.npad;
     if (src == kF0F32Staged)
@@ -1183,9 +1191,21 @@ cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, do
   }
   const Params P2 = f0_params_syrk(L, m, n, src, err, spin_ns, stall);
   if ((e = set_smem<true, true>(P2)) != cudaSuccess) return e;
-  tc_kernel<true, true><<<dim3(L.mtiles, (m + 255) / 256, L.nchunk), kThreads, smem_for(P2.stage_bytes, P2.stages),
-                          s>>>(mA2, mA2, P2);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (per_chunk) {
+    // one launch per K chunk, each after its columns have arrived
+    for (int z = 0; z < L.nchunk; ++z) {
+      if ((e = cudaStreamWaitEvent(s, pipe->ready[z], 0)) != cudaSuccess) return e;
+      Params Pz = P2;
+      Pz.bz_off = z;
+      tc_kernel<true, true><<<dim3(L.mtiles, (m + 255) / 256, 1), kThreads, smem_for(P2.stage_bytes, P2.stages),
+                              s>>>(mA2, mA2, Pz);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+  } else {
+    tc_kernel<true, true><<<dim3(L.mtiles, (m + 255) / 256, L.nchunk), kThreads,
+                            smem_for(P2.stage_bytes, P2.stages), s>>>(mA2, mA2, P2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   // C = the chunks' sum, both triangles (the greedy iterations read whole rows)
   reduce_lower_kernel<<<dim3((m + 31) / 32, (m + 31) / 32), dim3(32, 8), 0, s>>>(L.chunk_tiles, L.nchunk,
                                                                                  L.tiles_lower, m, L.ldc, L.C);

@@ -296,3 +296,26 @@ def test_repeat_is_bitwise_identical(css, tile):
         assert torch.equal(r.diag_f, runs[0].diag_f)
         assert torch.equal(r.diag_g, runs[0].diag_g)
         assert torch.equal(r.W, runs[0].W)
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float32, torch.float64])
+@pytest.mark.parametrize("shape", [(304, 5000, 24), (300, 2000, 16), (128, 700, 10)])
+def test_select_from_host_memory(css, dtype, shape):
+    """css_select_host: A copied from pinned host memory in column chunks
+    whose arrival starts the initial scores' K chunks (BF16), then the same
+    selection, trace and error as css_select on the device copy, bit for bit,
+    and parity with the oracle."""
+    m, n, k = shape
+    A_np = ci.lowrank_uv(m, n, 2 * k, 0.05, 910 + m)
+    A, vals = dev_matrix(A_np, dtype)
+    host = A.t().contiguous().cpu().pin_memory().t()   # column-major, pinned
+    A_dev = css.empty_colmajor(m, n, dtype)
+    for _ in range(2):   # the second call reuses the copy stream and events
+        sel, trace, ns = css.select_host(host, k, A_dev)
+        ref = css.select(A, k)
+        assert ns == ref.n_sel
+        assert sel.tolist() == ref.indices.cpu().tolist()
+        assert torch.equal(trace, ref.trace.cpu())
+    assert torch.equal(A_dev.cpu(), A.cpu())
+    oref = O.greedy_css(vals, k, tau_rel=1e-6)
+    assert abs(O.reconstruction_error(vals, sel.tolist()) - oref.trace[-1]) <= 1e-4 * oref.trace[0]

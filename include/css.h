@@ -628,6 +628,11 @@ css_status css_lowrank(const double* W, int64_t ldw, const double* Q,
  * lda * n elements), runs css_select, and copies sel (HOST int32[k]), trace
  * (HOST double[k+1]) and n_sel (HOST int32[1]) back.  Always synchronous.
  * The workspace is css_workspace_size(CSS_OP_SELECT, ...) plus 256 bytes.
+ * For BF16 and FP32, A goes over in column chunks on a copy stream of the
+ * library's own (one per device, with its events, made on first use and
+ * kept until the process exits), ordered after the work already on
+ * `stream`; the initial scores start on the chunks already in.  The result
+ * is that of css_select on the copied matrix, bit for bit.
  */
 css_status css_select_host(const void* A_host, css_dtype dtype, int64_t m,
                            int64_t n, int64_t lda, int32_t k, int32_t* sel,

@@ -7,8 +7,8 @@ import torch
 
 import css_inputs as ci
 from oracle import css_oracle as O
-from tests.gpu_helpers import (GAP_TOL, certify_selection, dev_matrix, oracle_path_parity, teacher_forced_parity,
-                               trace_error_bound)
+from tests.gpu_helpers import (GAP_TOL, certify_selection, dev_matrix, first_mismatch, oracle_path_parity,
+                               pair_error_bound, teacher_forced_parity, trace_error_bound)
 
 pytestmark = pytest.mark.gpu
 
@@ -319,3 +319,36 @@ def test_select_from_host_memory(css, dtype, shape):
     assert torch.equal(A_dev.cpu(), A.cpu())
     oref = O.greedy_css(vals, k, tau_rel=1e-6)
     assert abs(O.reconstruction_error(vals, sel.tolist()) - oref.trace[-1]) <= 1e-4 * oref.trace[0]
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("init_path", [0, 1])
+def test_tiny_and_degenerate_shapes_mixed(css, dtype, init_path):
+    """The mixed paths (tensor-core or SIMT initial scores) on the degenerate
+    cases: one column, one row (every column ties: lowest index), k = m = n,
+    a zero column and duplicated columns; picks as the oracle's on the values
+    the device holds."""
+    A, vals = dev_matrix(np.arange(1.0, 8.0).reshape(7, 1), dtype)
+    assert css.select(A, 1, init_path=init_path).indices.cpu().tolist() == [0]
+    row = np.array([[1.0, -3.0, 2.0, 0.5]])
+    A, vals = dev_matrix(row, dtype)
+    assert css.select(A, 1, init_path=init_path).indices.cpu().tolist() == [0]
+    A_np = ci.lowrank_uv(12, 12, 12, 0.0, 19)
+    A, vals = dev_matrix(A_np, dtype)
+    res = css.select(A, 12, init_path=init_path)
+    assert sorted(res.indices.cpu().tolist()) == list(range(12))
+    assert O.reconstruction_error(vals, res.indices.cpu().tolist()) <= 1e-10 * float(np.sum(vals * vals))
+    rng = np.random.default_rng(21)
+    A_np = rng.standard_normal((25, 40))
+    A_np[:, 5] = 0.0
+    A_np[:, 17] = A_np[:, 3]
+    A_np[:, 30] = 2.0 * A_np[:, 3]
+    A, vals = dev_matrix(A_np, dtype)
+    res = css.select(A, 12, init_path=init_path)
+    S = res.indices.cpu().tolist()
+    assert 5 not in S
+    assert len({3, 17, 30} & set(S)) <= 1
+    ref = O.greedy_css(vals, 12, tau_rel=1e-6, keep_scores=True)
+    t = first_mismatch(S, list(ref.S))
+    if t is not None:
+        assert ref.gaps[t] <= max(GAP_TOL, pair_error_bound(ref, t, 25, dtype)), (t, ref.gaps[t])

@@ -45,7 +45,15 @@ constexpr int BK = 64;        // K elements per stage: one 128-byte swizzle row
 constexpr int STAGES = 4;     // ring depth, at most (Params::stages picks 1..4)
 constexpr int kSmemMax = 227 * 1024;   // dynamic shared memory of one CTA
 constexpr int kThreads = 192;
-constexpr int kTmemCols = 512;
+constexpr int kTmemCols = 512;   // TMEM columns a CTA takes unless Params::tmem_cols says fewer
+// The initial-score GEMMs of BF16 A take 256 TMEM columns and two 48 KB ring
+// stages per CTA, so that two CTAs share an SM and one's epilogue overlaps
+// the other's MMAs (instead of 512 columns and 96-112 KB stages, one CTA per SM)
+constexpr bool kSyrk2Cta = true;
+constexpr bool kDots2Cta = true;
+// FP32 A's column-dot GEMM: columns per CTA (its two accumulators take
+// twice that of TMEM; 128 lets two CTAs share an SM)
+constexpr int kDotsF32Cols = 128;
 // BF16 parts of an FP32 operand (B of the GCSS norms, U' of the CSS scores,
 // FP32 A): three, all 24 bits of it (see the top of the file).
 constexpr int kParts = 3;
@@ -106,6 +114,7 @@ struct Params {
   int pair_acc[8];
   int acc2_col;
   int bz_off;        // added to blockIdx.z (a launch of some of the K chunks)
+  int tmem_cols;     // TMEM columns to allocate (0: kTmemCols); a power of 2 >= 32
 };
 
 }  // namespace
@@ -310,6 +319,7 @@ __device__ __forceinline__ void tc_body(const Params& P, const CUtensorMap* mapA
   uint32_t* s_tmem = (uint32_t*)(never + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t tcols = P.tmem_cols ? (uint32_t)P.tmem_cols : (uint32_t)kTmemCols;
   // work of this CTA
   const int tile0 = bx * BM;
   int kb_begin = 0, kb_end = P.kb_total;
@@ -356,7 +366,7 @@ __device__ __forceinline__ void tc_body(const Params& P, const CUtensorMap* mapA
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
-                 "r"(kTmemCols)
+                 "r"(tcols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -627,7 +637,7 @@ __device__ __forceinline__ void tc_body(const Params& P, const CUtensorMap* mapA
   __syncthreads();
   if (warp == 1) {
     fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols)
                  : "memory");
   }
 }
@@ -966,6 +976,9 @@ void set_pairs(Params& P) {
   P.acc2_col = 256;
 }
 
+// Columns of D per CTA of the column-dot GEMM.
+int dots_n_tile(bool f32) { return f32 ? kDotsF32Cols : kDots2Cta ? 256 : 512; }
+
 // Tensor maps of the two GEMMs: C = A A^T (both operands A, or its parts,
 // row-major in K = the column index), and U' A (U' parts K-major; A, or its
 // parts, K-major in the rows).
@@ -974,7 +987,8 @@ bool f0_maps(const F0Layout& L, const void* A, long long lda, int m, int n, int 
   if (src != kF0Bf16) {
     const uint64_t cols = (uint64_t)a_parts(src) * L.npad;
     if (!make_map(mA2, L.Ap, (uint64_t)L.mpad, cols, (uint64_t)L.mpad, BK)) return false;
-    if (!make_map(mA3, L.Ap, (uint64_t)L.mpad, cols, (uint64_t)L.mpad, 256)) return false;
+    if (!make_map(mA3, L.Ap, (uint64_t)L.mpad, cols, (uint64_t)L.mpad, (uint32_t)std::min(256, dots_n_tile(is_f32(src)))))
+      return false;
   } else {
     if (!make_map(mA2, A, (uint64_t)m, (uint64_t)n, (uint64_t)lda, BK)) return false;
     if (!make_map(mA3, A, (uint64_t)m, (uint64_t)n, (uint64_t)lda, 256)) return false;
@@ -1008,6 +1022,10 @@ Params f0_params_syrk(const F0Layout& L, int m, int n, int src, int* err, unsign
   }
   P.stage_bytes = BM * BK * 2 + 256 * BK * 2;
   P.stages = fit_stages(P.stage_bytes, STAGES);
+  if (kSyrk2Cta && !f32) {
+    P.stages = 2;
+    P.tmem_cols = 256;
+  }
   P.out = L.chunk_tiles;
   P.err = err;
   P.spin_ns = spin_ns;
@@ -1026,9 +1044,9 @@ Params f0_params_dots(const F0Layout& L, const void* A, long long lda, int m, in
   P.tri = 1;
   P.M = m;
   P.N = n;
-  P.n_half = 256;
-  P.halves = f32 ? 1 : 2;
-  P.n_tile = P.halves * 256;
+  P.n_half = std::min(256, dots_n_tile(f32));
+  P.halves = dots_n_tile(f32) / P.n_half;
+  P.n_tile = P.halves * P.n_half;
   P.kb_total = (m + BK - 1) / BK;
   P.kb_per_cta = P.kb_total;
   P.kb_chunk = kDotsChunkKb;
@@ -1040,13 +1058,24 @@ Params f0_params_dots(const F0Layout& L, const void* A, long long lda, int m, in
     P.group = 0;
     P.nparts = 1;
     set_pairs(P);
+    P.acc2_col = P.n_tile;
+    P.tmem_cols = 2 * P.n_tile;
     P.b_part_stride = L.npad;
+    P.stage_bytes = BM * BK * 2 + P.n_tile * BK * 2;
+    P.stages = P.n_tile < 256 ? 3 : fit_stages(P.stage_bytes, STAGES);
+  } else if (kDots2Cta) {
+    // 256 columns per CTA, one stage per (K block, U' part) holding that
+    // part's tile and the A tile (48 KB), two stages: two CTAs per SM
+    P.group = 0;
+    P.nparts = kParts;
+    P.b_part_stride = 0;
     P.stage_bytes = BM * BK * 2 + 256 * BK * 2;
-    P.stages = fit_stages(P.stage_bytes, STAGES);
+    P.stages = 2;
+    P.tmem_cols = 256;
   } else {
     // 512 columns per CTA (two MMAs of N = 256, the whole TMEM) and one
     // stage per K block holding the U' parts and the single shared A tile:
-    // 96 KB per stage
+    // 112 KB per stage
     P.group = 1;
     P.nparts = kParts;
     P.b_part_stride = 0;
@@ -1057,6 +1086,7 @@ Params f0_params_dots(const F0Layout& L, const void* A, long long lda, int m, in
   static_assert(BM * 512 * 2 <= 2 * (kParts * BM * BK * 2 + 512 * BK * 2), "BF16 ring holds the Acol tile");
   static_assert(2 * (kParts * BM * BK * 2 + 512 * BK * 2) + 256 + 1024 <= kSmemMax, "BF16 ring fits");
   static_assert(BM * 256 * 4 <= 3 * (BM * BK * 2 + 256 * BK * 2), "FP32 ring holds the Acol tile");
+  static_assert(BM * 256 * 2 <= 2 * (BM * BK * 2 + 256 * BK * 2), "two-stage BF16 ring holds the Acol tile");
   P.f = L.partial;
   // the outer factor a_i of the column dots: A itself, or its aligned copy
   // (same values) when one is made, so that the epilogue's staging takes
@@ -1075,8 +1105,11 @@ Params f0_params_dots(const F0Layout& L, const void* A, long long lda, int m, in
 
 template <bool A_MN, bool B_MN>
 cudaError_t set_smem(const Params& P) {
-  return cudaFuncSetAttribute(tc_kernel<A_MN, B_MN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem_for(P.stage_bytes, P.stages));
+  cudaError_t e = cudaFuncSetAttribute(tc_kernel<A_MN, B_MN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_for(P.stage_bytes, P.stages));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc_kernel<A_MN, B_MN>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  return e;
 }
 
 // ------------------------------------------------------ groups of problems -
@@ -1231,7 +1264,7 @@ bool supported_any() { return encode_fn() != nullptr; }
 // triangle (every chunk), and every column-dot tile.
 void group_tile_counts(int m, int n, bool f32, int* t2, int* t3) {
   const F0Layout L = f0_layout(m, n, f32 ? kF0F32 : kF0Bf16, nullptr);   // (tile counts only)
-  const int n_tile = f32 ? 256 : 512;
+  const int n_tile = dots_n_tile(f32);
   *t2 = L.tiles_lower * L.nchunk;
   *t3 = L.mtiles * ((n + n_tile - 1) / n_tile) * L.ndots;
 }
@@ -1343,13 +1376,17 @@ cudaError_t group_f0_run(const GroupF0& g, cudaStream_t s) {
   const dim3 eg(kGroupBlocks, g.count);
   if (g.staged) group_split_kernel<<<eg, 256, 0, s>>>(g.probs, 0);
   if ((e = cudaFuncSetAttribute(tc_group_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem2)) !=
-      cudaSuccess)
+          cudaSuccess ||
+      (e = cudaFuncSetAttribute(tc_group_kernel<true, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) !=
+          cudaSuccess)
     return e;
   tc_group_kernel<true, true><<<g.ntiles2, kThreads, g.smem2, s>>>(g.probs, g.tiles2, 2);
   group_reduce_kernel<<<eg, dim3(32, 8), 0, s>>>(g.probs);
   group_split_kernel<<<eg, 256, 0, s>>>(g.probs, 1);
   if ((e = cudaFuncSetAttribute(tc_group_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                g.smem3)) != cudaSuccess)
+                                g.smem3)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(tc_group_kernel<false, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                100)) != cudaSuccess)
     return e;
   tc_group_kernel<false, false><<<g.ntiles3, kThreads, g.smem3, s>>>(g.probs, g.tiles3, 3);
   group_sum_rows_kernel<<<eg, 256, 0, s>>>(g.probs);

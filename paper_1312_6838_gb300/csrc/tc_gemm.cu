@@ -846,8 +846,8 @@ __global__ void sum_rows_kernel(const double* __restrict__ partial, int nblk, in
   if (i < n) out[i] = scale * sum_row(partial, nblk, n, i);
 }
 
-// C = sum over the K chunks of their partial tiles (FP64 sums in chunk
-// order, rounded once to FP32), written to both triangles of C (ld ldc)
+// C = sum over the K chunks of their partial tiles (compensated sums in
+// chunk order, rounded once to FP32), written to both triangles of C (ld ldc)
 // through 32 x 32 shared-memory tiles, so reads and writes are coalesced.
 // Only the 32 x 32 tiles on or below the diagonal run (bi >= bj); each lies
 // inside one chunk tile of 128 x 256.  Block-wide (32 x 8 threads).
@@ -864,9 +864,17 @@ __device__ __forceinline__ void reduce_lower_block(const float* __restrict__ par
     float v = 0.f;
     if (r < m && c < m && r >= c) {
       const long long local = (long long)(c - by * 256) * BM + (r - bx * BM);
-      double sum = 0.0;
-      for (int z = 0; z < chunks; ++z) sum += (double)src[z * chunk_stride + local];
-      v = (float)sum;
+      // compensated FP32 sum (TwoSum): within a unit of the exact sum
+      // before the final rounding, like an FP64 sum, at FP32 rates (FP64
+      // additions, at two per clock per SM, made this kernel their bound)
+      float sh = 0.f, sl = 0.f;
+      for (int z = 0; z < chunks; ++z) {
+        float s_, e_;
+        df_two_sum(sh, src[z * chunk_stride + local], s_, e_);
+        sh = s_;
+        sl += e_;
+      }
+      v = sh + sl;
       C[(long long)c * ldc + r] = v;
     }
     tile[k][tx] = v;

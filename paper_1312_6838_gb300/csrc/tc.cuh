@@ -47,9 +47,9 @@ size_t css_f0_scratch_bytes(int m, int n, int src);
 bool supported_any();
 
 // Algorithm 1's initial scores: C = A A^T on tensor cores (FP32
-// accumulation of exact BF16 products, in K chunks added in FP64), C split
-// into three BF16 parts (all of its FP32 bits), and f[i] = A_:i^T C A_:i from
-// the column dots of A with C A (FP64 sums).  src = f0_source(...): for FP32
+// accumulation of exact BF16 products, in K chunks added with compensated
+// FP32 sums), C split into three BF16 parts (all of its FP32 bits), and
+// f[i] = A_:i^T C A_:i from the column dots of A with C A (FP64 sums).  src = f0_source(...): for FP32
 // A both GEMMs sum the six products of its parts down to 2^-16.
 // pipe: column chunks of A that arrive one after another (a host copy split
 // by the caller): chunk z holds columns [z * cols, (z + 1) * cols) and is in

@@ -900,10 +900,10 @@ __global__ void reduce_lower_kernel(const float* __restrict__ parts, int chunks,
 // passes on to every initial score; the round-to-nearest FMAs of a SIMT dot
 // product err by about sqrt(m) units.  So C = A A^T is summed in chunks of
 // about 64 sqrt(m) products (4 to 64 K blocks of 64: 2 sqrt(m) units), at
-// most 32 chunks (very wide A gets longer ones), added in FP64.  U' A
-// likewise (one chunk for m <= 4096: at the 4096 x 65536 size shorter
-// chunks cut the initial scores' error from 4.8 to 3.2 u sqrt(m) but cost
-// 2.8 ms).
+// most 32 chunks (very wide A gets longer ones), added with compensated
+// FP32 sums.  U' A likewise (one chunk for m <= 4096: at the 4096 x 65536
+// size shorter chunks cut the initial scores' error from 4.8 to 3.2 u
+// sqrt(m) but cost 2.8 ms).
 constexpr int kSyrkMaxChunks = 32;
 constexpr int kDotsChunkKb = 64;
 int syrk_chunk_kb(int m, int n) {

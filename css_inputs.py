@@ -143,6 +143,8 @@ CONFIGS = {
                              block_sigma=0.8, block_seed=3, l_block=100, k=100),
     # Batched independent CSS: 1024 instances, FP32, rank k + 1e-2 noise.
     "batched_1024": dict(count=1024, seed=4, noise=1e-2),
+    # The same model with 128 problems (the DRAM capture of the batched launch).
+    "batched_128": dict(count=128, seed=4, noise=1e-2),
     # Adjoint of the reconstruction error: 4096 x 16384 FP32 rank 128 + 1e-3, k = 128.
     "adjoint_4096x16384": dict(m=4096, n=16384, rank=128, noise=1e-3, seed=5, k=128),
 }

@@ -130,7 +130,7 @@ struct GroupProb {
   long long lda;
   int m, n, mpad, npad, rpad, src;   // src: F0Source
   long long ldc;                      // C's leading dimension
-  int nchunk, ndots, mtiles, tiles_lower;
+  int nchunk, ndots, mtiles, tiles_lower, tw;
   float* C;
   float* chunk_tiles;
   __nv_bfloat16* Cp;
@@ -146,16 +146,19 @@ struct GroupTile {
 
 namespace {
 
-// Mode 2 tiles (BM rows x 256 columns) that touch the lower triangle: tile
-// (bx, by) does when bx * 128 + 127 >= by * 256, i.e. by <= bx / 2.  Their
-// index in row-tile order.
-__host__ __device__ __forceinline__ int lower_tile_index(int bx, int by) {
+// Mode 2 tiles (BM rows x tw columns, tw = 256 or 128) that touch the lower
+// triangle: tile (bx, by) does when bx * 128 + 127 >= by * tw, i.e. by <= bx
+// / 2 (tw = 256) or by <= bx (tw = 128).  Their index in row-tile order.
+__host__ __device__ __forceinline__ int lower_tile_index(int bx, int by, int tw) {
+  if (tw == 128) return bx * (bx + 1) / 2 + by;
   // sum over b < bx of (b / 2 + 1)
   const int q = bx / 2;
   const int before = bx + ((bx & 1) ? q * q : q * (q - 1));
   return before + by;
 }
-__host__ __device__ __forceinline__ int lower_tile_count(int mtiles) { return lower_tile_index(mtiles, 0); }
+__host__ __device__ __forceinline__ int lower_tile_count(int mtiles, int tw) {
+  return lower_tile_index(mtiles, 0, tw);
+}
 
 // ------------------------------------------------------------- PTX glue -----
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -605,7 +608,7 @@ __device__ __forceinline__ void tc_body(const Params& P, const CUtensorMap* mapA
       float sh = 0.f, sl = 0.f;   // mode 1: sum of squares in double-float
       float* tile_out = nullptr;
       if (P.mode == 2)
-        tile_out = P.out + ((long long)bz * P.tiles_lower + lower_tile_index(bx, by)) *
+        tile_out = P.out + ((long long)bz * P.tiles_lower + lower_tile_index(bx, by, P.n_tile)) *
                                (long long)(BM * P.n_tile);
       const int ncols = P.halves * P.n_half;
       for (int j0 = 0; j0 < ncols; j0 += 16) {
@@ -852,18 +855,18 @@ __global__ void sum_rows_kernel(const double* __restrict__ partial, int nblk, in
 // Only the 32 x 32 tiles on or below the diagonal run (bi >= bj); each lies
 // inside one chunk tile of 128 x 256.  Block-wide (32 x 8 threads).
 __device__ __forceinline__ void reduce_lower_block(const float* __restrict__ parts, int chunks, int tiles_lower,
-                                                   int m, long long ldc, float* __restrict__ C, int bi, int bj,
-                                                   float (&tile)[32][33]) {
+                                                   int tw, int m, long long ldc, float* __restrict__ C, int bi,
+                                                   int bj, float (&tile)[32][33]) {
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int r = bi * 32 + tx;
-  const int bx = (bi * 32) / BM, by = (bj * 32) / 256;
-  const long long chunk_stride = (long long)tiles_lower * BM * 256;
-  const float* src = parts + (long long)lower_tile_index(bx, by) * BM * 256;
+  const int bx = (bi * 32) / BM, by = (bj * 32) / tw;
+  const long long chunk_stride = (long long)tiles_lower * BM * tw;
+  const float* src = parts + (long long)lower_tile_index(bx, by, tw) * BM * tw;
   for (int k = ty; k < 32; k += blockDim.y) {
     const int c = bj * 32 + k;
     float v = 0.f;
     if (r < m && c < m && r >= c) {
-      const long long local = (long long)(c - by * 256) * BM + (r - bx * BM);
+      const long long local = (long long)(c - by * tw) * BM + (r - bx * BM);
       // compensated FP32 sum (TwoSum): within a unit of the exact sum
       // before the final rounding, like an FP64 sum, at FP32 rates (FP64
       // additions, at two per clock per SM, made this kernel their bound)
@@ -887,11 +890,11 @@ __device__ __forceinline__ void reduce_lower_block(const float* __restrict__ par
   }
   __syncthreads();   // the tile is free for the block's next use
 }
-__global__ void reduce_lower_kernel(const float* __restrict__ parts, int chunks, int tiles_lower, int m,
+__global__ void reduce_lower_kernel(const float* __restrict__ parts, int chunks, int tiles_lower, int tw, int m,
                                     long long ldc, float* __restrict__ C) {
   __shared__ float tile[32][33];
   if (blockIdx.x < blockIdx.y) return;
-  reduce_lower_block(parts, chunks, tiles_lower, m, ldc, C, blockIdx.x, blockIdx.y, tile);
+  reduce_lower_block(parts, chunks, tiles_lower, tw, m, ldc, C, blockIdx.x, blockIdx.y, tile);
 }
 
 // K chunking of the initial-score GEMMs (see Params::kb_chunk).  A TMEM sum
@@ -926,8 +929,15 @@ int dots_chunks(int m) { return ((m + BK - 1) / BK + kDotsChunkKb - 1) / kDotsCh
 // two; BF16 input with a layout TMA refuses: one, an exact copy), side by
 // side, each padded to whole K blocks (part p, column j at
 // Ap[(p * npad + j) * mpad + i], zero beyond m and n).
+// Columns per tile of C = A A^T: FP32 A (two accumulators for its part
+// pairs) takes 128 so that the two fit in 256 TMEM columns and two CTAs
+// share an SM; BF16 takes 256.
+constexpr int kSyrkF32Cols = 128;
+int syrk_tile_cols(bool f32) { return f32 ? kSyrkF32Cols : 256; }
+
 struct F0Layout {
   int mpad, rpad, npad, mtiles, nchunk, ndots, tiles_lower;
+  int tw;          // columns of C = A A^T per tile (syrk_tile_cols)
   long long ldc;   // C's leading dimension (c_ld)
   size_t bytes;
   float* C;
@@ -948,10 +958,11 @@ F0Layout f0_layout(int m, int n, int src, void* scratch) {
   L.mtiles = (m + BM - 1) / BM;
   L.nchunk = syrk_chunks(m, n);
   L.ndots = dots_chunks(m);
-  L.tiles_lower = lower_tile_count(L.mtiles);
+  L.tw = syrk_tile_cols(is_f32(src));
+  L.tiles_lower = lower_tile_count(L.mtiles, L.tw);
   L.ldc = c_ld(m, 4);
   const size_t c = align_up((size_t)m * L.ldc * 4);
-  const size_t chunks = align_up((size_t)L.nchunk * L.tiles_lower * BM * 256 * 4);
+  const size_t chunks = align_up((size_t)L.nchunk * L.tiles_lower * BM * L.tw * 4);
   const size_t parts = align_up((size_t)L.mpad * kParts * L.rpad * 2);
   const size_t part = align_up((size_t)L.mtiles * L.ndots * n * 8);
   const size_t ap = align_up((size_t)L.mpad * a_parts(src) * L.npad * 2);
@@ -1014,24 +1025,30 @@ Params f0_params_syrk(const F0Layout& L, int m, int n, int src, int* err, unsign
   P.tri = 1;
   P.M = m;
   P.N = m;
-  P.n_half = 256;
+  P.n_half = L.tw;
   P.halves = 1;
-  P.n_tile = 256;
+  P.n_tile = L.tw;
   P.kb_total = (n + BK - 1) / BK;
   P.kb_per_cta = P.kb_total;
   P.kb_chunk = syrk_chunk_kb(m, n);
   P.tiles_lower = L.tiles_lower;
   P.nparts = 1;
   if (f32) {
-    // C = (A1 + A2)(A1 + A2)^T: one ring stage per (K block, pair)
+    // C = (A1 + A2 + A3)(A1 + A2 + A3)^T: one ring stage per (K block, pair)
     set_pairs(P);
+    P.acc2_col = L.tw;
     P.a_kpart = L.npad;
     P.b_kpart = L.npad;
   }
-  P.stage_bytes = BM * BK * 2 + 256 * BK * 2;
+  P.stage_bytes = BM * BK * 2 + L.tw * BK * 2;
   P.stages = fit_stages(P.stage_bytes, STAGES);
   if (kSyrk2Cta && !f32) {
     P.stages = 2;
+    P.tmem_cols = 256;
+  }
+  if (f32 && L.tw == 128) {
+    // two accumulators of 128 columns: 256 TMEM columns, three 32 KB stages
+    P.stages = 3;
     P.tmem_cols = 256;
   }
   P.out = L.chunk_tiles;
@@ -1160,7 +1177,7 @@ __global__ void group_reduce_kernel(const GroupProb* __restrict__ probs) {
   const int nb = (g.m + 31) / 32;
   for (int q = blockIdx.x; q < nb * nb; q += gridDim.x) {
     const int bi = q % nb, bj = q / nb;
-    if (bi >= bj) reduce_lower_block(g.chunk_tiles, g.nchunk, g.tiles_lower, g.m, g.ldc, g.C, bi, bj, tile);
+    if (bi >= bj) reduce_lower_block(g.chunk_tiles, g.nchunk, g.tiles_lower, g.tw, g.m, g.ldc, g.C, bi, bj, tile);
   }
 }
 
@@ -1238,18 +1255,18 @@ cudaError_t css_f0(const void* A, long long lda, int m, int n, void* scratch, do
       if ((e = cudaStreamWaitEvent(s, pipe->ready[z], 0)) != cudaSuccess) return e;
       Params Pz = P2;
       Pz.bz_off = z;
-      tc_kernel<true, true><<<dim3(L.mtiles, (m + 255) / 256, 1), kThreads, smem_for(P2.stage_bytes, P2.stages),
+      tc_kernel<true, true><<<dim3(L.mtiles, (m + L.tw - 1) / L.tw, 1), kThreads, smem_for(P2.stage_bytes, P2.stages),
                               s>>>(mA2, mA2, Pz);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
   } else {
-    tc_kernel<true, true><<<dim3(L.mtiles, (m + 255) / 256, L.nchunk), kThreads,
+    tc_kernel<true, true><<<dim3(L.mtiles, (m + L.tw - 1) / L.tw, L.nchunk), kThreads,
                             smem_for(P2.stage_bytes, P2.stages), s>>>(mA2, mA2, P2);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   // C = the chunks' sum, both triangles (the greedy iterations read whole rows)
   reduce_lower_kernel<<<dim3((m + 31) / 32, (m + 31) / 32), dim3(32, 8), 0, s>>>(L.chunk_tiles, L.nchunk,
-                                                                                 L.tiles_lower, m, L.ldc, L.C);
+                                                                                 L.tiles_lower, L.tw, m, L.ldc, L.C);
   // U' (upper triangle of C, diagonal halved) = U1 + U2 + U3 in BF16
   {
     const long long tot = (long long)L.mpad * L.rpad;
@@ -1316,6 +1333,7 @@ cudaError_t group_f0_prepare(int count, const void* const* A, const long long* l
     g.ndots = L.ndots;
     g.mtiles = L.mtiles;
     g.tiles_lower = L.tiles_lower;
+    g.tw = L.tw;
     g.C = L.C;
     g.ldc = L.ldc;
     g.chunk_tiles = L.chunk_tiles;
@@ -1327,7 +1345,7 @@ cudaError_t group_f0_prepare(int count, const void* const* A, const long long* l
     const Params& P2 = g.p2;
     for (int bz = 0; bz < L.nchunk; ++bz)
       for (int bx = 0; bx < L.mtiles; ++bx)
-        for (int by = 0; by <= bx / 2; ++by) {
+        for (int by = 0; by <= (L.tw == 256 ? bx / 2 : bx); ++by) {
           t2.push_back(GroupTile{i, bx, by, bz});
           c2.push_back((long long)std::min(P2.kb_chunk, P2.kb_total - bz * P2.kb_chunk) * std::max(1, P2.npairs));
         }

@@ -904,11 +904,12 @@ __global__ void reduce_lower_kernel(const float* __restrict__ parts, int chunks,
 // product err by about sqrt(m) units.  So C = A A^T is summed in chunks of
 // about 64 sqrt(m) products (4 to 64 K blocks of 64: 2 sqrt(m) units), at
 // most 32 chunks (very wide A gets longer ones), added with compensated
-// FP32 sums.  U' A likewise (one chunk for m <= 4096: at the 4096 x 65536
-// size shorter chunks cut the initial scores' error from 4.8 to 3.2 u
-// sqrt(m) but cost 2.8 ms).
+// FP32 sums.  U' A likewise, in chunks of 2048 (at 4096 x 65536: f0 within
+// 4.2 u sqrt(m) of the oracle's instead of 5.5 for 0.33 ms more, and the
+// selection then agrees with the oracle's at every iteration; chunks of
+// 1024: 3.5 u sqrt(m), 1.2 ms more).
 constexpr int kSyrkMaxChunks = 32;
-constexpr int kDotsChunkKb = 64;
+constexpr int kDotsChunkKb = 32;
 int syrk_chunk_kb(int m, int n) {
   const int kb = (n + BK - 1) / BK;
   int c = 4;

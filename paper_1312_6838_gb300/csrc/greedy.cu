@@ -202,6 +202,30 @@ __device__ void col_dots(const Ctx<Acc>& x, int len, int nj, const TM* M, long l
   }
 }
 
+// col_dots for an FP32 matrix whose columns start on 16-byte boundaries (ldm
+// a multiple of 4) and len a multiple of 4: one warp per column, four floats
+// per lane per load, eight loads in flight (the GCSS pivot's B^T e).
+template <typename Acc, typename Fin>
+__device__ void col_dots_f4(const Ctx<Acc>& x, int len, int nj, const float* M, long long ldm, const float* v,
+                            Fin fin) {
+  const int len4 = len / 4;
+  const float4* v4 = reinterpret_cast<const float4*>(v);
+  for (int j = x.rank * NW + x.warp; j < nj; j += x.ncta * NW) {
+    const float4* col = reinterpret_cast<const float4*>(M + (long long)j * ldm);
+    float acc = 0.f;
+#pragma unroll 8
+    for (int i = x.lane; i < len4; i += 32) {
+      const float4 a = ld_cg(col + i), b = v4[i];
+      acc = fmaf(a.x, b.x, acc);
+      acc = fmaf(a.y, b.y, acc);
+      acc = fmaf(a.z, b.z, acc);
+      acc = fmaf(a.w, b.w, acc);
+    }
+    acc = warp_sum(acc);
+    if (x.lane == 0) fin(j, (double)acc);
+  }
+}
+
 // ------------------------------------------------ double-float products ----
 // The Gram-Schmidt products of the BF16/FP32 path (Q^T a_p, Q c, Z^T e, Q d:
 // m x t multiply-adds each) run in double-float arithmetic: every FP64 value
@@ -882,7 +906,14 @@ __device__ void run_unit(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc&
       mark(9);
     } else {
       const Acc* B = reinterpret_cast<const Acc*>(u.T);
-      col_dots<Acc>(x, m, u.r, B, u.ldt, x.seacc, [&](int j, double v) { u.ups[j] = v; });
+      if constexpr (kDF) {
+        if (u.t_vec_ok && m % 4 == 0)
+          col_dots_f4(x, m, u.r, B, u.ldt, x.seacc, [&](int j, double v) { u.ups[j] = v; });
+        else
+          col_dots<Acc>(x, m, u.r, B, u.ldt, x.seacc, [&](int j, double v) { u.ups[j] = v; });
+      } else {
+        col_dots<Acc>(x, m, u.r, B, u.ldt, x.seacc, [&](int j, double v) { u.ups[j] = v; });
+      }
       if (!team_barrier(tm.bar, x.ncta, x.st, 5, x.epoch)) return;
       for (int j = x.tid; j < u.r; j += NT) {
         const double v = ld_cg(u.ups + j);

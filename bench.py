@@ -334,11 +334,11 @@ def run_distributed(args):
         "initial_scores_ms": init_ms,
         "block_phase_ms": block_ms,
         # traffic: DRAM bytes read + written by the blocks' launch, from an
-        # ncu capture on the 2048 x 65536 case (16 blocks): 26.927 GB for
+        # ncu capture on the 2048 x 65536 case (16 blocks): 26.946 GB for
         # 27.427 GB algorithmic, scaled by this launch's algorithmic bytes
         "roofline": {"bound": "hbm", "achieved": block_gbs, "peak": hbm_peak, "unit": "GB/s",
                      "frac": block_gbs / hbm_peak,
-                     "traffic": block_bytes * (26.893364480e9 + 0.033207552e9) / 27.426553856e9,
+                     "traffic": block_bytes * (26.913610240e9 + 0.032265984e9) / 27.426553856e9,
                      "peak_kind": hbm_kind,
                      "kernel": "greedy_kernel (the 64 blocks' persistent launch, Algorithm 4's map phase)",
                      "bytes_per_launch": block_bytes,
@@ -458,11 +458,11 @@ def run_batched(args):
                              "selection's error, both on the values the device holds (FP64, "
                              "reconstruction_error)"},
         # DRAM traffic per launch: the ncu capture of the BF16 launch of the
-        # 128-problem case of the same model read and wrote 1.063 x its
+        # 128-problem case of the same model read and wrote 1.064 x its
         # algorithmic bytes (each C = A A^T comes from DRAM every iteration,
         # as counted), scaled by the bytes of this launch
         "roofline": {"bound": "hbm", "achieved": batch_gbs, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": batch_gbs / hbm_peak, "traffic": 1.063 * batch_bytes, "peak_kind": hbm_kind,
+                     "frac": batch_gbs / hbm_peak, "traffic": 1.064 * batch_bytes, "peak_kind": hbm_kind,
                      "kernel": f"greedy_kernel (all {len(specs)} problems in one persistent launch, BF16)",
                      "bytes_per_launch": batch_bytes,
                      "bytes": "per problem: (k + 1) passes over A in BF16, C = A A^T (FP32) read "
@@ -780,12 +780,12 @@ def main():
     per_iter = a_bytes + c_bytes + 48 * n
     achieved = per_iter * res.n_sel / (statistics.mean(loop_ms) / 1e3) / 1e9
     # DRAM traffic per launch from an ncu capture of the greedy kernel on the
-    # 4096 x 32768 case of the same model (17 A passes): reads 1.0159 x the
-    # bytes of A and writes 56 B per column per A pass (C stays in L2),
+    # 4096 x 32768 case of the same model (17 A passes): reads 1.0153 x the
+    # bytes of A and writes 57 B per column per A pass (C stays in L2),
     # scaled by the A passes of this launch
     traffic = None
     if args.workload in (WORKLOAD, "decay_4096x32768") and args.dtype == "bf16":
-        traffic = (res.n_sel + 1) * (a_bytes * 1.0159 + 56.0 * n)
+        traffic = (res.n_sel + 1) * (a_bytes * 1.0153 + 57.3 * n)
     peak, peak_kind = peaks()
     out = {
         "metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": ws,

@@ -22,6 +22,7 @@ import ctypes as C
 from dataclasses import dataclass
 from typing import Optional, Sequence
 
+import numpy as np
 import torch
 
 from . import _lib as L
@@ -462,45 +463,80 @@ def select_randomized(A: torch.Tensor, l: int, seed: int, dist="gaussian", *, ta
     return Selection(sel, trace, int(nsel.item()), code)
 
 
+# css_problem as a numpy record (same field offsets), so that a batch's
+# descriptors are filled by array operations rather than field by field
+_PROBLEM = np.dtype({"names": [f for f, _ in L.css_problem._fields_],
+                     "formats": ["<u8", "<i8", "<i8", "<i8", "<i4", "<i4", "<u8", "<u8", "<u8", "<u8"],
+                     "offsets": [getattr(L.css_problem, f).offset for f, _ in L.css_problem._fields_],
+                     "itemsize": C.sizeof(L.css_problem)})
+
+
+class _Batch:
+    """The css_problem descriptors of a batch and its outputs: one tensor each
+    for every problem's indices, traces and counts (problem i's are views)."""
+
+    def __init__(self, As: Sequence[torch.Tensor], ks: Sequence[int]):
+        if len(As) != len(ks) or not As:
+            raise ValueError("need one k per matrix")
+        self.dtype = As[0].dtype
+        self.device = As[0].device
+        count = len(As)
+        shape = np.empty((count, 3), dtype=np.int64)
+        ptr = np.empty(count, dtype=np.uint64)
+        for i, A in enumerate(As):
+            if A.dtype != self.dtype:
+                raise TypeError("all matrices must share one dtype")
+            shape[i] = _colmajor(A)
+            ptr[i] = A.data_ptr()
+        k = np.asarray([int(v) for v in ks], dtype=np.int64)
+        if (k < 1).any() or (k > np.iinfo(np.int32).max).any():
+            raise ValueError("every k must be a positive int32")
+        self.sel_off = np.concatenate(([0], np.cumsum(k)))
+        self.trace_off = np.concatenate(([0], np.cumsum(k + 1)))
+        self.sel = torch.empty(int(self.sel_off[-1]), dtype=torch.int32, device=self.device)
+        self.trace = torch.empty(int(self.trace_off[-1]), dtype=torch.float64, device=self.device)
+        self.n_sel = torch.zeros(count, dtype=torch.int32, device=self.device)
+        rec = np.zeros(count, dtype=_PROBLEM)
+        rec["A"] = ptr
+        rec["m"], rec["n"], rec["lda"] = shape[:, 0], shape[:, 1], shape[:, 2]
+        rec["k"] = k
+        rec["sel"] = np.uint64(self.sel.data_ptr()) + 4 * self.sel_off[:-1].astype(np.uint64)
+        rec["trace"] = np.uint64(self.trace.data_ptr()) + 8 * self.trace_off[:-1].astype(np.uint64)
+        rec["n_sel"] = np.uint64(self.n_sel.data_ptr()) + 4 * np.arange(count, dtype=np.uint64)
+        self.rec = rec
+        self.count = count
+
+    def probs(self):
+        return self.rec.ctypes.data_as(C.POINTER(L.css_problem))
+
+    def results(self, code=0):
+        ns = self.n_sel.tolist()
+        so, to = self.sel_off.tolist(), self.trace_off.tolist()
+        return [Selection(self.sel[so[i]:so[i + 1]], self.trace[to[i]:to[i + 1]], int(ns[i]), code)
+                for i in range(self.count)]
+
+
 def select_batched(As: Sequence[torch.Tensor], ks: Sequence[int], *, grid_ctas=0, tile_cols=0,
                    tau_rel=None, stream=None, timing=None, init_path=0):
     """Independent greedy CSS problems in one persistent launch.  Returns a list
     of Selection.  ``init_path=1`` keeps the initial scores on the SIMT
     kernels (css_opts.init_path)."""
-    if len(As) != len(ks) or not As:
-        raise ValueError("need one k per matrix")
-    dtype = As[0].dtype
-    dev = As[0].device
-    dt = _DT[dtype]
+    b = _Batch(As, ks)
+    dt = _DT[b.dtype]
     lib = L.load()
-    probs = (L.css_problem * len(As))()
-    outs = []
-    for i, (A, k) in enumerate(zip(As, ks)):
-        if A.dtype != dtype:
-            raise TypeError("all matrices must share one dtype")
-        m, n, lda = _colmajor(A)
-        sel = torch.empty(k, dtype=torch.int32, device=dev)
-        trace = torch.empty(k + 1, dtype=torch.float64, device=dev)
-        nsel = torch.zeros(1, dtype=torch.int32, device=dev)
-        probs[i].A = A.data_ptr()
-        probs[i].m, probs[i].n, probs[i].lda, probs[i].k = m, n, lda, int(k)
-        probs[i].sel, probs[i].trace, probs[i].n_sel = sel.data_ptr(), trace.data_ptr(), nsel.data_ptr()
-        probs[i].W = None
-        outs.append((sel, trace, nsel))
     o = _opts(tau_rel, None, 0, grid_ctas, tile_cols, init_path=init_path)
     tms = (C.c_double * 2)() if timing is not None else None
     if tms is not None:
         o.timing_ms = C.cast(tms, C.c_void_p)
-    nbytes = lib.css_batched_workspace_size(probs, len(As), dt, C.byref(o))
+    nbytes = lib.css_batched_workspace_size(b.probs(), b.count, dt, C.byref(o))
     if nbytes == 0:
         raise ValueError("invalid batch")
-    _keep, ws = _workspace(nbytes, dev)
-    code = lib.css_select_batched(probs, len(As), dt, _ptr(ws), nbytes, C.byref(o), _stream(stream))
+    _keep, ws = _workspace(nbytes, b.device)
+    code = lib.css_select_batched(b.probs(), b.count, dt, _ptr(ws), nbytes, C.byref(o), _stream(stream))
     _check(code, "css_select_batched")
     if tms is not None:
         timing.extend([tms[0], tms[1]])
-    nsels = torch.cat([x[2] for x in outs]).tolist()
-    return [Selection(s, t, int(ns), code) for (s, t, _), ns in zip(outs, nsels)]
+    return b.results(code)
 
 
 class BatchedPlan:
@@ -511,34 +547,18 @@ class BatchedPlan:
 
     def __init__(self, As: Sequence[torch.Tensor], ks: Sequence[int], *, grid_ctas=0,
                  tile_cols=0, tau_rel=None, stream=None, init_path=0):
-        if len(As) != len(ks) or not As:
-            raise ValueError("need one k per matrix")
-        dtype = As[0].dtype
-        dev = As[0].device
-        dt = _DT[dtype]
+        b = _Batch(As, ks)
+        dt = _DT[b.dtype]
         self._lib = L.load()
-        probs = (L.css_problem * len(As))()
-        self._outs = []
-        for i, (A, k) in enumerate(zip(As, ks)):
-            if A.dtype != dtype:
-                raise TypeError("all matrices must share one dtype")
-            m, n, lda = _colmajor(A)
-            sel = torch.empty(k, dtype=torch.int32, device=dev)
-            trace = torch.empty(k + 1, dtype=torch.float64, device=dev)
-            nsel = torch.zeros(1, dtype=torch.int32, device=dev)
-            probs[i].A = A.data_ptr()
-            probs[i].m, probs[i].n, probs[i].lda, probs[i].k = m, n, lda, int(k)
-            probs[i].sel, probs[i].trace, probs[i].n_sel = sel.data_ptr(), trace.data_ptr(), nsel.data_ptr()
-            probs[i].W = None
-            self._outs.append((sel, trace, nsel))
+        self._batch = b
         self._As = list(As)
         o = _opts(tau_rel, None, 0, grid_ctas, tile_cols, init_path=init_path)
-        nbytes = self._lib.css_batched_workspace_size(probs, len(As), dt, C.byref(o))
+        nbytes = self._lib.css_batched_workspace_size(b.probs(), b.count, dt, C.byref(o))
         if nbytes == 0:
             raise ValueError("invalid batch")
-        self._keep, self._ws = _workspace(nbytes, dev)
+        self._keep, self._ws = _workspace(nbytes, b.device)
         self._plan = L.css_batched_plan()
-        code = self._lib.css_select_batched_prepare(probs, len(As), dt, _ptr(self._ws), nbytes,
+        code = self._lib.css_select_batched_prepare(b.probs(), b.count, dt, _ptr(self._ws), nbytes,
                                                     C.byref(o), C.byref(self._plan), _stream(stream))
         _check(code, "css_select_batched_prepare")
 
@@ -552,8 +572,7 @@ class BatchedPlan:
         return self._lib.css_read_status(_ptr(self._ws), _stream(stream))
 
     def results(self):
-        nsels = torch.cat([x[2] for x in self._outs]).tolist()
-        return [Selection(s, t, int(ns), 0) for (s, t, _), ns in zip(self._outs, nsels)]
+        return self._batch.results()
 
 
 def autotune_distributed(A: torch.Tensor, B: torch.Tensor, block_offsets: Sequence[int], l_block: int,

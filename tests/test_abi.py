@@ -157,3 +157,37 @@ def test_embed_and_lowrank_host_checks(lib):
     r = lib.css_lowrank(fake, 20, P(0), 0, 0, 20, 4, 2, fake, P(0), 1, P(0), 20, P(0), P(0), fake, 64,
                         C.byref(o), P(0))
     assert r == L.CSS_ERR_WORKSPACE
+
+
+def test_batch_descriptors_match_the_struct(lib):
+    """css.select_batched fills css_problem[count] as a numpy record array:
+    every field must land where the C struct has it (read back through
+    ctypes), the outputs of problem i are views at the running offsets, and
+    the host-only workspace query sees the same batch as a field-by-field
+    fill."""
+    import torch
+    from paper_1312_6838_gb300 import _lib as L, css
+    As = [torch.empty((7, 5)).t(), torch.empty((40, 33)).t()[:30], torch.empty((9, 4)).t()]
+    ks = [2, 3, 4]
+    b = css._Batch(As, ks)
+    arr = (L.css_problem * len(As)).from_address(b.rec.ctypes.data)
+    ref = (L.css_problem * len(As))()
+    for i, (A, k) in enumerate(zip(As, ks)):
+        p = arr[i]
+        m, n, lda = css._colmajor(A)
+        assert (p.A, p.m, p.n, p.lda, p.k) == (A.data_ptr(), m, n, lda, k)
+        assert p.sel == b.sel.data_ptr() + 4 * sum(ks[:i])
+        assert p.trace == b.trace.data_ptr() + 8 * sum(v + 1 for v in ks[:i])
+        assert p.n_sel == b.n_sel.data_ptr() + 4 * i and not p.W
+        ref[i].A, ref[i].m, ref[i].n, ref[i].lda, ref[i].k = A.data_ptr(), m, n, lda, k
+        ref[i].sel, ref[i].trace, ref[i].n_sel = p.sel, p.trace, p.n_sel
+    o = L.default_opts()
+    for dt in (L.CSS_F32, L.CSS_BF16, L.CSS_F64):
+        got = lib.css_batched_workspace_size(b.probs(), len(As), dt, C.byref(o))
+        assert got > 0 and got == lib.css_batched_workspace_size(ref, len(As), dt, C.byref(o))
+    res = b.results()
+    assert [tuple(r.sel.shape) + tuple(r.trace.shape) for r in res] == [(2, 3), (3, 4), (4, 5)]
+    with pytest.raises(ValueError):
+        css._Batch(As, [2, 0, 4])
+    with pytest.raises(TypeError):
+        css._Batch([As[0], As[1].double()], [2, 3])

@@ -167,7 +167,7 @@ typedef struct {
        last tiles of each step for 1 / split_share of the team's warps (1,
        2, 4 or 8; default 2).  pivot_cost: gcss_distributed's planner
        charges each block iteration's pivot as this many streamed columns
-       when it sizes the blocks' teams (default 700). */
+       when it sizes the blocks' teams (default 1500). */
     int32_t split_share;
     int32_t pivot_cost;
     int32_t reserved[4];
@@ -494,8 +494,8 @@ css_status css_tile_cache_load(const char* path);
  *   css_autotune_select (above) also times split shares 1, 2 and 4 at the
  *       fastest width and records the fastest share.
  *   css_autotune_distributed  runs gcss_distributed on the caller's problem
- *       (arguments as gcss_distributed) with pivot costs 0, 300, 700 and
- *       1500 columns, each once untimed and once timed (the blocks'
+ *       (arguments as gcss_distributed) with pivot costs 300, 700, 1500
+ *       and 3000 columns, each once untimed and once timed (the blocks'
  *       launch), records the fastest for the device, dtype and (m, n)
  *       bucket and returns it in *best_cost (HOST int32); times_ms is a HOST
  *       double[4] or NULL.  Synchronises `stream`.

@@ -23,7 +23,7 @@ namespace {
 constexpr int kMaxK = 1024;          // columns selected per problem
 constexpr int kMaxCtas = 1024;       // descriptor space reserved per call
 constexpr uint64_t kDefaultSpinNs = 2000000000ull;
-constexpr double kPivotColumnEquiv = 700.0;  // planner default: one pivot step in streamed columns
+constexpr double kPivotColumnEquiv = 1500.0;  // planner default: one pivot step in streamed columns
 constexpr int kDefaultSplitShare = 2;        // fused step: split tail tiles for half of the warps
 
 size_t esize(int dt) { return dt == CSS_F64 ? 8 : dt == CSS_F32 ? 4 : 2; }
@@ -241,16 +241,17 @@ struct LaunchInfo {
 
 css_status prepare_units(const Header& h, std::vector<UnitDesc>& units, const std::vector<double>& work,
                          int dt, int grid_max, int tile_cols, uint64_t spin_ns, cudaStream_t s,
-                         LaunchInfo& info, int stall_where = 0, int split_share = kDefaultSplitShare) {
+                         LaunchInfo& info, int stall_where = 0, int split_share = kDefaultSplitShare,
+                         int threads = kGreedyThreads) {
   int m_max = 1, k_max = 1, r_max = 1;
   for (auto& u : units) {
     m_max = std::max(m_max, u.m);
     k_max = std::max(k_max, u.k);
     r_max = std::max(r_max, u.r);
   }
-  const size_t smem = greedy_smem_bytes(dt, m_max, k_max, r_max);
+  const size_t smem = greedy_smem_bytes(dt, m_max, k_max, r_max, threads);
   if (smem > 227 * 1024) return CSS_ERR_UNSUPPORTED;
-  const int occ = greedy_occupancy(dt, tile_cols, smem);
+  const int occ = greedy_occupancy(dt, tile_cols, smem, threads);
   const int sms = sm_count();
   if (occ <= 0 || sms <= 0) return CSS_ERR_CUDA;
   int grid = std::min(grid_max > 0 ? grid_max : sms * occ, sms * occ);
@@ -268,7 +269,7 @@ css_status prepare_units(const Header& h, std::vector<UnitDesc>& units, const st
     int widest = 0;
     for (int q = d.u_begin; q < d.u_end; ++q)
       widest = std::max(widest, (units[P.order[q]].n + tile_cols - 1) / tile_cols);
-    const int cap = std::min({widest, d.ncta * (kGreedyThreads / 32) / std::max(1, split_share),
+    const int cap = std::min({widest, d.ncta * (threads / 32) / std::max(1, split_share),
                               h.split_slots - split_used});
     d.split_cap = std::max(cap, 0);
     d.split_part = static_cast<char*>(h.split_part) + (size_t)split_used * kSplitSlotBytes;
@@ -296,7 +297,7 @@ css_status prepare_units(const Header& h, std::vector<UnitDesc>& units, const st
   L.k_max = k_max;
   L.r_max = r_max;
   L.grid = P.grid;
-  L.threads = kGreedyThreads;
+  L.threads = threads;
   L.smem = smem;
   info.L = L;
   info.split_used = split_used;
@@ -1099,14 +1100,20 @@ css_status dist_prepare(const void* A, css_dtype dtype, int64_t m, int64_t n, in
                               L.bnsel + b, ob));
     // a block's cost: kb iterations, each a streaming pass over its w columns
     // plus the pivot, whose latency-bound cost is charged as a fixed number
-    // of column-equivalents (default 700, swept on the 2048 x 262144
-    // workload; css_autotune_distributed tunes it)
+    // of column-equivalents (default 1500, swept on the 2048 x 262144
+    // workload with the blocks in the two-CTAs-per-SM shape: 100 / 300 / 700
+    // / 1500 / 3000 gave the blocks' launch 34.8 / 27.8 / 26.6 / 24.8 / 27.9
+    // ms; css_autotune_distributed tunes it)
     work.push_back((double)kb * ((double)w + pivot_cost));
   }
   const int tile = pick_tile(o, dtype, m, n);
   P = DistPlanImpl{};
+  // the blocks run in the kernel's two-CTAs-per-SM shape: each block's team
+  // of a few CTAs gets twice as many (measured on 2048 x 262144 BF16, 64
+  // blocks: the blocks' launch 27.9 -> 26.3 ms; the single-problem and
+  // batched launches are faster in the one-CTA shape)
   css_status cs = prepare_units(L.h, units, work, dtype, o.grid_ctas, tile, o.spin_budget_ns, s, P.blocks, 0,
-                                share);
+                                share, kGreedyThreadsPaired);
   if (cs != CSS_OK) return cs;
   // reduce phase: the union unit is planned for its largest size; the union
   // scan writes its actual column count into the descriptor on the device

@@ -20,12 +20,23 @@
 //             f_i <- f_i - 2 omega_i h_i + s omega_i^2, g_i <- g_i - omega_i^2,
 //             W[t, i] = omega_i, then the masked argmax of f_i / g_i.
 //   trace     F <- F - f_p / g_p (Theorems 1 and 3).
+//
+// Two CTA shapes are built from this file: 512 threads with one CTA per SM
+// (this translation unit, the defaults below) and 256 threads with two CTAs
+// per SM (greedy_pair.cu), both with the same 128 registers per thread.
 #include "greedy.cuh"
+
+#ifndef CSS_GREEDY_NT
+#define CSS_GREEDY_NT 512           // threads per CTA
+#define CSS_GREEDY_CTAS_PER_SM 1    // co-resident CTAs the registers are budgeted for
+#define CSS_GREEDY_SHAPE one_per_sm // namespace of this shape's host entry points
+#define CSS_GREEDY_EXPORT_BASIS 1   // export_basis is built once, here
+#endif
 
 namespace css {
 namespace {
 
-constexpr int NT = kGreedyThreads;
+constexpr int NT = CSS_GREEDY_NT;
 constexpr int NW = NT / 32;
 constexpr int NS = 2 * NW;  // half-warp streams of the row GEMVs
 constexpr int RB = 16;      // rows per row tile
@@ -1024,7 +1035,7 @@ __device__ void run_unit(const Ctx<typename AccOf<TA>::type>& x, const UnitDesc&
 }
 
 template <typename TA, int CW>
-__global__ void __launch_bounds__(NT, 1) greedy_kernel(GreedyLaunch L) {
+__global__ void __launch_bounds__(NT, CSS_GREEDY_CTAS_PER_SM) greedy_kernel(GreedyLaunch L) {
   using Acc = typename AccOf<TA>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   const int team_id = L.cta_team[blockIdx.x];
@@ -1081,6 +1092,8 @@ void* pick_kernel(int dtype, int cw) {
 
 }  // namespace
 
+namespace CSS_GREEDY_SHAPE {
+
 size_t greedy_smem_bytes(int dtype, int m_max, int k_max, int r_max) {
   const size_t sa = (dtype == CSS_F64) ? 8 : 4;
   const size_t mp = ((size_t)m_max + 3) & ~(size_t)3;
@@ -1111,8 +1124,13 @@ cudaError_t greedy_launch(const GreedyLaunch& L, cudaStream_t stream) {
   }
   GreedyLaunch arg = L;
   void* args[] = {&arg};
+  if (L.threads != NT) return cudaErrorInvalidConfiguration;
   return cudaLaunchCooperativeKernel(k, dim3(L.grid), dim3(NT), args, L.smem, stream);
 }
+
+}  // namespace CSS_GREEDY_SHAPE
+
+#ifdef CSS_GREEDY_EXPORT_BASIS
 
 // Q (FP64, or double-float pairs for FP32/BF16 input) to a caller buffer as
 // FP64; columns at or beyond the number selected become zero.
@@ -1140,5 +1158,7 @@ cudaError_t export_basis(int dtype, const double* Q, int m, int k, const int* n_
                                                                            out);
   return cudaGetLastError();
 }
+
+#endif  // CSS_GREEDY_EXPORT_BASIS
 
 }  // namespace css

@@ -82,14 +82,38 @@ struct GreedyLaunch {
   size_t smem;
 };
 
+// The kernel's two CTA shapes, both with 128 registers per thread: 512
+// threads and one CTA per SM (the default), or 256 threads and two CTAs per
+// SM, where teams of small problems gain from twice as many CTAs (Algorithm
+// 4's column blocks).
 constexpr int kGreedyThreads = 512;
+constexpr int kGreedyThreadsPaired = 256;
 
-// Bytes of dynamic shared memory the kernel needs.
-size_t greedy_smem_bytes(int dtype, int m_max, int k_max, int r_max);
-// Max co-resident CTAs per SM for the given configuration (0 on error).
-int greedy_occupancy(int dtype, int tile_cols, size_t smem);
-// Enqueue the persistent kernel (cooperative launch).  Returns a cudaError_t.
-cudaError_t greedy_launch(const GreedyLaunch& L, cudaStream_t stream);
+#define CSS_GREEDY_SHAPE_API                                                     \
+  /* Bytes of dynamic shared memory the kernel needs. */                        \
+  size_t greedy_smem_bytes(int dtype, int m_max, int k_max, int r_max);         \
+  /* Max co-resident CTAs per SM for the given configuration (0 on error). */   \
+  int greedy_occupancy(int dtype, int tile_cols, size_t smem);                  \
+  /* Enqueue the persistent kernel (cooperative launch). */                     \
+  cudaError_t greedy_launch(const GreedyLaunch& L, cudaStream_t stream);
+namespace one_per_sm { CSS_GREEDY_SHAPE_API }
+namespace two_per_sm { CSS_GREEDY_SHAPE_API }
+#undef CSS_GREEDY_SHAPE_API
+
+// The same three calls for the shape with `threads` threads per CTA
+// (kGreedyThreads or kGreedyThreadsPaired; GreedyLaunch::threads for the launch).
+inline size_t greedy_smem_bytes(int dtype, int m_max, int k_max, int r_max, int threads) {
+  return threads == kGreedyThreadsPaired ? two_per_sm::greedy_smem_bytes(dtype, m_max, k_max, r_max)
+                                         : one_per_sm::greedy_smem_bytes(dtype, m_max, k_max, r_max);
+}
+inline int greedy_occupancy(int dtype, int tile_cols, size_t smem, int threads) {
+  return threads == kGreedyThreadsPaired ? two_per_sm::greedy_occupancy(dtype, tile_cols, smem)
+                                         : one_per_sm::greedy_occupancy(dtype, tile_cols, smem);
+}
+inline cudaError_t greedy_launch(const GreedyLaunch& L, cudaStream_t stream) {
+  return L.threads == kGreedyThreadsPaired ? two_per_sm::greedy_launch(L, stream)
+                                           : one_per_sm::greedy_launch(L, stream);
+}
 // Copies the basis Q of one unit (m x k, FP64 or double-float pairs) to `out`
 // as FP64, zeroing columns t >= *n_sel (opts->basis).
 cudaError_t export_basis(int dtype, const double* Q, int m, int k, const int* n_sel, double* out,

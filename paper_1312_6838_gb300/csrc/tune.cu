@@ -251,15 +251,13 @@ css_status css_autotune_distributed(const void* A, css_dtype dtype, int64_t m, i
                                     int32_t* n_sel, void* ws, size_t ws_bytes, int32_t* best_cost,
                                     double* times_ms, css_stream_t stream) {
   if (!best_cost) return CSS_ERR_INVALID_ARG;
-  static const int kCosts[4] = {0, 300, 700, 1500};
+  static const int kCosts[4] = {300, 700, 1500, 3000};
   double best = 0.0;
   int best_c = -1;
   for (int q = 0; q < 4; ++q) {
     css_opts o;
     css_opts_default(&o);
-    // opts.pivot_cost = 0 selects the tuned or default value, so the sweep's
-    // 0 is passed as 1 column (the same plan to within one column-equivalent)
-    o.pivot_cost = kCosts[q] > 0 ? kCosts[q] : 1;
+    o.pivot_cost = kCosts[q];
     double tms[2] = {0.0, 0.0};
     o.timing_ms = tms;
     for (int rep = 0; rep < 2; ++rep) {

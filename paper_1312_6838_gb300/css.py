@@ -577,7 +577,7 @@ class BatchedPlan:
 
 def autotune_distributed(A: torch.Tensor, B: torch.Tensor, block_offsets: Sequence[int], l_block: int,
                          k: int, *, stream=None):
-    """Time Algorithm 4's planner pivot costs (0, 300, 700, 1500 columns) on
+    """Time Algorithm 4's planner pivot costs (300, 700, 1500, 3000 columns) on
     this problem and record the fastest for this device and shape bucket
     (css_autotune_distributed).  Returns (best cost, {cost: block-launch ms})."""
     m, n, lda = _colmajor(A)
@@ -598,7 +598,7 @@ def autotune_distributed(A: torch.Tensor, B: torch.Tensor, block_offsets: Sequen
                                         _ptr(sel), _ptr(trace), _ptr(nsel), _ptr(ws), nbytes, C.byref(best),
                                         C.cast(times, C.c_void_p), _stream(stream))
     _check(code, "css_autotune_distributed")
-    return best.value, {c: times[i] for i, c in enumerate((0, 300, 700, 1500))}
+    return best.value, {c: times[i] for i, c in enumerate((300, 700, 1500, 3000))}
 
 
 def autotune(A: torch.Tensor, k: int, *, stream=None):

@@ -147,7 +147,7 @@ def test_autotune_records_split_share_and_pivot_cost(lib):
     B = css.to_colmajor(torch.from_numpy(A_np @ ci.gaussian_omega(12000, 32, 36, dtype=np.float64)).float().cuda())
     offs = ci.lognormal_blocks(12000, 8, 1500, 0.8, 37).tolist()
     best, times = css.autotune_distributed(A2, B, offs, 20, 20)
-    assert best in (0, 300, 700, 1500)
+    assert best in (300, 700, 1500, 3000)
     assert times[best] == min(times.values())
     assert lib.css_tune_lookup(name, L.CSS_BF16, 256, 12000, L.CSS_KNOB_PIVOT_COST) == best
     # the recorded cost is what the next call without a cost uses; results stay valid

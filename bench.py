@@ -334,11 +334,12 @@ def run_distributed(args):
         "initial_scores_ms": init_ms,
         "block_phase_ms": block_ms,
         # traffic: DRAM bytes read + written by the blocks' launch, from an
-        # ncu capture on the 2048 x 65536 case (16 blocks): 26.946 GB for
-        # 27.427 GB algorithmic, scaled by this launch's algorithmic bytes
+        # ncu capture on the 2048 x 65536 case (16 blocks, the kernel's
+        # two-CTAs-per-SM shape): 26.984 GB for 27.427 GB algorithmic, scaled
+        # by this launch's algorithmic bytes
         "roofline": {"bound": "hbm", "achieved": block_gbs, "peak": hbm_peak, "unit": "GB/s",
                      "frac": block_gbs / hbm_peak,
-                     "traffic": block_bytes * (26.913610240e9 + 0.032265984e9) / 27.426553856e9,
+                     "traffic": block_bytes * (26.947826176e9 + 0.036115200e9) / 27.426553856e9,
                      "peak_kind": hbm_kind,
                      "kernel": "greedy_kernel (the 64 blocks' persistent launch, Algorithm 4's map phase)",
                      "bytes_per_launch": block_bytes,

@@ -126,7 +126,9 @@ typedef struct {
        0 selects the default (2 s). */
     uint64_t spin_budget_ns;
     /* Number of CTAs of the persistent greedy kernel (0 = all SMs times the
-       occupancy).  Tuning knob. */
+       occupancy).  Tuning knob.  gcss_distributed's blocks' launch counts
+       CTAs of 256 threads (two per SM); every other launch, and its union
+       launch, CTAs of 512 threads (one per SM). */
     int32_t grid_ctas;
     /* Columns per warp tile of the fused step: 2, 4 or 8 (0 = default, 8).
        The last tiles of each step are further cut into row chunks. */

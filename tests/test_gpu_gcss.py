@@ -86,7 +86,7 @@ def test_gcss_fp64_trace_and_W(css):
     np.testing.assert_allclose(res.W.cpu().numpy(), ref.W, rtol=1e-8, atol=1e-9 * np.abs(ref.W).max())
 
 
-@pytest.mark.parametrize("dtype", [torch.float64, torch.bfloat16])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32, torch.bfloat16])
 def test_distributed_parity(css, dtype):
     m, n, r = 48, 900, 10
     A_np = ci.lowrank_uv(m, n, 12, 0.05, 31)

@@ -481,13 +481,21 @@ class _Batch:
         self.dtype = As[0].dtype
         self.device = As[0].device
         count = len(As)
-        shape = np.empty((count, 3), dtype=np.int64)
-        ptr = np.empty(count, dtype=np.uint64)
-        for i, A in enumerate(As):
+        _colmajor(As[0])   # the dtype and layout checks' messages
+        rows = []
+        for A in As:
             if A.dtype != self.dtype:
                 raise TypeError("all matrices must share one dtype")
-            shape[i] = _colmajor(A)
-            ptr[i] = A.data_ptr()
+            if A.dim() != 2:
+                raise ValueError("A must be 2-D")
+            m, n = A.shape
+            s0, s1 = A.stride()
+            if m > 1 and s0 != 1:
+                raise ValueError("A must be column-major (stride(0) == 1)")
+            rows.append((m, n, max(s1 if n > 1 else m, m), A.data_ptr()))
+        tab = np.array(rows, dtype=np.uint64).reshape(count, 4)
+        shape = tab[:, :3].astype(np.int64)
+        ptr = tab[:, 3]
         k = np.asarray([int(v) for v in ks], dtype=np.int64)
         if (k < 1).any() or (k > np.iinfo(np.int32).max).any():
             raise ValueError("every k must be a positive int32")
@@ -505,15 +513,16 @@ class _Batch:
         rec["n_sel"] = np.uint64(self.n_sel.data_ptr()) + 4 * np.arange(count, dtype=np.uint64)
         self.rec = rec
         self.count = count
+        self.k = k.tolist()
 
     def probs(self):
         return self.rec.ctypes.data_as(C.POINTER(L.css_problem))
 
     def results(self, code=0):
         ns = self.n_sel.tolist()
-        so, to = self.sel_off.tolist(), self.trace_off.tolist()
-        return [Selection(self.sel[so[i]:so[i + 1]], self.trace[to[i]:to[i + 1]], int(ns[i]), code)
-                for i in range(self.count)]
+        sels = self.sel.split(self.k)
+        traces = self.trace.split([v + 1 for v in self.k])
+        return [Selection(s, t, v, code) for s, t, v in zip(sels, traces, ns)]
 
 
 def select_batched(As: Sequence[torch.Tensor], ks: Sequence[int], *, grid_ctas=0, tile_cols=0,

@@ -191,3 +191,41 @@ def test_batch_descriptors_match_the_struct(lib):
         css._Batch(As, [2, 0, 4])
     with pytest.raises(TypeError):
         css._Batch([As[0], As[1].double()], [2, 3])
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of css_opts, css_problem and the two plan structs
+    (paper_1312_6838_gb300/_lib.py) against include/css.h as a C compiler
+    lays it out: every field's offset and size, and each struct's size."""
+    import shutil
+    import subprocess
+    from paper_1312_6838_gb300 import _lib as L
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [L.css_opts, L.css_problem, L.css_batched_plan, L.css_distributed_plan]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "css.h"', "int main(void) {"]
+    for S in structs:
+        name = S.__name__
+        lines.append(f'  printf("{name} . %zu %zu\\n", (size_t)0, sizeof({name}));')
+        for f, _ in S._fields_:
+            lines.append(f'  printf("{name} {f} %zu %zu\\n", offsetof({name}, {f}), '
+                         f'sizeof((({name}*)0)->{f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    seen = 0
+    for line in filter(None, out):
+        name, field, off, size = line.split()
+        S = getattr(L, name)
+        if field == ".":
+            assert C.sizeof(S) == int(size), (name, C.sizeof(S), size)
+        else:
+            d = getattr(S, field)
+            assert (d.offset, d.size) == (int(off), int(size)), (name, field, d.offset, d.size, off, size)
+        seen += 1
+    assert seen == sum(len(S._fields_) + 1 for S in structs)

@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import os
+import re
 import shutil
 import subprocess
 import sys
@@ -35,6 +36,14 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
+def included_sources(src):
+    """The .cu files that `src` includes (a translation unit built from
+    another one's source, e.g. a second shape of the same kernel)."""
+    with open(src) as fh:
+        names = re.findall(r'^\s*#\s*include\s+"([^"]+\.cu)"', fh.read(), flags=re.M)
+    return [os.path.join(os.path.dirname(src), n) for n in names]
+
+
 def _stale(obj, src, deps):
     if not os.path.exists(obj):
         return True
@@ -52,7 +61,7 @@ def build(verbose=False, force=False, extra_flags=()):
     for src in sources():
         obj = os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
-        if force or _stale(obj, src, headers):
+        if force or _stale(obj, src, headers + included_sources(src)):
             jobs.append((src, obj))
 
     def compile_one(job):

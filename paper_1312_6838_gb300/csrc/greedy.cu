@@ -1117,6 +1117,8 @@ int greedy_occupancy(int dtype, int tile_cols, size_t smem) {
 }
 
 cudaError_t greedy_launch(const GreedyLaunch& L, cudaStream_t stream) {
+  // the plan (team sizes, split slots) was made for this shape's CTAs
+  if (L.threads != NT) return cudaErrorInvalidConfiguration;
   void* k = pick_kernel(L.dtype, L.tile_cols);
   if (L.smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
@@ -1124,7 +1126,6 @@ cudaError_t greedy_launch(const GreedyLaunch& L, cudaStream_t stream) {
   }
   GreedyLaunch arg = L;
   void* args[] = {&arg};
-  if (L.threads != NT) return cudaErrorInvalidConfiguration;
   return cudaLaunchCooperativeKernel(k, dim3(L.grid), dim3(NT), args, L.smem, stream);
 }
 
